@@ -1,0 +1,131 @@
+"""Sequential FP64 oracle for the time-varying LP filter and its adjoint.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow statement of what
+the CUDA library computes (Eq. 5, Eq. 11 and Eq. 12 of Yu & Fazekas,
+arXiv 2406.05128).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference legs may import it.  The product path
+(``paper_2406_05128_gb300``) never imports it and the two share no code.
+
+The arithmetic lives in ``tvlp_oracle.c`` (plain C, double precision,
+compiled here with gcc).  This module only marshals numpy arrays: inputs are
+converted to float64 (exactly, from the float32 values the GPU sees) and
+passed to the C routines one batch at a time.
+
+Parity status of each routine (see the tests under ``tests/test_oracle_*``):
+  forward   pinned: closed-form impulse responses, dense triangular solve,
+            scipy.signal.lfilter, the IIR expansion of Eqs. 6-8, invariants.
+  backward  pinned: dense transposed solve, finite differences, Eqs. 9-10,
+            GOLF's time-invariant gradient (Eq. 3), adjoint identity.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tvlp_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libtvlp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: no fused multiply-add, so the x86 and aarch64 builds
+# round identically.
+CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off"]
+
+
+def build(force: bool = False) -> str:
+    """Compile tvlp_oracle.c into oracle/_build/libtvlp_oracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_SO)) or os.path.getmtime(_SO) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def load_library(path: str) -> ctypes.CDLL:
+    """Open a compiled oracle (the real one or a test-built variant)."""
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    lib.tvlp_oracle_forward_batch.argtypes = [i64, i64, ctypes.c_int, dp, dp, dp, dp]
+    lib.tvlp_oracle_forward_batch.restype = None
+    lib.tvlp_oracle_backward_batch.argtypes = [i64, i64, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
+    lib.tvlp_oracle_backward_batch.restype = None
+    return lib
+
+
+def _get():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load_library(build())
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(x):
+    return None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _batched(a, *vecs):
+    """Promote single-signal arrays ([T,M], [T], [M]) to batch form."""
+    single = a.ndim == 2
+    if single:
+        a = a[None]
+        vecs = tuple(None if v is None else v[None] for v in vecs)
+    return single, a, vecs
+
+
+def forward(a, e, zi=None, lib=None):
+    """Eq. 5: s(t) = e(t) - sum_i a_i(t) s(t-i).
+
+    a: [B,T,M] (or [T,M]); e: [B,T]; zi: [B,M] with zi[...,j-1] = s(-j), or None.
+    Returns s as float64 with the shape of e.
+    """
+    lib = lib or _get()
+    a, e, zi = _f64(a), _f64(e), _f64(zi)
+    single, a, (e, zi) = _batched(a, e, zi)
+    B, T, M = a.shape
+    assert e.shape == (B, T)
+    assert zi is None or zi.shape == (B, M)
+    s = np.empty((B, T), np.float64)
+    lib.tvlp_oracle_forward_batch(B, T, M, _ptr(a), _ptr(e), _ptr(zi), _ptr(s))
+    return s[0] if single else s
+
+
+def backward(a, s, gs, zi=None, lib=None):
+    """Eqs. 11-12 plus the initial-state gradient.
+
+    Returns (ge [B,T], ga [B,T,M], gzi [B,M]) as float64.
+    """
+    lib = lib or _get()
+    a, s, gs, zi = _f64(a), _f64(s), _f64(gs), _f64(zi)
+    single, a, (s, gs, zi) = _batched(a, s, gs, zi)
+    B, T, M = a.shape
+    ge = np.empty((B, T), np.float64)
+    ga = np.empty((B, T, M), np.float64)
+    gzi = np.empty((B, M), np.float64)
+    lib.tvlp_oracle_backward_batch(B, T, M, _ptr(a), _ptr(s), _ptr(zi), _ptr(gs),
+                                   _ptr(ge), _ptr(ga), _ptr(gzi))
+    if single:
+        return ge[0], ga[0], gzi[0]
+    return ge, ga, gzi
+
+
+def forward_backward(a, e, gs, zi=None, lib=None):
+    """One forward and one adjoint pass: returns (s, ge, ga, gzi)."""
+    s = forward(a, e, zi, lib=lib)
+    ge, ga, gzi = backward(a, s, gs, zi, lib=lib)
+    return s, ge, ga, gzi

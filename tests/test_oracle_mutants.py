@@ -1,0 +1,92 @@
+"""Plant plausible slips in a copy of the oracle and check the pins catch them.
+
+Each mutant is a textual edit of oracle/tvlp_oracle.c compiled into a
+temporary directory (the real oracle is untouched).  The pins of
+test_oracle_pins.py are then run against the mutant library; every mutant
+must make at least one pin fail.  Mutations keep every array index in
+bounds so a mutant can only compute a wrong value, never crash.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+import pytest
+
+import oracle as O
+from tests import test_oracle_pins as P
+
+SRC = open(os.path.join(os.path.dirname(O.__file__), "tvlp_oracle.c")).read()
+
+MUTANTS = {
+    "forward drops the order-M term":
+        ("for (int i = 1; i <= M; ++i)\n            acc -= a[t * M + (i - 1)] * past_output",
+         "for (int i = 1; i < M; ++i)\n            acc -= a[t * M + (i - 1)] * past_output"),
+    "forward sign flipped":
+        ("acc -= a[t * M + (i - 1)] * past_output", "acc += a[t * M + (i - 1)] * past_output"),
+    "forward coefficient order reversed":
+        ("acc -= a[t * M + (i - 1)] * past_output", "acc -= a[t * M + (M - i)] * past_output"),
+    "initial state read one lag late":
+        ("return zi ? zi[(i - t) - 1] : 0.0;", "return zi ? zi[(i - t) > 1 ? (i - t) - 2 : 0] : 0.0;"),
+    "initial state ignored":
+        ("return zi ? zi[(i - t) - 1] : 0.0;", "return 0.0;"),
+    "adjoint without the lag shift":
+        ("double a_hat = a[(t + i) * M + (i - 1)];", "double a_hat = a[t * M + (i - 1)];"),
+    "adjoint shifted by one sample too few":
+        ("double a_hat = a[(t + i) * M + (i - 1)];", "double a_hat = a[(t + i - 1) * M + (i - 1)];"),
+    "adjoint drops the last lag":
+        ("if (t + i < T) {", "if (t + i < T && i < M) {"),
+    "adjoint sign flipped":
+        ("acc -= a_hat * ge[t + i];", "acc += a_hat * ge[t + i];"),
+    "coefficient gradient sign flipped":
+        ("= -ge[t] * past_output(s, zi, t, i);", "= ge[t] * past_output(s, zi, t, i);"),
+    "coefficient gradient lag off by one":
+        ("= -ge[t] * past_output(s, zi, t, i);", "= -ge[t] * past_output(s, zi, t, i - 1);"),
+    "initial-state gradient uses the unshifted coefficient":
+        ("acc -= ge[t] * a[t * M + (t + j - 1)];", "acc -= ge[t] * a[t * M + (j - 1)];"),
+    "initial-state gradient stops one sample early":
+        ("t <= (int64_t)(M - j) && t < T", "t < (int64_t)(M - j) && t < T"),
+}
+
+PINS = [
+    (P.test_golden_worked_example_exact, {}),
+    (P.test_m1_time_varying_product_form, {}),
+    (P.test_m2_resonator_closed_form, {}),
+    (P.test_partial_fraction_impulse_response, {"M": 6}),
+    (P.test_time_invariant_matches_lfilter_with_initial_state, {"M": 4}),
+    (P.test_dense_solve_forward_and_adjoint, {"T": 33, "M": 4}),
+    (P.test_finite_differences, {"T": 12, "M": 3}),
+    (P.test_iir_expansion_eqs_6_to_10, {"T": 9, "M": 3}),
+    (P.test_golf_time_invariant_gradients, {"M": 5}),
+    (P.test_adjoint_dot_product_identity, {}),
+    (P.test_slicing_with_carried_state, {}),
+]
+
+
+def _build_mutant(tmp_path, name, old, new):
+    assert SRC.count(old) >= 1, f"mutation site not found for {name!r}"
+    src = tmp_path / "mutant.c"
+    src.write_text(SRC.replace(old, new, 1))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", *O.CFLAGS, str(src), "-o", str(so)], check=True)
+    return O.load_library(str(so))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path, monkeypatch):
+    lib = _build_mutant(tmp_path, name, *MUTANTS[name])
+    monkeypatch.setattr(O, "_lib", lib)
+    caught = []
+    for fn, kw in PINS:
+        try:
+            fn(**kw)
+        except AssertionError:
+            caught.append(fn.__name__)
+    assert caught, f"no pin detects the mutant {name!r}"
+
+
+def test_unmutated_copy_passes_all_pins(tmp_path, monkeypatch):
+    lib = _build_mutant(tmp_path, "identity", "#include <stddef.h>", "#include <stddef.h>")
+    monkeypatch.setattr(O, "_lib", lib)
+    for fn, kw in PINS:
+        fn(**kw)
