@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the time-varying LP hot path on GB300.
+
+One step = the whole hot path over one batch: lp_tv_forward (Eq. 5) then
+lp_tv_backward (Eqs. 11-12: dL/de and dL/da) through the C ABI, on the
+batched workload B=32 signals x T=48000 samples (2 s at 24 kHz), order
+M=22, FP32, with inputs resident in HBM.  Inputs are synthetic and seeded:
+excitation = pulse train at F0 ~ U(100, 600) Hz plus 0.1 N(0,1); reflection
+coefficients k ~ U(-0.95, 0.95) per 120-sample frame, linearly interpolated
+per sample and stepped up to direct form; dL/ds ~ N(0,1).
+
+Metric: forward+backward Msamples/s (B*T samples per step, each counted
+once).  Per rank one JSON line is formed; rank 0 prints it.  Multi-GPU runs
+are independent replicas (each rank its own batch, no collective on the data
+path): value = all ranks' samples / max-over-ranks time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Msamples/s at M=22 vs plain sequential kernel (<=1e-4 rel); serving p99"
+UNIT = "Msamples/s"
+WORKLOAD = "batched forward+backward time-varying LP, B=32, T=48000, M=22, FP32"
+KERNELS_FWD = ("fwd_summary", "fwd_chain", "fwd_rerun")
+KERNELS_BWD = ("bwd_zero_state", "bwd_chain", "bwd_rerun", "grad_a")
+KERNELS_PLAIN_FWD = ("plain_fwd",)
+KERNELS_PLAIN_BWD = ("plain_bwd", "grad_a")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--algo", choices=("chunked", "plain"), default="chunked")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--B", type=int, default=32)
+    ap.add_argument("--T", type=int, default=48000)
+    ap.add_argument("--M", type=int, default=22)
+    ap.add_argument("--gen", choices=("literal", "stable"), default="literal")
+    ap.add_argument("--min-warmup-s", type=float, default=1.0, help="keep warming up at least this long")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-plain", action="store_true", help="also time the plain one-thread-per-signal kernels")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload(args, rank):
+    from paper_2406_05128_gb300 import inputs
+    return inputs.batched_headline(seed=2 + rank, gen=args.gen, B=args.B, T=args.T, M=args.M)
+
+
+def config(args, l2):
+    return {"workload": WORKLOAD if (args.B, args.T, args.M) == (32, 48000, 22)
+            else f"batched forward+backward time-varying LP, B={args.B}, T={args.T}, M={args.M}, FP32",
+            "B": args.B, "T": args.T, "M": args.M, "coefficients": f"{args.gen} reflection generator, hop 120",
+            "excitation": "pulse train F0~U(100,600) Hz + 0.1 N(0,1)", "algo": args.algo,
+            "l2": l2}
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the FP64 oracle on the host cores (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_step(w, pool, cores):
+    import oracle
+    B = w.a.shape[0]
+
+    def one(b):
+        s = oracle.forward(w.a[b], w.e[b])
+        oracle.backward(w.a[b], s, w.gs[b])
+
+    list(pool.map(one, range(B)))
+
+
+def oracle_time(w, steps, warmup):
+    cores = min(w.a.shape[0], os.cpu_count() or 1)
+    with ThreadPoolExecutor(cores) as pool:
+        for _ in range(warmup):
+            oracle_step(w, pool, cores)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            oracle_step(w, pool, cores)
+        dt = (time.perf_counter() - t0) / steps
+    B, T, _ = w.a.shape
+    return B * T / dt / 1e6, cores, dt
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args, 0)
+    steps, warmup = max(1, args.steps), max(0, args.warmup)
+    value, cores, dt = oracle_time(w, steps, warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": steps, "warmup": warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config(args, "n/a (host CPU)"),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"full batch {w.a.shape[0]}x{w.a.shape[1]} (M={w.a.shape[2]}) per step, "
+                                   "sequential FP64 C oracle, one thread per signal"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append((time.perf_counter(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [p for (t, p) in self.rows if t0 <= t <= t1] or [p for (_, p) in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        loaded = [r for r in rows if (num(r[3]) or 0) > 0] or rows
+        sm = [num(r[0]) for r in loaded if num(r[0]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in loaded for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(loaded[0][1]),
+                "reasons": reasons, "samples": len(loaded),
+                "power_w_max": max((num(r[2]) or 0) for r in loaded)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2406_05128_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if data.get("source_hash") != source_hash():
+        return None
+    k = data.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_05128_gb300 import _lib
+
+    w = workload(args, rank)
+    B, T, M = w.a.shape
+    a = torch.from_numpy(w.a).to(dev)
+    e = torch.from_numpy(w.e).to(dev)
+    gs = torch.from_numpy(w.gs).to(dev)
+    s = torch.empty((B, T), device=dev)
+    ge = torch.empty((B, T), device=dev)
+    ga = torch.empty((B, T, M), device=dev)
+    chunk = args.chunk or _lib.lp_tv_pick_chunk(B, T, M)
+    algo = _lib.LP_ALGO_CHUNKED if args.algo == "chunked" else _lib.LP_ALGO_PLAIN
+    wsb = _lib.lp_tv_workspace_bytes(B, T, M, chunk)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    bwd_flags = _lib.LP_BWD_REUSE_FORWARD if args.algo == "chunked" else 0
+    names_f = KERNELS_FWD if args.algo == "chunked" else KERNELS_PLAIN_FWD
+    names_b = KERNELS_BWD if args.algo == "chunked" else KERNELS_PLAIN_BWD
+    ev_f = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(names_f))]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(names_b))]
+
+    def step(profile):
+        if profile:
+            keep = _lib.lp_tv_set_profile_events(h_f)
+        _lib.lp_tv_forward(_lib.LP_DTYPE_F32, B, T, M, a.data_ptr(), e.data_ptr(), None, s.data_ptr(), None,
+                           chunk, algo, ws.data_ptr(), ws.numel(), sp)
+        if profile:
+            keep = _lib.lp_tv_set_profile_events(h_b)
+        _lib.lp_tv_backward(_lib.LP_DTYPE_F32, B, T, M, gs.data_ptr(), a.data_ptr(), s.data_ptr(), None,
+                            ge.data_ptr(), ga.data_ptr(), None, chunk, algo, bwd_flags, ws.data_ptr(), ws.numel(), sp)
+        if profile:
+            _lib.lp_tv_set_profile_events(None)
+            del keep
+
+    # torch creates an event on its first record; take the handles after that
+    for ev in ev_f + ev_b:
+        ev.record(stream)
+    torch.cuda.synchronize()
+    h_f = [ev.cuda_event for ev in ev_f]
+    h_b = [ev.cuda_event for ev in ev_b]
+    assert all(h_f) and all(h_b), "CUDA events were not created"
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid)) if rank == 0 else None
+
+    # warm-up: at least W steps and at least ~1 s of load so clocks settle
+    t_w0 = time.perf_counter()
+    n = 0
+    while n < max(3, args.warmup) or time.perf_counter() - t_w0 < args.min_warmup_s:
+        flush.zero_()
+        step(False)
+        n += 1
+        if n % 20 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms, kern_ms = [], {k: [] for k in names_f + names_b}
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t_region0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (not timed)
+        ev0.record(stream)
+        step(True)
+        ev1.record(stream)
+        stream.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for i, k in enumerate(names_f):
+            kern_ms[k].append(ev_f[2 * i].elapsed_time(ev_f[2 * i + 1]))
+        for i, k in enumerate(names_b):
+            kern_ms[k].append(ev_b[2 * i].elapsed_time(ev_b[2 * i + 1]))
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    t_region1 = time.perf_counter()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = B * T * world * args.steps / (total_ms * 1e-3) / 1e6
+
+    # plain one-thread-per-signal comparator on the same GPU (context)
+    plain = None
+    if args.compare_plain and args.algo == "chunked":
+        palgo = _lib.LP_ALGO_PLAIN
+        pt = []
+        for i in range(3 + 5):
+            flush.zero_()
+            ev0.record(stream)
+            _lib.lp_tv_forward(_lib.LP_DTYPE_F32, B, T, M, a.data_ptr(), e.data_ptr(), None, s.data_ptr(), None,
+                               chunk, palgo, None, 0, sp)
+            _lib.lp_tv_backward(_lib.LP_DTYPE_F32, B, T, M, gs.data_ptr(), a.data_ptr(), s.data_ptr(), None,
+                                ge.data_ptr(), ga.data_ptr(), None, chunk, palgo, 0, None, 0, sp)
+            ev1.record(stream)
+            stream.synchronize()
+            if i >= 3:
+                pt.append(ev0.elapsed_time(ev1))
+        plain = {"ms_per_step": round(statistics.mean(pt), 4),
+                 "value": round(B * T / (statistics.mean(pt) * 1e-3) / 1e6, 3), "unit": UNIT}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        ha, he, hgs = (torch.from_numpy(x).pin_memory() for x in (w.a, w.e, w.gs))
+        hs = torch.empty((B, T)).pin_memory()
+        hge = torch.empty((B, T)).pin_memory()
+        hga = torch.empty((B, T, M)).pin_memory()
+        h2d = ha.numel() * 4 + he.numel() * 4 + hgs.numel() * 4
+        d2h = hs.numel() * 4 + hge.numel() * 4 + hga.numel() * 4
+        e2e_ms = []
+        n_e2e = max(3, min(args.steps, 20))
+        for i in range(2 + n_e2e):
+            ev0.record(stream)
+            a.copy_(ha, non_blocking=True)
+            e.copy_(he, non_blocking=True)
+            gs.copy_(hgs, non_blocking=True)
+            step(False)
+            hs.copy_(s, non_blocking=True)
+            hge.copy_(ge, non_blocking=True)
+            hga.copy_(ga, non_blocking=True)
+            ev1.record(stream)
+            stream.synchronize()
+            if i >= 2:
+                e2e_ms.append(ev0.elapsed_time(ev1))
+        e2e_t = statistics.mean(e2e_ms)
+        e2e = {"value": round(B * T * world / (e2e_t * 1e-3) / 1e6, 4), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_t, 4)}
+
+    clocks = None
+    if sampler is not None:
+        sampler.stop()
+        clocks = sampler.summary(t_w0, t_region1)
+
+    if rank != 0:
+        if world > 1:
+            tdist.barrier()
+            tdist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    means = {k: statistics.mean(v) for k, v in kern_ms.items()}
+    dom = max(means, key=means.get)
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max / 1e12
+    nsamp = B * T
+    MP = M  # exact instantiation for the benchmark orders
+    bytes_per_sample = {
+        "fwd_summary": 4 * M + 4, "bwd_zero_state": 4 * M + 4,
+        "fwd_rerun": 4 * M + 8, "bwd_rerun": 4 * M + 8, "grad_a": 4 * M + 8,
+        "plain_fwd": 4 * M + 8, "plain_bwd": 4 * M + 8,
+    }
+    flops_per_sample = {"fwd_summary": 2 * (MP + 1) * MP}
+    kern_detail = {}
+    for k, ms in means.items():
+        d = {"ms": round(ms, 5), "share": round(ms / sum(means.values()), 4)}
+        if k in bytes_per_sample:
+            d["GB/s"] = round(bytes_per_sample[k] * nsamp / (ms * 1e-3) / 1e9, 1)
+        if k in flops_per_sample:
+            d["TFLOP/s"] = round(flops_per_sample[k] * nsamp / (ms * 1e-3) / 1e12, 2)
+        kern_detail[k] = d
+    if dom in flops_per_sample:
+        ach_t = flops_per_sample[dom] * nsamp / (means[dom] * 1e-3) / 1e12
+        ach_b = bytes_per_sample[dom] * nsamp / (means[dom] * 1e-3) / 1e9
+        if ach_t / fp32_peak_tflops >= ach_b / hbm_peak:
+            roof = {"bound": "alu", "achieved": round(ach_t, 3), "peak": round(fp32_peak_tflops, 2),
+                    "unit": "TFLOP/s", "frac": round(ach_t / fp32_peak_tflops, 4),
+                    "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+        else:
+            roof = {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(ach_b / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        ach_b = bytes_per_sample.get(dom, 0) * nsamp / (means[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach_b / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["kernel"] = dom
+    roof["traffic"] = load_traffic(dom)
+    step_bytes = (12 * M + 20) * nsamp
+    step_roof = {"algorithmic_bytes_per_step": step_bytes,
+                 "GB/s": round(step_bytes / (ms_per_step * 1e-3) / 1e9, 1),
+                 "frac_of_hbm": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak, 4)}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cv, cores, cdt = oracle_time(w, steps=3, warmup=1)
+        cpu = {"value": round(cv, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"full batch {B}x{T} (M={M}) fwd+bwd, 3 timed passes after 1 warm-up, "
+                         "FP64 sequential C oracle, one host thread per signal"}
+
+    launches_per_step = len(names_f) + len(names_b)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(args, "flushed between timed steps (256 MiB write)") | {"chunk": chunk},
+        "roofline": roof, "step_roofline": step_roof, "kernels": kern_detail,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks, "plain_gpu_kernel": plain, "source_hash": source_hash(),
+        "region_wall_s": round(t_region1 - t_region0, 3),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * tvlp.h — C ABI of the GB300 (sm_103a) time-varying linear-prediction
+ * library.
+ *
+ * The library computes the sample-wise time-varying all-pole (LP) filter of
+ * Yu & Fazekas, "Differentiable Time-Varying Linear Prediction in the
+ * Context of End-to-End Analysis-by-Synthesis" (arXiv 2406.05128), and its
+ * adjoint, batched over B independent signals:
+ *
+ *   forward   (Eq. 5)   s(t)  = e(t) - sum_{i=1..M} a_i(t) s(t-i)
+ *   adjoint   (Eq. 11)  ge(t) = gs(t) - sum_{i=1..M} a_i(t+i) ge(t+i),
+ *                       run from t = T-1 down to 0, ge(t >= T) = 0
+ *   coeffs    (Eq. 12)  ga_i(t) = -ge(t) s(t-i)
+ *   state     (extension of the zero initial conditions of Sec. 2.2)
+ *                       s(-j) = zi[j-1];  gzi[j-1] = dL/ds(-j)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named a, e, s, ... are DEVICE pointers owned by the caller,
+ *   row-major and densely packed:
+ *     a      [B][T][M]   a[(b*T + t)*M + (i-1)] = a_i(t) of signal b
+ *     e, s   [B][T]
+ *     zi     [B][M]      zi[b*M + j-1] = s_b(-j); NULL means zero state
+ *   _f32 entry points take float, _f64 entry points take double.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every call only enqueues work on that stream; none
+ *   synchronises it.  Results are valid once the stream has reached the
+ *   point of the call.
+ * - `workspace` is caller-owned device memory of at least
+ *   lp_tv_workspace_bytes(...) bytes, 256-byte aligned, for the same
+ *   (B, T, M, chunk, dtype).  The library allocates no device memory.
+ *   A workspace must not be used by two calls that may run concurrently.
+ *   After lp_tv_forward it holds the chunk transfer matrices of `a`, which
+ *   lp_tv_backward can reuse (LP_BWD_REUSE_FORWARD).
+ * - `chunk` is the chunk length L of the parallel scan (samples).  0 asks
+ *   the library to pick it (lp_tv_pick_chunk).  A non-zero value is rounded
+ *   up to a multiple of the padded order.  Results depend on the chunk
+ *   length only through floating-point rounding.
+ * - No input may alias an output.
+ * - Shapes: B >= 0, T >= 0, 0 <= M <= 32 (M <= 16 for _f64).  B == 0 or
+ *   T == 0 is a no-op.  M == 0 copies e to s (and gs to ge).  M > T is
+ *   allowed.
+ * - Return value: LP_OK (0) or a negative error code; lp_strerror() names
+ *   it.  An error is returned before any work is enqueued, except
+ *   LP_ECUDA, which reports a failed launch (the stream may then hold part
+ *   of the work).  Errors never abort the process.
+ */
+#ifndef TVLP_H
+#define TVLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LP_OK = 0,
+    LP_EINVAL = -1,       /* bad shape, NULL required pointer, bad flag  */
+    LP_EUNSUPPORTED = -2, /* order M beyond what this build supports     */
+    LP_EWORKSPACE = -3,   /* workspace NULL, too small or misaligned      */
+    LP_ECUDA = -4,        /* a CUDA launch or runtime call failed         */
+    LP_EALIGN = -5        /* a data pointer is not aligned to its type    */
+};
+
+enum { LP_DTYPE_F32 = 0, LP_DTYPE_F64 = 1 };
+
+/* lp_tv_backward flags. */
+enum {
+    /* The workspace still holds what lp_tv_forward left in it for the same
+     * a, B, T, M, chunk and dtype: the chunk transfer matrices of the
+     * forward.  The adjoint's chunk transfer is their transpose (the
+     * adjoint state is the gradient with respect to the forward state), so
+     * the backward then runs one recursion per chunk instead of M+1. */
+    LP_BWD_REUSE_FORWARD = 1
+};
+
+/* Which kernels compute the recursion. */
+enum {
+    LP_ALGO_CHUNKED = 0, /* chunked parallel scan (default, fast path)  */
+    LP_ALGO_PLAIN = 1    /* one thread per signal, sequential in time   */
+};
+
+/*
+ * Per-kernel timing hook.  `events` points to 2*n cudaEvent_t handles
+ * (passed as void*) created by the caller.  While installed, every later
+ * forward/backward call made from the calling thread records events[2k]
+ * just before and events[2k+1] just after its k-th kernel launch (k < n) on
+ * the call's stream.  Kernel order: forward (chunked) summary, chain,
+ * re-run; backward (chunked) summary, chain, re-run, coefficient gradient;
+ * the plain algorithm launches re-run (and coefficient gradient).  NULL
+ * uninstalls the hook.  The library neither creates nor destroys events.
+ */
+int lp_tv_set_profile_events(void **events, int n);
+
+/* Human-readable name of an error code. Never NULL. */
+const char *lp_strerror(int code);
+
+/* Library version string, e.g. "tvlp 0.1 sm_103a". */
+const char *lp_version(void);
+
+/* Chunk length the library picks for (B, T, M) when `chunk` is 0. */
+int lp_tv_pick_chunk(int B, int64_t T, int M, int dtype);
+
+/* Number of chunks per signal for (T, M, chunk) after rounding. */
+int64_t lp_tv_num_chunks(int64_t T, int M, int chunk);
+
+/*
+ * Workspace bytes needed by lp_tv_forward_* / lp_tv_backward_* for the
+ * given problem (scan summaries and chunk states).  Returns 0 for an
+ * invalid shape.
+ */
+size_t lp_tv_workspace_bytes(int B, int64_t T, int M, int chunk, int dtype);
+
+/*
+ * Forward filter, Eq. 5 (Sec. 3.2), batched.
+ *   a    [B][T][M]  coefficients a_i(t)                        (in)
+ *   e    [B][T]     excitation                                  (in)
+ *   zi   [B][M]     initial state s(-j) = zi[j-1], or NULL      (in)
+ *   s    [B][T]     output                                      (out)
+ *   ckpt [B][nC][M] incoming state of each chunk, or NULL       (out)
+ *                   ckpt[(b*nC + c)*M + j-1] = s_b(c*L - j), nC =
+ *                   lp_tv_num_chunks(T, M, chunk); these are the chunk
+ *                   checkpoints the backward can recompute s from.
+ *   algo            LP_ALGO_CHUNKED or LP_ALGO_PLAIN (ckpt requires CHUNKED)
+ */
+int lp_tv_forward_f32(int B, int64_t T, int M, const float *a, const float *e,
+                      const float *zi, float *s, float *ckpt, int chunk,
+                      int algo, void *workspace, size_t workspace_bytes,
+                      void *stream);
+int lp_tv_forward_f64(int B, int64_t T, int M, const double *a, const double *e,
+                      const double *zi, double *s, double *ckpt, int chunk,
+                      int algo, void *workspace, size_t workspace_bytes,
+                      void *stream);
+
+/*
+ * Adjoint, Eqs. 11-12 (Sec. 3.2.1-3.2.2), batched.
+ *   gs   [B][T]     upstream gradient dL/ds                     (in)
+ *   a    [B][T][M]  coefficients used by the forward            (in)
+ *   s    [B][T]     forward output (needed for ga)              (in)
+ *   zi   [B][M]     forward initial state or NULL               (in)
+ *   ge   [B][T]     dL/de                                       (out)
+ *   ga   [B][T][M]  dL/da_i(t) = -ge(t) s(t-i), or NULL         (out)
+ *   gzi  [B][M]     dL/ds(-j), or NULL                          (out)
+ *   flags           0 or LP_BWD_REUSE_FORWARD
+ * `s` may be NULL only when `ga` is NULL.
+ */
+int lp_tv_backward_f32(int B, int64_t T, int M, const float *gs, const float *a,
+                       const float *s, const float *zi, float *ge, float *ga,
+                       float *gzi, int chunk, int algo, int flags,
+                       void *workspace, size_t workspace_bytes, void *stream);
+int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs,
+                       const double *a, const double *s, const double *zi,
+                       double *ge, double *ga, double *gzi, int chunk, int algo,
+                       int flags, void *workspace, size_t workspace_bytes,
+                       void *stream);
+
+/*
+ * Device status word of the current device: 0 while every bounded wait
+ * inside the kernels completed, 1 once a shared-memory bulk-copy wait gave
+ * up (the kernel then stopped early and its outputs are not valid).  Reads
+ * it synchronously (waits for the device's outstanding work) and clears it
+ * when `reset` is non-zero.  Returns the status or LP_ECUDA.
+ */
+int lp_tv_device_status(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVLP_H */

@@ -1,0 +1,152 @@
+"""ctypes binding of libtvlp.so (the C ABI declared in include/tvlp.h).
+
+Argument marshalling only: every computation runs in the CUDA kernels of the
+shared library.  Importing this module does not load the library; the first
+call does, and raises LPLibraryMissing if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LP_OK = 0
+LP_EINVAL = -1
+LP_EUNSUPPORTED = -2
+LP_EWORKSPACE = -3
+LP_ECUDA = -4
+LP_EALIGN = -5
+
+LP_DTYPE_F32 = 0
+LP_DTYPE_F64 = 1
+
+LP_ALGO_CHUNKED = 0
+LP_ALGO_PLAIN = 1
+
+# Every function declared in include/tvlp.h.
+EXPORTS = (
+    "lp_strerror", "lp_version", "lp_tv_pick_chunk", "lp_tv_num_chunks",
+    "lp_tv_workspace_bytes", "lp_tv_forward_f32", "lp_tv_forward_f64",
+    "lp_tv_backward_f32", "lp_tv_backward_f64", "lp_tv_set_profile_events",
+    "lp_tv_device_status",
+)
+
+LP_BWD_REUSE_FORWARD = 1
+
+
+class LPLibraryMissing(RuntimeError):
+    pass
+
+
+class LPError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(lib):
+    c = ctypes
+    vp, sz, i32, i64 = c.c_void_p, c.c_size_t, c.c_int, c.c_int64
+    lib.lp_strerror.argtypes = [i32]
+    lib.lp_strerror.restype = c.c_char_p
+    lib.lp_version.argtypes = []
+    lib.lp_version.restype = c.c_char_p
+    lib.lp_tv_pick_chunk.argtypes = [i32, i64, i32, i32]
+    lib.lp_tv_pick_chunk.restype = i32
+    lib.lp_tv_num_chunks.argtypes = [i64, i32, i32]
+    lib.lp_tv_num_chunks.restype = i64
+    lib.lp_tv_workspace_bytes.argtypes = [i32, i64, i32, i32, i32]
+    lib.lp_tv_workspace_bytes.restype = sz
+    for name in ("lp_tv_forward_f32", "lp_tv_forward_f64"):
+        f = getattr(lib, name)
+        f.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+        f.restype = i32
+    for name in ("lp_tv_backward_f32", "lp_tv_backward_f64"):
+        f = getattr(lib, name)
+        f.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]
+        f.restype = i32
+    lib.lp_tv_device_status.argtypes = [i32]
+    lib.lp_tv_device_status.restype = i32
+    lib.lp_tv_set_profile_events.argtypes = [c.POINTER(vp), i32]
+    lib.lp_tv_set_profile_events.restype = i32
+    return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load (once) and return the ctypes handle of libtvlp.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _build.LIB
+            if not os.path.exists(p):
+                raise LPLibraryMissing(
+                    f"{p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                    "(needs nvcc for sm_103a)")
+            _lib = _declare(ctypes.CDLL(p))
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return load().lp_strerror(code).decode()
+
+
+def version() -> str:
+    return load().lp_version().decode()
+
+
+def lp_tv_pick_chunk(B: int, T: int, M: int, dtype: int = LP_DTYPE_F32) -> int:
+    return load().lp_tv_pick_chunk(B, T, M, dtype)
+
+
+def lp_tv_num_chunks(T: int, M: int, chunk: int) -> int:
+    return load().lp_tv_num_chunks(T, M, chunk)
+
+
+def lp_tv_workspace_bytes(B: int, T: int, M: int, chunk: int = 0, dtype: int = LP_DTYPE_F32) -> int:
+    return load().lp_tv_workspace_bytes(B, T, M, chunk, dtype)
+
+
+def lp_tv_set_profile_events(event_handles):
+    """Install per-kernel timing events (list of 2*n raw cudaEvent_t handles
+    as ints) for calls from this thread; None uninstalls."""
+    if not event_handles:
+        _check(load().lp_tv_set_profile_events(None, 0), "lp_tv_set_profile_events")
+        return None
+    arr = (ctypes.c_void_p * len(event_handles))(*event_handles)
+    _check(load().lp_tv_set_profile_events(arr, len(event_handles) // 2), "lp_tv_set_profile_events")
+    return arr  # keep alive while installed
+
+
+def _check(rc: int, where: str):
+    if rc != LP_OK:
+        raise LPError(rc, where)
+
+
+def lp_tv_forward(dtype: int, B, T, M, a, e, zi, s, ckpt, chunk, algo, ws, ws_bytes, stream):
+    """Raw forward call; pointers are ints (device addresses) or None."""
+    fn = load().lp_tv_forward_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_forward_f64
+    _check(fn(B, T, M, a, e, zi, s, ckpt, chunk, algo, ws, ws_bytes, stream), "lp_tv_forward")
+
+
+def lp_tv_backward(dtype: int, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, flags, ws, ws_bytes, stream):
+    """Raw backward call; pointers are ints (device addresses) or None."""
+    fn = load().lp_tv_backward_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_backward_f64
+    _check(fn(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, flags, ws, ws_bytes, stream), "lp_tv_backward")
+
+
+def lp_tv_device_status(reset: bool = False) -> int:
+    """Status word of the current device (0 = every bounded wait completed)."""
+    rc = load().lp_tv_device_status(1 if reset else 0)
+    if rc < 0:
+        raise LPError(rc, "lp_tv_device_status")
+    return rc

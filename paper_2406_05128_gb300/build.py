@@ -1,0 +1,95 @@
+"""Build the CUDA library libtvlp.so for sm_103a, in-tree.
+
+Each (scalar type, padded order) instantiation is its own translation unit,
+compiled in parallel with nvcc, then linked with the C ABI into one shared
+library: paper_2406_05128_gb300/_build/libtvlp.so.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(PKG, "_build")
+LIB = os.path.join(BUILD, "libtvlp.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
+
+F32_ORDERS = (2, 4, 8, 12, 16, 22, 30, 32)
+F64_ORDERS = (2, 4, 8, 12, 16)
+
+
+def nvcc() -> str:
+    path = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(path):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libtvlp")
+    return path
+
+
+def _sources():
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "tvlp.h")]
+
+
+def _units():
+    units = []
+    for scalar, orders in (("float", F32_ORDERS), ("double", F64_ORDERS)):
+        for mp in orders:
+            obj = os.path.join(BUILD, f"inst_{scalar}_{mp}.o")
+            units.append((os.path.join(CSRC, "tvlp_inst.cu"), obj,
+                          [f"-DTVLP_SCALAR={scalar}", f"-DTVLP_MP={mp}"]))
+    units.append((os.path.join(CSRC, "tvlp_api.cu"), os.path.join(BUILD, "tvlp_api.o"), []))
+    return units
+
+
+def _stale(target: str, deps) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def _compile(unit, verbose: bool, ptxas_v: bool):
+    src, obj, defs = unit
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
+    if ptxas_v:
+        cmd += ["-Xptxas", "-v"]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {os.path.basename(obj)}:\n{res.stderr}")
+    return res.stderr
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, jobs: int | None = None) -> str:
+    """Compile every instantiation (in parallel) and link libtvlp.so."""
+    os.makedirs(BUILD, exist_ok=True)
+    deps = _sources()
+    todo = [u for u in _units() if force or ptxas_v or _stale(u[1], deps)]
+    if todo:
+        jobs = jobs or max(1, min(len(todo), os.cpu_count() or 4))
+        with ThreadPoolExecutor(jobs) as ex:
+            logs = list(ex.map(lambda u: _compile(u, verbose, ptxas_v), todo))
+        if ptxas_v:
+            for u, log in zip(todo, logs):
+                print(f"== {os.path.basename(u[1])}\n{log}")
+    objs = [u[1] for u in _units()]
+    if force or todo or _stale(LIB, objs):
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stderr}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, ptxas_v="--ptxas" in sys.argv))

@@ -1,0 +1,392 @@
+// C ABI of the time-varying LP library: argument checks, chunk selection
+// and dispatch to the per-order instantiations (see include/tvlp.h).
+#include <limits.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "tvlp.h"
+#include "tvlp_impl.h"
+
+namespace tvlp {
+extern template struct Impl<float, 2>;
+extern template struct Impl<float, 4>;
+extern template struct Impl<float, 8>;
+extern template struct Impl<float, 12>;
+extern template struct Impl<float, 16>;
+extern template struct Impl<float, 22>;
+extern template struct Impl<float, 30>;
+extern template struct Impl<float, 32>;
+extern template struct Impl<double, 2>;
+extern template struct Impl<double, 4>;
+extern template struct Impl<double, 8>;
+extern template struct Impl<double, 12>;
+extern template struct Impl<double, 16>;
+}  // namespace tvlp
+
+// Device status word: kernels record a bounded wait that gave up here.
+__device__ int g_tvlp_status = 0;
+
+namespace tvlp {
+namespace {
+thread_local void **g_prof_events = nullptr;
+thread_local int g_prof_n = 0;
+}  // namespace
+
+void profile_mark(int k, bool end, cudaStream_t st) {
+    if (g_prof_events == nullptr || k < 0 || k >= g_prof_n) return;
+    cudaEvent_t ev = static_cast<cudaEvent_t>(g_prof_events[2 * k + (end ? 1 : 0)]);
+    if (ev != nullptr) cudaEventRecord(ev, st);
+}
+}  // namespace tvlp
+
+using namespace tvlp;
+
+namespace {
+
+constexpr int kMaxDevicesApi = 64;
+
+// Padded orders compiled into the library.
+int pad_order(int M, int dtype) {
+    if (M <= 0) return 0;
+    if (dtype == LP_DTYPE_F32) {
+        static const int mp[] = {2, 4, 8, 12, 16, 22, 30, 32};
+        for (int v : mp)
+            if (M <= v) return v;
+    } else if (dtype == LP_DTYPE_F64) {
+        static const int mp[] = {2, 4, 8, 12, 16};
+        for (int v : mp)
+            if (M <= v) return v;
+    }
+    return -1;
+}
+
+template <typename S> struct Dispatch;
+
+#define TVLP_CASE(MPV, CALL) \
+    case MPV:                \
+        return Impl<S, MPV>::CALL;
+
+template <> struct Dispatch<float> {
+    using S = float;
+    static Shape shape(int MP) {
+        switch (MP) {
+            TVLP_CASE(2, shape()) TVLP_CASE(4, shape()) TVLP_CASE(8, shape()) TVLP_CASE(12, shape())
+            TVLP_CASE(16, shape()) TVLP_CASE(22, shape()) TVLP_CASE(30, shape()) TVLP_CASE(32, shape())
+        }
+        return Shape{};
+    }
+    static int forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ck, int algo, void *ws,
+                       cudaStream_t st) {
+        switch (p.MP) {
+            TVLP_CASE(2, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(4, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(8, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(12, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(16, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(22, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(30, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(32, forward(p, a, e, zi, s, ck, algo, ws, st))
+        }
+        return EUNSUPPORTED;
+    }
+    static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga, S *gzi,
+                        int algo, int flags, void *ws, cudaStream_t st) {
+        switch (p.MP) {
+            TVLP_CASE(2, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(4, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(8, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(12, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(16, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(22, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(30, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(32, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+        }
+        return EUNSUPPORTED;
+    }
+};
+
+template <> struct Dispatch<double> {
+    using S = double;
+    static Shape shape(int MP) {
+        switch (MP) {
+            TVLP_CASE(2, shape()) TVLP_CASE(4, shape()) TVLP_CASE(8, shape()) TVLP_CASE(12, shape())
+            TVLP_CASE(16, shape())
+        }
+        return Shape{};
+    }
+    static int forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ck, int algo, void *ws,
+                       cudaStream_t st) {
+        switch (p.MP) {
+            TVLP_CASE(2, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(4, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(8, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(12, forward(p, a, e, zi, s, ck, algo, ws, st))
+            TVLP_CASE(16, forward(p, a, e, zi, s, ck, algo, ws, st))
+        }
+        return EUNSUPPORTED;
+    }
+    static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga, S *gzi,
+                        int algo, int flags, void *ws, cudaStream_t st) {
+        switch (p.MP) {
+            TVLP_CASE(2, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(4, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(8, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(12, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+            TVLP_CASE(16, backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st))
+        }
+        return EUNSUPPORTED;
+    }
+};
+#undef TVLP_CASE
+
+int num_sms() {
+    static int cached[kMaxDevicesApi] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesApi) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+int *status_word() {
+    static int *cached[kMaxDevicesApi] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesApi) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cached[dev] == nullptr) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_tvlp_status) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cached[dev] = static_cast<int *>(ptr);
+    }
+    return cached[dev];
+}
+
+Shape shape_for(int MP, int dtype) {
+    return dtype == LP_DTYPE_F32 ? Dispatch<float>::shape(MP) : Dispatch<double>::shape(MP);
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Rough cost model (cycles) of the chunked scan for chunk length L:
+// summaries run in waves of resident blocks, each chunk costing L steps;
+// the chain costs a fixed latency per chunk; the re-run is L sequential steps.
+int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
+    if (T <= 0 || B <= 0) return MP;
+    const Shape sh = shape_for(MP, dtype);
+    const int64_t per_wave = (int64_t)num_sms() * sh.warps_per_block * sh.chunks_per_warp;
+    const int64_t max_nblk = ceil_div(T, MP);
+    double best = 1e300;
+    int best_L = MP;
+    for (int64_t nblk = 1; nblk <= max_nblk; ++nblk) {
+        const int64_t L = nblk * MP;
+        if (L > INT_MAX / 2) break;
+        const int64_t nC = ceil_div(T, L);
+        const int64_t NQ = (int64_t)B * nC;
+        const int64_t waves = ceil_div(NQ, per_wave);
+        const double cost = (double)waves * L * sh.per_step_cycles + (double)nC * 150.0 + (double)L * 40.0;
+        if (cost < best) {
+            best = cost;
+            best_L = (int)L;
+        }
+    }
+    return best_L;
+}
+
+bool valid_shape(int B, int64_t T, int M) { return B >= 0 && T >= 0 && M >= 0; }
+
+// Fill a Problem; returns LP_OK or an error code.
+int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
+    if (!valid_shape(B, T, M)) return LP_EINVAL;
+    if (chunk < 0) return LP_EINVAL;
+    if (T >= (int64_t)INT_MAX / 2) return LP_EUNSUPPORTED;
+    const int MP = pad_order(M, dtype);
+    if (M > 0 && MP < 0) return LP_EUNSUPPORTED;
+    p->B = B;
+    p->T = T;
+    p->M = M;
+    p->MP = MP;
+    p->status = nullptr;
+    if (M == 0) {
+        p->L = 0;
+        p->nC = 0;
+        p->NQ = 0;
+        return LP_OK;
+    }
+    int L = chunk > 0 ? chunk : pick_chunk_impl(B, T, MP, dtype);
+    L = (int)(ceil_div(L, MP) * MP);
+    if (L <= 0) return LP_EINVAL;
+    p->L = L;
+    p->nC = T > 0 ? ceil_div(T, L) : 0;
+    p->NQ = (int64_t)B * p->nC;
+    return LP_OK;
+}
+
+size_t workspace_for(const Problem &p, int dtype) {
+    if (p.M == 0 || p.NQ == 0) return 0;
+    return ws_bytes(p, dtype == LP_DTYPE_F32 ? 4 : 8);
+}
+
+bool aligned(const void *ptr, size_t n) { return (reinterpret_cast<uintptr_t>(ptr) % n) == 0; }
+
+int check_workspace(const Problem &p, int dtype, int algo, const void *ws, size_t bytes) {
+    if (algo == LP_ALGO_PLAIN) return LP_OK;
+    const size_t need = workspace_for(p, dtype);
+    if (need == 0) return LP_OK;
+    if (ws == nullptr || bytes < need || !aligned(ws, 256)) return LP_EWORKSPACE;
+    return LP_OK;
+}
+
+template <typename S>
+int forward_impl(int dtype, int B, int64_t T, int M, const S *a, const S *e, const S *zi, S *s, S *ckpt,
+                 int chunk, int algo, void *ws, size_t wsb, void *stream) {
+    if (algo != LP_ALGO_CHUNKED && algo != LP_ALGO_PLAIN) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem(B, T, M, chunk, dtype, &p);
+    if (rc != LP_OK) return rc;
+    if (B == 0 || T == 0) return LP_OK;
+    if (e == nullptr || s == nullptr || (M > 0 && a == nullptr)) return LP_EINVAL;
+    if (ckpt != nullptr && algo != LP_ALGO_CHUNKED) return LP_EINVAL;
+    if (!aligned(e, sizeof(S)) || !aligned(s, sizeof(S)) || !aligned(a, 2 * sizeof(S)) ||
+        !aligned(zi, sizeof(S)) || !aligned(ckpt, sizeof(S)))
+        return LP_EALIGN;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M == 0) {
+        if (cudaMemcpyAsync(s, e, (size_t)B * T * sizeof(S), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if ((rc = check_workspace(p, dtype, algo, ws, wsb)) != LP_OK) return rc;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    return Dispatch<S>::forward(p, a, e, zi, s, ckpt, algo, ws, st);
+}
+
+template <typename S>
+int backward_impl(int dtype, int B, int64_t T, int M, const S *gs, const S *a, const S *s, const S *zi, S *ge,
+                  S *ga, S *gzi, int chunk, int algo, int flags, void *ws, size_t wsb, void *stream) {
+    if (algo != LP_ALGO_CHUNKED && algo != LP_ALGO_PLAIN) return LP_EINVAL;
+    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem(B, T, M, chunk, dtype, &p);
+    if (rc != LP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B == 0) return LP_OK;
+    if (T == 0) {
+        // no samples: the initial-state gradient is zero
+        if (gzi != nullptr && M > 0 && cudaMemsetAsync(gzi, 0, (size_t)B * M * sizeof(S), st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if (gs == nullptr || ge == nullptr || (M > 0 && a == nullptr) || (ga != nullptr && s == nullptr))
+        return LP_EINVAL;
+    if (!aligned(gs, sizeof(S)) || !aligned(ge, sizeof(S)) || !aligned(a, 2 * sizeof(S)) ||
+        !aligned(s, sizeof(S)) || !aligned(zi, sizeof(S)) || !aligned(ga, sizeof(S)) || !aligned(gzi, sizeof(S)))
+        return LP_EALIGN;
+    if (M == 0) {
+        if (cudaMemcpyAsync(ge, gs, (size_t)B * T * sizeof(S), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if ((rc = check_workspace(p, dtype, algo, ws, wsb)) != LP_OK) return rc;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    return Dispatch<S>::backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lp_strerror(int code) {
+    switch (code) {
+        case LP_OK: return "ok";
+        case LP_EINVAL: return "invalid argument (shape, NULL pointer or flag)";
+        case LP_EUNSUPPORTED: return "unsupported order or length for this build";
+        case LP_EWORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+        case LP_ECUDA: return "CUDA launch or runtime call failed";
+        case LP_EALIGN: return "data pointer not aligned to its element type";
+    }
+    return "unknown error code";
+}
+
+const char *lp_version(void) { return "tvlp 0.1 sm_103a"; }
+
+int lp_tv_set_profile_events(void **events, int n) {
+    if (events != nullptr && n < 0) return LP_EINVAL;
+    g_prof_events = events;
+    g_prof_n = events ? n : 0;
+    return LP_OK;
+}
+
+int lp_tv_pick_chunk(int B, int64_t T, int M, int dtype) {
+    Problem p;
+    if (make_problem(B, T, M, 0, dtype, &p) != LP_OK) return 0;
+    return p.L;
+}
+
+int64_t lp_tv_num_chunks(int64_t T, int M, int chunk) {
+    if (T <= 0 || M <= 0 || chunk <= 0) return 0;
+    const int MP = pad_order(M, LP_DTYPE_F32);
+    if (MP <= 0) return 0;
+    const int64_t L = ceil_div(chunk, MP) * MP;
+    return ceil_div(T, L);
+}
+
+size_t lp_tv_workspace_bytes(int B, int64_t T, int M, int chunk, int dtype) {
+    if (dtype != LP_DTYPE_F32 && dtype != LP_DTYPE_F64) return 0;
+    Problem p;
+    if (make_problem(B, T, M, chunk, dtype, &p) != LP_OK) return 0;
+    return workspace_for(p, dtype);
+}
+
+int lp_tv_forward_f32(int B, int64_t T, int M, const float *a, const float *e, const float *zi, float *s,
+                      float *ckpt, int chunk, int algo, void *workspace, size_t workspace_bytes, void *stream) {
+    return forward_impl<float>(LP_DTYPE_F32, B, T, M, a, e, zi, s, ckpt, chunk, algo, workspace, workspace_bytes,
+                               stream);
+}
+
+int lp_tv_forward_f64(int B, int64_t T, int M, const double *a, const double *e, const double *zi, double *s,
+                      double *ckpt, int chunk, int algo, void *workspace, size_t workspace_bytes, void *stream) {
+    return forward_impl<double>(LP_DTYPE_F64, B, T, M, a, e, zi, s, ckpt, chunk, algo, workspace,
+                                workspace_bytes, stream);
+}
+
+int lp_tv_backward_f32(int B, int64_t T, int M, const float *gs, const float *a, const float *s, const float *zi,
+                       float *ge, float *ga, float *gzi, int chunk, int algo, int flags, void *workspace,
+                       size_t workspace_bytes, void *stream) {
+    return backward_impl<float>(LP_DTYPE_F32, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, flags, workspace,
+                                workspace_bytes, stream);
+}
+
+int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs, const double *a, const double *s,
+                       const double *zi, double *ge, double *ga, double *gzi, int chunk, int algo, int flags,
+                       void *workspace, size_t workspace_bytes, void *stream) {
+    return backward_impl<double>(LP_DTYPE_F64, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, flags, workspace,
+                                 workspace_bytes, stream);
+}
+
+int lp_tv_device_status(int reset) {
+    int *w = status_word();
+    if (w == nullptr) return LP_ECUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LP_ECUDA;
+    if (reset && v != 0) {
+        const int zero = 0;
+        if (cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return LP_ECUDA;
+    }
+    return v;
+}
+
+}  // extern "C"

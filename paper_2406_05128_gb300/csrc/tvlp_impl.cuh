@@ -1,0 +1,170 @@
+// Host launchers of the time-varying LP kernels for one (scalar, MP) pair.
+#pragma once
+#include "tvlp_impl.h"
+#include "tvlp_kernels.cuh"
+
+namespace tvlp {
+
+constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per K1 block
+constexpr int kMaxDevices = 64;
+
+template <typename S, int MP> inline int k1_warps_per_block() {
+    using GE = Geo<S, MP>;
+    int w = (int)(kSmemBudget / GE::WARP_BYTES);
+    return w > 8 ? 8 : (w < 1 ? 1 : w);
+}
+
+// cudaFuncSetAttribute once per kernel and device.
+template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes, bool *done) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err == cudaSuccess) done[dev] = true;
+    return err;
+}
+
+template <typename S, int MP> Shape Impl<S, MP>::shape() {
+    using GE = Geo<S, MP>;
+    Shape sh;
+    sh.chunks_per_warp = GE::CPW;
+    sh.warps_per_block = k1_warps_per_block<S, MP>();
+    const int wps = (sh.warps_per_block + 3) / 4;  // warps sharing a scheduler
+    sh.per_step_cycles = (GE::R * MP + MP / 2 + 4) * wps;
+    sh.ws_per_chunk = (size_t)(GE::YS + 3 * MP) * sizeof(S);
+    return sh;
+}
+
+template <typename S, int MP> struct Launch {
+    using GE = Geo<S, MP>;
+
+    static S *region(const Problem &p, void *ws, int r) {
+        return reinterpret_cast<S *>(static_cast<char *>(ws) + ws_offset(p, sizeof(S), r));
+    }
+
+    template <bool BWD> static cudaError_t summary(const Problem &p, const S *a, const S *u, S *Y, cudaStream_t st) {
+        static bool done[kMaxDevices] = {};
+        const int W = k1_warps_per_block<S, MP>();
+        const size_t smem = (size_t)W * GE::WARP_BYTES;
+        auto kern = k1_summary<S, MP, BWD>;
+        cudaError_t err = allow_smem(kern, smem, done);
+        if (err != cudaSuccess) return err;
+        const int64_t per_block = (int64_t)W * GE::CPW;
+        const int64_t grid = (p.NQ + per_block - 1) / per_block;
+        kern<<<(unsigned)grid, 32 * W, smem, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Y, p.M == MP ? 1 : 0, p.status);
+        return cudaGetLastError();
+    }
+
+    template <int MODE> static cudaError_t chain(const Problem &p, const S *Y, const S *Z, const S *zi, S *X, S *ckpt,
+                                                 cudaStream_t st) {
+        static bool done[kMaxDevices] = {};
+        constexpr size_t smem = ChainGeo<S, MP>::SMEM;
+        auto kern = k2_chain<S, MP, MODE>;
+        cudaError_t err = allow_smem(kern, smem, done);
+        if (err != cudaSuccess) return err;
+        kern<<<(unsigned)p.B, 32, smem, st>>>(p.B, p.M, p.nC, Y, Z, zi, X, ckpt);
+        return cudaGetLastError();
+    }
+
+    template <int MODE, bool EXACT>
+    static cudaError_t rec_exact(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
+                                 S *gzi, int reverse, cudaStream_t st) {
+        static bool done[kMaxDevices] = {};
+        using RG = RingGeo<S, MP>;
+        auto kern = k_rec<S, MP, EXACT, MODE>;
+        cudaError_t err = allow_smem(kern, RG::SMEM, done);
+        if (err != cudaSuccess) return err;
+        const int64_t grid = (p.NQ + RG::THREADS - 1) / RG::THREADS;
+        kern<<<(unsigned)grid, RG::THREADS, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi,
+                                                            reverse);
+        return cudaGetLastError();
+    }
+
+    template <int MODE>
+    static cudaError_t rec(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
+                           S *gzi, int reverse, cudaStream_t st) {
+        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, st);
+        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, st);
+    }
+
+    static cudaError_t grad_a(const Problem &p, const S *ge, const S *s, const S *zi, S *ga, cudaStream_t st) {
+        if ((int64_t)p.B * p.T * p.M == 0) return cudaSuccess;
+        constexpr int TR = GradGeo<S, MP, true>::TR;
+        const int64_t tiles = (p.T + TR - 1) / TR;
+        const int64_t grid = tiles * p.B;
+        if (p.M == MP)
+            k_grad_a<S, MP, true><<<(unsigned)grid, GradGeo<S, MP, true>::THREADS, 0, st>>>(p.T, p.M, tiles, ge, s, zi, ga);
+        else
+            k_grad_a<S, MP, false><<<(unsigned)grid, GradGeo<S, MP, false>::THREADS, 0, st>>>(p.T, p.M, tiles, ge, s, zi,
+                                                                                           ga);
+        return cudaGetLastError();
+    }
+};
+
+// The plain path runs the one-recursion kernels with one chunk per signal.
+inline Problem plain_problem(const Problem &p) {
+    Problem q = p;
+    q.L = (int)(((p.T + p.MP - 1) / p.MP) * p.MP);
+    if (q.L == 0) q.L = p.MP;
+    q.nC = 1;
+    q.NQ = p.B;
+    return q;
+}
+
+// Launch helper: wraps one kernel launch in the profiling marks.
+#define TVLP_LAUNCH(K, CALL)                          \
+    do {                                              \
+        profile_mark((K), false, st);                 \
+        if ((CALL) != cudaSuccess) return ECUDA;      \
+        profile_mark((K), true, st);                  \
+    } while (0)
+
+template <typename S, int MP>
+int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ckpt, int algo,
+                         void *ws, cudaStream_t st) {
+    using LN = Launch<S, MP>;
+    if (algo == ALGO_PLAIN) {
+        TVLP_LAUNCH(0, (LN::template rec<FWD_RERUN>(plain_problem(p), a, e, nullptr, zi, s, nullptr, nullptr, 0, st)));
+        return OK;
+    }
+    S *Y = LN::region(p, ws, 0);
+    S *X = LN::region(p, ws, 1);
+    TVLP_LAUNCH(0, (LN::template summary<false>(p, a, e, Y, st)));
+    TVLP_LAUNCH(1, (LN::template chain<CH_FWD>(p, Y, nullptr, zi, X, ckpt, st)));
+    // the re-run walks the chunks in reverse so it starts on rows the
+    // summary pass loaded last
+    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
+    return OK;
+}
+
+template <typename S, int MP>
+int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga,
+                          S *gzi, int algo, int flags, void *ws, cudaStream_t st) {
+    using LN = Launch<S, MP>;
+    int k = 0;
+    if (algo == ALGO_PLAIN) {
+        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(plain_problem(p), a, gs, nullptr, nullptr, ge, nullptr, gzi, 0, st)));
+    } else {
+        S *Y = LN::region(p, ws, 0);
+        S *Z = LN::region(p, ws, 2);
+        S *Wst = LN::region(p, ws, 3);
+        if (flags & BWD_REUSE_FORWARD) {
+            // forward transfers P_c are in Y: the adjoint needs one zero-state
+            // recursion per chunk, then w_{c-1} = P_c^T w_c + z_c
+            TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st)));
+            TVLP_LAUNCH(k++, (LN::template chain<CH_TRANS>(p, Y, Z, nullptr, Wst, nullptr, st)));
+        } else {
+            TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, st)));
+            TVLP_LAUNCH(k++, (LN::template chain<CH_BWD>(p, Y, nullptr, nullptr, Wst, nullptr, st)));
+        }
+        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st)));
+    }
+    if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(p, ge, s, zi, ga, st)));
+    return OK;
+}
+
+#undef TVLP_LAUNCH
+
+}  // namespace tvlp

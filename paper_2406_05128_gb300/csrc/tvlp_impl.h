@@ -1,0 +1,65 @@
+// Host-side declarations shared by the C ABI and the per-order kernel
+// instantiations.  Each (scalar type, padded order MP) pair is compiled in
+// its own translation unit (tvlp_inst.cu with -DTVLP_SCALAR/-DTVLP_MP) so the
+// build runs in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace tvlp {
+
+// One batched problem after validation and chunk selection.
+struct Problem {
+    int B;        // signals
+    int64_t T;    // samples per signal
+    int M;        // real order (1..MP)
+    int MP;       // padded order (template parameter of the kernels)
+    int L;        // chunk length, a multiple of MP
+    int64_t nC;   // chunks per signal
+    int64_t NQ;   // B * nC
+    int *status;  // device status word (bounded waits record timeouts here)
+};
+
+// Per-instantiation geometry the host needs before launching.
+struct Shape {
+    int chunks_per_warp;   // K1 chunks held by one warp
+    int warps_per_block;   // K1 block size / 32
+    int per_step_cycles;   // rough K1 issue cost of one time step (chunk picker)
+    size_t ws_per_chunk;   // workspace bytes per chunk (summaries + states)
+};
+
+template <typename S, int MP> struct Impl {
+    static Shape shape();
+    static int forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ckpt, int algo,
+                       void *ws, cudaStream_t st);
+    static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga,
+                        S *gzi, int algo, int flags, void *ws, cudaStream_t st);
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Status codes (mirror include/tvlp.h).
+enum { OK = 0, EINVAL_ = -1, EUNSUPPORTED = -2, EWORKSPACE = -3, ECUDA = -4, EALIGN = -5 };
+enum { ALGO_CHUNKED = 0, ALGO_PLAIN = 1 };
+enum { BWD_REUSE_FORWARD = 1 };
+
+// Workspace regions (each 256-byte aligned), in elements of the scalar:
+//   Y [NQ][YS]  chunk summaries (forward; the adjoint's own when it
+//               cannot reuse the forward's)
+//   X [NQ][MP]  forward incoming state of every chunk
+//   Z [NQ][MP]  adjoint zero-state summaries
+//   W [NQ][MP]  adjoint incoming state of every chunk
+inline size_t ys_elems(int MP, size_t sz) { return (((size_t)(MP + 1) * MP * sz + 15) / 16) * 16 / sz; }
+inline size_t ws_offset(const Problem &p, size_t sz, int region) {
+    const size_t y = align256((size_t)p.NQ * ys_elems(p.MP, sz) * sz);
+    const size_t v = align256((size_t)p.NQ * p.MP * sz);
+    return region == 0 ? 0 : y + (size_t)(region - 1) * v;
+}
+inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 4); }
+
+// Records the caller's profiling event for kernel k (begin or end) when a
+// hook is installed on this thread (lp_tv_set_profile_events).
+void profile_mark(int k, bool end, cudaStream_t st);
+
+}  // namespace tvlp

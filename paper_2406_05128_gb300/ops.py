@@ -1,0 +1,143 @@
+"""PyTorch front end of the time-varying LP library.
+
+PyTorch supplies device memory and the current CUDA stream; every step of
+the filter, its adjoint and the coefficient gradient runs in libtvlp.so.
+There is no CPU path: tensors must live on a CUDA device, and a missing
+library raises instead of falling back.
+
+    s = lp_filter(a, e, zi=None)          # differentiable, Eq. 5
+    s = lp_tv_forward(a, e, zi)            # plain call
+    ge, ga, gzi = lp_tv_backward(gs, a, s, zi)
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+_ALGOS = {"chunked": _lib.LP_ALGO_CHUNKED, "plain": _lib.LP_ALGO_PLAIN}
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return _lib.LP_DTYPE_F32
+    if t.dtype == torch.float64:
+        return _lib.LP_DTYPE_F64
+    raise TypeError(f"unsupported dtype {t.dtype}; use float32 or float64")
+
+
+def _check(t, name, shape, dtype, device):
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(device):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def workspace(B: int, T: int, M: int, chunk: int = 0, dtype=torch.float32, device=None) -> torch.Tensor:
+    """Workspace tensor (uint8) sized for one forward or backward call."""
+    code = _lib.LP_DTYPE_F32 if dtype == torch.float32 else _lib.LP_DTYPE_F64
+    n = _lib.lp_tv_workspace_bytes(B, T, M, chunk, code)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+
+
+def lp_tv_forward(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked", ckpt: bool = False, ws=None):
+    """s(t) = e(t) - sum_i a_i(t) s(t-i)  (Eq. 5), batched.
+
+    a [B,T,M], e [B,T], zi [B,M] or None (zi[:, j-1] = s(-j)).
+    Returns s, or (s, ckpt) with ckpt [B, nC, M] the incoming state of every
+    chunk when ckpt=True.
+    """
+    B, T, M = a.shape
+    dev = a.device
+    _check(a, "a", (B, T, M), a.dtype, dev)
+    _check(e, "e", (B, T), a.dtype, dev)
+    _check(zi, "zi", (B, M), a.dtype, dev)
+    code = _dtype_code(a)
+    with torch.cuda.device(dev):
+        s = torch.empty((B, T), dtype=a.dtype, device=dev)
+        ck = None
+        if ckpt:
+            nC = _lib.lp_tv_num_chunks(T, M, chunk or _lib.lp_tv_pick_chunk(B, T, M, code)) if M > 0 else 0
+            ck = torch.empty((B, nC, M), dtype=a.dtype, device=dev)
+        if ws is None:
+            ws = workspace(B, T, M, chunk, a.dtype, dev)
+        _lib.lp_tv_forward(code, B, T, M, _ptr(a), _ptr(e), _ptr(zi), _ptr(s), _ptr(ck), chunk,
+                           _ALGOS[algo], _ptr(ws), ws.numel(), _stream(dev))
+    return (s, ck) if ckpt else s
+
+
+def lp_tv_backward(gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = True, chunk: int = 0,
+                   algo: str = "chunked", ws=None, reuse_forward: bool = False):
+    """Adjoint (Eqs. 11-12): returns (ge [B,T], ga [B,T,M] or None, gzi [B,M] or None).
+
+    reuse_forward=True requires `ws` to be the workspace the forward call on
+    the same `a` (and chunk) filled; the adjoint then reuses its chunk
+    transfer matrices.
+    """
+    B, T, M = a.shape
+    dev = a.device
+    _check(a, "a", (B, T, M), a.dtype, dev)
+    _check(gs, "gs", (B, T), a.dtype, dev)
+    _check(s, "s", (B, T), a.dtype, dev)
+    _check(zi, "zi", (B, M), a.dtype, dev)
+    code = _dtype_code(a)
+    if reuse_forward and ws is None:
+        raise ValueError("reuse_forward needs the forward's workspace")
+    with torch.cuda.device(dev):
+        ge = torch.empty((B, T), dtype=a.dtype, device=dev)
+        ga = torch.empty((B, T, M), dtype=a.dtype, device=dev) if need_ga else None
+        gzi = torch.empty((B, M), dtype=a.dtype, device=dev) if need_gzi else None
+        if ws is None:
+            ws = workspace(B, T, M, chunk, a.dtype, dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward(code, B, T, M, _ptr(gs), _ptr(a), _ptr(s), _ptr(zi), _ptr(ge), _ptr(ga), _ptr(gzi),
+                            chunk, _ALGOS[algo], flags, _ptr(ws), ws.numel(), _stream(dev))
+    return ge, ga, gzi
+
+
+class LPFunction(torch.autograd.Function):
+    """Differentiable TV-LP filter: a non-differentiable fast kernel
+    registered into the autograd graph with its adjoint (Sec. 2.2, Sec. 3.2).
+    The forward's workspace (its chunk transfer matrices) is kept for the
+    backward, which then runs one recursion per chunk."""
+
+    @staticmethod
+    def forward(ctx, a, e, zi, chunk, algo):
+        a, e = a.contiguous(), e.contiguous()
+        zi = zi.contiguous() if zi is not None else None
+        B, T, M = a.shape
+        ws = workspace(B, T, M, chunk, a.dtype, a.device)
+        s = lp_tv_forward(a, e, zi, chunk=chunk, algo=algo, ws=ws)
+        ctx.save_for_backward(a, s, zi, ws)
+        ctx.chunk, ctx.algo = chunk, algo
+        return s
+
+    @staticmethod
+    def backward(ctx, gs):
+        a, s, zi, ws = ctx.saved_tensors
+        need_a, need_e, need_zi = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+        ge, ga, gzi = lp_tv_backward(gs.contiguous(), a, s, zi, need_ga=need_a,
+                                     need_gzi=need_zi and zi is not None, chunk=ctx.chunk, algo=ctx.algo,
+                                     ws=ws, reuse_forward=ctx.algo == "chunked")
+        return (ga if need_a else None, ge if need_e else None, gzi if need_zi else None, None, None)
+
+
+def lp_filter(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked"):
+    """Differentiable s = LP_{a(t)}(e) with optional initial state zi."""
+    return LPFunction.apply(a, e, zi, chunk, algo)

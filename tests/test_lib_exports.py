@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every function include/tvlp.h declares.  Host-only entry points (error
+strings, chunk and workspace queries, argument checks) are exercised; no
+call here launches a kernel."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tvlp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2406_05128_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lp_\w+)\s*\(", text)))
+
+
+def test_header_lists_match_binding():
+    from paper_2406_05128_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_functions()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_host_only_entry_points(lib):
+    from paper_2406_05128_gb300 import _lib
+    assert "sm_103a" in _lib.version()
+    for code in (0, -1, -2, -3, -4, -5):
+        assert _lib.strerror(code)
+    L = _lib.lp_tv_pick_chunk(32, 48000, 22)
+    assert L > 0 and L % 22 == 0
+    assert _lib.lp_tv_num_chunks(48000, 22, L) == -(-48000 // L)
+    assert _lib.lp_tv_workspace_bytes(32, 48000, 22, L) > 0
+    assert _lib.lp_tv_workspace_bytes(-1, 10, 2) == 0
+    assert _lib.lp_tv_workspace_bytes(2, 10, 40) == 0  # order above 32
+
+
+def test_argument_errors_without_launching(lib):
+    from paper_2406_05128_gb300 import _lib
+    f = lib.lp_tv_forward_f32
+    assert f(-1, 10, 2, None, None, None, None, None, 0, 0, None, 0, None) == _lib.LP_EINVAL
+    assert f(2, 10, 40, 8, 8, None, 8, None, 0, 0, None, 0, None) == _lib.LP_EUNSUPPORTED
+    assert f(2, 10, 4, 16, None, None, 16, None, 0, 0, None, 0, None) == _lib.LP_EINVAL   # e NULL
+    assert f(2, 10, 4, 16, 16, None, 16, None, 0, 7, None, 0, None) == _lib.LP_EINVAL     # bad algo
+    assert f(2, 10, 4, 16, 16, None, 16, None, 0, 0, None, 0, None) == _lib.LP_EWORKSPACE  # no workspace
+    assert f(2, 10, 4, 20, 16, None, 16, None, 0, 0, None, 0, None) == _lib.LP_EALIGN     # a misaligned
+    assert f(0, 10, 4, None, None, None, None, None, 0, 0, None, 0, None) == _lib.LP_OK   # empty batch
+    g = lib.lp_tv_backward_f64
+    assert g(2, 10, 40, 8, 8, 8, None, 8, None, None, 0, 0, 0, None, 0, None) == _lib.LP_EUNSUPPORTED  # f64: M <= 16
+    assert g(2, 10, 4, 16, 16, None, None, 16, 16, None, 0, 0, 0, None, 0, None) == _lib.LP_EINVAL  # ga needs s
+    assert g(2, 10, 4, 16, 16, 16, None, 16, None, None, 0, 0, 4, None, 0, None) == _lib.LP_EINVAL  # bad flag
