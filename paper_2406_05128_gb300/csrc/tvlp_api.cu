@@ -185,14 +185,15 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // summaries run in waves of resident blocks, each chunk costing L steps;
 // the chain costs a fixed latency per chunk; the re-run is L sequential steps.
 int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
-    if (T <= 0 || B <= 0) return MP;
+    constexpr int SRV = 8;  // chunk lengths are multiples of the stage height
+    if (T <= 0 || B <= 0) return SRV;
     const Shape sh = shape_for(MP, dtype);
     const int64_t per_wave = (int64_t)num_sms() * sh.warps_per_block * sh.chunks_per_warp;
-    const int64_t max_nblk = ceil_div(T, MP);
+    const int64_t max_nblk = ceil_div(T, SRV);
     double best = 1e300;
-    int best_L = MP;
+    int best_L = SRV;
     for (int64_t nblk = 1; nblk <= max_nblk; ++nblk) {
-        const int64_t L = nblk * MP;
+        const int64_t L = nblk * SRV;
         if (L > INT_MAX / 2) break;
         const int64_t nC = ceil_div(T, L);
         const int64_t NQ = (int64_t)B * nC;
@@ -227,7 +228,7 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
         return LP_OK;
     }
     int L = chunk > 0 ? chunk : pick_chunk_impl(B, T, MP, dtype);
-    L = (int)(ceil_div(L, MP) * MP);
+    L = (int)(ceil_div(L, 8) * 8);
     if (L <= 0) return LP_EINVAL;
     p->L = L;
     p->nC = T > 0 ? ceil_div(T, L) : 0;
@@ -338,9 +339,7 @@ int lp_tv_pick_chunk(int B, int64_t T, int M, int dtype) {
 
 int64_t lp_tv_num_chunks(int64_t T, int M, int chunk) {
     if (T <= 0 || M <= 0 || chunk <= 0) return 0;
-    const int MP = pad_order(M, LP_DTYPE_F32);
-    if (MP <= 0) return 0;
-    const int64_t L = ceil_div(chunk, MP) * MP;
+    const int64_t L = ceil_div(chunk, 8) * 8;
     return ceil_div(T, L);
 }
 

@@ -8,9 +8,10 @@ namespace tvlp {
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per K1 block
 constexpr int kMaxDevices = 64;
 
+template <typename S, int MP> using DefaultSumGeo = SumGeo<S, MP, Pack<MP>::G, Pack<MP>::R>;
+
 template <typename S, int MP> inline int k1_warps_per_block() {
-    using GE = Geo<S, MP>;
-    int w = (int)(kSmemBudget / GE::WARP_BYTES);
+    int w = (int)(kSmemBudget / DefaultSumGeo<S, MP>::WARP_BYTES);
     return w > 8 ? 8 : (w < 1 ? 1 : w);
 }
 
@@ -27,18 +28,18 @@ template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes, bool
 }
 
 template <typename S, int MP> Shape Impl<S, MP>::shape() {
-    using GE = Geo<S, MP>;
+    using GE = DefaultSumGeo<S, MP>;
     Shape sh;
     sh.chunks_per_warp = GE::CPW;
     sh.warps_per_block = k1_warps_per_block<S, MP>();
     const int wps = (sh.warps_per_block + 3) / 4;  // warps sharing a scheduler
-    sh.per_step_cycles = (GE::R * MP + MP / 2 + 4) * wps;
-    sh.ws_per_chunk = (size_t)(GE::YS + 3 * MP) * sizeof(S);
+    sh.per_step_cycles = (GE::R * MP + MP / 2 + GE::R * MP / SR + 4) * wps;
+    sh.ws_per_chunk = (size_t)(YGeo<S, MP>::YS + 3 * MP) * sizeof(S);
     return sh;
 }
 
 template <typename S, int MP> struct Launch {
-    using GE = Geo<S, MP>;
+    using GE = DefaultSumGeo<S, MP>;
 
     static S *region(const Problem &p, void *ws, int r) {
         return reinterpret_cast<S *>(static_cast<char *>(ws) + ws_offset(p, sizeof(S), r));
@@ -48,7 +49,7 @@ template <typename S, int MP> struct Launch {
         static bool done[kMaxDevices] = {};
         const int W = k1_warps_per_block<S, MP>();
         const size_t smem = (size_t)W * GE::WARP_BYTES;
-        auto kern = k1_summary<S, MP, BWD>;
+        auto kern = k1_summary<S, MP, GE::G, GE::R, BWD>;
         cudaError_t err = allow_smem(kern, smem, done);
         if (err != cudaSuccess) return err;
         const int64_t per_block = (int64_t)W * GE::CPW;
@@ -72,13 +73,13 @@ template <typename S, int MP> struct Launch {
     static cudaError_t rec_exact(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
                                  S *gzi, int reverse, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
-        using RG = RingGeo<S, MP>;
+        using RG = RecGeo<S, MP>;
         auto kern = k_rec<S, MP, EXACT, MODE>;
         cudaError_t err = allow_smem(kern, RG::SMEM, done);
         if (err != cudaSuccess) return err;
-        const int64_t grid = (p.NQ + RG::THREADS - 1) / RG::THREADS;
-        kern<<<(unsigned)grid, RG::THREADS, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi,
-                                                            reverse);
+        const int64_t grid = (p.NQ + 31) / 32;
+        kern<<<(unsigned)grid, 32, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
+                                                   p.status);
         return cudaGetLastError();
     }
 
@@ -106,8 +107,8 @@ template <typename S, int MP> struct Launch {
 // The plain path runs the one-recursion kernels with one chunk per signal.
 inline Problem plain_problem(const Problem &p) {
     Problem q = p;
-    q.L = (int)(((p.T + p.MP - 1) / p.MP) * p.MP);
-    if (q.L == 0) q.L = p.MP;
+    q.L = (int)(((p.T + SR - 1) / SR) * SR);
+    if (q.L == 0) q.L = SR;
     q.nC = 1;
     q.NQ = p.B;
     return q;
@@ -116,9 +117,10 @@ inline Problem plain_problem(const Problem &p) {
 // Launch helper: wraps one kernel launch in the profiling marks.
 #define TVLP_LAUNCH(K, CALL)                          \
     do {                                              \
-        profile_mark((K), false, st);                 \
+        const int k_ = (K);                           \
+        profile_mark(k_, false, st);                  \
         if ((CALL) != cudaSuccess) return ECUDA;      \
-        profile_mark((K), true, st);                  \
+        profile_mark(k_, true, st);                   \
     } while (0)
 
 template <typename S, int MP>

@@ -16,7 +16,8 @@
 // adjoint's transfer over a chunk is the transpose of the forward's.  After
 // the last step (t = 0), q_j = dL/ds(-j), the initial-state gradient.
 //
-// Parallel scan over time.  A signal is cut into chunks of L samples.
+// Parallel scan over time.  A signal is cut into chunks of L samples (L a
+// multiple of SR = 8), streamed in stages of SR rows.
 //   k1_summary      per chunk, the end states of MP+1 recursions: zero state
 //                   driven by the input (column 0) and the MP unit initial
 //                   states with zero input (columns 1..MP, the chunk transfer
@@ -30,12 +31,22 @@
 //                   chunk per signal this is the plain sequential filter.
 //   k_grad_a        dL/da_i(t) = -ge(t) s(t-i) (Eq. 12), tiled.
 // Orders are padded to MP (compile time); coefficients of order > M are
-// zero, which leaves every result unchanged.
+// zero, which leaves every result unchanged.  Rows past the end of a signal
+// are staged as zeros: in the forward they follow its last output, in the
+// adjoint they precede its first step with a zero pending state, so both
+// leave every result unchanged.
+//
+// Register state.  A recursion keeps a window of MP + SR values: the MP
+// values entering a stage, then the SR values the stage produces.  Every
+// index is a compile-time constant inside the unrolled stage; at the end of
+// the stage the window slides down by SR (MP moves).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace tvlp {
+
+constexpr int SR = 8;  // rows per stage; chunk lengths are multiples of SR
 
 // Status codes written by kernels to the device status word.
 enum { DEV_OK = 0, DEV_TIMEOUT_TMA = 1 };
@@ -76,27 +87,28 @@ constexpr int conflict_free_pad(int base_words, int groups, int step) {
     }
     return best;
 }
+__host__ __device__ constexpr int wrapm(int x, int m) { return ((x % m) + m) % m; }
 
-template <typename S, int MP> struct Geo {
-    static constexpr int G = Pack<MP>::G;
-    static constexpr int R = Pack<MP>::R;
+// Geometry of the summary kernel for packing (G, R).
+template <typename S, int MP, int G_, int R_> struct SumGeo {
+    static constexpr int G = G_, R = R_;
     static constexpr int CPW = 32 / G;                     // chunks per warp
-    static constexpr int NS = 2;                            // stages in flight
+    static constexpr int NS = 3;                            // stages in the ring
     static constexpr int WPS = (int)sizeof(S) / 4;          // 32-bit words per element
     static constexpr int GPH = (16 / G) > 1 ? 16 / G : 1;   // chunk groups per half-warp
-    // chunk-stage stride (elements): MP rows of MP coefficients + padding,
-    // a multiple of 16 bytes (TMA destination alignment)
-    static constexpr int CS = MP * MP + conflict_free_pad(MP * MP * WPS, GPH, 4) / WPS;
-    static constexpr int US = MP + 1;                        // input stride per chunk-stage
+    // chunk-stage stride (elements): SR rows of MP coefficients + padding,
+    // a multiple of 16 bytes (bulk-copy destination)
+    static constexpr int CS = SR * MP + conflict_free_pad(SR * MP * WPS, GPH, 4) / WPS;
+    static constexpr int US = SR;                            // input samples per chunk-stage
     static constexpr int A_STAGE = CPW * CS;
-    static constexpr int U_STAGE = ((CPW * US + 3) / 4) * 4;
-    static constexpr int WARP_ELEMS = NS * (A_STAGE + U_STAGE);
-    static constexpr size_t WARP_BYTES = size_t(WARP_ELEMS) * sizeof(S) + NS * 8;  // + mbarriers
-    // per-chunk stride of the summaries Y[c][MP+1][MP], a multiple of 16 bytes
-    static constexpr int YS = (((MP + 1) * MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
+    static constexpr int U_STAGE = CPW * US;
+    static constexpr size_t WARP_BYTES = size_t(NS) * (A_STAGE + U_STAGE) * sizeof(S) + NS * 8;
     static_assert(G * R >= MP + 1, "packing must hold MP+1 recursions");
-    static_assert((CS * sizeof(S)) % 16 == 0, "chunk stage must stay 16-byte aligned");
-    static_assert((WARP_ELEMS * sizeof(S)) % 16 == 0, "warp region must stay 16-byte aligned");
+    static_assert((CS * sizeof(S)) % 16 == 0 && (US * sizeof(S)) % 16 == 0, "16-byte stage alignment");
+};
+// per-chunk stride of the summaries Y[c][MP+1][MP], a multiple of 16 bytes
+template <typename S, int MP> struct YGeo {
+    static constexpr int YS = (((MP + 1) * MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
 };
 
 // ---------------------------------------------------------------------------
@@ -143,11 +155,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for an mbarrier phase; false after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int limit) {
-    for (int i = 0; i < limit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+// Bounded wait for an mbarrier phase by every lane of the warp; the outcome
+// is warp-uniform (false if any lane gave up after `limit` polls).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, unsigned parity, int limit) {
+    bool ok = false;
+    for (int i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(bar, parity);
+    return __all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
@@ -157,8 +170,9 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-__host__ __device__ constexpr int wrapm(int x, int m) { return ((x % m) + m) % m; }
+constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before a wait gives up
 
 // Load the MP coefficients of one shared-memory row (8-byte aligned for
 // float, 16-byte for double; MP is even) into registers.
@@ -182,79 +196,111 @@ __device__ __forceinline__ void load_row_smem(S (&c)[MP], const S *row) {
         }
     }
 }
-
-// Forward direct-form step at chunk-local time t with t % MP == TT:
-// h[t % MP] holds s(t).  Four partial sums over the older terms, then the
-// two freshest outputs, keep the critical path to a few FMAs per step.
+// Load two consecutive rows (16-byte aligned) with 16-byte loads.
 template <typename S, int MP>
-__device__ __forceinline__ S fwd_step(S (&h)[MP], const S (&c)[MP], S u, int tt) {
+__device__ __forceinline__ void load_pair_smem(S (&c0)[MP], S (&c1)[MP], const S *rows) {
+    S v[2 * MP];
+    if constexpr (sizeof(S) == 4) {
+        const float4 *p = reinterpret_cast<const float4 *>(rows);
+#pragma unroll
+        for (int i = 0; i < MP / 2; ++i) {
+            const float4 x = p[i];
+            v[4 * i] = x.x;
+            v[4 * i + 1] = x.y;
+            v[4 * i + 2] = x.z;
+            v[4 * i + 3] = x.w;
+        }
+    } else {
+        const double2 *p = reinterpret_cast<const double2 *>(rows);
+#pragma unroll
+        for (int i = 0; i < MP; ++i) {
+            const double2 x = p[i];
+            v[2 * i] = x.x;
+            v[2 * i + 1] = x.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < MP; ++i) {
+        c0[i] = v[i];
+        c1[i] = v[MP + i];
+    }
+}
+
+// Forward step on a window h (h[MP + j - i] = s(t - i)); writes s(t) to
+// h[MP + j].  Partial sums over the older terms keep the critical path to a
+// few FMAs per step.
+template <typename S, int MP, int W>
+__device__ __forceinline__ S fwd_step_win(S (&h)[W], const S (&c)[MP], S u, int j) {
     S p0 = u, p1 = S(0), p2 = S(0), p3 = S(0);
 #pragma unroll
     for (int i = MP; i >= 3; --i) {
-        const S hv = h[wrapm(tt - i, MP)];
+        const S hv = h[MP + j - i];
         if ((i & 3) == 0) p0 = fma(-c[i - 1], hv, p0);
         else if ((i & 3) == 1) p1 = fma(-c[i - 1], hv, p1);
         else if ((i & 3) == 2) p2 = fma(-c[i - 1], hv, p2);
         else p3 = fma(-c[i - 1], hv, p3);
     }
     S acc = (p0 + p1) + (p2 + p3);
-    if constexpr (MP >= 2) acc = fma(-c[1], h[wrapm(tt - 2, MP)], acc);
-    acc = fma(-c[0], h[wrapm(tt - 1, MP)], acc);
-    h[tt] = acc;
+    if constexpr (MP >= 2) acc = fma(-c[1], h[MP + j - 2], acc);
+    acc = fma(-c[0], h[MP + j - 1], acc);
+    h[MP + j] = acc;
     return acc;
 }
 
-// Backward transposed-form step: q_1 sits in slot p and q_k in slot
-// (p + k - 1) % MP before the step; after it q_k sits in (p + k) % MP.
-template <typename S, int MP>
-__device__ __forceinline__ S bwd_step(S (&q)[MP], const S (&c)[MP], S u, int p) {
-    const S y = u + q[p];
-    q[p] = -c[MP - 1] * y;
+// Adjoint step on a window q: before step j, q_k sits at q[j + k - 1]; after
+// it, q_k sits at q[j + k].  Returns ge(t).
+template <typename S, int MP, int W>
+__device__ __forceinline__ S bwd_step_win(S (&q)[W], const S (&c)[MP], S u, int j) {
+    const S y = u + q[j];
 #pragma unroll
-    for (int k = 1; k < MP; ++k) q[wrapm(p + k, MP)] = fma(-c[k - 1], y, q[wrapm(p + k, MP)]);
+    for (int k = 1; k < MP; ++k) q[j + k] = fma(-c[k - 1], y, q[j + k]);
+    q[j + MP] = -c[MP - 1] * y;
     return y;
+}
+
+// slide a window down by SR
+template <typename S, int MP, int W>
+__device__ __forceinline__ void slide(S (&h)[W]) {
+#pragma unroll
+    for (int i = 0; i < MP; ++i) h[i] = h[i + SR];
 }
 
 // ---------------------------------------------------------------------------
 // K1: chunk summaries.
 // Flattened chunk index q = b*nC + c; chunk c of signal b covers samples
-// [c*L, c*L + L); rows at or beyond T read as zero (exact: the forward's
-// last chunk has no successor; in the adjoint, zero input and coefficients
-// past T keep the pending state at zero).
-// Each warp owns CPW consecutive chunks; lane (grp = lane/G, g = lane%G)
-// runs recursions r = g*R + k, k < R.  Coefficient rows are staged through
-// shared memory, MP rows per stage, two stages in flight: full chunk-stages
-// arrive by one 1-D bulk (TMA) copy each, completing on a per-stage
-// mbarrier; ragged or misaligned chunk-stages and the input samples use
-// cp.async with zero fill.  Forward stages advance in time, backward stages
-// go back in time.
+// [c*L, c*L + L).  Each warp owns CPW consecutive chunks; lane (grp = lane/G,
+// g = lane%G) runs recursions r = g*R + k, k < R.  Coefficient rows and
+// input samples are staged in shared memory, SR rows per stage, NS stages in
+// a ring: a full, 16-byte-aligned chunk-stage arrives as one bulk (TMA)
+// copy completing on the stage's mbarrier; others (a ragged tail, a
+// misaligned start, a padded order) use cp.async with zero fill.
 // Output Y[q][r][k] (per-chunk stride YS):
 //   forward:  s(c*L + L - 1 - k) of recursion r
 //   backward: q_{k+1} after the chunk, i.e. the pending dL/ds(c*L - 1 - k)
 // ---------------------------------------------------------------------------
-template <typename S, int MP, bool BWD>
+template <typename S, int MP, typename GE, bool BWD>
 __device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, const S *__restrict__ a,
                                                const S *__restrict__ u, int M, int L, int k, int lane,
                                                int64_t my_base, int my_valid, bool exact) {
-    using GE = Geo<S, MP>;
     constexpr int CPW = GE::CPW;
-    constexpr unsigned STAGE_BYTES = MP * MP * sizeof(S);
-    const int roff = BWD ? L - (k + 1) * MP : k * MP;  // chunk-local first row of the stage
-    // lane ch < CPW describes chunk ch
+    constexpr unsigned A_BYTES = SR * MP * sizeof(S);
+    constexpr unsigned U_BYTES = SR * sizeof(S);
+    const int roff = BWD ? L - (k + 1) * SR : k * SR;  // chunk-local first row of the stage
     int nvalid = my_valid - roff;
-    nvalid = nvalid < 0 ? 0 : (nvalid > MP ? MP : nvalid);
-    const S *src = a + (my_base + roff) * (int64_t)MP;
-    bool tma = false;
-    if (lane < CPW) tma = exact && nvalid == MP && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
-    const unsigned tma_mask = __ballot_sync(0xffffffffu, tma);
-    if (lane == 0) mbar_arrive_expect_tx(bar, __popc(tma_mask) * STAGE_BYTES);
+    nvalid = nvalid < 0 ? 0 : (nvalid > SR ? SR : nvalid);
+    const bool mine = lane < CPW;
+    const S *src_a = a + (my_base + roff) * (int64_t)MP;
+    const S *src_u = u + my_base + roff;
+    const bool tma_a = mine && exact && nvalid == SR && aligned16(src_a);
+    const bool tma_u = mine && nvalid == SR && aligned16(src_u);
+    const unsigned bytes = __reduce_add_sync(0xffffffffu, (tma_a ? A_BYTES : 0u) + (tma_u ? U_BYTES : 0u));
+    if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
     __syncwarp();
-    if (tma) {
-        fence_proxy_async();
-        bulk_load(a_st + lane * GE::CS, src, STAGE_BYTES, bar);
-    }
-    // fallback chunk-stages (ragged tail, misaligned start, padded order)
-    unsigned slow = __ballot_sync(0xffffffffu, lane < CPW && !tma) & ((1u << CPW) - 1u);
+    if (tma_a || tma_u) fence_proxy_async();
+    if (tma_a) bulk_load(a_st + lane * GE::CS, src_a, A_BYTES, bar);
+    if (tma_u) bulk_load(u_st + lane * GE::US, src_u, U_BYTES, bar);
+    // fallback chunk-stages
+    unsigned slow = __ballot_sync(0xffffffffu, mine && !tma_a);
     while (slow) {
         const int ch = __ffs(slow) - 1;
         slow &= slow - 1;
@@ -263,12 +309,14 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, 
         S *dst = a_st + ch * GE::CS;
         if (exact) {
             const S *s0 = a + (base + roff) * (int64_t)MP;
-            for (int idx = lane; idx < MP * MP; idx += 32) {
+            for (int idx = lane; idx < SR * MP; idx += 32) {
                 const bool v = idx < nv * MP;
                 cp_async<sizeof(S)>(dst + idx, v ? s0 + idx : a, v ? (int)sizeof(S) : 0);
             }
         } else {
-            for (int r = 0; r < MP; ++r) {
+            // padded order: the M real coefficients of every row; the padded
+            // columns were zeroed once and are never written
+            for (int r = 0; r < SR; ++r) {
                 if (lane < M) {
                     const bool v = r < nv;
                     const S *s0 = v ? a + (base + roff + r) * (int64_t)M + lane : a;
@@ -277,12 +325,13 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, 
             }
         }
     }
-    // input samples of every chunk-stage (lane r copies row r)
-#pragma unroll 1
-    for (int ch = 0; ch < CPW; ++ch) {
+    slow = __ballot_sync(0xffffffffu, mine && !tma_u);
+    while (slow) {
+        const int ch = __ffs(slow) - 1;
+        slow &= slow - 1;
         const int64_t base = __shfl_sync(0xffffffffu, my_base, ch);
         const int nv = __shfl_sync(0xffffffffu, nvalid, ch);
-        if (lane < MP) {
+        if (lane < SR) {
             const bool v = lane < nv;
             cp_async<sizeof(S)>(u_st + ch * GE::US + lane, v ? u + base + roff + lane : u, v ? (int)sizeof(S) : 0);
         }
@@ -290,12 +339,13 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, 
     cp_async_commit();
 }
 
-template <typename S, int MP, bool BWD>
+template <typename S, int MP, int G, int R, bool BWD>
 __global__ void __launch_bounds__(256, 1)
     k1_summary(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
                S *__restrict__ Y, int exact_flag, int *__restrict__ status) {
-    using GE = Geo<S, MP>;
-    constexpr int G = GE::G, R = GE::R, CPW = GE::CPW;
+    using GE = SumGeo<S, MP, G, R>;
+    constexpr int CPW = GE::CPW, NS = GE::NS, WIN = MP + SR;
+    constexpr int YS = YGeo<S, MP>::YS;
     extern __shared__ __align__(128) unsigned char k1_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
@@ -303,18 +353,18 @@ __global__ void __launch_bounds__(256, 1)
     if (q0 >= NQ) return;
     const bool exact = exact_flag != 0;
     unsigned char *wbase = k1_smem + (size_t)warp * GE::WARP_BYTES;
-    S *a_buf = reinterpret_cast<S *>(wbase);                 // [NS][A_STAGE]
-    S *u_buf = a_buf + GE::NS * GE::A_STAGE;                  // [NS][U_STAGE]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(u_buf + GE::NS * GE::U_STAGE);
+    S *a_buf = reinterpret_cast<S *>(wbase);      // [NS][A_STAGE]
+    S *u_buf = a_buf + NS * GE::A_STAGE;           // [NS][U_STAGE]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(u_buf + NS * GE::U_STAGE);
     if (!exact) {
-        for (int idx = lane; idx < GE::NS * GE::A_STAGE; idx += 32) a_buf[idx] = S(0);
+        for (int idx = lane; idx < NS * GE::A_STAGE; idx += 32) a_buf[idx] = S(0);
     }
     if (lane == 0) {
-        for (int s = 0; s < GE::NS; ++s) mbar_init(bars + s, 1);
+        for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
         mbar_init_fence();
     }
     __syncwarp();
-    // lane ch < CPW describes chunk q0 + ch: first row b*T + c*L and valid rows
+    // lane ch < CPW describes chunk q0 + ch: first row b*T + c*L, valid rows
     int64_t my_base = 0;
     int my_valid = 0;
     if (lane < CPW && q0 + lane < NQ) {
@@ -326,68 +376,69 @@ __global__ void __launch_bounds__(256, 1)
         my_valid = rem < L ? (int)rem : L;
     }
     const int grp = lane / G, g = lane % G;
-    const int nblk = L / MP;
+    const int nblk = L / SR;
 
-    // forward: h[k][t % MP] = output of recursion k at chunk-local time t
-    // backward: h[k][slot] = pending state (q_j in slot j % MP at start)
-    S h[R][MP];
+    // forward window: h[k][MP - i] = s(t - i) at a stage start; backward
+    // window: h[k][j - 1] = q_j at a stage start
+    S h[R][WIN];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int r = g * R + k;
 #pragma unroll
-        for (int m = 0; m < MP; ++m) {
-            const int unit_slot = BWD ? (r % MP) : ((MP - (r % MP)) % MP);
-            h[k][m] = (r >= 1 && r <= MP && m == unit_slot) ? S(1) : S(0);
+        for (int m = 0; m < WIN; ++m) {
+            const int unit = BWD ? r - 1 : MP - r;
+            h[k][m] = (r >= 1 && r <= MP && m == unit) ? S(1) : S(0);
         }
     }
     const S flag0 = (g == 0) ? S(1) : S(0);
 
-    k1_issue_stage<S, MP, BWD>(a_buf, u_buf, bars, a, u, M, L, 0, lane, my_base, my_valid, exact);
 #pragma unroll 1
-    for (int k = 0; k < nblk; ++k) {
-        const int slot = k & 1;
-        if (k + 1 < nblk)
-            k1_issue_stage<S, MP, BWD>(a_buf + (slot ^ 1) * GE::A_STAGE, u_buf + (slot ^ 1) * GE::U_STAGE,
-                                       bars + (slot ^ 1), a, u, M, L, k + 1, lane, my_base, my_valid, exact);
+    for (int s = 0; s < NS - 1; ++s) {
+        if (s < nblk)
+            k1_issue_stage<S, MP, GE, BWD>(a_buf + s * GE::A_STAGE, u_buf + s * GE::U_STAGE, bars + s, a, u, M, L,
+                                           s, lane, my_base, my_valid, exact);
         else
             cp_async_commit();
-        cp_async_wait<1>();
-        int ok = 1;
-        if (lane == 0) ok = mbar_wait_bounded(bars + slot, (k >> 1) & 1, 1 << 22) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-            // a bulk copy never completed: record it, give the copy in flight
-            // for the other stage a bounded chance to land, and leave
-            if (lane == 0) {
-                atomicExch(status, DEV_TIMEOUT_TMA);
-                if (k + 1 < nblk) mbar_wait_bounded(bars + (slot ^ 1), ((k + 1) >> 1) & 1, 1 << 22);
-            }
+    }
+#pragma unroll 1
+    for (int k = 0; k < nblk; ++k) {
+        const int slot = k % NS;
+        const int ahead = k + NS - 1;  // refill the slot of stage k-1
+        if (ahead < nblk)
+            k1_issue_stage<S, MP, GE, BWD>(a_buf + (ahead % NS) * GE::A_STAGE, u_buf + (ahead % NS) * GE::U_STAGE,
+                                           bars + ahead % NS, a, u, M, L, ahead, lane, my_base, my_valid, exact);
+        else
+            cp_async_commit();
+        cp_async_wait<NS - 1>();
+        if (!mbar_wait_warp(bars + slot, (k / NS) & 1, kWaitLimit)) {
+            // a bulk copy never completed: record it, give the copies this
+            // warp still has in flight a bounded chance to land, and leave
+            if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+            for (int s2 = k + 1; s2 < k + NS && s2 < nblk; ++s2)
+                mbar_wait_warp(bars + s2 % NS, (s2 / NS) & 1, kWaitLimit);
             cp_async_wait<0>();
-            __syncwarp();
             return;
         }
         __syncwarp();
         const S *arow = a_buf + slot * GE::A_STAGE + grp * GE::CS;
         const S *urow = u_buf + slot * GE::U_STAGE + grp * GE::US;
 #pragma unroll
-        for (int step = 0; step < MP; ++step) {
-            // forward: row tt = step (t % MP == tt); backward: row tt = MP-1-step,
-            // and q_1 sits in slot (step + 1) % MP
-            const int tt = BWD ? MP - 1 - step : step;
+        for (int j = 0; j < SR; ++j) {
+            // forward: row j; backward: row SR-1-j (rows run back in time)
+            const int row = BWD ? SR - 1 - j : j;
             S c[MP];
-            load_row_smem<S, MP>(c, arow + tt * MP);
-            const S uu = flag0 * urow[tt];
+            load_row_smem<S, MP>(c, arow + row * MP);
+            const S uu = flag0 * urow[row];
             if constexpr (BWD) {
-                const int p = (step + 1) % MP;
                 S y[R];
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) y[kk] = ((kk == 0) ? uu : S(0)) + h[kk][p];
+                for (int kk = 0; kk < R; ++kk) y[kk] = ((kk == 0) ? uu : S(0)) + h[kk][j];
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) h[kk][p] = -c[MP - 1] * y[kk];
+                for (int i = 1; i < MP; ++i)
 #pragma unroll
-                for (int j = 1; j < MP; ++j)
+                    for (int kk = 0; kk < R; ++kk) h[kk][j + i] = fma(-c[i - 1], y[kk], h[kk][j + i]);
 #pragma unroll
-                    for (int kk = 0; kk < R; ++kk) h[kk][(p + j) % MP] = fma(-c[j - 1], y[kk], h[kk][(p + j) % MP]);
+                for (int kk = 0; kk < R; ++kk) h[kk][j + MP] = -c[MP - 1] * y[kk];
             } else {
                 S acc[R];
 #pragma unroll
@@ -395,187 +446,222 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                 for (int i = MP; i >= 1; --i)
 #pragma unroll
-                    for (int kk = 0; kk < R; ++kk) acc[kk] = fma(-c[i - 1], h[kk][wrapm(tt - i, MP)], acc[kk]);
+                    for (int kk = 0; kk < R; ++kk) acc[kk] = fma(-c[i - 1], h[kk][MP + j - i], acc[kk]);
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) h[kk][tt] = acc[kk];
+                for (int kk = 0; kk < R; ++kk) h[kk][MP + j] = acc[kk];
             }
         }
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk) slide<S, MP, WIN>(h[kk]);
         __syncwarp();
     }
     // end states
     const int64_t q = q0 + grp;
     if (q < NQ) {
-        S *yq = Y + q * GE::YS;
+        S *yq = Y + q * YS;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int r = g * R + k;
             if (r <= MP) {
 #pragma unroll
-                for (int j = 0; j < MP; ++j) {
-                    // forward: s(L-1-j) sits in slot (MP-1-j); backward: q_{j+1} in (j+1) % MP
-                    const int sl = BWD ? (j + 1) % MP : MP - 1 - j;
-                    yq[r * MP + j] = h[k][sl];
-                }
+                for (int j = 0; j < MP; ++j) yq[r * MP + j] = BWD ? h[k][j] : h[k][MP - 1 - j];
             }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// One recursion per thread over its chunk ("lane per chunk").  Coefficient
-// rows and input samples stream through a private shared-memory ring of D
-// rows per thread, filled by cp.async D-2 rows ahead, two rows per group.
+// One recursion per lane over its chunk ("lane per chunk"): a warp owns 32
+// consecutive chunks.  Each lane has a private ring of NS stages of SR rows
+// (coefficients and input samples); a full, aligned lane-stage arrives by
+// two bulk copies completing on the warp's per-stage mbarrier, others by
+// cp.async with zero fill.
 //   FWD_RERUN: start from X[q] (or zi / zero), write s.
 //   BWD_ZERO:  adjoint from zero state, store the end state to Z[q].
 //   BWD_RERUN: adjoint from W[q], write ge; chunk 0 also writes gzi.
 // A launch with one chunk per signal (L >= T) is the plain sequential filter.
-// Blocks walk the chunks in reverse order when `reverse` is set, so that a
-// pass right after another one over the same rows starts with the rows that
-// pass loaded last (most likely still in L2).
+// With `reverse` set, warps walk the chunks from the end, so a pass right
+// after another over the same rows starts with the rows that pass loaded
+// last (most likely still in L2).
 // ---------------------------------------------------------------------------
 enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2 };
 
-template <typename S, int MP> struct RingGeo {
-    static constexpr int D = 16;                       // rows per thread ring (power of two)
-    static constexpr int SLOT = MP + 2;                // MP coefficients, input, pad (elements)
-    static constexpr int WPS = (int)sizeof(S) / 4;
-    static constexpr int RAW = D * SLOT * WPS;         // words per thread
-    // thread stride in words, 2*WPS mod 32, so 8-byte (float) / 16-byte
-    // (double) row loads of a half / quarter warp hit distinct banks
-    static constexpr int TW = RAW + wrapm(2 * WPS - RAW, 32);
-    static constexpr int THREADS = 32;
-    static constexpr size_t SMEM = size_t(THREADS) * TW * 4;
+template <typename S, int MP> struct RecGeo {
+    static constexpr int NS = 4;                                         // stages per lane ring
+    static constexpr int A_ST = SR * MP;                                 // coefficient elements per lane-stage
+    static constexpr int RAW = (NS * (A_ST + SR) * (int)sizeof(S)) / 4;  // words per lane
+    // lane stride in words: an odd multiple of 4, so the 16-byte row loads of
+    // a quarter warp hit distinct bank quads
+    static constexpr int LW = ((RAW + 3) / 4) % 2 == 1 ? ((RAW + 3) / 4) * 4 : ((RAW + 3) / 4 + 1) * 4;
+    static constexpr size_t SMEM = size_t(32) * LW * 4 + NS * 8;
+    static_assert((A_ST * sizeof(S)) % 16 == 0 && (SR * sizeof(S)) % 16 == 0, "16-byte lane stages");
 };
 
-template <typename S, int MP, bool EXACT>
-__device__ __forceinline__ void ring_issue_row(S *slot, const S *__restrict__ row, const S *__restrict__ up,
-                                               int M) {
-    if constexpr (EXACT) {
-        // M == MP: the row is MP contiguous elements, 8-byte aligned
-#pragma unroll
-        for (int j = 0; j < MP * (int)sizeof(S) / 8; ++j)
-            cp_async<8>(reinterpret_cast<char *>(slot) + 8 * j, reinterpret_cast<const char *>(row) + 8 * j, 8);
-    } else {
-        for (int j = 0; j < M; ++j) cp_async<sizeof(S)>(slot + j, row + j, (int)sizeof(S));
+template <typename S, int MP, bool EXACT, bool BWD>
+__device__ __forceinline__ void rec_issue_stage(S *a_st, S *u_st, uint64_t *bar, const S *__restrict__ a,
+                                                const S *__restrict__ u, int M, int L, int s, bool active,
+                                                int64_t base, int n) {
+    constexpr unsigned A_BYTES = SR * MP * sizeof(S);
+    constexpr unsigned U_BYTES = SR * sizeof(S);
+    const int roff = BWD ? L - (s + 1) * SR : s * SR;
+    int nv = n - roff;
+    nv = nv < 0 ? 0 : (nv > SR ? SR : nv);
+    if (!active) nv = 0;
+    const S *src_a = a + (base + roff) * (int64_t)M;
+    const S *src_u = u + base + roff;
+    const bool tma_a = EXACT && nv == SR && aligned16(src_a);
+    const bool tma_u = nv == SR && aligned16(src_u);
+    const unsigned bytes = __reduce_add_sync(0xffffffffu, (tma_a ? A_BYTES : 0u) + (tma_u ? U_BYTES : 0u));
+    if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, bytes);
+    __syncwarp();
+    if (tma_a || tma_u) fence_proxy_async();
+    if (tma_a) bulk_load(a_st, src_a, A_BYTES, bar);
+    if (tma_u) bulk_load(u_st, src_u, U_BYTES, bar);
+    if (!tma_a) {
+        if (EXACT) {
+            for (int idx = 0; idx < SR * MP; ++idx) {
+                const bool v = idx < nv * MP;
+                cp_async<sizeof(S)>(a_st + idx, v ? src_a + idx : a, v ? (int)sizeof(S) : 0);
+            }
+        } else {
+            for (int r = 0; r < SR; ++r)
+                for (int i = 0; i < M; ++i) {
+                    const bool v = r < nv;
+                    cp_async<sizeof(S)>(a_st + r * MP + i, v ? src_a + (int64_t)r * M + i : a, v ? (int)sizeof(S) : 0);
+                }
+        }
     }
-    cp_async<sizeof(S)>(slot + MP, up, (int)sizeof(S));
+    if (!tma_u) {
+        for (int r = 0; r < SR; ++r) {
+            const bool v = r < nv;
+            cp_async<sizeof(S)>(u_st + r, v ? src_u + r : u, v ? (int)sizeof(S) : 0);
+        }
+    }
+    cp_async_commit();
 }
 
 template <typename S, int MP, bool EXACT, int MODE>
 __global__ void __launch_bounds__(32)
     k_rec(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
-          S *__restrict__ gzi, int reverse) {
-    using RG = RingGeo<S, MP>;
-    constexpr int D = RG::D, SLOT = RG::SLOT;
+          S *__restrict__ gzi, int reverse, int *__restrict__ status) {
+    using RG = RecGeo<S, MP>;
+    constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
-    extern __shared__ __align__(16) unsigned char rec_smem[];
+    extern __shared__ __align__(128) unsigned char rec_smem[];
+    const int lane = threadIdx.x & 31;
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
-    const int64_t q = blk * RG::THREADS + threadIdx.x;
-    if (q >= NQ) return;
-    S *ring = reinterpret_cast<S *>(rec_smem + (size_t)threadIdx.x * RG::TW * 4);
+    const int64_t q = blk * 32 + lane;
+    const bool active = q < NQ;
+    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)lane * RG::LW * 4);  // [NS][SR*MP]
+    S *u_ring = a_ring + NS * RG::A_ST;                                         // [NS][SR]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)32 * RG::LW * 4);
     if (!EXACT) {
-        for (int j = 0; j < D * SLOT; ++j) ring[j] = S(0);
+        for (int j = 0; j < NS * RG::A_ST; ++j) a_ring[j] = S(0);
     }
-    const int64_t b = q / nC;
-    const int64_t c = q - b * nC;
-    const int64_t t0 = c * (int64_t)L;
-    const int64_t rem = T - t0;
-    const int n = rem < L ? (int)rem : L;  // valid rows of this chunk
-    const S *arow = a + (b * T + t0) * (int64_t)M;
-    const S *up = u + b * T + t0;
-
-    S h[MP];
-    if constexpr (MODE == FWD_RERUN) {
-        // s(t0-1-j) sits in slot (t0-1-j) % MP = MP-1-j  (t0 is a multiple of MP)
-#pragma unroll
-        for (int j = 0; j < MP; ++j) {
-            S v = S(0);
-            if (Xin != nullptr) v = Xin[q * MP + j];
-            else if (zi != nullptr && j < M) v = zi[b * M + j];
-            h[MP - 1 - j] = v;
-        }
-    } else {
-        // pending state entering from the chunk's end: q_j in slot j % MP
-#pragma unroll
-        for (int j = 1; j <= MP; ++j) h[j % MP] = (MODE == BWD_RERUN && Xin != nullptr) ? Xin[q * MP + (j - 1)] : S(0);
+    if (lane == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
+        mbar_init_fence();
     }
-
-    // valid rows in processing order: forward t0, t0+1, ...; backward
-    // t0+n-1, ..., t0.  Row r of that order sits in ring slot r % D.
-    auto row_of = [&](int r) -> int { return BWD ? n - 1 - r : r; };
-    int nx = 0;  // next row to issue
-    auto issue_upto = [&](int last) {
-        const int hi = last < n - 1 ? last : n - 1;
-        for (; nx <= hi; ++nx) {
-            const int lr = row_of(nx);
-            ring_issue_row<S, MP, EXACT>(ring + (nx & (D - 1)) * SLOT, arow + (int64_t)lr * M, up + lr, M);
-        }
-        cp_async_commit();
-    };
-    // prologue: rows 0..D-3, two per group
-#pragma unroll 1
-    for (int g = 0; g < (D - 2) / 2; ++g) issue_upto(2 * g + 1);
-    // Nominal steps run over the whole chunk (L, a multiple of MP) so the
-    // rotation phases are compile-time constants; rows beyond T are skipped
-    // (only in the last chunk, where they sit after the forward's last valid
-    // row or before the adjoint's first one, with a zero pending state).
-    const int skip = BWD ? L - n : 0;  // nominal steps before the first valid row
-    int r = 0;                          // valid rows processed so far
-    auto one_step = [&](const S(&cc)[MP], S uu, int step) {
-        const int lr = row_of(r);
+    __syncwarp();
+    int64_t b = 0, c = 0, base = 0;
+    int n = 0;
+    if (active) {
+        b = q / nC;
+        c = q - b * nC;
+        const int64_t t0 = c * (int64_t)L;
+        base = b * T + t0;
+        const int64_t rem = T - t0;
+        n = rem < L ? (int)rem : L;
+    }
+    S h[WIN];
+#pragma unroll
+    for (int m = 0; m < WIN; ++m) h[m] = S(0);
+    if (active) {
         if constexpr (MODE == FWD_RERUN) {
-            out[b * T + t0 + lr] = fwd_step<S, MP>(h, cc, uu, step);
-        } else {
-            const S y = bwd_step<S, MP>(h, cc, uu, (step + 1) % MP);
-            if constexpr (MODE == BWD_RERUN) out[b * T + t0 + lr] = y;
-        }
-        ++r;
-    };
-    const int nblk = L / MP;
-#pragma unroll 1
-    for (int bk = 0; bk < nblk; ++bk) {
-        if (!BWD && bk * MP >= n) break;
-        if (BWD && (bk + 1) * MP <= skip) continue;
+            // h[MP - j] = s(t0 - j)
 #pragma unroll
-        for (int st = 0; st < MP; st += 2) {
-            const int nom0 = bk * MP + st;  // nominal step index of the pair's first step
-            const bool v0 = BWD ? (nom0 >= skip) : (nom0 < n);
-            const bool v1 = BWD ? (nom0 + 1 >= skip) : (nom0 + 1 < n);
-            if (!v0 && !v1) continue;
-            // refill up to D-1 rows ahead (slots of rows already consumed),
-            // one cp.async group per pair; then wait for this pair's rows
-            issue_upto(r + D - 1);
-            cp_async_wait<(D - 2) / 2>();
-            const S *s0 = ring + (r & (D - 1)) * SLOT;
-            if (v0 && v1) {
-                const S *s1 = ring + ((r + 1) & (D - 1)) * SLOT;
-                S c0[MP], c1[MP];
-                load_row_smem<S, MP>(c0, s0);
-                load_row_smem<S, MP>(c1, s1);
-                const S u0 = s0[MP], u1 = s1[MP];
-                one_step(c0, u0, st);
-                one_step(c1, u1, st + 1);
-            } else {
-                // a lone row: the forward's last row or the adjoint's first
-                S c0[MP];
-                load_row_smem<S, MP>(c0, s0);
-                if (v0) one_step(c0, s0[MP], st);
-                else one_step(c0, s0[MP], st + 1);
+            for (int j = 1; j <= MP; ++j) {
+                S v = S(0);
+                if (Xin != nullptr) v = Xin[q * MP + (j - 1)];
+                else if (zi != nullptr && j <= M) v = zi[b * M + (j - 1)];
+                h[MP - j] = v;
+            }
+        } else if constexpr (MODE == BWD_RERUN) {
+            // h[j - 1] = q_j entering from the chunk's end
+            if (Xin != nullptr) {
+#pragma unroll
+                for (int j = 0; j < MP; ++j) h[j] = Xin[q * MP + j];
             }
         }
     }
-    cp_async_wait<0>();
-    if constexpr (MODE == BWD_ZERO) {
-        // after L nominal steps (a multiple of MP) q_j is back in slot j % MP
+    const int nblk = L / SR;
+#pragma unroll 1
+    for (int s = 0; s < NS - 1; ++s) {
+        if (s < nblk)
+            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + s * RG::A_ST, u_ring + s * SR, bars + s, a, u, M, L, s, active,
+                                               base, n);
+        else
+            cp_async_commit();
+    }
+#pragma unroll 1
+    for (int s = 0; s < nblk; ++s) {
+        const int slot = s % NS;
+        const int ahead = s + NS - 1;
+        if (ahead < nblk)
+            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + (ahead % NS) * RG::A_ST, u_ring + (ahead % NS) * SR,
+                                               bars + ahead % NS, a, u, M, L, ahead, active, base, n);
+        else
+            cp_async_commit();
+        cp_async_wait<NS - 1>();
+        if (!mbar_wait_warp(bars + slot, (s / NS) & 1, kWaitLimit)) {
+            if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+            for (int s2 = s + 1; s2 < s + NS && s2 < nblk; ++s2)
+                mbar_wait_warp(bars + s2 % NS, (s2 / NS) & 1, kWaitLimit);
+            cp_async_wait<0>();
+            return;
+        }
+        __syncwarp();
+        const S *ar = a_ring + slot * RG::A_ST;
+        const S *ur = u_ring + slot * SR;
+        const int roff = BWD ? L - (s + 1) * SR : s * SR;
 #pragma unroll
-        for (int j = 1; j <= MP; ++j) Zout[q * MP + (j - 1)] = h[j % MP];
+        for (int pr = 0; pr < SR / 2; ++pr) {
+            // rows 2p, 2p+1 of the stage; the adjoint runs the pairs, and the
+            // rows inside a pair, in reverse
+            const int p = BWD ? SR / 2 - 1 - pr : pr;
+            S c0[MP], c1[MP];
+            load_pair_smem<S, MP>(c0, c1, ar + 2 * p * MP);
+            const S u0 = ur[2 * p], u1 = ur[2 * p + 1];
+            const int r0 = roff + 2 * p;
+            if constexpr (MODE == FWD_RERUN) {
+                const S y0 = fwd_step_win<S, MP, WIN>(h, c0, u0, 2 * p);
+                const S y1 = fwd_step_win<S, MP, WIN>(h, c1, u1, 2 * p + 1);
+                if (r0 < n) out[base + r0] = y0;
+                if (r0 + 1 < n) out[base + r0 + 1] = y1;
+            } else {
+                const S y1 = bwd_step_win<S, MP, WIN>(h, c1, u1, 2 * pr);
+                const S y0 = bwd_step_win<S, MP, WIN>(h, c0, u0, 2 * pr + 1);
+                if constexpr (MODE == BWD_RERUN) {
+                    if (r0 + 1 < n) out[base + r0 + 1] = y1;
+                    if (r0 < n) out[base + r0] = y0;
+                }
+            }
+        }
+        slide<S, MP, WIN>(h);
+        __syncwarp();
+    }
+    cp_async_wait<0>();
+    if (!active) return;
+    if constexpr (MODE == BWD_ZERO) {
+#pragma unroll
+        for (int j = 0; j < MP; ++j) Zout[q * MP + j] = h[j];
     }
     if constexpr (MODE == BWD_RERUN) {
         if (gzi != nullptr && c == 0) {
 #pragma unroll
-            for (int j = 1; j <= MP; ++j)
-                if (j <= M) gzi[b * M + (j - 1)] = h[j % MP];
+            for (int j = 0; j < MP; ++j)
+                if (j < M) gzi[b * M + j] = h[j];
         }
     }
 }
@@ -595,9 +681,9 @@ __global__ void __launch_bounds__(32)
 enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2 };
 
 template <typename S, int MP> struct ChainGeo {
-    static constexpr int NB = 8;                                       // chunks prefetched
+    static constexpr int NB = 32;                                      // chunks prefetched
     static constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
-    static constexpr int SLOT = Geo<S, MP>::YS + ZS;                   // Y block + z vector
+    static constexpr int SLOT = YGeo<S, MP>::YS + ZS;                   // Y block + z vector
     static constexpr size_t SMEM = size_t(NB) * SLOT * sizeof(S);
 };
 
@@ -605,10 +691,9 @@ template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(32)
     k2_chain(int B, int M, int64_t nC, const S *__restrict__ Y, const S *__restrict__ Z, const S *__restrict__ zi,
              S *__restrict__ X, S *__restrict__ ckpt) {
-    using GE = Geo<S, MP>;
     using CG = ChainGeo<S, MP>;
     constexpr int NB = CG::NB;
-    constexpr int YS = GE::YS;
+    constexpr int YS = YGeo<S, MP>::YS;
     constexpr bool REV = MODE != CH_FWD;
     extern __shared__ __align__(16) unsigned char k2_smem[];
     S *ybuf = reinterpret_cast<S *>(k2_smem);
@@ -715,7 +800,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     S *dst = ga + (b * T + t0) * (int64_t)Mc;
     const int total = rows * Mc;
-    const bool vec = sizeof(S) == 4 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+    const bool vec = sizeof(S) == 4 && aligned16(dst);
     if (vec) {
         float4 *d4 = reinterpret_cast<float4 *>(dst);
         const int n4 = total / 4;
