@@ -102,9 +102,14 @@ template <typename S, int MP, int G_, int R_> struct SumGeo {
     static constexpr int US = SR;                            // input samples per chunk-stage
     static constexpr int A_STAGE = CPW * CS;
     static constexpr int U_STAGE = CPW * US;
-    static constexpr size_t WARP_BYTES = size_t(NS) * (A_STAGE + U_STAGE) * sizeof(S) + NS * 8;
+    // per-warp slice: the stage ring then NS mbarriers, rounded to 128 bytes
+    // so every warp's bulk-copy destinations stay 16-byte aligned
+    static constexpr size_t RING_BYTES = size_t(NS) * (A_STAGE + U_STAGE) * sizeof(S);
+    static constexpr size_t WARP_BYTES = ((RING_BYTES + NS * 8 + 127) / 128) * 128;
     static_assert(G * R >= MP + 1, "packing must hold MP+1 recursions");
     static_assert((CS * sizeof(S)) % 16 == 0 && (US * sizeof(S)) % 16 == 0, "16-byte stage alignment");
+    static_assert((A_STAGE * sizeof(S)) % 16 == 0 && (U_STAGE * sizeof(S)) % 16 == 0, "16-byte ring alignment");
+    static_assert(RING_BYTES % 8 == 0 && WARP_BYTES % 16 == 0, "mbarrier and warp-slice alignment");
 };
 // per-chunk stride of the summaries Y[c][MP+1][MP], a multiple of 16 bytes
 template <typename S, int MP> struct YGeo {
@@ -495,6 +500,8 @@ template <typename S, int MP> struct RecGeo {
     static constexpr int LW = ((RAW + 3) / 4) % 2 == 1 ? ((RAW + 3) / 4) * 4 : ((RAW + 3) / 4 + 1) * 4;
     static constexpr size_t SMEM = size_t(32) * LW * 4 + NS * 8;
     static_assert((A_ST * sizeof(S)) % 16 == 0 && (SR * sizeof(S)) % 16 == 0, "16-byte lane stages");
+    static_assert((LW * 4) % 16 == 0 && (NS * A_ST * sizeof(S)) % 16 == 0, "16-byte lane ring alignment");
+    static_assert(NS * (A_ST + SR) * sizeof(S) <= size_t(LW) * 4, "lane ring fits its stride");
 };
 
 template <typename S, int MP, bool EXACT, bool BWD>
@@ -685,6 +692,7 @@ template <typename S, int MP> struct ChainGeo {
     static constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
     static constexpr int SLOT = YGeo<S, MP>::YS + ZS;                   // Y block + z vector
     static constexpr size_t SMEM = size_t(NB) * SLOT * sizeof(S);
+    static_assert((SLOT * sizeof(S)) % 16 == 0 && (YGeo<S, MP>::YS * sizeof(S)) % 16 == 0, "16-byte chain slots");
 };
 
 template <typename S, int MP, int MODE>
