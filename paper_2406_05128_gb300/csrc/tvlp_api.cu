@@ -182,8 +182,9 @@ Shape shape_for(int MP, int dtype) {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Rough cost model (cycles) of the chunked scan for chunk length L:
-// summaries run in waves of resident blocks, each chunk costing L steps;
-// the chain costs a fixed latency per chunk; the re-run is L sequential steps.
+// summaries run in waves of resident blocks, each chunk costing L steps; the
+// two-level scan costs its group compositions and hops; the re-run is L
+// sequential steps.
 int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
     constexpr int SRV = 8;  // chunk lengths are multiples of the stage height
     if (T <= 0 || B <= 0) return SRV;
@@ -198,7 +199,11 @@ int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
         const int64_t nC = ceil_div(T, L);
         const int64_t NQ = (int64_t)B * nC;
         const int64_t waves = ceil_div(NQ, per_wave);
-        const double cost = (double)waves * L * sh.per_step_cycles + (double)nC * 150.0 + (double)L * 40.0;
+        // two-level scan: G2 compositions + nG group hops + G2 chunk hops
+        const int64_t nG = nC < sh.scan_max_warps ? nC : sh.scan_max_warps;
+        const int64_t G2 = ceil_div(nC, nG);
+        const double scan = (double)G2 * (8.0 * MP * MP / 2 + 150.0) + (double)ceil_div(nC, G2) * 150.0;
+        const double cost = (double)waves * L * sh.per_step_cycles + scan + (double)L * 40.0;
         if (cost < best) {
             best = cost;
             best_L = (int)L;
@@ -225,6 +230,8 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
         p->L = 0;
         p->nC = 0;
         p->NQ = 0;
+        p->G2 = 1;
+        p->nG = 0;
         return LP_OK;
     }
     int L = chunk > 0 ? chunk : pick_chunk_impl(B, T, MP, dtype);
@@ -233,6 +240,14 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
     p->L = L;
     p->nC = T > 0 ? ceil_div(T, L) : 0;
     p->NQ = (int64_t)B * p->nC;
+    // two-level scan: as many groups as one block holds, G2 chunks each
+    const Shape sh = shape_for(MP, dtype);
+    int64_t nG = p->nC < sh.scan_max_warps ? p->nC : sh.scan_max_warps;
+    if (nG < 1) nG = 1;
+    const int64_t G2 = ceil_div(p->nC > 0 ? p->nC : 1, nG);
+    if (G2 > INT_MAX) return LP_EUNSUPPORTED;
+    p->G2 = (int)G2;
+    p->nG = (int)ceil_div(p->nC > 0 ? p->nC : 1, G2);
     return LP_OK;
 }
 

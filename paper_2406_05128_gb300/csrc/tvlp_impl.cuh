@@ -35,6 +35,9 @@ template <typename S, int MP> Shape Impl<S, MP>::shape() {
     const int wps = (sh.warps_per_block + 3) / 4;  // warps sharing a scheduler
     sh.per_step_cycles = (GE::R * MP + MP / 2 + GE::R * MP / SR + 4) * wps;
     sh.ws_per_chunk = (size_t)(YGeo<S, MP>::YS + 3 * MP) * sizeof(S);
+    using SG = ScanGeo<S, MP>;
+    const int w = (int)(kSmemBudget / (SG::WARP_BYTES + SG::ZS * sizeof(S)));
+    sh.scan_max_warps = w > 32 ? 32 : (w < 1 ? 1 : w);
     return sh;
 }
 
@@ -58,14 +61,15 @@ template <typename S, int MP> struct Launch {
         return cudaGetLastError();
     }
 
-    template <int MODE> static cudaError_t chain(const Problem &p, const S *Y, const S *Z, const S *zi, S *X, S *ckpt,
-                                                 cudaStream_t st) {
+    template <int MODE> static cudaError_t chain(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, const S *zi,
+                                                 S *X, S *ckpt, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
-        constexpr size_t smem = ChainGeo<S, MP>::SMEM;
-        auto kern = k2_chain<S, MP, MODE>;
-        cudaError_t err = allow_smem(kern, smem, done);
+        using SG = ScanGeo<S, MP>;
+        const size_t smem = (size_t)p.nG * (SG::WARP_BYTES + SG::ZS * sizeof(S));
+        auto kern = k2_scan<S, MP, MODE>;
+        cudaError_t err = allow_smem(kern, kSmemBudget, done);
         if (err != cudaSuccess) return err;
-        kern<<<(unsigned)p.B, 32, smem, st>>>(p.B, p.M, p.nC, Y, Z, zi, X, ckpt);
+        kern<<<(unsigned)p.B, 32 * p.nG, smem, st>>>(p.M, p.nC, p.G2, p.nG, Y, Z, GY, GZ, zi, X, ckpt, p.status);
         return cudaGetLastError();
     }
 
@@ -133,8 +137,9 @@ int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, 
     }
     S *Y = LN::region(p, ws, 0);
     S *X = LN::region(p, ws, 1);
+    S *GY = LN::region(p, ws, 4);
     TVLP_LAUNCH(0, (LN::template summary<false>(p, a, e, Y, st)));
-    TVLP_LAUNCH(1, (LN::template chain<CH_FWD>(p, Y, nullptr, zi, X, ckpt, st)));
+    TVLP_LAUNCH(1, (LN::template chain<CH_FWD>(p, Y, nullptr, GY, nullptr, zi, X, ckpt, st)));
     // the re-run walks the chunks in reverse so it starts on rows the
     // summary pass loaded last
     TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
@@ -152,14 +157,17 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
         S *Y = LN::region(p, ws, 0);
         S *Z = LN::region(p, ws, 2);
         S *Wst = LN::region(p, ws, 3);
+        S *GY = LN::region(p, ws, 4);
+        S *GZ = LN::region(p, ws, 5);
         if (flags & BWD_REUSE_FORWARD) {
-            // forward transfers P_c are in Y: the adjoint needs one zero-state
-            // recursion per chunk, then w_{c-1} = P_c^T w_c + z_c
+            // forward transfers P_c (and their group compositions) are in the
+            // workspace: the adjoint needs one zero-state recursion per chunk,
+            // then w_{c-1} = P_c^T w_c + z_c
             TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st)));
-            TVLP_LAUNCH(k++, (LN::template chain<CH_TRANS>(p, Y, Z, nullptr, Wst, nullptr, st)));
+            TVLP_LAUNCH(k++, (LN::template chain<CH_TRANS>(p, Y, Z, GY, GZ, nullptr, Wst, nullptr, st)));
         } else {
             TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, st)));
-            TVLP_LAUNCH(k++, (LN::template chain<CH_BWD>(p, Y, nullptr, nullptr, Wst, nullptr, st)));
+            TVLP_LAUNCH(k++, (LN::template chain<CH_BWD>(p, Y, nullptr, GY, nullptr, nullptr, Wst, nullptr, st)));
         }
         TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st)));
     }

@@ -18,6 +18,8 @@ struct Problem {
     int L;        // chunk length, a multiple of MP
     int64_t nC;   // chunks per signal
     int64_t NQ;   // B * nC
+    int G2;       // chunks per group of the two-level scan
+    int nG;       // groups per signal
     int *status;  // device status word (bounded waits record timeouts here)
 };
 
@@ -27,6 +29,7 @@ struct Shape {
     int warps_per_block;   // K1 block size / 32
     int per_step_cycles;   // rough K1 issue cost of one time step (chunk picker)
     size_t ws_per_chunk;   // workspace bytes per chunk (summaries + states)
+    int scan_max_warps;    // most groups one scan block can hold
 };
 
 template <typename S, int MP> struct Impl {
@@ -45,18 +48,24 @@ enum { ALGO_CHUNKED = 0, ALGO_PLAIN = 1 };
 enum { BWD_REUSE_FORWARD = 1 };
 
 // Workspace regions (each 256-byte aligned), in elements of the scalar:
-//   Y [NQ][YS]  chunk summaries (forward; the adjoint's own when it
-//               cannot reuse the forward's)
-//   X [NQ][MP]  forward incoming state of every chunk
-//   Z [NQ][MP]  adjoint zero-state summaries
-//   W [NQ][MP]  adjoint incoming state of every chunk
+//   0 Y  [NQ][YS]     chunk maps (forward; the adjoint's own when it
+//                     cannot reuse the forward's)
+//   1 X  [NQ][MP]     forward incoming state of every chunk
+//   2 Z  [NQ][ZS]     adjoint zero-state summaries
+//   3 W  [NQ][MP]     adjoint incoming state of every chunk
+//   4 GY [B*nG][YS]   group maps of the two-level scan
+//   5 GZ [B*nG][ZS]   adjoint group zero-state summaries
 inline size_t ys_elems(int MP, size_t sz) { return (((size_t)(MP + 1) * MP * sz + 15) / 16) * 16 / sz; }
+inline size_t zs_elems(int MP, size_t sz) { return (((size_t)MP * sz + 15) / 16) * 16 / sz; }
 inline size_t ws_offset(const Problem &p, size_t sz, int region) {
-    const size_t y = align256((size_t)p.NQ * ys_elems(p.MP, sz) * sz);
-    const size_t v = align256((size_t)p.NQ * p.MP * sz);
-    return region == 0 ? 0 : y + (size_t)(region - 1) * v;
+    const size_t rows[6] = {(size_t)p.NQ * ys_elems(p.MP, sz), (size_t)p.NQ * p.MP, (size_t)p.NQ * zs_elems(p.MP, sz),
+                            (size_t)p.NQ * p.MP, (size_t)p.B * p.nG * ys_elems(p.MP, sz),
+                            (size_t)p.B * p.nG * zs_elems(p.MP, sz)};
+    size_t off = 0;
+    for (int r = 0; r < region; ++r) off += align256(rows[r] * sz);
+    return off;
 }
-inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 4); }
+inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 6); }
 
 // Records the caller's profiling event for kernel k (begin or end) when a
 // hook is installed on this thread (lp_tv_set_profile_events).

@@ -24,8 +24,9 @@
 //                   P_c).  Forward direction; also available backwards.
 //   k_rec (ZERO)    per chunk, one recursion from zero state; end state only
 //                   (the adjoint's zero-state summary z_c).
-//   k2_chain        x_{c+1} = P_c x_c + y_c (forward) or
-//                   w_{c-1} = P_c^T w_c + z_c (adjoint) per signal.
+//   k2_scan         x_{c+1} = P_c x_c + y_c (forward) or
+//                   w_{c-1} = P_c^T w_c + z_c (adjoint) per signal, as a
+//                   two-level scan over groups of chunks.
 //   k_rec (RERUN)   each chunk re-runs its recursion from its true incoming
 //                   state and writes s (forward) or ge (adjoint).  With one
 //                   chunk per signal this is the plain sequential filter.
@@ -661,8 +662,10 @@ __global__ void __launch_bounds__(32)
     cp_async_wait<0>();
     if (!active) return;
     if constexpr (MODE == BWD_ZERO) {
+        // adjoint zero-state summaries use the 16-byte stride of the scan's z
+        constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
 #pragma unroll
-        for (int j = 0; j < MP; ++j) Zout[q * MP + j] = h[j];
+        for (int j = 0; j < MP; ++j) Zout[q * ZS + j] = h[j];
     }
     if constexpr (MODE == BWD_RERUN) {
         if (gzi != nullptr && c == 0) {
@@ -674,105 +677,233 @@ __global__ void __launch_bounds__(32)
 }
 
 // ---------------------------------------------------------------------------
-// K2: cross-chunk chain, one warp per signal.  Lane j (< MP) holds state
-// component j+1.  Summaries of upcoming chunks are prefetched into shared
-// memory NB chunks ahead and into registers one chunk ahead.
-//   CH_FWD:   X[b][0] = zi (0 if none); X[b][c+1] = Y0[c] + P[c] X[b][c]
-//   CH_BWD:   W[b][nC-1] = 0;  W[b][c-1] = Y0[c] + P[c] W[b][c]   (adjoint's
-//             own summaries, P in the pending-state basis)
-//   CH_TRANS: W[b][nC-1] = 0;  W[b][c-1] = Z[c] + P[c]^T W[b][c]  (forward
-//             transfers, transposed; Z the adjoint's zero-state summaries)
-// X/W hold the incoming state of each chunk (stride MP).  The forward also
-// writes the chunk checkpoints ckpt[b][c][0..M-1] when asked.
+// K2: cross-chunk scan, one block per signal, two levels.  Chunks are grouped
+// G2 at a time by chunk index (group g = chunks [g*G2, (g+1)*G2)), one warp
+// per group.  Along the chain the forward visits chunks (and groups) in
+// increasing order, the adjoint in decreasing order.
+//   phase A  warp g summarises group g:
+//            CH_FWD / CH_BWD: composes its chunk maps x -> P x + y into one
+//              map (Phi_g, y_g), stored in the chunk-summary layout at GY;
+//            CH_TRANS: folds the adjoint's chunk maps w -> P^T w + z into the
+//              group's zero-state adjoint zeta_g (at GZ); the group transfer
+//              is the transpose of the forward's Phi_g, read from GY.
+//   phase B  warp 0 chains the groups: the incoming state of every group.
+//   phase C  warp g runs its group's chunks from the group's incoming state
+//            and writes each chunk's incoming state X[b][c] (and, forward,
+//            the checkpoints).
+// Chunk summaries reach shared memory through a two-slot ring per warp
+// filled by bulk (TMA) copies; phase B stages the group summaries, written
+// by phase A in this kernel, with cp.async.
+// Chunk map layout (Y[c], stride YS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
 // ---------------------------------------------------------------------------
 enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2 };
 
-template <typename S, int MP> struct ChainGeo {
-    static constexpr int NB = 32;                                      // chunks prefetched
+template <typename S, int MP> struct ScanGeo {
+    static constexpr int YS = YGeo<S, MP>::YS;
     static constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
-    static constexpr int SLOT = YGeo<S, MP>::YS + ZS;                   // Y block + z vector
-    static constexpr size_t SMEM = size_t(NB) * SLOT * sizeof(S);
-    static_assert((SLOT * sizeof(S)) % 16 == 0 && (YGeo<S, MP>::YS * sizeof(S)) % 16 == 0, "16-byte chain slots");
+    static constexpr int SLOT = YS + ZS;  // a chunk map and, for the adjoint, its z
+    static constexpr int NSLOT = 2;
+    static constexpr size_t WARP_BYTES = ((NSLOT * SLOT * sizeof(S) + NSLOT * 8 + 127) / 128) * 128;
+    static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte chunk maps");
 };
 
-template <typename S, int MP, int MODE>
-__global__ void __launch_bounds__(32)
-    k2_chain(int B, int M, int64_t nC, const S *__restrict__ Y, const S *__restrict__ Z, const S *__restrict__ zi,
-             S *__restrict__ X, S *__restrict__ ckpt) {
-    using CG = ChainGeo<S, MP>;
-    constexpr int NB = CG::NB;
-    constexpr int YS = YGeo<S, MP>::YS;
-    constexpr bool REV = MODE != CH_FWD;
-    extern __shared__ __align__(16) unsigned char k2_smem[];
-    S *ybuf = reinterpret_cast<S *>(k2_smem);
-    const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x;
-    if (b >= B) return;
-    const S *Yb = Y + (int64_t)b * nC * YS;
-    const int j0 = lane < MP ? lane : 0;
-
-    auto chunk_of = [&](int64_t n) -> int64_t { return REV ? nC - 1 - n : n; };
-    // one cp.async group per chunk: its Y block (16-byte pieces) and, for
-    // the transposed chain, the adjoint's zero-state vector z
-    auto issue = [&](int64_t n) {
-        if (n < nC) {
-            const int64_t c = chunk_of(n);
-            const S *src = Yb + c * YS;
-            S *dst = ybuf + (n % NB) * CG::SLOT;
-            constexpr int nbytes = YS * (int)sizeof(S);
-            for (int off = lane * 16; off < nbytes; off += 32 * 16)
-                cp_async<16>(reinterpret_cast<char *>(dst) + off, reinterpret_cast<const char *>(src) + off, 16);
-            if (MODE == CH_TRANS && lane < MP)
-                cp_async<sizeof(S)>(dst + YS + lane, Z + ((int64_t)b * nC + c) * MP + lane, (int)sizeof(S));
-        }
-        cp_async_commit();
-    };
-    // the lane's coefficients for chunk n: p[0] constant term, p[r] factor of x[r-1]
-    auto load_cols = [&](int64_t n, S (&p)[MP + 1]) {
-        const S *yc = ybuf + (n % NB) * CG::SLOT;
-        if constexpr (MODE == CH_TRANS) {
-            // w_new[j] = z[j] + sum_k P[k][j] w[k],  P[k][j] = Y[j+1][k]
+// x_new[lane] = p[0] + sum_{r=1..MP} p[r] * x[r-1], x held one component per lane
+template <typename S, int MP>
+__device__ __forceinline__ S hop(const S (&p)[MP + 1], S x, int lane) {
+    S a0 = p[0], a1 = S(0), a2 = S(0), a3 = S(0);
 #pragma unroll
-            for (int k = 0; k < MP; ++k) p[k + 1] = yc[(j0 + 1) * MP + k];
-            p[0] = yc[YS + j0];
-        } else {
-            // x_new[j] = Y[0][j] + sum_r Y[r][j] x[r-1]
-#pragma unroll
-            for (int r = 0; r <= MP; ++r) p[r] = yc[r * MP + j0];
-        }
-    };
-
-    for (int n = 0; n < NB - 1; ++n) issue(n);
-    S x = S(0);
-    if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[(int64_t)b * M + lane];
-    S p[MP + 1];
-    cp_async_wait<NB - 2>();  // chunk 0 landed
-    __syncwarp();
-    load_cols(0, p);
-#pragma unroll 1
-    for (int64_t n = 0; n < nC; ++n) {
-        const int64_t c = chunk_of(n);
-        if (lane < MP) X[((int64_t)b * nC + c) * MP + lane] = x;
-        if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[((int64_t)b * nC + c) * M + lane] = x;
-        if (n == nC - 1) break;
-        S a0 = p[0], a1 = S(0), a2 = S(0), a3 = S(0);
-#pragma unroll
-        for (int r = 1; r <= MP; ++r) {
-            const S xr = __shfl_sync(0xffffffffu, x, r - 1);
-            if ((r & 3) == 0) a0 = fma(p[r], xr, a0);
-            else if ((r & 3) == 1) a1 = fma(p[r], xr, a1);
-            else if ((r & 3) == 2) a2 = fma(p[r], xr, a2);
-            else a3 = fma(p[r], xr, a3);
-        }
-        // chunk n+1 landed once NB-2 groups at most are pending; its slot
-        // refill (chunk n+NB-1) reuses the slot of chunk n-1, read already
-        issue(n + NB - 1);
-        cp_async_wait<NB - 2>();
-        __syncwarp();
-        load_cols(n + 1, p);
-        x = lane < MP ? (a0 + a1) + (a2 + a3) : S(0);
+    for (int r = 1; r <= MP; ++r) {
+        const S xr = __shfl_sync(0xffffffffu, x, r - 1);
+        if ((r & 3) == 0) a0 = fma(p[r], xr, a0);
+        else if ((r & 3) == 1) a1 = fma(p[r], xr, a1);
+        else if ((r & 3) == 2) a2 = fma(p[r], xr, a2);
+        else a3 = fma(p[r], xr, a3);
     }
-    cp_async_wait<0>();
+    return lane < MP ? (a0 + a1) + (a2 + a3) : S(0);
+}
+
+// coefficients of the lane's output component for one map held in shared
+// memory: straight (x -> P x + y, map at m) or transposed (w -> P^T w + z,
+// P from the map at m, z at zv)
+template <typename S, int MP, bool TRANS>
+__device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv, int j0) {
+    if constexpr (TRANS) {
+#pragma unroll
+        for (int k = 0; k < MP; ++k) p[k + 1] = m[(j0 + 1) * MP + k];
+        p[0] = zv[j0];
+    } else {
+#pragma unroll
+        for (int r = 0; r <= MP; ++r) p[r] = m[r * MP + j0];
+    }
+}
+
+template <typename S, int MP, int MODE>
+__global__ void __launch_bounds__(1024)
+    k2_scan(int M, int64_t nC, int G2, int nG, const S *__restrict__ Y, const S *__restrict__ Z, S *__restrict__ GY,
+            S *__restrict__ GZ, const S *__restrict__ zi, S *__restrict__ X, S *__restrict__ ckpt,
+            int *__restrict__ status) {
+    using SG = ScanGeo<S, MP>;
+    constexpr int YS = SG::YS, ZS = SG::ZS, SLOT = SG::SLOT, NSLOT = SG::NSLOT;
+    constexpr bool REV = MODE != CH_FWD;
+    constexpr bool TRANS = MODE == CH_TRANS;
+    extern __shared__ __align__(128) unsigned char k2_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x;
+    const int j0 = lane < MP ? lane : 0;
+    S *ring = reinterpret_cast<S *>(k2_smem + (size_t)warp * SG::WARP_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + NSLOT * SLOT * sizeof(S));
+    S *GX = reinterpret_cast<S *>(k2_smem + (size_t)nG * SG::WARP_BYTES);  // [nG][ZS] group incoming states
+    const S *Yb = Y + b * nC * YS;
+    const S *Zb = TRANS ? Z + b * nC * ZS : nullptr;
+    S *GYb = GY + b * nG * YS;
+    S *GZb = TRANS ? GZ + b * nG * ZS : nullptr;
+
+    if (lane == 0) {
+        for (int s = 0; s < NSLOT; ++s) mbar_init(bars + s, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+
+    // this warp's group, its chunks in chain order: chunk_at(i), i < len
+    const int g = warp;
+    const int64_t c_lo = (int64_t)g * G2;
+    const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
+    auto chunk_at = [&](int i) -> int64_t { return REV ? c_lo + len - 1 - i : c_lo + i; };
+    int uses = 0;  // bulk-copy phases consumed on this warp's ring
+    auto issue = [&](int i) {  // stage chunk chunk_at(i) into slot (uses + i) % NSLOT
+        if (i < len) {
+            const int sl = (uses + i) % NSLOT;
+            const unsigned bytes = (YS + (TRANS ? ZS : 0)) * sizeof(S);
+            if (lane == 0) {
+                mbar_arrive_expect_tx(bars + sl, bytes);
+                fence_proxy_async();
+                bulk_load(ring + sl * SLOT, Yb + chunk_at(i) * YS, YS * sizeof(S), bars + sl);
+                if (TRANS) bulk_load(ring + sl * SLOT + YS, Zb + chunk_at(i) * ZS, ZS * sizeof(S), bars + sl);
+            }
+        }
+    };
+    auto wait = [&](int i) -> const S * {  // chunk chunk_at(i) landed; its slot
+        const int u = uses + i, sl = u % NSLOT;
+        if (!mbar_wait_warp(bars + sl, (u / NSLOT) & 1, kWaitLimit)) {
+            if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+            return nullptr;
+        }
+        return ring + sl * SLOT;
+    };
+    bool ok = true;
+
+    // ---- phase A: group summaries ----
+    if (g < nG) {
+        issue(0);
+        issue(1);
+        if constexpr (TRANS) {
+            S zeta = S(0);
+            for (int i = 0; i < len && ok; ++i) {
+                const S *m = wait(i);
+                if (m == nullptr) { ok = false; break; }
+                S p[MP + 1];
+                map_cols<S, MP, true>(p, m, m + YS, j0);
+                __syncwarp();
+                issue(i + 2);
+                zeta = hop<S, MP>(p, zeta, lane);
+            }
+            if (ok && lane < MP) GZb[(int64_t)g * ZS + lane] = zeta;
+        } else {
+            // lane j <= MP holds column j of the composed map: column 0 the
+            // accumulated response y, columns 1..MP the transfer
+            S col[MP];
+#pragma unroll
+            for (int k = 0; k < MP; ++k) col[k] = (lane >= 1 && k == lane - 1) ? S(1) : S(0);
+            for (int i = 0; i < len && ok; ++i) {
+                const S *m = wait(i);
+                if (m == nullptr) { ok = false; break; }
+                S acc[MP];
+#pragma unroll
+                for (int k = 0; k < MP; ++k) acc[k] = lane == 0 ? m[k] : S(0);
+#pragma unroll
+                for (int r = 1; r <= MP; ++r) {
+                    const S xr = col[r - 1];
+                    const S *row = m + r * MP;  // P[k][r-1] = m[r*MP + k]
+#pragma unroll
+                    for (int k = 0; k < MP; k += 2) {
+                        if constexpr (sizeof(S) == 4) {
+                            const float2 v = *reinterpret_cast<const float2 *>(row + k);
+                            acc[k] = fma((S)v.x, xr, acc[k]);
+                            acc[k + 1] = fma((S)v.y, xr, acc[k + 1]);
+                        } else {
+                            acc[k] = fma(row[k], xr, acc[k]);
+                            acc[k + 1] = fma(row[k + 1], xr, acc[k + 1]);
+                        }
+                    }
+                }
+                __syncwarp();
+                issue(i + 2);
+#pragma unroll
+                for (int k = 0; k < MP; ++k) col[k] = acc[k];
+            }
+            if (ok && lane <= MP) {
+#pragma unroll
+                for (int k = 0; k < MP; ++k) GYb[(int64_t)g * YS + lane * MP + k] = col[k];
+            }
+        }
+        uses += len;
+    }
+    ok = __syncthreads_and(ok ? 1 : 0);
+    if (!ok) return;
+
+    // ---- phase B: chain over the groups (warp 0), group summaries staged by cp.async ----
+    if (warp == 0) {
+        S x = S(0);
+        if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
+        auto gof = [&](int n) -> int { return REV ? nG - 1 - n : n; };
+        auto stage = [&](int n) {
+            if (n < nG) {
+                S *dst = ring + (n % NSLOT) * SLOT;
+                const S *src = GYb + (int64_t)gof(n) * YS;
+                for (int off = lane * 16; off < YS * (int)sizeof(S); off += 32 * 16)
+                    cp_async<16>(reinterpret_cast<char *>(dst) + off, reinterpret_cast<const char *>(src) + off, 16);
+                if (TRANS && lane < MP) cp_async<sizeof(S)>(dst + YS + lane, GZb + (int64_t)gof(n) * ZS + lane, (int)sizeof(S));
+            }
+            cp_async_commit();
+        };
+        stage(0);
+        for (int n = 0; n < nG; ++n) {
+            if (lane < MP) GX[gof(n) * ZS + lane] = x;
+            if (n == nG - 1) break;
+            stage(n + 1);
+            cp_async_wait<1>();
+            __syncwarp();
+            S p[MP + 1];
+            const S *m = ring + (n % NSLOT) * SLOT;
+            map_cols<S, MP, TRANS>(p, m, m + YS, j0);
+            __syncwarp();
+            x = hop<S, MP>(p, x, lane);
+        }
+        cp_async_wait<0>();
+    }
+    __syncthreads();
+
+    // ---- phase C: every chunk's incoming state ----
+    if (g < nG) {
+        fence_proxy_async();  // the ring was last written by cp.async
+        __syncwarp();
+        S x = lane < MP ? GX[g * ZS + lane] : S(0);
+        issue(0);
+        issue(1);
+        for (int i = 0; i < len; ++i) {
+            const int64_t c = chunk_at(i);
+            if (lane < MP) X[(b * nC + c) * MP + lane] = x;
+            if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[(b * nC + c) * M + lane] = x;
+            const S *m = wait(i);
+            if (m == nullptr) return;
+            if (i == len - 1) break;
+            S p[MP + 1];
+            map_cols<S, MP, TRANS>(p, m, m + YS, j0);
+            __syncwarp();
+            issue(i + 2);
+            x = hop<S, MP>(p, x, lane);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
