@@ -87,9 +87,11 @@ enum {
  * (passed as void*) created by the caller.  While installed, every later
  * forward/backward call made from the calling thread records events[2k]
  * just before and events[2k+1] just after its k-th kernel launch (k < n) on
- * the call's stream.  Kernel order: forward (chunked) summary, chain,
- * re-run; backward (chunked) summary, chain, re-run, coefficient gradient;
- * the plain algorithm launches re-run (and coefficient gradient).  NULL
+ * the call's stream.  Kernel order: forward (chunked) summary, group maps,
+ * group chain, chunk states, re-run; backward (chunked) zero-state summary
+ * (or full summary without LP_BWD_REUSE_FORWARD), group maps, group chain,
+ * chunk states, re-run, coefficient gradient; the plain algorithm launches
+ * re-run (and coefficient gradient).  NULL
  * uninstalls the hook.  The library neither creates nor destroys events.
  */
 int lp_tv_set_profile_events(void **events, int n);

@@ -199,10 +199,10 @@ int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
         const int64_t nC = ceil_div(T, L);
         const int64_t NQ = (int64_t)B * nC;
         const int64_t waves = ceil_div(NQ, per_wave);
-        // two-level scan: G2 compositions + nG group hops + G2 chunk hops
-        const int64_t nG = nC < sh.scan_max_warps ? nC : sh.scan_max_warps;
-        const int64_t G2 = ceil_div(nC, nG);
-        const double scan = (double)G2 * (8.0 * MP * MP / 2 + 150.0) + (double)ceil_div(nC, G2) * 150.0;
+        // two-level scan: G2 compositions and hops, nC / G2 group hops
+        int64_t G2 = 1;
+        while (G2 * G2 * 4 < nC) ++G2;
+        const double scan = (double)G2 * (8.0 * MP * MP / 2 + 300.0) + (double)ceil_div(nC, G2) * 150.0 + 3 * 3000.0;
         const double cost = (double)waves * L * sh.per_step_cycles + scan + (double)L * 40.0;
         if (cost < best) {
             best = cost;
@@ -240,12 +240,9 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
     p->L = L;
     p->nC = T > 0 ? ceil_div(T, L) : 0;
     p->NQ = (int64_t)B * p->nC;
-    // two-level scan: as many groups as one block holds, G2 chunks each
-    const Shape sh = shape_for(MP, dtype);
-    int64_t nG = p->nC < sh.scan_max_warps ? p->nC : sh.scan_max_warps;
-    if (nG < 1) nG = 1;
-    const int64_t G2 = ceil_div(p->nC > 0 ? p->nC : 1, nG);
-    if (G2 > INT_MAX) return LP_EUNSUPPORTED;
+    // two-level scan: groups of about sqrt(nC / 4) chunks
+    int64_t G2 = 1;
+    while (G2 * G2 * 4 < p->nC) ++G2;
     p->G2 = (int)G2;
     p->nG = (int)ceil_div(p->nC > 0 ? p->nC : 1, G2);
     return LP_OK;

@@ -35,9 +35,6 @@ template <typename S, int MP> Shape Impl<S, MP>::shape() {
     const int wps = (sh.warps_per_block + 3) / 4;  // warps sharing a scheduler
     sh.per_step_cycles = (GE::R * MP + MP / 2 + GE::R * MP / SR + 4) * wps;
     sh.ws_per_chunk = (size_t)(YGeo<S, MP>::YS + 3 * MP) * sizeof(S);
-    using SG = ScanGeo<S, MP>;
-    const int w = (int)(kSmemBudget / (SG::WARP_BYTES + SG::ZS * sizeof(S)));
-    sh.scan_max_warps = w > 32 ? 32 : (w < 1 ? 1 : w);
     return sh;
 }
 
@@ -61,16 +58,35 @@ template <typename S, int MP> struct Launch {
         return cudaGetLastError();
     }
 
-    template <int MODE> static cudaError_t chain(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, const S *zi,
-                                                 S *X, S *ckpt, cudaStream_t st) {
-        static bool done[kMaxDevices] = {};
+    // two-level scan: group maps, group chain, chunk states
+    template <int MODE> static cudaError_t scan(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, S *GX,
+                                                const S *zi, S *X, S *ckpt, cudaStream_t st, int k0) {
         using SG = ScanGeo<S, MP>;
-        const size_t smem = (size_t)p.nG * (SG::WARP_BYTES + SG::ZS * sizeof(S));
-        auto kern = k2_scan<S, MP, MODE>;
-        cudaError_t err = allow_smem(kern, kSmemBudget, done);
-        if (err != cudaSuccess) return err;
-        kern<<<(unsigned)p.B, 32 * p.nG, smem, st>>>(p.M, p.nC, p.G2, p.nG, Y, Z, GY, GZ, zi, X, ckpt, p.status);
-        return cudaGetLastError();
+        static bool done_g[kMaxDevices] = {}, done_c[kMaxDevices] = {}, done_e[kMaxDevices] = {};
+        const int64_t items = (int64_t)p.B * p.nG;
+        const int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
+        const size_t smem_g = kScanWarps * SG::template warp_bytes<kGroupSlots>();
+        const size_t smem_c = SG::template warp_bytes<kChainSlots>();
+        cudaError_t err;
+        auto kg = k2_group<S, MP, MODE>;
+        auto kc = k2_chain<S, MP, MODE>;
+        auto ke = k2_expand<S, MP, MODE>;
+        if ((err = allow_smem(kg, smem_g, done_g)) != cudaSuccess) return err;
+        if ((err = allow_smem(kc, smem_c, done_c)) != cudaSuccess) return err;
+        if ((err = allow_smem(ke, smem_g, done_e)) != cudaSuccess) return err;
+        profile_mark(k0, false, st);
+        kg<<<(unsigned)blocks, kScanWarps * 32, smem_g, st>>>(p.nC, p.G2, p.nG, items, Y, Z, GY, GZ, p.status);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        profile_mark(k0, true, st);
+        profile_mark(k0 + 1, false, st);
+        kc<<<(unsigned)p.B, 32, smem_c, st>>>(p.M, p.nG, GY, GZ, zi, GX, p.status);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        profile_mark(k0 + 1, true, st);
+        profile_mark(k0 + 2, false, st);
+        ke<<<(unsigned)blocks, kScanWarps * 32, smem_g, st>>>(p.M, p.nC, p.G2, p.nG, items, Y, Z, GX, X, ckpt, p.status);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        profile_mark(k0 + 2, true, st);
+        return cudaSuccess;
     }
 
     template <int MODE, bool EXACT>
@@ -138,11 +154,12 @@ int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, 
     S *Y = LN::region(p, ws, 0);
     S *X = LN::region(p, ws, 1);
     S *GY = LN::region(p, ws, 4);
+    S *GX = LN::region(p, ws, 6);
     TVLP_LAUNCH(0, (LN::template summary<false>(p, a, e, Y, st)));
-    TVLP_LAUNCH(1, (LN::template chain<CH_FWD>(p, Y, nullptr, GY, nullptr, zi, X, ckpt, st)));
+    if (LN::template scan<CH_FWD>(p, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, st, 1) != cudaSuccess) return ECUDA;
     // the re-run walks the chunks in reverse so it starts on rows the
     // summary pass loaded last
-    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
+    TVLP_LAUNCH(4, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
     return OK;
 }
 
@@ -159,16 +176,20 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
         S *Wst = LN::region(p, ws, 3);
         S *GY = LN::region(p, ws, 4);
         S *GZ = LN::region(p, ws, 5);
+        S *GX = LN::region(p, ws, 6);
         if (flags & BWD_REUSE_FORWARD) {
             // forward transfers P_c (and their group compositions) are in the
             // workspace: the adjoint needs one zero-state recursion per chunk,
             // then w_{c-1} = P_c^T w_c + z_c
             TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st)));
-            TVLP_LAUNCH(k++, (LN::template chain<CH_TRANS>(p, Y, Z, GY, GZ, nullptr, Wst, nullptr, st)));
+            if (LN::template scan<CH_TRANS>(p, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, st, k) != cudaSuccess)
+                return ECUDA;
         } else {
             TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, st)));
-            TVLP_LAUNCH(k++, (LN::template chain<CH_BWD>(p, Y, nullptr, GY, nullptr, nullptr, Wst, nullptr, st)));
+            if (LN::template scan<CH_BWD>(p, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, st, k) != cudaSuccess)
+                return ECUDA;
         }
+        k += 3;
         TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st)));
     }
     if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(p, ge, s, zi, ga, st)));

@@ -29,7 +29,6 @@ struct Shape {
     int warps_per_block;   // K1 block size / 32
     int per_step_cycles;   // rough K1 issue cost of one time step (chunk picker)
     size_t ws_per_chunk;   // workspace bytes per chunk (summaries + states)
-    int scan_max_warps;    // most groups one scan block can hold
 };
 
 template <typename S, int MP> struct Impl {
@@ -55,17 +54,18 @@ enum { BWD_REUSE_FORWARD = 1 };
 //   3 W  [NQ][MP]     adjoint incoming state of every chunk
 //   4 GY [B*nG][YS]   group maps of the two-level scan
 //   5 GZ [B*nG][ZS]   adjoint group zero-state summaries
+//   6 GX [B*nG][ZS]   incoming state of every group
 inline size_t ys_elems(int MP, size_t sz) { return (((size_t)(MP + 1) * MP * sz + 15) / 16) * 16 / sz; }
 inline size_t zs_elems(int MP, size_t sz) { return (((size_t)MP * sz + 15) / 16) * 16 / sz; }
 inline size_t ws_offset(const Problem &p, size_t sz, int region) {
-    const size_t rows[6] = {(size_t)p.NQ * ys_elems(p.MP, sz), (size_t)p.NQ * p.MP, (size_t)p.NQ * zs_elems(p.MP, sz),
+    const size_t rows[7] = {(size_t)p.NQ * ys_elems(p.MP, sz), (size_t)p.NQ * p.MP, (size_t)p.NQ * zs_elems(p.MP, sz),
                             (size_t)p.NQ * p.MP, (size_t)p.B * p.nG * ys_elems(p.MP, sz),
-                            (size_t)p.B * p.nG * zs_elems(p.MP, sz)};
+                            (size_t)p.B * p.nG * zs_elems(p.MP, sz), (size_t)p.B * p.nG * zs_elems(p.MP, sz)};
     size_t off = 0;
     for (int r = 0; r < region; ++r) off += align256(rows[r] * sz);
     return off;
 }
-inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 6); }
+inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 7); }
 
 // Records the caller's profiling event for kernel k (begin or end) when a
 // hook is installed on this thread (lp_tv_set_profile_events).

@@ -24,7 +24,8 @@
 //                   P_c).  Forward direction; also available backwards.
 //   k_rec (ZERO)    per chunk, one recursion from zero state; end state only
 //                   (the adjoint's zero-state summary z_c).
-//   k2_scan         x_{c+1} = P_c x_c + y_c (forward) or
+//   k2_group/chain/expand
+//                   x_{c+1} = P_c x_c + y_c (forward) or
 //                   w_{c-1} = P_c^T w_c + z_c (adjoint) per signal, as a
 //                   two-level scan over groups of chunks.
 //   k_rec (RERUN)   each chunk re-runs its recursion from its true incoming
@@ -677,34 +678,36 @@ __global__ void __launch_bounds__(32)
 }
 
 // ---------------------------------------------------------------------------
-// K2: cross-chunk scan, one block per signal, two levels.  Chunks are grouped
-// G2 at a time by chunk index (group g = chunks [g*G2, (g+1)*G2)), one warp
-// per group.  Along the chain the forward visits chunks (and groups) in
-// increasing order, the adjoint in decreasing order.
-//   phase A  warp g summarises group g:
-//            CH_FWD / CH_BWD: composes its chunk maps x -> P x + y into one
-//              map (Phi_g, y_g), stored in the chunk-summary layout at GY;
-//            CH_TRANS: folds the adjoint's chunk maps w -> P^T w + z into the
-//              group's zero-state adjoint zeta_g (at GZ); the group transfer
-//              is the transpose of the forward's Phi_g, read from GY.
-//   phase B  warp 0 chains the groups: the incoming state of every group.
-//   phase C  warp g runs its group's chunks from the group's incoming state
-//            and writes each chunk's incoming state X[b][c] (and, forward,
-//            the checkpoints).
-// Chunk summaries reach shared memory through a two-slot ring per warp
-// filled by bulk (TMA) copies; phase B stages the group summaries, written
-// by phase A in this kernel, with cp.async.
-// Chunk map layout (Y[c], stride YS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
+// K2: cross-chunk scan in two levels.  Chunks are grouped G2 at a time by
+// chunk index (group g = chunks [g*G2, (g+1)*G2)).  Along the chain the
+// forward visits chunks and groups in increasing order, the adjoint in
+// decreasing order.
+//   k2_group   one warp per group (all signals at once):
+//              CH_FWD / CH_BWD: composes the group's chunk maps x -> P x + y
+//                into one map (Phi_g, y_g), stored in the chunk-map layout
+//                at GY;
+//              CH_TRANS: folds the adjoint's chunk maps w -> P^T w + z into
+//                the group's zero-state adjoint zeta_g (GZ); the group's
+//                transfer is the transpose of the forward's Phi_g.
+//   k2_chain   one warp per signal: chains the groups -> the incoming state
+//              of every group (GX).
+//   k2_expand  one warp per group: runs the group's chunks from its incoming
+//              state and writes each chunk's incoming state X (and, in the
+//              forward, the checkpoints).
+// Maps reach shared memory through a ring of NSLOT slots per warp filled by
+// bulk (TMA) copies NSLOT-1 maps ahead.
+// Chunk map layout (stride YS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
 // ---------------------------------------------------------------------------
 enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2 };
 
 template <typename S, int MP> struct ScanGeo {
     static constexpr int YS = YGeo<S, MP>::YS;
     static constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
-    static constexpr int SLOT = YS + ZS;  // a chunk map and, for the adjoint, its z
-    static constexpr int NSLOT = 2;
-    static constexpr size_t WARP_BYTES = ((NSLOT * SLOT * sizeof(S) + NSLOT * 8 + 127) / 128) * 128;
-    static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte chunk maps");
+    static constexpr int SLOT = YS + ZS;  // a map and, for the adjoint, its z
+    static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte maps");
+    template <int NSLOT> __host__ __device__ static constexpr size_t warp_bytes() {
+        return ((NSLOT * SLOT * sizeof(S) + NSLOT * 8 + 127) / 128) * 128;
+    }
 };
 
 // x_new[lane] = p[0] + sum_{r=1..MP} p[r] * x[r-1], x held one component per lane
@@ -737,172 +740,218 @@ __device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv
     }
 }
 
-template <typename S, int MP, int MODE>
-__global__ void __launch_bounds__(1024)
-    k2_scan(int M, int64_t nC, int G2, int nG, const S *__restrict__ Y, const S *__restrict__ Z, S *__restrict__ GY,
-            S *__restrict__ GZ, const S *__restrict__ zi, S *__restrict__ X, S *__restrict__ ckpt,
-            int *__restrict__ status) {
+// A warp's ring of NSLOT map slots filled by bulk copies.  Item i of the
+// warp's sequence goes to slot i % NSLOT; its map comes from `map(i)` and,
+// when `with_z`, a z vector from `zvec(i)`.
+template <typename S, int MP, int NSLOT> struct MapRing {
     using SG = ScanGeo<S, MP>;
-    constexpr int YS = SG::YS, ZS = SG::ZS, SLOT = SG::SLOT, NSLOT = SG::NSLOT;
+    S *ring;
+    uint64_t *bars;
+    int lane;
+    __device__ void init(unsigned char *base, int lane_) {
+        ring = reinterpret_cast<S *>(base);
+        bars = reinterpret_cast<uint64_t *>(base + NSLOT * SG::SLOT * sizeof(S));
+        lane = lane_;
+        if (lane == 0) {
+            for (int s = 0; s < NSLOT; ++s) mbar_init(bars + s, 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+    }
+    __device__ void issue(int i, const S *map, const S *zvec) {
+        const int sl = i % NSLOT;
+        if (lane == 0) {
+            const unsigned bytes = SG::YS * sizeof(S) + (zvec ? SG::ZS * sizeof(S) : 0);
+            mbar_arrive_expect_tx(bars + sl, bytes);
+            fence_proxy_async();
+            bulk_load(ring + sl * SG::SLOT, map, SG::YS * sizeof(S), bars + sl);
+            if (zvec) bulk_load(ring + sl * SG::SLOT + SG::YS, zvec, SG::ZS * sizeof(S), bars + sl);
+        }
+    }
+    // nullptr when the wait gave up; the copies still in flight (items
+    // i+1 .. issued-1) then get a bounded chance to land before the warp leaves
+    __device__ const S *wait(int i, int issued, int *status) {
+        const int sl = i % NSLOT;
+        if (!mbar_wait_warp(bars + sl, (i / NSLOT) & 1, kWaitLimit)) {
+            if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+            for (int k = i + 1; k < issued; ++k) mbar_wait_warp(bars + k % NSLOT, (k / NSLOT) & 1, kWaitLimit);
+            return nullptr;
+        }
+        return ring + sl * SG::SLOT;
+    }
+};
+
+constexpr int kScanWarps = 4;  // warps per block of k2_group / k2_expand
+constexpr int kGroupSlots = 4;
+constexpr int kChainSlots = 8;
+
+template <typename S, int MP, int MODE>
+__global__ void __launch_bounds__(kScanWarps * 32)
+    k2_group(int64_t nC, int G2, int nG, int64_t n_items, const S *__restrict__ Y, const S *__restrict__ Z,
+             S *__restrict__ GY, S *__restrict__ GZ, int *__restrict__ status) {
+    using SG = ScanGeo<S, MP>;
+    constexpr int YS = SG::YS, ZS = SG::ZS;
     constexpr bool REV = MODE != CH_FWD;
     constexpr bool TRANS = MODE == CH_TRANS;
-    extern __shared__ __align__(128) unsigned char k2_smem[];
+    extern __shared__ __align__(128) unsigned char k2g_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x;
+    const int64_t item = (int64_t)blockIdx.x * kScanWarps + warp;  // b * nG + g
+    if (item >= n_items) return;
+    const int64_t b = item / nG;
+    const int g = (int)(item - b * nG);
+    MapRing<S, MP, kGroupSlots> R;
+    R.init(k2g_smem + (size_t)warp * SG::template warp_bytes<kGroupSlots>(), lane);
+    const int64_t c_lo = (int64_t)g * G2;
+    const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
+    auto chunk_at = [&](int i) -> int64_t { return b * nC + (REV ? c_lo + len - 1 - i : c_lo + i); };
+    int issued = 0;
+    auto issue = [&](int i) {
+        if (i < len) {
+            R.issue(i, Y + chunk_at(i) * YS, TRANS ? Z + chunk_at(i) * ZS : nullptr);
+            issued = i + 1;
+        }
+    };
+    for (int i = 0; i < kGroupSlots - 1; ++i) issue(i);
     const int j0 = lane < MP ? lane : 0;
-    S *ring = reinterpret_cast<S *>(k2_smem + (size_t)warp * SG::WARP_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + NSLOT * SLOT * sizeof(S));
-    S *GX = reinterpret_cast<S *>(k2_smem + (size_t)nG * SG::WARP_BYTES);  // [nG][ZS] group incoming states
-    const S *Yb = Y + b * nC * YS;
-    const S *Zb = TRANS ? Z + b * nC * ZS : nullptr;
-    S *GYb = GY + b * nG * YS;
-    S *GZb = TRANS ? GZ + b * nG * ZS : nullptr;
-
-    if (lane == 0) {
-        for (int s = 0; s < NSLOT; ++s) mbar_init(bars + s, 1);
-        mbar_init_fence();
+    if constexpr (TRANS) {
+        S zeta = S(0);
+        for (int i = 0; i < len; ++i) {
+            const S *m = R.wait(i, issued, status);
+            if (m == nullptr) return;
+            S p[MP + 1];
+            map_cols<S, MP, true>(p, m, m + YS, j0);
+            __syncwarp();
+            issue(i + kGroupSlots - 1);
+            zeta = hop<S, MP>(p, zeta, lane);
+        }
+        if (lane < MP) GZ[item * ZS + lane] = zeta;
+    } else {
+        // lane j < MP holds column j of the composed transfer (its response
+        // to a unit incoming component j+1); the accumulated response y is
+        // folded by a hop chain, one component per lane
+        S col[MP];
+#pragma unroll
+        for (int k = 0; k < MP; ++k) col[k] = (k == lane) ? S(1) : S(0);
+        S yv = S(0);
+        for (int i = 0; i < len; ++i) {
+            const S *m = R.wait(i, issued, status);
+            if (m == nullptr) return;
+            S p[MP + 1];
+            map_cols<S, MP, false>(p, m, nullptr, j0);
+            S acc[MP];
+#pragma unroll
+            for (int k = 0; k < MP; ++k) acc[k] = S(0);
+#pragma unroll
+            for (int r = 1; r <= MP; ++r) {
+                const S xr = col[r - 1];
+                const S *row = m + r * MP;  // P[k][r-1] = m[r*MP + k]
+#pragma unroll
+                for (int k = 0; k < MP; k += 2) {
+                    if constexpr (sizeof(S) == 4) {
+                        const float2 v = *reinterpret_cast<const float2 *>(row + k);
+                        acc[k] = fma((S)v.x, xr, acc[k]);
+                        acc[k + 1] = fma((S)v.y, xr, acc[k + 1]);
+                    } else {
+                        acc[k] = fma(row[k], xr, acc[k]);
+                        acc[k + 1] = fma(row[k + 1], xr, acc[k + 1]);
+                    }
+                }
+            }
+            __syncwarp();
+            issue(i + kGroupSlots - 1);
+            yv = hop<S, MP>(p, yv, lane);
+#pragma unroll
+            for (int k = 0; k < MP; ++k) col[k] = acc[k];
+        }
+        if (lane < MP) {
+            GY[item * YS + lane] = yv;
+#pragma unroll
+            for (int k = 0; k < MP; ++k) GY[item * YS + (lane + 1) * MP + k] = col[k];
+        }
     }
-    __syncwarp();
+}
 
-    // this warp's group, its chunks in chain order: chunk_at(i), i < len
-    const int g = warp;
+template <typename S, int MP, int MODE>
+__global__ void __launch_bounds__(32)
+    k2_chain(int M, int nG, const S *__restrict__ GY, const S *__restrict__ GZ, const S *__restrict__ zi,
+             S *__restrict__ GX, int *__restrict__ status) {
+    using SG = ScanGeo<S, MP>;
+    constexpr int YS = SG::YS, ZS = SG::ZS;
+    constexpr bool REV = MODE != CH_FWD;
+    constexpr bool TRANS = MODE == CH_TRANS;
+    extern __shared__ __align__(128) unsigned char k2c_smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x;
+    MapRing<S, MP, kChainSlots> R;
+    R.init(k2c_smem, lane);
+    auto gof = [&](int n) -> int64_t { return b * nG + (REV ? nG - 1 - n : n); };
+    int issued = 0;
+    auto issue = [&](int n) {
+        // the last group's map is not needed: nothing follows it
+        if (n < nG - 1) {
+            R.issue(n, GY + gof(n) * YS, TRANS ? GZ + gof(n) * ZS : nullptr);
+            issued = n + 1;
+        }
+    };
+    for (int n = 0; n < kChainSlots - 1; ++n) issue(n);
+    const int j0 = lane < MP ? lane : 0;
+    S x = S(0);
+    if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
+    for (int n = 0; n < nG; ++n) {
+        if (lane < MP) GX[gof(n) * ZS + lane] = x;
+        if (n == nG - 1) break;
+        const S *m = R.wait(n, issued, status);
+        if (m == nullptr) return;
+        S p[MP + 1];
+        map_cols<S, MP, TRANS>(p, m, m + YS, j0);
+        __syncwarp();
+        issue(n + kChainSlots - 1);
+        x = hop<S, MP>(p, x, lane);
+    }
+}
+
+template <typename S, int MP, int MODE>
+__global__ void __launch_bounds__(kScanWarps * 32)
+    k2_expand(int M, int64_t nC, int G2, int nG, int64_t n_items, const S *__restrict__ Y, const S *__restrict__ Z,
+              const S *__restrict__ GX, S *__restrict__ X, S *__restrict__ ckpt, int *__restrict__ status) {
+    using SG = ScanGeo<S, MP>;
+    constexpr int YS = SG::YS, ZS = SG::ZS;
+    constexpr bool REV = MODE != CH_FWD;
+    constexpr bool TRANS = MODE == CH_TRANS;
+    extern __shared__ __align__(128) unsigned char k2e_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kScanWarps + warp;  // b * nG + g
+    if (item >= n_items) return;
+    const int64_t b = item / nG;
+    const int g = (int)(item - b * nG);
+    MapRing<S, MP, kGroupSlots> R;
+    R.init(k2e_smem + (size_t)warp * SG::template warp_bytes<kGroupSlots>(), lane);
     const int64_t c_lo = (int64_t)g * G2;
     const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
     auto chunk_at = [&](int i) -> int64_t { return REV ? c_lo + len - 1 - i : c_lo + i; };
-    int uses = 0;  // bulk-copy phases consumed on this warp's ring
-    auto issue = [&](int i) {  // stage chunk chunk_at(i) into slot (uses + i) % NSLOT
-        if (i < len) {
-            const int sl = (uses + i) % NSLOT;
-            const unsigned bytes = (YS + (TRANS ? ZS : 0)) * sizeof(S);
-            if (lane == 0) {
-                mbar_arrive_expect_tx(bars + sl, bytes);
-                fence_proxy_async();
-                bulk_load(ring + sl * SLOT, Yb + chunk_at(i) * YS, YS * sizeof(S), bars + sl);
-                if (TRANS) bulk_load(ring + sl * SLOT + YS, Zb + chunk_at(i) * ZS, ZS * sizeof(S), bars + sl);
-            }
+    int issued = 0;
+    auto issue = [&](int i) {
+        // the group's last chunk needs no map: nothing follows it in the group
+        if (i < len - 1) {
+            R.issue(i, Y + (b * nC + chunk_at(i)) * YS, TRANS ? Z + (b * nC + chunk_at(i)) * ZS : nullptr);
+            issued = i + 1;
         }
     };
-    auto wait = [&](int i) -> const S * {  // chunk chunk_at(i) landed; its slot
-        const int u = uses + i, sl = u % NSLOT;
-        if (!mbar_wait_warp(bars + sl, (u / NSLOT) & 1, kWaitLimit)) {
-            if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
-            return nullptr;
-        }
-        return ring + sl * SLOT;
-    };
-    bool ok = true;
-
-    // ---- phase A: group summaries ----
-    if (g < nG) {
-        issue(0);
-        issue(1);
-        if constexpr (TRANS) {
-            S zeta = S(0);
-            for (int i = 0; i < len && ok; ++i) {
-                const S *m = wait(i);
-                if (m == nullptr) { ok = false; break; }
-                S p[MP + 1];
-                map_cols<S, MP, true>(p, m, m + YS, j0);
-                __syncwarp();
-                issue(i + 2);
-                zeta = hop<S, MP>(p, zeta, lane);
-            }
-            if (ok && lane < MP) GZb[(int64_t)g * ZS + lane] = zeta;
-        } else {
-            // lane j <= MP holds column j of the composed map: column 0 the
-            // accumulated response y, columns 1..MP the transfer
-            S col[MP];
-#pragma unroll
-            for (int k = 0; k < MP; ++k) col[k] = (lane >= 1 && k == lane - 1) ? S(1) : S(0);
-            for (int i = 0; i < len && ok; ++i) {
-                const S *m = wait(i);
-                if (m == nullptr) { ok = false; break; }
-                S acc[MP];
-#pragma unroll
-                for (int k = 0; k < MP; ++k) acc[k] = lane == 0 ? m[k] : S(0);
-#pragma unroll
-                for (int r = 1; r <= MP; ++r) {
-                    const S xr = col[r - 1];
-                    const S *row = m + r * MP;  // P[k][r-1] = m[r*MP + k]
-#pragma unroll
-                    for (int k = 0; k < MP; k += 2) {
-                        if constexpr (sizeof(S) == 4) {
-                            const float2 v = *reinterpret_cast<const float2 *>(row + k);
-                            acc[k] = fma((S)v.x, xr, acc[k]);
-                            acc[k + 1] = fma((S)v.y, xr, acc[k + 1]);
-                        } else {
-                            acc[k] = fma(row[k], xr, acc[k]);
-                            acc[k + 1] = fma(row[k + 1], xr, acc[k + 1]);
-                        }
-                    }
-                }
-                __syncwarp();
-                issue(i + 2);
-#pragma unroll
-                for (int k = 0; k < MP; ++k) col[k] = acc[k];
-            }
-            if (ok && lane <= MP) {
-#pragma unroll
-                for (int k = 0; k < MP; ++k) GYb[(int64_t)g * YS + lane * MP + k] = col[k];
-            }
-        }
-        uses += len;
-    }
-    ok = __syncthreads_and(ok ? 1 : 0);
-    if (!ok) return;
-
-    // ---- phase B: chain over the groups (warp 0), group summaries staged by cp.async ----
-    if (warp == 0) {
-        S x = S(0);
-        if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
-        auto gof = [&](int n) -> int { return REV ? nG - 1 - n : n; };
-        auto stage = [&](int n) {
-            if (n < nG) {
-                S *dst = ring + (n % NSLOT) * SLOT;
-                const S *src = GYb + (int64_t)gof(n) * YS;
-                for (int off = lane * 16; off < YS * (int)sizeof(S); off += 32 * 16)
-                    cp_async<16>(reinterpret_cast<char *>(dst) + off, reinterpret_cast<const char *>(src) + off, 16);
-                if (TRANS && lane < MP) cp_async<sizeof(S)>(dst + YS + lane, GZb + (int64_t)gof(n) * ZS + lane, (int)sizeof(S));
-            }
-            cp_async_commit();
-        };
-        stage(0);
-        for (int n = 0; n < nG; ++n) {
-            if (lane < MP) GX[gof(n) * ZS + lane] = x;
-            if (n == nG - 1) break;
-            stage(n + 1);
-            cp_async_wait<1>();
-            __syncwarp();
-            S p[MP + 1];
-            const S *m = ring + (n % NSLOT) * SLOT;
-            map_cols<S, MP, TRANS>(p, m, m + YS, j0);
-            __syncwarp();
-            x = hop<S, MP>(p, x, lane);
-        }
-        cp_async_wait<0>();
-    }
-    __syncthreads();
-
-    // ---- phase C: every chunk's incoming state ----
-    if (g < nG) {
-        fence_proxy_async();  // the ring was last written by cp.async
+    for (int i = 0; i < kGroupSlots - 1; ++i) issue(i);
+    const int j0 = lane < MP ? lane : 0;
+    S x = lane < MP ? GX[item * ZS + lane] : S(0);
+    for (int i = 0; i < len; ++i) {
+        const int64_t c = chunk_at(i);
+        if (lane < MP) X[(b * nC + c) * MP + lane] = x;
+        if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[(b * nC + c) * M + lane] = x;
+        if (i == len - 1) break;
+        const S *m = R.wait(i, issued, status);
+        if (m == nullptr) return;
+        S p[MP + 1];
+        map_cols<S, MP, TRANS>(p, m, m + YS, j0);
         __syncwarp();
-        S x = lane < MP ? GX[g * ZS + lane] : S(0);
-        issue(0);
-        issue(1);
-        for (int i = 0; i < len; ++i) {
-            const int64_t c = chunk_at(i);
-            if (lane < MP) X[(b * nC + c) * MP + lane] = x;
-            if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[(b * nC + c) * M + lane] = x;
-            const S *m = wait(i);
-            if (m == nullptr) return;
-            if (i == len - 1) break;
-            S p[MP + 1];
-            map_cols<S, MP, TRANS>(p, m, m + YS, j0);
-            __syncwarp();
-            issue(i + 2);
-            x = hop<S, MP>(p, x, lane);
-        }
+        issue(i + kGroupSlots - 1);
+        x = hop<S, MP>(p, x, lane);
     }
 }
 
