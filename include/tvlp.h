@@ -34,7 +34,7 @@
  *   lp_tv_backward can reuse (LP_BWD_REUSE_FORWARD).
  * - `chunk` is the chunk length L of the parallel scan (samples).  0 asks
  *   the library to pick it (lp_tv_pick_chunk).  A non-zero value is rounded
- *   up to a multiple of 8.  Results depend on the chunk length only through
+ *   up to a multiple of 16.  Results depend on the chunk length only through
  *   floating-point rounding.
  * - No input may alias an output.
  * - Shapes: B >= 0, T >= 0, 0 <= M <= 32 (M <= 16 for _f64).  B == 0 or

@@ -186,7 +186,7 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // two-level scan costs its group compositions and hops; the re-run is L
 // sequential steps.
 int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
-    constexpr int SRV = 8;  // chunk lengths are multiples of the stage height
+    constexpr int SRV = 16;  // chunk lengths are multiples of the stage height
     if (T <= 0 || B <= 0) return SRV;
     const Shape sh = shape_for(MP, dtype);
     const int64_t per_wave = (int64_t)num_sms() * sh.warps_per_block * sh.chunks_per_warp;
@@ -235,7 +235,7 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
         return LP_OK;
     }
     int L = chunk > 0 ? chunk : pick_chunk_impl(B, T, MP, dtype);
-    L = (int)(ceil_div(L, 8) * 8);
+    L = (int)(ceil_div(L, 16) * 16);
     if (L <= 0) return LP_EINVAL;
     p->L = L;
     p->nC = T > 0 ? ceil_div(T, L) : 0;
@@ -351,7 +351,7 @@ int lp_tv_pick_chunk(int B, int64_t T, int M, int dtype) {
 
 int64_t lp_tv_num_chunks(int64_t T, int M, int chunk) {
     if (T <= 0 || M <= 0 || chunk <= 0) return 0;
-    const int64_t L = ceil_div(chunk, 8) * 8;
+    const int64_t L = ceil_div(chunk, 16) * 16;
     return ceil_div(T, L);
 }
 

@@ -58,32 +58,44 @@ template <typename S, int MP> struct Launch {
         return cudaGetLastError();
     }
 
+    // ring slots for a warp that waits on `need` maps: all of them when they
+    // fit in `budget` bytes, else a ring of at least two
+    static int ring_slots(int64_t need, size_t budget) {
+        int64_t fit = 2;
+        while (fit < need && ring_bytes<S, MP>((int)fit + 1) <= budget) ++fit;
+        return (int)(need < 1 ? 1 : (need <= fit ? need : fit));
+    }
+
     // two-level scan: group maps, group chain, chunk states
     template <int MODE> static cudaError_t scan(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, S *GX,
                                                 const S *zi, S *X, S *ckpt, cudaStream_t st, int k0) {
-        using SG = ScanGeo<S, MP>;
         static bool done_g[kMaxDevices] = {}, done_c[kMaxDevices] = {}, done_e[kMaxDevices] = {};
         const int64_t items = (int64_t)p.B * p.nG;
         const int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
-        const size_t smem_g = kScanWarps * SG::template warp_bytes<kGroupSlots>();
-        const size_t smem_c = SG::template warp_bytes<kChainSlots>();
+        const int ns_g = ring_slots(p.G2, kSmemBudget / kScanWarps);
+        const int ns_c = ring_slots(p.nG - 1, kSmemBudget);
+        const int ns_e = ring_slots(p.G2 - 1, kSmemBudget / kScanWarps);
+        const size_t smem_g = kScanWarps * ring_bytes<S, MP>(ns_g);
+        const size_t smem_c = ring_bytes<S, MP>(ns_c);
+        const size_t smem_e = kScanWarps * ring_bytes<S, MP>(ns_e);
         cudaError_t err;
         auto kg = k2_group<S, MP, MODE>;
         auto kc = k2_chain<S, MP, MODE>;
         auto ke = k2_expand<S, MP, MODE>;
-        if ((err = allow_smem(kg, smem_g, done_g)) != cudaSuccess) return err;
-        if ((err = allow_smem(kc, smem_c, done_c)) != cudaSuccess) return err;
-        if ((err = allow_smem(ke, smem_g, done_e)) != cudaSuccess) return err;
+        if ((err = allow_smem(kg, kSmemBudget, done_g)) != cudaSuccess) return err;
+        if ((err = allow_smem(kc, kSmemBudget, done_c)) != cudaSuccess) return err;
+        if ((err = allow_smem(ke, kSmemBudget, done_e)) != cudaSuccess) return err;
         profile_mark(k0, false, st);
-        kg<<<(unsigned)blocks, kScanWarps * 32, smem_g, st>>>(p.nC, p.G2, p.nG, items, Y, Z, GY, GZ, p.status);
+        kg<<<(unsigned)blocks, kScanWarps * 32, smem_g, st>>>(p.nC, p.G2, p.nG, items, ns_g, Y, Z, GY, GZ, p.status);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         profile_mark(k0, true, st);
         profile_mark(k0 + 1, false, st);
-        kc<<<(unsigned)p.B, 32, smem_c, st>>>(p.M, p.nG, GY, GZ, zi, GX, p.status);
+        kc<<<(unsigned)p.B, 32, smem_c, st>>>(p.M, p.nG, ns_c, GY, GZ, zi, GX, p.status);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         profile_mark(k0 + 1, true, st);
         profile_mark(k0 + 2, false, st);
-        ke<<<(unsigned)blocks, kScanWarps * 32, smem_g, st>>>(p.M, p.nC, p.G2, p.nG, items, Y, Z, GX, X, ckpt, p.status);
+        ke<<<(unsigned)blocks, kScanWarps * 32, smem_e, st>>>(p.M, p.nC, p.G2, p.nG, items, ns_e, Y, Z, GX, X, ckpt,
+                                                              p.status);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         profile_mark(k0 + 2, true, st);
         return cudaSuccess;
@@ -127,8 +139,8 @@ template <typename S, int MP> struct Launch {
 // The plain path runs the one-recursion kernels with one chunk per signal.
 inline Problem plain_problem(const Problem &p) {
     Problem q = p;
-    q.L = (int)(((p.T + SR - 1) / SR) * SR);
-    if (q.L == 0) q.L = SR;
+    q.L = (int)(((p.T + SRS - 1) / SRS) * SRS);
+    if (q.L == 0) q.L = SRS;
     q.nC = 1;
     q.NQ = p.B;
     return q;

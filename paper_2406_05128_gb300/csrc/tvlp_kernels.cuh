@@ -17,7 +17,8 @@
 // the last step (t = 0), q_j = dL/ds(-j), the initial-state gradient.
 //
 // Parallel scan over time.  A signal is cut into chunks of L samples (L a
-// multiple of SR = 8), streamed in stages of SR rows.
+// multiple of SRS = 16), streamed in stages of SRS rows and computed in
+// blocks of SR = 8 rows.
 //   k1_summary      per chunk, the end states of MP+1 recursions: zero state
 //                   driven by the input (column 0) and the MP unit initial
 //                   states with zero input (columns 1..MP, the chunk transfer
@@ -48,7 +49,8 @@
 
 namespace tvlp {
 
-constexpr int SR = 8;  // rows per stage; chunk lengths are multiples of SR
+constexpr int SR = 8;    // rows per compute block (register window)
+constexpr int SRS = 16;  // rows per staged copy; chunk lengths are multiples of SRS
 
 // Status codes written by kernels to the device status word.
 enum { DEV_OK = 0, DEV_TIMEOUT_TMA = 1 };
@@ -95,21 +97,21 @@ __host__ __device__ constexpr int wrapm(int x, int m) { return ((x % m) + m) % m
 template <typename S, int MP, int G_, int R_> struct SumGeo {
     static constexpr int G = G_, R = R_;
     static constexpr int CPW = 32 / G;                     // chunks per warp
-    static constexpr int NS = 3;                            // stages in the ring
+    static constexpr int NS = 2;                            // stages in the ring
     static constexpr int WPS = (int)sizeof(S) / 4;          // 32-bit words per element
     static constexpr int GPH = (16 / G) > 1 ? 16 / G : 1;   // chunk groups per half-warp
-    // chunk-stage stride (elements): SR rows of MP coefficients + padding,
+    // chunk-stage stride (elements): SRS rows of MP coefficients + padding,
     // a multiple of 16 bytes (bulk-copy destination)
-    static constexpr int CS = SR * MP + conflict_free_pad(SR * MP * WPS, GPH, 4) / WPS;
-    static constexpr int US = SR;                            // input samples per chunk-stage
+    static constexpr int CS = SRS * MP + conflict_free_pad(SRS * MP * WPS, GPH, 4) / WPS;
     static constexpr int A_STAGE = CPW * CS;
-    static constexpr int U_STAGE = CPW * US;
+    static constexpr int U_STAGE = CPW * SRS;               // input samples of a stage
+    static constexpr int UPL = (U_STAGE + 31) / 32;         // input samples each lane stages
     // per-warp slice: the stage ring then NS mbarriers, rounded to 128 bytes
     // so every warp's bulk-copy destinations stay 16-byte aligned
     static constexpr size_t RING_BYTES = size_t(NS) * (A_STAGE + U_STAGE) * sizeof(S);
     static constexpr size_t WARP_BYTES = ((RING_BYTES + NS * 8 + 127) / 128) * 128;
     static_assert(G * R >= MP + 1, "packing must hold MP+1 recursions");
-    static_assert((CS * sizeof(S)) % 16 == 0 && (US * sizeof(S)) % 16 == 0, "16-byte stage alignment");
+    static_assert((CS * sizeof(S)) % 16 == 0, "16-byte stage alignment");
     static_assert((A_STAGE * sizeof(S)) % 16 == 0 && (U_STAGE * sizeof(S)) % 16 == 0, "16-byte ring alignment");
     static_assert(RING_BYTES % 8 == 0 && WARP_BYTES % 16 == 0, "mbarrier and warp-slice alignment");
 };
@@ -276,36 +278,34 @@ __device__ __forceinline__ void slide(S (&h)[W]) {
 // K1: chunk summaries.
 // Flattened chunk index q = b*nC + c; chunk c of signal b covers samples
 // [c*L, c*L + L).  Each warp owns CPW consecutive chunks; lane (grp = lane/G,
-// g = lane%G) runs recursions r = g*R + k, k < R.  Coefficient rows and
-// input samples are staged in shared memory, SR rows per stage, NS stages in
-// a ring: a full, 16-byte-aligned chunk-stage arrives as one bulk (TMA)
-// copy completing on the stage's mbarrier; others (a ragged tail, a
-// misaligned start, a padded order) use cp.async with zero fill.
+// g = lane%G) runs recursions r = g*R + k, k < R.  Coefficient rows are
+// staged in shared memory, SRS rows per stage, two stages in a ring: a full,
+// 16-byte-aligned chunk-stage arrives as one bulk (TMA) copy completing on
+// the stage's mbarrier; others (a ragged tail, a misaligned start, a padded
+// order) use cp.async with zero fill.  Input samples are loaded by the warp
+// one stage ahead and parked in shared memory next to the coefficients.
 // Output Y[q][r][k] (per-chunk stride YS):
 //   forward:  s(c*L + L - 1 - k) of recursion r
 //   backward: q_{k+1} after the chunk, i.e. the pending dL/ds(c*L - 1 - k)
 // ---------------------------------------------------------------------------
 template <typename S, int MP, typename GE, bool BWD>
-__device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, const S *__restrict__ a,
-                                               const S *__restrict__ u, int M, int L, int k, int lane,
-                                               int64_t my_base, int my_valid, bool exact) {
+__device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int k,
+                                               int lane, int64_t my_base, int my_valid, bool exact) {
     constexpr int CPW = GE::CPW;
-    constexpr unsigned A_BYTES = SR * MP * sizeof(S);
-    constexpr unsigned U_BYTES = SR * sizeof(S);
-    const int roff = BWD ? L - (k + 1) * SR : k * SR;  // chunk-local first row of the stage
+    constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
+    const int roff = BWD ? L - (k + 1) * SRS : k * SRS;  // chunk-local first row of the stage
     int nvalid = my_valid - roff;
-    nvalid = nvalid < 0 ? 0 : (nvalid > SR ? SR : nvalid);
+    nvalid = nvalid < 0 ? 0 : (nvalid > SRS ? SRS : nvalid);
     const bool mine = lane < CPW;
     const S *src_a = a + (my_base + roff) * (int64_t)MP;
-    const S *src_u = u + my_base + roff;
-    const bool tma_a = mine && exact && nvalid == SR && aligned16(src_a);
-    const bool tma_u = mine && nvalid == SR && aligned16(src_u);
-    const unsigned bytes = __reduce_add_sync(0xffffffffu, (tma_a ? A_BYTES : 0u) + (tma_u ? U_BYTES : 0u));
-    if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+    const bool tma_a = mine && exact && nvalid == SRS && aligned16(src_a);
+    const unsigned ntma = __popc(__ballot_sync(0xffffffffu, tma_a));
+    if (lane == 0) mbar_arrive_expect_tx(bar, ntma * A_BYTES);
     __syncwarp();
-    if (tma_a || tma_u) fence_proxy_async();
-    if (tma_a) bulk_load(a_st + lane * GE::CS, src_a, A_BYTES, bar);
-    if (tma_u) bulk_load(u_st + lane * GE::US, src_u, U_BYTES, bar);
+    if (tma_a) {
+        fence_proxy_async();
+        bulk_load(a_st + lane * GE::CS, src_a, A_BYTES, bar);
+    }
     // fallback chunk-stages
     unsigned slow = __ballot_sync(0xffffffffu, mine && !tma_a);
     while (slow) {
@@ -316,14 +316,14 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, 
         S *dst = a_st + ch * GE::CS;
         if (exact) {
             const S *s0 = a + (base + roff) * (int64_t)MP;
-            for (int idx = lane; idx < SR * MP; idx += 32) {
+            for (int idx = lane; idx < SRS * MP; idx += 32) {
                 const bool v = idx < nv * MP;
                 cp_async<sizeof(S)>(dst + idx, v ? s0 + idx : a, v ? (int)sizeof(S) : 0);
             }
         } else {
             // padded order: the M real coefficients of every row; the padded
             // columns were zeroed once and are never written
-            for (int r = 0; r < SR; ++r) {
+            for (int r = 0; r < SRS; ++r) {
                 if (lane < M) {
                     const bool v = r < nv;
                     const S *s0 = v ? a + (base + roff + r) * (int64_t)M + lane : a;
@@ -332,18 +332,24 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, S *u_st, uint64_t *bar, 
             }
         }
     }
-    slow = __ballot_sync(0xffffffffu, mine && !tma_u);
-    while (slow) {
-        const int ch = __ffs(slow) - 1;
-        slow &= slow - 1;
-        const int64_t base = __shfl_sync(0xffffffffu, my_base, ch);
-        const int nv = __shfl_sync(0xffffffffu, nvalid, ch);
-        if (lane < SR) {
-            const bool v = lane < nv;
-            cp_async<sizeof(S)>(u_st + ch * GE::US + lane, v ? u + base + roff + lane : u, v ? (int)sizeof(S) : 0);
-        }
-    }
     cp_async_commit();
+}
+
+// Input samples of stage k for the warp's chunks: element e = lane + 32*i
+// (i < UPL) is row e % SRS of chunk e / SRS; zero past the signal's end.
+template <typename S, int MP, typename GE, bool BWD>
+__device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__restrict__ u, int L, int k, int lane,
+                                               int64_t my_base, int my_valid) {
+    const int roff = BWD ? L - (k + 1) * SRS : k * SRS;
+#pragma unroll
+    for (int i = 0; i < GE::UPL; ++i) {
+        const int e = lane + 32 * i;
+        const int ch = (e / SRS) < GE::CPW ? e / SRS : 0;
+        const int64_t base = __shfl_sync(0xffffffffu, my_base, ch);
+        const int valid = __shfl_sync(0xffffffffu, my_valid, ch);
+        const int r = e % SRS;
+        uv[i] = (e < GE::U_STAGE && roff + r < valid) ? __ldg(u + base + roff + r) : S(0);
+    }
 }
 
 template <typename S, int MP, int G, int R, bool BWD>
@@ -383,10 +389,10 @@ __global__ void __launch_bounds__(256, 1)
         my_valid = rem < L ? (int)rem : L;
     }
     const int grp = lane / G, g = lane % G;
-    const int nblk = L / SR;
+    const int nblk = L / SRS;
 
-    // forward window: h[k][MP - i] = s(t - i) at a stage start; backward
-    // window: h[k][j - 1] = q_j at a stage start
+    // forward window: h[k][MP - i] = s(t - i) at a block start; backward
+    // window: h[k][j - 1] = q_j at a block start
     S h[R][WIN];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -399,67 +405,78 @@ __global__ void __launch_bounds__(256, 1)
     }
     const S flag0 = (g == 0) ? S(1) : S(0);
 
-#pragma unroll 1
-    for (int s = 0; s < NS - 1; ++s) {
-        if (s < nblk)
-            k1_issue_stage<S, MP, GE, BWD>(a_buf + s * GE::A_STAGE, u_buf + s * GE::U_STAGE, bars + s, a, u, M, L,
-                                           s, lane, my_base, my_valid, exact);
-        else
-            cp_async_commit();
-    }
+    S uv[GE::UPL];
+    k1_issue_stage<S, MP, GE, BWD>(a_buf, bars, a, M, L, 0, lane, my_base, my_valid, exact);
+    k1_load_inputs<S, MP, GE, BWD>(uv, u, L, 0, lane, my_base, my_valid);
+#pragma unroll
+    for (int i = 0; i < GE::UPL; ++i)
+        if (lane + 32 * i < GE::U_STAGE) u_buf[lane + 32 * i] = uv[i];
 #pragma unroll 1
     for (int k = 0; k < nblk; ++k) {
-        const int slot = k % NS;
-        const int ahead = k + NS - 1;  // refill the slot of stage k-1
-        if (ahead < nblk)
-            k1_issue_stage<S, MP, GE, BWD>(a_buf + (ahead % NS) * GE::A_STAGE, u_buf + (ahead % NS) * GE::U_STAGE,
-                                           bars + ahead % NS, a, u, M, L, ahead, lane, my_base, my_valid, exact);
-        else
+        const int slot = k & 1;
+        const bool more = k + 1 < nblk;
+        if (more) {
+            // the other slot was consumed in the previous iteration
+            k1_issue_stage<S, MP, GE, BWD>(a_buf + (slot ^ 1) * GE::A_STAGE, bars + (slot ^ 1), a, M, L, k + 1, lane,
+                                           my_base, my_valid, exact);
+            k1_load_inputs<S, MP, GE, BWD>(uv, u, L, k + 1, lane, my_base, my_valid);
+        } else {
             cp_async_commit();
-        cp_async_wait<NS - 1>();
-        if (!mbar_wait_warp(bars + slot, (k / NS) & 1, kWaitLimit)) {
-            // a bulk copy never completed: record it, give the copies this
-            // warp still has in flight a bounded chance to land, and leave
+        }
+        cp_async_wait<1>();
+        if (!mbar_wait_warp(bars + slot, (k >> 1) & 1, kWaitLimit)) {
+            // a bulk copy never completed: record it, give the copy this warp
+            // still has in flight a bounded chance to land, and leave
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
-            for (int s2 = k + 1; s2 < k + NS && s2 < nblk; ++s2)
-                mbar_wait_warp(bars + s2 % NS, (s2 / NS) & 1, kWaitLimit);
+            if (more) mbar_wait_warp(bars + (slot ^ 1), ((k + 1) >> 1) & 1, kWaitLimit);
             cp_async_wait<0>();
             return;
         }
         __syncwarp();
         const S *arow = a_buf + slot * GE::A_STAGE + grp * GE::CS;
-        const S *urow = u_buf + slot * GE::U_STAGE + grp * GE::US;
+        const S *urow = u_buf + slot * GE::U_STAGE + grp * SRS;
 #pragma unroll
-        for (int j = 0; j < SR; ++j) {
-            // forward: row j; backward: row SR-1-j (rows run back in time)
-            const int row = BWD ? SR - 1 - j : j;
-            S c[MP];
-            load_row_smem<S, MP>(c, arow + row * MP);
-            const S uu = flag0 * urow[row];
-            if constexpr (BWD) {
-                S y[R];
+        for (int cb = 0; cb < SRS / SR; ++cb) {
+            // forward: rows cb*SR + j; backward: the stage's rows in reverse
+            const int rb = BWD ? (SRS / SR - 1 - cb) * SR : cb * SR;
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) y[kk] = ((kk == 0) ? uu : S(0)) + h[kk][j];
+            for (int j = 0; j < SR; ++j) {
+                const int row = BWD ? rb + SR - 1 - j : rb + j;
+                S c[MP];
+                load_row_smem<S, MP>(c, arow + row * MP);
+                const S uu = flag0 * urow[row];
+                if constexpr (BWD) {
+                    S y[R];
 #pragma unroll
-                for (int i = 1; i < MP; ++i)
+                    for (int kk = 0; kk < R; ++kk) y[kk] = ((kk == 0) ? uu : S(0)) + h[kk][j];
 #pragma unroll
-                    for (int kk = 0; kk < R; ++kk) h[kk][j + i] = fma(-c[i - 1], y[kk], h[kk][j + i]);
+                    for (int i = 1; i < MP; ++i)
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) h[kk][j + MP] = -c[MP - 1] * y[kk];
-            } else {
-                S acc[R];
+                        for (int kk = 0; kk < R; ++kk) h[kk][j + i] = fma(-c[i - 1], y[kk], h[kk][j + i]);
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) acc[kk] = (kk == 0) ? uu : S(0);
+                    for (int kk = 0; kk < R; ++kk) h[kk][j + MP] = -c[MP - 1] * y[kk];
+                } else {
+                    S acc[R];
 #pragma unroll
-                for (int i = MP; i >= 1; --i)
+                    for (int kk = 0; kk < R; ++kk) acc[kk] = (kk == 0) ? uu : S(0);
 #pragma unroll
-                    for (int kk = 0; kk < R; ++kk) acc[kk] = fma(-c[i - 1], h[kk][MP + j - i], acc[kk]);
+                    for (int i = MP; i >= 1; --i)
 #pragma unroll
-                for (int kk = 0; kk < R; ++kk) h[kk][MP + j] = acc[kk];
+                        for (int kk = 0; kk < R; ++kk) acc[kk] = fma(-c[i - 1], h[kk][MP + j - i], acc[kk]);
+#pragma unroll
+                    for (int kk = 0; kk < R; ++kk) h[kk][MP + j] = acc[kk];
+                }
             }
-        }
 #pragma unroll
-        for (int kk = 0; kk < R; ++kk) slide<S, MP, WIN>(h[kk]);
+            for (int kk = 0; kk < R; ++kk) slide<S, MP, WIN>(h[kk]);
+        }
+        // park the next stage's input samples in the slot this iteration read
+        // last time round (consumed before the previous iteration ended)
+        if (more) {
+#pragma unroll
+            for (int i = 0; i < GE::UPL; ++i)
+                if (lane + 32 * i < GE::U_STAGE) u_buf[(slot ^ 1) * GE::U_STAGE + lane + 32 * i] = uv[i];
+        }
         __syncwarp();
     }
     // end states
@@ -479,10 +496,10 @@ __global__ void __launch_bounds__(256, 1)
 
 // ---------------------------------------------------------------------------
 // One recursion per lane over its chunk ("lane per chunk"): a warp owns 32
-// consecutive chunks.  Each lane has a private ring of NS stages of SR rows
-// (coefficients and input samples); a full, aligned lane-stage arrives by
-// two bulk copies completing on the warp's per-stage mbarrier, others by
-// cp.async with zero fill.
+// consecutive chunks.  Each lane has a private ring of two stages of SRS
+// coefficient rows; a full, aligned lane-stage arrives by one bulk copy
+// completing on the warp's per-stage mbarrier, others by cp.async with zero
+// fill.  Input samples are loaded into registers one stage ahead.
 //   FWD_RERUN: start from X[q] (or zi / zero), write s.
 //   BWD_ZERO:  adjoint from zero state, store the end state to Z[q].
 //   BWD_RERUN: adjoint from W[q], write ge; chunk 0 also writes gzi.
@@ -494,59 +511,55 @@ __global__ void __launch_bounds__(256, 1)
 enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2 };
 
 template <typename S, int MP> struct RecGeo {
-    static constexpr int NS = 4;                                         // stages per lane ring
-    static constexpr int A_ST = SR * MP;                                 // coefficient elements per lane-stage
-    static constexpr int RAW = (NS * (A_ST + SR) * (int)sizeof(S)) / 4;  // words per lane
+    static constexpr int NS = 2;                                    // stages per lane ring
+    static constexpr int A_ST = SRS * MP;                           // coefficient elements per lane-stage
+    static constexpr int RAW = (NS * A_ST * (int)sizeof(S)) / 4;    // words per lane
     // lane stride in words: an odd multiple of 4, so the 16-byte row loads of
     // a quarter warp hit distinct bank quads
     static constexpr int LW = ((RAW + 3) / 4) % 2 == 1 ? ((RAW + 3) / 4) * 4 : ((RAW + 3) / 4 + 1) * 4;
     static constexpr size_t SMEM = size_t(32) * LW * 4 + NS * 8;
-    static_assert((A_ST * sizeof(S)) % 16 == 0 && (SR * sizeof(S)) % 16 == 0, "16-byte lane stages");
-    static_assert((LW * 4) % 16 == 0 && (NS * A_ST * sizeof(S)) % 16 == 0, "16-byte lane ring alignment");
-    static_assert(NS * (A_ST + SR) * sizeof(S) <= size_t(LW) * 4, "lane ring fits its stride");
+    static_assert((A_ST * sizeof(S)) % 16 == 0, "16-byte lane stages");
+    static_assert((LW * 4) % 16 == 0, "16-byte lane ring alignment");
+    static_assert(NS * A_ST * sizeof(S) <= size_t(LW) * 4, "lane ring fits its stride");
 };
 
 template <typename S, int MP, bool EXACT, bool BWD>
-__device__ __forceinline__ void rec_issue_stage(S *a_st, S *u_st, uint64_t *bar, const S *__restrict__ a,
-                                                const S *__restrict__ u, int M, int L, int s, bool active,
-                                                int64_t base, int n) {
-    constexpr unsigned A_BYTES = SR * MP * sizeof(S);
-    constexpr unsigned U_BYTES = SR * sizeof(S);
-    const int roff = BWD ? L - (s + 1) * SR : s * SR;
+__device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int s,
+                                                bool active, int64_t base, int n) {
+    constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
+    const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
     int nv = n - roff;
-    nv = nv < 0 ? 0 : (nv > SR ? SR : nv);
+    nv = nv < 0 ? 0 : (nv > SRS ? SRS : nv);
     if (!active) nv = 0;
     const S *src_a = a + (base + roff) * (int64_t)M;
-    const S *src_u = u + base + roff;
-    const bool tma_a = EXACT && nv == SR && aligned16(src_a);
-    const bool tma_u = nv == SR && aligned16(src_u);
-    const unsigned bytes = __reduce_add_sync(0xffffffffu, (tma_a ? A_BYTES : 0u) + (tma_u ? U_BYTES : 0u));
-    if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, bytes);
+    const bool tma_a = EXACT && nv == SRS && aligned16(src_a);
+    const unsigned ntma = __popc(__ballot_sync(0xffffffffu, tma_a));
+    if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, ntma * A_BYTES);
     __syncwarp();
-    if (tma_a || tma_u) fence_proxy_async();
-    if (tma_a) bulk_load(a_st, src_a, A_BYTES, bar);
-    if (tma_u) bulk_load(u_st, src_u, U_BYTES, bar);
-    if (!tma_a) {
-        if (EXACT) {
-            for (int idx = 0; idx < SR * MP; ++idx) {
-                const bool v = idx < nv * MP;
-                cp_async<sizeof(S)>(a_st + idx, v ? src_a + idx : a, v ? (int)sizeof(S) : 0);
+    if (tma_a) {
+        fence_proxy_async();
+        bulk_load(a_st, src_a, A_BYTES, bar);
+    } else if (EXACT) {
+        for (int idx = 0; idx < SRS * MP; ++idx) {
+            const bool v = idx < nv * MP;
+            cp_async<sizeof(S)>(a_st + idx, v ? src_a + idx : a, v ? (int)sizeof(S) : 0);
+        }
+    } else {
+        for (int r = 0; r < SRS; ++r)
+            for (int i = 0; i < M; ++i) {
+                const bool v = r < nv;
+                cp_async<sizeof(S)>(a_st + r * MP + i, v ? src_a + (int64_t)r * M + i : a, v ? (int)sizeof(S) : 0);
             }
-        } else {
-            for (int r = 0; r < SR; ++r)
-                for (int i = 0; i < M; ++i) {
-                    const bool v = r < nv;
-                    cp_async<sizeof(S)>(a_st + r * MP + i, v ? src_a + (int64_t)r * M + i : a, v ? (int)sizeof(S) : 0);
-                }
-        }
-    }
-    if (!tma_u) {
-        for (int r = 0; r < SR; ++r) {
-            const bool v = r < nv;
-            cp_async<sizeof(S)>(u_st + r, v ? src_u + r : u, v ? (int)sizeof(S) : 0);
-        }
     }
     cp_async_commit();
+}
+
+template <typename S, bool BWD>
+__device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restrict__ u, int L, int s, bool active,
+                                                int64_t base, int n) {
+    const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
+#pragma unroll
+    for (int r = 0; r < SRS; ++r) uv[r] = (active && roff + r < n) ? __ldg(u + base + roff + r) : S(0);
 }
 
 template <typename S, int MP, bool EXACT, int MODE>
@@ -562,8 +575,7 @@ __global__ void __launch_bounds__(32)
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int64_t q = blk * 32 + lane;
     const bool active = q < NQ;
-    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)lane * RG::LW * 4);  // [NS][SR*MP]
-    S *u_ring = a_ring + NS * RG::A_ST;                                         // [NS][SR]
+    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)lane * RG::LW * 4);  // [NS][SRS*MP]
     uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)32 * RG::LW * 4);
     if (!EXACT) {
         for (int j = 0; j < NS * RG::A_ST; ++j) a_ring[j] = S(0);
@@ -604,60 +616,60 @@ __global__ void __launch_bounds__(32)
             }
         }
     }
-    const int nblk = L / SR;
-#pragma unroll 1
-    for (int s = 0; s < NS - 1; ++s) {
-        if (s < nblk)
-            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + s * RG::A_ST, u_ring + s * SR, bars + s, a, u, M, L, s, active,
-                                               base, n);
-        else
-            cp_async_commit();
-    }
+    const int nblk = L / SRS;
+    S ucur[SRS], unxt[SRS];
+    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n);
+    rec_load_inputs<S, BWD>(ucur, u, L, 0, active, base, n);
 #pragma unroll 1
     for (int s = 0; s < nblk; ++s) {
-        const int slot = s % NS;
-        const int ahead = s + NS - 1;
-        if (ahead < nblk)
-            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + (ahead % NS) * RG::A_ST, u_ring + (ahead % NS) * SR,
-                                               bars + ahead % NS, a, u, M, L, ahead, active, base, n);
-        else
+        const int slot = s & 1;
+        const bool more = s + 1 < nblk;
+        if (more) {
+            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + (slot ^ 1) * RG::A_ST, bars + (slot ^ 1), a, M, L, s + 1, active,
+                                               base, n);
+            rec_load_inputs<S, BWD>(unxt, u, L, s + 1, active, base, n);
+        } else {
             cp_async_commit();
-        cp_async_wait<NS - 1>();
-        if (!mbar_wait_warp(bars + slot, (s / NS) & 1, kWaitLimit)) {
+        }
+        cp_async_wait<1>();
+        if (!mbar_wait_warp(bars + slot, (s >> 1) & 1, kWaitLimit)) {
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
-            for (int s2 = s + 1; s2 < s + NS && s2 < nblk; ++s2)
-                mbar_wait_warp(bars + s2 % NS, (s2 / NS) & 1, kWaitLimit);
+            if (more) mbar_wait_warp(bars + (slot ^ 1), ((s + 1) >> 1) & 1, kWaitLimit);
             cp_async_wait<0>();
             return;
         }
         __syncwarp();
         const S *ar = a_ring + slot * RG::A_ST;
-        const S *ur = u_ring + slot * SR;
-        const int roff = BWD ? L - (s + 1) * SR : s * SR;
+        const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
 #pragma unroll
-        for (int pr = 0; pr < SR / 2; ++pr) {
-            // rows 2p, 2p+1 of the stage; the adjoint runs the pairs, and the
-            // rows inside a pair, in reverse
-            const int p = BWD ? SR / 2 - 1 - pr : pr;
-            S c0[MP], c1[MP];
-            load_pair_smem<S, MP>(c0, c1, ar + 2 * p * MP);
-            const S u0 = ur[2 * p], u1 = ur[2 * p + 1];
-            const int r0 = roff + 2 * p;
-            if constexpr (MODE == FWD_RERUN) {
-                const S y0 = fwd_step_win<S, MP, WIN>(h, c0, u0, 2 * p);
-                const S y1 = fwd_step_win<S, MP, WIN>(h, c1, u1, 2 * p + 1);
-                if (r0 < n) out[base + r0] = y0;
-                if (r0 + 1 < n) out[base + r0 + 1] = y1;
-            } else {
-                const S y1 = bwd_step_win<S, MP, WIN>(h, c1, u1, 2 * pr);
-                const S y0 = bwd_step_win<S, MP, WIN>(h, c0, u0, 2 * pr + 1);
-                if constexpr (MODE == BWD_RERUN) {
-                    if (r0 + 1 < n) out[base + r0 + 1] = y1;
-                    if (r0 < n) out[base + r0] = y0;
+        for (int cb = 0; cb < SRS / SR; ++cb) {
+            const int rb = BWD ? (SRS / SR - 1 - cb) * SR : cb * SR;  // first stage row of the block
+#pragma unroll
+            for (int pr = 0; pr < SR / 2; ++pr) {
+                // rows rb+2p, rb+2p+1; the adjoint runs the pairs, and the
+                // rows inside a pair, in reverse
+                const int p = BWD ? SR / 2 - 1 - pr : pr;
+                const int r0 = rb + 2 * p;
+                S c0[MP], c1[MP];
+                load_pair_smem<S, MP>(c0, c1, ar + r0 * MP);
+                if constexpr (MODE == FWD_RERUN) {
+                    const S y0 = fwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * p);
+                    const S y1 = fwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * p + 1);
+                    if (roff + r0 < n) out[base + roff + r0] = y0;
+                    if (roff + r0 + 1 < n) out[base + roff + r0 + 1] = y1;
+                } else {
+                    const S y1 = bwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * pr);
+                    const S y0 = bwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * pr + 1);
+                    if constexpr (MODE == BWD_RERUN) {
+                        if (roff + r0 + 1 < n) out[base + roff + r0 + 1] = y1;
+                        if (roff + r0 < n) out[base + roff + r0] = y0;
+                    }
                 }
             }
+            slide<S, MP, WIN>(h);
         }
-        slide<S, MP, WIN>(h);
+#pragma unroll
+        for (int r = 0; r < SRS; ++r) ucur[r] = unxt[r];
         __syncwarp();
     }
     cp_async_wait<0>();
@@ -694,8 +706,8 @@ __global__ void __launch_bounds__(32)
 //   k2_expand  one warp per group: runs the group's chunks from its incoming
 //              state and writes each chunk's incoming state X (and, in the
 //              forward, the checkpoints).
-// Maps reach shared memory through a ring of NSLOT slots per warp filled by
-// bulk (TMA) copies NSLOT-1 maps ahead.
+// Maps reach shared memory through a ring per warp filled by bulk (TMA)
+// copies; when it holds a warp's whole sequence, all copies go out at once.
 // Chunk map layout (stride YS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
 // ---------------------------------------------------------------------------
 enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2 };
@@ -705,9 +717,6 @@ template <typename S, int MP> struct ScanGeo {
     static constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
     static constexpr int SLOT = YS + ZS;  // a map and, for the adjoint, its z
     static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte maps");
-    template <int NSLOT> __host__ __device__ static constexpr size_t warp_bytes() {
-        return ((NSLOT * SLOT * sizeof(S) + NSLOT * 8 + 127) / 128) * 128;
-    }
 };
 
 // x_new[lane] = p[0] + sum_{r=1..MP} p[r] * x[r-1], x held one component per lane
@@ -740,30 +749,31 @@ __device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv
     }
 }
 
-// A warp's ring of NSLOT map slots filled by bulk copies.  Item i of the
-// warp's sequence goes to slot i % NSLOT; its map comes from `map(i)` and,
-// when `with_z`, a z vector from `zvec(i)`.
-template <typename S, int MP, int NSLOT> struct MapRing {
+// A warp's ring of `nslot` map slots filled by bulk copies.  Item i of the
+// warp's sequence goes to slot i % nslot; its map comes from `map` and, for
+// the adjoint, a z vector from `zvec`.  When the ring holds every item of the
+// sequence, everything is issued up front and no slot is reused.
+template <typename S, int MP> struct MapRing {
     using SG = ScanGeo<S, MP>;
     S *ring;
     uint64_t *bars;
-    int lane;
-    __device__ void init(unsigned char *base, int lane_) {
+    int lane, nslot;
+    __device__ void init(unsigned char *base, int lane_, int nslot_) {
+        nslot = nslot_;
         ring = reinterpret_cast<S *>(base);
-        bars = reinterpret_cast<uint64_t *>(base + NSLOT * SG::SLOT * sizeof(S));
+        bars = reinterpret_cast<uint64_t *>(base + (size_t)nslot * SG::SLOT * sizeof(S));
         lane = lane_;
         if (lane == 0) {
-            for (int s = 0; s < NSLOT; ++s) mbar_init(bars + s, 1);
+            for (int s = 0; s < nslot; ++s) mbar_init(bars + s, 1);
             mbar_init_fence();
         }
         __syncwarp();
     }
     __device__ void issue(int i, const S *map, const S *zvec) {
-        const int sl = i % NSLOT;
+        const int sl = i % nslot;
         if (lane == 0) {
             const unsigned bytes = SG::YS * sizeof(S) + (zvec ? SG::ZS * sizeof(S) : 0);
             mbar_arrive_expect_tx(bars + sl, bytes);
-            fence_proxy_async();
             bulk_load(ring + sl * SG::SLOT, map, SG::YS * sizeof(S), bars + sl);
             if (zvec) bulk_load(ring + sl * SG::SLOT + SG::YS, zvec, SG::ZS * sizeof(S), bars + sl);
         }
@@ -771,24 +781,26 @@ template <typename S, int MP, int NSLOT> struct MapRing {
     // nullptr when the wait gave up; the copies still in flight (items
     // i+1 .. issued-1) then get a bounded chance to land before the warp leaves
     __device__ const S *wait(int i, int issued, int *status) {
-        const int sl = i % NSLOT;
-        if (!mbar_wait_warp(bars + sl, (i / NSLOT) & 1, kWaitLimit)) {
+        const int sl = i % nslot;
+        if (!mbar_wait_warp(bars + sl, (i / nslot) & 1, kWaitLimit)) {
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
-            for (int k = i + 1; k < issued; ++k) mbar_wait_warp(bars + k % NSLOT, (k / NSLOT) & 1, kWaitLimit);
+            for (int k = i + 1; k < issued; ++k) mbar_wait_warp(bars + k % nslot, (k / nslot) & 1, kWaitLimit);
             return nullptr;
         }
         return ring + sl * SG::SLOT;
     }
 };
+// bytes of a warp's ring of `nslot` slots (128-byte multiple)
+template <typename S, int MP> __host__ __device__ constexpr size_t ring_bytes(int nslot) {
+    return ((size_t(nslot) * ScanGeo<S, MP>::SLOT * sizeof(S) + size_t(nslot) * 8 + 127) / 128) * 128;
+}
 
 constexpr int kScanWarps = 4;  // warps per block of k2_group / k2_expand
-constexpr int kGroupSlots = 4;
-constexpr int kChainSlots = 8;
 
 template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(kScanWarps * 32)
-    k2_group(int64_t nC, int G2, int nG, int64_t n_items, const S *__restrict__ Y, const S *__restrict__ Z,
-             S *__restrict__ GY, S *__restrict__ GZ, int *__restrict__ status) {
+    k2_group(int64_t nC, int G2, int nG, int64_t n_items, int nslot, const S *__restrict__ Y,
+             const S *__restrict__ Z, S *__restrict__ GY, S *__restrict__ GZ, int *__restrict__ status) {
     using SG = ScanGeo<S, MP>;
     constexpr int YS = SG::YS, ZS = SG::ZS;
     constexpr bool REV = MODE != CH_FWD;
@@ -799,8 +811,8 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     if (item >= n_items) return;
     const int64_t b = item / nG;
     const int g = (int)(item - b * nG);
-    MapRing<S, MP, kGroupSlots> R;
-    R.init(k2g_smem + (size_t)warp * SG::template warp_bytes<kGroupSlots>(), lane);
+    MapRing<S, MP> R;
+    R.init(k2g_smem + (size_t)warp * ring_bytes<S, MP>(nslot), lane, nslot);
     const int64_t c_lo = (int64_t)g * G2;
     const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
     auto chunk_at = [&](int i) -> int64_t { return b * nC + (REV ? c_lo + len - 1 - i : c_lo + i); };
@@ -811,7 +823,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
             issued = i + 1;
         }
     };
-    for (int i = 0; i < kGroupSlots - 1; ++i) issue(i);
+    for (int i = 0; i < nslot - 1 || (nslot >= len && i < len); ++i) issue(i);
     const int j0 = lane < MP ? lane : 0;
     if constexpr (TRANS) {
         S zeta = S(0);
@@ -821,7 +833,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
             S p[MP + 1];
             map_cols<S, MP, true>(p, m, m + YS, j0);
             __syncwarp();
-            issue(i + kGroupSlots - 1);
+            if (nslot < len) issue(i + nslot - 1);
             zeta = hop<S, MP>(p, zeta, lane);
         }
         if (lane < MP) GZ[item * ZS + lane] = zeta;
@@ -858,7 +870,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
                 }
             }
             __syncwarp();
-            issue(i + kGroupSlots - 1);
+            if (nslot < len) issue(i + nslot - 1);
             yv = hop<S, MP>(p, yv, lane);
 #pragma unroll
             for (int k = 0; k < MP; ++k) col[k] = acc[k];
@@ -873,7 +885,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
 
 template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(32)
-    k2_chain(int M, int nG, const S *__restrict__ GY, const S *__restrict__ GZ, const S *__restrict__ zi,
+    k2_chain(int M, int nG, int nslot, const S *__restrict__ GY, const S *__restrict__ GZ, const S *__restrict__ zi,
              S *__restrict__ GX, int *__restrict__ status) {
     using SG = ScanGeo<S, MP>;
     constexpr int YS = SG::YS, ZS = SG::ZS;
@@ -882,8 +894,8 @@ __global__ void __launch_bounds__(32)
     extern __shared__ __align__(128) unsigned char k2c_smem[];
     const int lane = threadIdx.x & 31;
     const int64_t b = blockIdx.x;
-    MapRing<S, MP, kChainSlots> R;
-    R.init(k2c_smem, lane);
+    MapRing<S, MP> R;
+    R.init(k2c_smem, lane, nslot);
     auto gof = [&](int n) -> int64_t { return b * nG + (REV ? nG - 1 - n : n); };
     int issued = 0;
     auto issue = [&](int n) {
@@ -893,7 +905,7 @@ __global__ void __launch_bounds__(32)
             issued = n + 1;
         }
     };
-    for (int n = 0; n < kChainSlots - 1; ++n) issue(n);
+    for (int n = 0; n < nslot - 1 || (nslot >= nG - 1 && n < nG - 1); ++n) issue(n);
     const int j0 = lane < MP ? lane : 0;
     S x = S(0);
     if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
@@ -905,15 +917,16 @@ __global__ void __launch_bounds__(32)
         S p[MP + 1];
         map_cols<S, MP, TRANS>(p, m, m + YS, j0);
         __syncwarp();
-        issue(n + kChainSlots - 1);
+        if (nslot < nG - 1) issue(n + nslot - 1);
         x = hop<S, MP>(p, x, lane);
     }
 }
 
 template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(kScanWarps * 32)
-    k2_expand(int M, int64_t nC, int G2, int nG, int64_t n_items, const S *__restrict__ Y, const S *__restrict__ Z,
-              const S *__restrict__ GX, S *__restrict__ X, S *__restrict__ ckpt, int *__restrict__ status) {
+    k2_expand(int M, int64_t nC, int G2, int nG, int64_t n_items, int nslot, const S *__restrict__ Y,
+              const S *__restrict__ Z, const S *__restrict__ GX, S *__restrict__ X, S *__restrict__ ckpt,
+              int *__restrict__ status) {
     using SG = ScanGeo<S, MP>;
     constexpr int YS = SG::YS, ZS = SG::ZS;
     constexpr bool REV = MODE != CH_FWD;
@@ -924,8 +937,8 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     if (item >= n_items) return;
     const int64_t b = item / nG;
     const int g = (int)(item - b * nG);
-    MapRing<S, MP, kGroupSlots> R;
-    R.init(k2e_smem + (size_t)warp * SG::template warp_bytes<kGroupSlots>(), lane);
+    MapRing<S, MP> R;
+    R.init(k2e_smem + (size_t)warp * ring_bytes<S, MP>(nslot), lane, nslot);
     const int64_t c_lo = (int64_t)g * G2;
     const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
     auto chunk_at = [&](int i) -> int64_t { return REV ? c_lo + len - 1 - i : c_lo + i; };
@@ -937,7 +950,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
             issued = i + 1;
         }
     };
-    for (int i = 0; i < kGroupSlots - 1; ++i) issue(i);
+    for (int i = 0; i < nslot - 1 || (nslot >= len - 1 && i < len - 1); ++i) issue(i);
     const int j0 = lane < MP ? lane : 0;
     S x = lane < MP ? GX[item * ZS + lane] : S(0);
     for (int i = 0; i < len; ++i) {
@@ -950,7 +963,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         S p[MP + 1];
         map_cols<S, MP, TRANS>(p, m, m + YS, j0);
         __syncwarp();
-        issue(i + kGroupSlots - 1);
+        if (nslot < len - 1) issue(i + nslot - 1);
         x = hop<S, MP>(p, x, lane);
     }
 }

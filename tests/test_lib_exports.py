@@ -46,7 +46,7 @@ def test_host_only_entry_points(lib):
     for code in (0, -1, -2, -3, -4, -5):
         assert _lib.strerror(code)
     L = _lib.lp_tv_pick_chunk(32, 48000, 22)
-    assert L > 0 and L % 8 == 0
+    assert L > 0 and L % 16 == 0
     assert _lib.lp_tv_num_chunks(48000, 22, L) == -(-48000 // L)
     assert _lib.lp_tv_workspace_bytes(32, 48000, 22, L) > 0
     assert _lib.lp_tv_workspace_bytes(-1, 10, 2) == 0
