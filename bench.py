@@ -249,8 +249,15 @@ def run_ours(args):
     bwd_flags = _lib.LP_BWD_REUSE_FORWARD if args.algo == "chunked" else 0
     names_f = KERNELS_FWD if args.algo == "chunked" else KERNELS_PLAIN_FWD
     names_b = KERNELS_BWD if args.algo == "chunked" else KERNELS_PLAIN_BWD
-    ev_f = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(names_f))]
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(names_b))]
+    def timing_event():
+        # external events are recorded by every replay of a captured graph
+        try:
+            return torch.cuda.Event(enable_timing=True, external=True)
+        except TypeError:
+            return torch.cuda.Event(enable_timing=True)
+
+    ev_f = [timing_event() for _ in range(2 * len(names_f))]
+    ev_b = [timing_event() for _ in range(2 * len(names_b))]
 
     def step(profile):
         sp = torch.cuda.current_stream(dev).cuda_stream  # the capture stream while a graph is captured
@@ -286,8 +293,7 @@ def run_ours(args):
             torch.cuda.synchronize()
     torch.cuda.synchronize()
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0, ev1 = timing_event(), timing_event()
     step_ms, kern_ms = [], {k: [] for k in names_f + names_b}
 
     # one step (forward + adjoint, with the per-kernel timing events) captured

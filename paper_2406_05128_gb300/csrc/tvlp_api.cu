@@ -35,7 +35,14 @@ thread_local int g_prof_n = 0;
 void profile_mark(int k, bool end, cudaStream_t st) {
     if (g_prof_events == nullptr || k < 0 || k >= g_prof_n) return;
     cudaEvent_t ev = static_cast<cudaEvent_t>(g_prof_events[2 * k + (end ? 1 : 0)]);
-    if (ev != nullptr) cudaEventRecord(ev, st);
+    if (ev == nullptr) return;
+    // while the stream is being captured into a graph, record the event as an
+    // external node so each replay records it
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
 }
 }  // namespace tvlp
 
