@@ -61,7 +61,8 @@ enum {
     LP_EUNSUPPORTED = -2, /* order M beyond what this build supports     */
     LP_EWORKSPACE = -3,   /* workspace NULL, too small or misaligned      */
     LP_ECUDA = -4,        /* a CUDA launch or runtime call failed         */
-    LP_EALIGN = -5        /* a data pointer is not aligned to its type    */
+    LP_EALIGN = -5,       /* a data pointer is not aligned to its type    */
+    LP_ETOOBIG = -6       /* problem too large for the fixed scratch      */
 };
 
 enum { LP_DTYPE_F32 = 0, LP_DTYPE_F64 = 1 };
@@ -166,6 +167,32 @@ int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs,
  * when `reset` is non-zero.  Returns the status or LP_ECUDA.
  */
 int lp_tv_device_status(int reset);
+
+/*
+ * Allocation-free forward filter (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory when they run the filter, such
+ * as a real-time audio callback that must not wait on the CUDA allocator or
+ * a plugin whose host application owns the GPU memory budget).
+ *
+ * Same arguments, layouts and results as lp_tv_forward_f32 with chunk = 0
+ * and the chunked algorithm, but no workspace: the scan's scratch data live
+ * in an array of LP_NOALLOC_SCRATCH_BYTES compiled into the library.  Every
+ * GPU that loads the library holds that array until the process exits.
+ * - Problems whose scratch (lp_tv_workspace_bytes(B, T, M, 0, LP_DTYPE_F32))
+ *   exceeds LP_NOALLOC_SCRATCH_BYTES are rejected with LP_ETOOBIG before any
+ *   work is enqueued; order limits are those of lp_tv_forward_f32.
+ * - The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ *   library routine.
+ * - The first call on a device looks up the array's device address for that
+ *   device; make that first call before any stream capture on the device.
+ * - All calls share the one array, which keeps what the last call wrote:
+ *   calls that may overlap on the GPU (different streams, no ordering
+ *   between them) race on it and must be serialised by the caller.
+ */
+#define LP_NOALLOC_SCRATCH_BYTES (32u << 20)
+int lp_tv_forward_noalloc_f32(int B, int64_t T, int M, const float *a,
+                              const float *e, const float *zi, float *s,
+                              void *stream);
 
 #ifdef __cplusplus
 }

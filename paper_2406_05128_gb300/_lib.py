@@ -18,6 +18,8 @@ LP_EUNSUPPORTED = -2
 LP_EWORKSPACE = -3
 LP_ECUDA = -4
 LP_EALIGN = -5
+LP_ETOOBIG = -6
+LP_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 LP_DTYPE_F32 = 0
 LP_DTYPE_F64 = 1
@@ -30,7 +32,7 @@ EXPORTS = (
     "lp_strerror", "lp_version", "lp_tv_pick_chunk", "lp_tv_num_chunks",
     "lp_tv_workspace_bytes", "lp_tv_forward_f32", "lp_tv_forward_f64",
     "lp_tv_backward_f32", "lp_tv_backward_f64", "lp_tv_set_profile_events",
-    "lp_tv_device_status",
+    "lp_tv_device_status", "lp_tv_forward_noalloc_f32",
 )
 
 LP_BWD_REUSE_FORWARD = 1
@@ -71,6 +73,8 @@ def _declare(lib):
         f = getattr(lib, name)
         f.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]
         f.restype = i32
+    lib.lp_tv_forward_noalloc_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp]
+    lib.lp_tv_forward_noalloc_f32.restype = i32
     lib.lp_tv_device_status.argtypes = [i32]
     lib.lp_tv_device_status.restype = i32
     lib.lp_tv_set_profile_events.argtypes = [c.POINTER(vp), i32]
@@ -142,6 +146,11 @@ def lp_tv_backward(dtype: int, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, 
     """Raw backward call; pointers are ints (device addresses) or None."""
     fn = load().lp_tv_backward_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_backward_f64
     _check(fn(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, flags, ws, ws_bytes, stream), "lp_tv_backward")
+
+
+def lp_tv_forward_noalloc_f32(B, T, M, a, e, zi, s, stream):
+    """Raw allocation-free forward call (FP32); pointers are ints or None."""
+    _check(load().lp_tv_forward_noalloc_f32(B, T, M, a, e, zi, s, stream), "lp_tv_forward_noalloc_f32")
 
 
 def lp_tv_device_status(reset: bool = False) -> int:

@@ -45,6 +45,7 @@ def _units():
             units.append((os.path.join(CSRC, "tvlp_inst.cu"), obj,
                           [f"-DTVLP_SCALAR={scalar}", f"-DTVLP_MP={mp}"]))
     units.append((os.path.join(CSRC, "tvlp_api.cu"), os.path.join(BUILD, "tvlp_api.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_noalloc.cu"), os.path.join(BUILD, "tvlp_noalloc.o"), []))
     return units
 
 

@@ -337,6 +337,7 @@ const char *lp_strerror(int code) {
         case LP_EWORKSPACE: return "workspace missing, too small or not 256-byte aligned";
         case LP_ECUDA: return "CUDA launch or runtime call failed";
         case LP_EALIGN: return "data pointer not aligned to its element type";
+        case LP_ETOOBIG: return "problem needs more scratch than the fixed no-allocation array holds";
     }
     return "unknown error code";
 }
