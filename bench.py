@@ -38,8 +38,8 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd Msamples/s at M=22 vs plain sequential kernel (<=1e-4 rel); serving p99"
 UNIT = "Msamples/s"
 WORKLOAD = "batched forward+backward time-varying LP, B=32, T=48000, M=22, FP32"
-KERNELS_FWD = ("fwd_summary", "fwd_group", "fwd_chain", "fwd_expand", "fwd_rerun")
-KERNELS_BWD = ("bwd_zero_state", "bwd_group", "bwd_chain", "bwd_expand", "bwd_rerun", "grad_a")
+KERNELS_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun")
+KERNELS_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun", "grad_a")
 KERNELS_PLAIN_FWD = ("plain_fwd",)
 KERNELS_PLAIN_BWD = ("plain_bwd", "grad_a")
 L2_FLUSH_BYTES = 256 << 20

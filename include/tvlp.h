@@ -88,12 +88,11 @@ enum {
  * (passed as void*) created by the caller.  While installed, every later
  * forward/backward call made from the calling thread records events[2k]
  * just before and events[2k+1] just after its k-th kernel launch (k < n) on
- * the call's stream.  Kernel order: forward (chunked) summary, group maps,
- * group chain, chunk states, re-run; backward (chunked) zero-state summary
- * (or full summary without LP_BWD_REUSE_FORWARD), group maps, group chain,
- * chunk states, re-run, coefficient gradient; the plain algorithm launches
- * re-run (and coefficient gradient).  NULL
- * uninstalls the hook.  The library neither creates nor destroys events.
+ * the call's stream.  Kernel order: forward (chunked) summary, scan,
+ * re-run; backward (chunked) zero-state summary (or full summary without
+ * LP_BWD_REUSE_FORWARD), scan, re-run, coefficient gradient; the plain
+ * algorithm launches re-run (and coefficient gradient).  NULL uninstalls the
+ * hook.  The library neither creates nor destroys events.
  */
 int lp_tv_set_profile_events(void **events, int n);
 
@@ -162,7 +161,8 @@ int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs,
 /*
  * Device status word of the current device: 0 while every bounded wait
  * inside the kernels completed, 1 once a shared-memory bulk-copy wait gave
- * up (the kernel then stopped early and its outputs are not valid).  Reads
+ * up, 2 once a scan wait for other warps' results gave up (the kernel then
+ * stopped early and its outputs are not valid).  Reads
  * it synchronously (waits for the device's outstanding work) and clears it
  * when `reset` is non-zero.  Returns the status or LP_ECUDA.
  */

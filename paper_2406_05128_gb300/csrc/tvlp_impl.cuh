@@ -45,7 +45,12 @@ template <typename S, int MP> struct Launch {
         return reinterpret_cast<S *>(static_cast<char *>(ws) + ws_offset(p, sizeof(S), r));
     }
 
-    template <bool BWD> static cudaError_t summary(const Problem &p, const S *a, const S *u, S *Y, cudaStream_t st) {
+    static unsigned *counters(const Problem &p, void *ws) {
+        return reinterpret_cast<unsigned *>(static_cast<char *>(ws) + ws_offset(p, sizeof(S), 7));
+    }
+
+    template <bool BWD>
+    static cudaError_t summary(const Problem &p, const S *a, const S *u, S *Y, unsigned *cnt, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         const int W = k1_warps_per_block<S, MP>();
         const size_t smem = (size_t)W * GE::WARP_BYTES;
@@ -54,56 +59,56 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         const int64_t per_block = (int64_t)W * GE::CPW;
         const int64_t grid = (p.NQ + per_block - 1) / per_block;
-        kern<<<(unsigned)grid, 32 * W, smem, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Y, p.M == MP ? 1 : 0, p.status);
+        kern<<<(unsigned)grid, 32 * W, smem, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Y, p.M == MP ? 1 : 0, cnt, p.B,
+                                                   p.status);
         return cudaGetLastError();
     }
 
-    // ring slots for a warp that waits on `need` maps: all of them when they
-    // fit in `budget` bytes, else a ring of at least two
-    static int ring_slots(int64_t need, size_t budget) {
-        int64_t fit = 2;
-        while (fit < need && ring_bytes<S, MP>((int)fit + 1) <= budget) ++fit;
-        return (int)(need < 1 ? 1 : (need <= fit ? need : fit));
-    }
-
-    // two-level scan: group maps, group chain, chunk states
-    template <int MODE> static cudaError_t scan(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, S *GX,
-                                                const S *zi, S *X, S *ckpt, cudaStream_t st, int k0) {
-        static bool done_g[kMaxDevices] = {}, done_c[kMaxDevices] = {}, done_e[kMaxDevices] = {};
+    // Two-level scan in one cooperative launch: as many blocks as the items
+    // need, at most as many as fit on the device at once.
+    template <int MODE>
+    static cudaError_t scan(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, S *GX, const S *zi, S *X,
+                            S *ckpt, unsigned *cnt, cudaStream_t st) {
+        static bool done[kMaxDevices] = {};
+        static int resident[kMaxDevices] = {};
+        using SG = ScanGeo<S, MP>;
+        auto kern = k2_scan<S, MP, MODE>;
+        const size_t smem = (size_t)kScanWarps * SG::WARP_BYTES;
+        cudaError_t err = allow_smem(kern, smem, done);
+        if (err != cudaSuccess) return err;
+        int dev = 0;
+        if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+        if (resident[dev] == 0) {
+            int per_sm = 0, sms = 0;
+            if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScanWarps * 32, smem)) !=
+                cudaSuccess)
+                return err;
+            if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            resident[dev] = per_sm * sms;
+        }
         const int64_t items = (int64_t)p.B * p.nG;
-        const int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
-        const int ns_g = ring_slots(p.G2, kSmemBudget / kScanWarps);
-        const int ns_c = ring_slots(p.nG - 1, kSmemBudget);
-        const int ns_e = ring_slots(p.G2 - 1, kSmemBudget / kScanWarps);
-        const size_t smem_g = kScanWarps * ring_bytes<S, MP>(ns_g);
-        const size_t smem_c = ring_bytes<S, MP>(ns_c);
-        const size_t smem_e = kScanWarps * ring_bytes<S, MP>(ns_e);
-        cudaError_t err;
-        auto kg = k2_group<S, MP, MODE>;
-        auto kc = k2_chain<S, MP, MODE>;
-        auto ke = k2_expand<S, MP, MODE>;
-        if ((err = allow_smem(kg, kSmemBudget, done_g)) != cudaSuccess) return err;
-        if ((err = allow_smem(kc, kSmemBudget, done_c)) != cudaSuccess) return err;
-        if ((err = allow_smem(ke, kSmemBudget, done_e)) != cudaSuccess) return err;
-        profile_mark(k0, false, st);
-        kg<<<(unsigned)blocks, kScanWarps * 32, smem_g, st>>>(p.nC, p.G2, p.nG, items, ns_g, Y, Z, GY, GZ, p.status);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        profile_mark(k0, true, st);
-        profile_mark(k0 + 1, false, st);
-        kc<<<(unsigned)p.B, 32, smem_c, st>>>(p.M, p.nG, ns_c, GY, GZ, zi, GX, p.status);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        profile_mark(k0 + 1, true, st);
-        profile_mark(k0 + 2, false, st);
-        ke<<<(unsigned)blocks, kScanWarps * 32, smem_e, st>>>(p.M, p.nC, p.G2, p.nG, items, ns_e, Y, Z, GX, X, ckpt,
-                                                              p.status);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        profile_mark(k0 + 2, true, st);
-        return cudaSuccess;
+        int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
+        if (blocks > resident[dev]) blocks = resident[dev];
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(kScanWarps * 32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const int M = p.M, B = p.B, G2 = p.G2, nG = p.nG;
+        const int64_t nC = p.nC;
+        int *status = p.status;
+        return cudaLaunchKernelEx(&cfg, kern, M, nC, G2, nG, B, Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, status);
     }
 
     template <int MODE, bool EXACT>
     static cudaError_t rec_exact(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                                 S *gzi, int reverse, cudaStream_t st) {
+                                 S *gzi, int reverse, unsigned *cnt, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         using RG = RecGeo<S, MP>;
         auto kern = k_rec<S, MP, EXACT, MODE>;
@@ -111,15 +116,16 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + 31) / 32;
         kern<<<(unsigned)grid, 32, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
-                                                   p.status);
+                                                   cnt, p.B, p.status);
         return cudaGetLastError();
     }
 
+    // one recursion per chunk; `cnt`, when given, is zeroed for a scan that follows
     template <int MODE>
     static cudaError_t rec(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                           S *gzi, int reverse, cudaStream_t st) {
-        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, st);
-        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, st);
+                           S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr) {
+        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, st);
+        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, st);
     }
 
     static cudaError_t grad_a(const Problem &p, const S *ge, const S *s, const S *zi, S *ga, cudaStream_t st) {
@@ -167,11 +173,12 @@ int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, 
     S *X = LN::region(p, ws, 1);
     S *GY = LN::region(p, ws, 4);
     S *GX = LN::region(p, ws, 6);
-    TVLP_LAUNCH(0, (LN::template summary<false>(p, a, e, Y, st)));
-    if (LN::template scan<CH_FWD>(p, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, st, 1) != cudaSuccess) return ECUDA;
+    unsigned *cnt = LN::counters(p, ws);
+    TVLP_LAUNCH(0, (LN::template summary<false>(p, a, e, Y, cnt, st)));
+    TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
     // the re-run walks the chunks in reverse so it starts on rows the
     // summary pass loaded last
-    TVLP_LAUNCH(4, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
+    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
     return OK;
 }
 
@@ -189,19 +196,18 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
         S *GY = LN::region(p, ws, 4);
         S *GZ = LN::region(p, ws, 5);
         S *GX = LN::region(p, ws, 6);
+        unsigned *cnt = LN::counters(p, ws);
         if (flags & BWD_REUSE_FORWARD) {
             // forward transfers P_c (and their group compositions) are in the
             // workspace: the adjoint needs one zero-state recursion per chunk,
             // then w_{c-1} = P_c^T w_c + z_c
-            TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st)));
-            if (LN::template scan<CH_TRANS>(p, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, st, k) != cudaSuccess)
-                return ECUDA;
+            TVLP_LAUNCH(k++,
+                        (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st, cnt)));
+            TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS>(p, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
         } else {
-            TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, st)));
-            if (LN::template scan<CH_BWD>(p, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, st, k) != cudaSuccess)
-                return ECUDA;
+            TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, cnt, st)));
+            TVLP_LAUNCH(k++, (LN::template scan<CH_BWD>(p, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt, st)));
         }
-        k += 3;
         TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st)));
     }
     if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(p, ge, s, zi, ga, st)));

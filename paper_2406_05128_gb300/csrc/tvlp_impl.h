@@ -15,7 +15,7 @@ struct Problem {
     int64_t T;    // samples per signal
     int M;        // real order (1..MP)
     int MP;       // padded order (template parameter of the kernels)
-    int L;        // chunk length, a multiple of MP
+    int L;        // chunk length, a multiple of 16
     int64_t nC;   // chunks per signal
     int64_t NQ;   // B * nC
     int G2;       // chunks per group of the two-level scan
@@ -46,7 +46,8 @@ enum { OK = 0, EINVAL_ = -1, EUNSUPPORTED = -2, EWORKSPACE = -3, ECUDA = -4, EAL
 enum { ALGO_CHUNKED = 0, ALGO_PLAIN = 1 };
 enum { BWD_REUSE_FORWARD = 1 };
 
-// Workspace regions (each 256-byte aligned), in elements of the scalar:
+// Workspace regions (each 256-byte aligned), in elements of the scalar
+// (RS = MP padded to 16 bytes, YS = (MP+1)*RS, ZS = RS):
 //   0 Y  [NQ][YS]     chunk maps (forward; the adjoint's own when it
 //                     cannot reuse the forward's)
 //   1 X  [NQ][MP]     forward incoming state of every chunk
@@ -55,17 +56,21 @@ enum { BWD_REUSE_FORWARD = 1 };
 //   4 GY [B*nG][YS]   group maps of the two-level scan
 //   5 GZ [B*nG][ZS]   adjoint group zero-state summaries
 //   6 GX [B*nG][ZS]   incoming state of every group
-inline size_t ys_elems(int MP, size_t sz) { return (((size_t)(MP + 1) * MP * sz + 15) / 16) * 16 / sz; }
-inline size_t zs_elems(int MP, size_t sz) { return (((size_t)MP * sz + 15) / 16) * 16 / sz; }
+//   7 CNT [B][32]     scan progress per signal (unsigned, one 128-byte
+//                     line each), zeroed by the kernel before each scan
+inline size_t rs_elems(int MP, size_t sz) { return (((size_t)MP * sz + 15) / 16) * 16 / sz; }
+inline size_t ys_elems(int MP, size_t sz) { return (size_t)(MP + 1) * rs_elems(MP, sz); }
+inline size_t zs_elems(int MP, size_t sz) { return rs_elems(MP, sz); }
 inline size_t ws_offset(const Problem &p, size_t sz, int region) {
-    const size_t rows[7] = {(size_t)p.NQ * ys_elems(p.MP, sz), (size_t)p.NQ * p.MP, (size_t)p.NQ * zs_elems(p.MP, sz),
-                            (size_t)p.NQ * p.MP, (size_t)p.B * p.nG * ys_elems(p.MP, sz),
-                            (size_t)p.B * p.nG * zs_elems(p.MP, sz), (size_t)p.B * p.nG * zs_elems(p.MP, sz)};
+    const size_t rows[8] = {(size_t)p.NQ * ys_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
+                            (size_t)p.NQ * zs_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
+                            (size_t)p.B * p.nG * ys_elems(p.MP, sz), (size_t)p.B * p.nG * zs_elems(p.MP, sz),
+                            (size_t)p.B * p.nG * zs_elems(p.MP, sz), ((size_t)p.B * 32 * sizeof(unsigned) + sz - 1) / sz};
     size_t off = 0;
     for (int r = 0; r < region; ++r) off += align256(rows[r] * sz);
     return off;
 }
-inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 7); }
+inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 8); }
 
 // Records the caller's profiling event for kernel k (begin or end) when a
 // hook is installed on this thread (lp_tv_set_profile_events).

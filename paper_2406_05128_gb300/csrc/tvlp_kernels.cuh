@@ -25,10 +25,9 @@
 //                   P_c).  Forward direction; also available backwards.
 //   k_rec (ZERO)    per chunk, one recursion from zero state; end state only
 //                   (the adjoint's zero-state summary z_c).
-//   k2_group/chain/expand
-//                   x_{c+1} = P_c x_c + y_c (forward) or
+//   k2_scan         x_{c+1} = P_c x_c + y_c (forward) or
 //                   w_{c-1} = P_c^T w_c + z_c (adjoint) per signal, as a
-//                   two-level scan over groups of chunks.
+//                   two-level scan over groups of chunks in one launch.
 //   k_rec (RERUN)   each chunk re-runs its recursion from its true incoming
 //                   state and writes s (forward) or ge (adjoint).  With one
 //                   chunk per signal this is the plain sequential filter.
@@ -53,7 +52,9 @@ constexpr int SR = 8;    // rows per compute block (register window)
 constexpr int SRS = 16;  // rows per staged copy; chunk lengths are multiples of SRS
 
 // Status codes written by kernels to the device status word.
-enum { DEV_OK = 0, DEV_TIMEOUT_TMA = 1 };
+enum { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_SCAN = 2 };
+
+constexpr int kCntStride = 32;  // scan counters sit 128 bytes apart, one L2 line each
 
 // Packing of the MP+1 summary recursions of one chunk onto G lanes with R
 // recursions per lane (G*R >= MP+1).  A warp holds 32/G chunks.
@@ -115,9 +116,11 @@ template <typename S, int MP, int G_, int R_> struct SumGeo {
     static_assert((A_STAGE * sizeof(S)) % 16 == 0 && (U_STAGE * sizeof(S)) % 16 == 0, "16-byte ring alignment");
     static_assert(RING_BYTES % 8 == 0 && WARP_BYTES % 16 == 0, "mbarrier and warp-slice alignment");
 };
-// per-chunk stride of the summaries Y[c][MP+1][MP], a multiple of 16 bytes
+// chunk summaries Y[c][MP+1][RS]: rows of MP values padded to RS, a 16-byte
+// multiple, so that every row starts 16-byte aligned (vector loads of a row)
 template <typename S, int MP> struct YGeo {
-    static constexpr int YS = (((MP + 1) * MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
+    static constexpr int RS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
+    static constexpr int YS = (MP + 1) * RS;
 };
 
 // ---------------------------------------------------------------------------
@@ -181,7 +184,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 }
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before a wait gives up
+constexpr int kWaitLimit = 1 << 18;  // mbarrier polls before a wait gives up (well under a second)
 
 // Load the MP coefficients of one shared-memory row (8-byte aligned for
 // float, 16-byte for double; MP is even) into registers.
@@ -355,13 +358,17 @@ __device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__rest
 template <typename S, int MP, int G, int R, bool BWD>
 __global__ void __launch_bounds__(256, 1)
     k1_summary(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
-               S *__restrict__ Y, int exact_flag, int *__restrict__ status) {
+               S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt,
+               int *__restrict__ status) {
     using GE = SumGeo<S, MP, G, R>;
     constexpr int CPW = GE::CPW, NS = GE::NS, WIN = MP + SR;
-    constexpr int YS = YGeo<S, MP>::YS;
+    constexpr int RS = YGeo<S, MP>::RS, YS = YGeo<S, MP>::YS;
     extern __shared__ __align__(128) unsigned char k1_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
+    // the scan that follows counts finished groups per signal from zero
+    if (scan_cnt != nullptr && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n_cnt * kCntStride; i += blockDim.x) scan_cnt[i] = 0u;
     const int64_t q0 = ((int64_t)blockIdx.x * wpb + warp) * CPW;
     if (q0 >= NQ) return;
     const bool exact = exact_flag != 0;
@@ -488,7 +495,9 @@ __global__ void __launch_bounds__(256, 1)
             const int r = g * R + k;
             if (r <= MP) {
 #pragma unroll
-                for (int j = 0; j < MP; ++j) yq[r * MP + j] = BWD ? h[k][j] : h[k][MP - 1 - j];
+                for (int j = 0; j < MP; ++j) yq[r * RS + j] = BWD ? h[k][j] : h[k][MP - 1 - j];
+#pragma unroll
+                for (int j = MP; j < RS; ++j) yq[r * RS + j] = S(0);
             }
         }
     }
@@ -566,12 +575,15 @@ template <typename S, int MP, bool EXACT, int MODE>
 __global__ void __launch_bounds__(32)
     k_rec(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
-          S *__restrict__ gzi, int reverse, int *__restrict__ status) {
+          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int *__restrict__ status) {
     using RG = RecGeo<S, MP>;
     constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
     extern __shared__ __align__(128) unsigned char rec_smem[];
     const int lane = threadIdx.x & 31;
+    // a scan that follows counts finished groups per signal from zero
+    if (scan_cnt != nullptr && blockIdx.x == 0)
+        for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int64_t q = blk * 32 + lane;
     const bool active = q < NQ;
@@ -690,33 +702,52 @@ __global__ void __launch_bounds__(32)
 }
 
 // ---------------------------------------------------------------------------
-// K2: cross-chunk scan in two levels.  Chunks are grouped G2 at a time by
-// chunk index (group g = chunks [g*G2, (g+1)*G2)).  Along the chain the
-// forward visits chunks and groups in increasing order, the adjoint in
-// decreasing order.
-//   k2_group   one warp per group (all signals at once):
-//              CH_FWD / CH_BWD: composes the group's chunk maps x -> P x + y
-//                into one map (Phi_g, y_g), stored in the chunk-map layout
-//                at GY;
-//              CH_TRANS: folds the adjoint's chunk maps w -> P^T w + z into
-//                the group's zero-state adjoint zeta_g (GZ); the group's
-//                transfer is the transpose of the forward's Phi_g.
-//   k2_chain   one warp per signal: chains the groups -> the incoming state
-//              of every group (GX).
-//   k2_expand  one warp per group: runs the group's chunks from its incoming
-//              state and writes each chunk's incoming state X (and, in the
-//              forward, the checkpoints).
-// Maps reach shared memory through a ring per warp filled by bulk (TMA)
-// copies; when it holds a warp's whole sequence, all copies go out at once.
-// Chunk map layout (stride YS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
+// K2: cross-chunk scan, one cooperative launch.  Chunks are grouped G2 at a
+// time by chunk index (group g = chunks [g*G2, (g+1)*G2)).  Along the chain
+// the forward visits chunks and groups in increasing order, the adjoint in
+// decreasing order.  Each warp owns items (b, g) and runs three phases:
+//   A   fold: CH_FWD / CH_BWD compose the group's chunk maps x -> P x + y
+//       into one map (Phi_g, y_g), stored in the chunk-map layout at GY;
+//       CH_TRANS folds the adjoint's chunk maps w -> P^T w + z into the
+//       group's zero-state adjoint zeta_g (GZ); the group's transfer is the
+//       transpose of the forward's Phi_g, which GY already holds.  A
+//       finished item bumps its signal's counter.
+//   B1  once all nG groups of signal b are counted, the warp owning (b, 0)
+//       chains the group maps (one hop each) and stores the incoming state
+//       of every group in GX; then bumps the counter once more.
+//   B2  each group runs one hop per chunk from its incoming state, writing
+//       every chunk's incoming state X (and, in the forward, the
+//       checkpoints).  A warp with a single item still holds that group's
+//       chunk maps in shared memory from phase A and reads none again.
+// Every warp finishes phase A before it waits, and all chain work (B1) comes
+// before any B2 wait; the launch is cooperative (every block resident), so
+// the waits always end; each one is also bounded.  Maps reach shared memory
+// through a per-warp ring of kScanDepth slots filled by 16-byte cp.async
+// copies (L2 only, so maps written by other SMs during the launch are read
+// fresh).
+// Chunk map layout (stride YS, rows of RS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
 // ---------------------------------------------------------------------------
 enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2 };
 
+constexpr int kScanWarps = 4;       // warps per block
+constexpr int kScanDepth = 10;      // map slots per warp ring
+constexpr int kScanSpin = 1 << 19;  // counter polls (~250 ns each) before a wait gives up
+
 template <typename S, int MP> struct ScanGeo {
+    static constexpr int RS = YGeo<S, MP>::RS;
     static constexpr int YS = YGeo<S, MP>::YS;
-    static constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
-    static constexpr int SLOT = YS + ZS;  // a map and, for the adjoint, its z
+    static constexpr int ZS = RS;         // a z vector: MP values padded to 16 bytes
+    // per warp: kScanDepth map slots, kScanDepth z slots, two mbarriers and
+    // two state-exchange buffers of RS values
+    static constexpr size_t MAPS_BYTES = size_t(kScanDepth) * YS * sizeof(S);
+    static constexpr size_t ZS_BYTES = size_t(kScanDepth) * ZS * sizeof(S);
+    static constexpr size_t BAR_OFF = MAPS_BYTES + ZS_BYTES;
+    static constexpr size_t XB_OFF = BAR_OFF + 16;
+    static constexpr size_t WARP_BYTES = ((XB_OFF + 2 * RS * sizeof(S) + 127) / 128) * 128;
     static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte maps");
+    static_assert(BAR_OFF % 16 == 0 && WARP_BYTES % 128 == 0, "aligned warp slices");
+    static_assert(RS <= 32, "a padded row fits the lanes of a warp");
+    static_assert(kScanDepth % 2 == 0, "two halves for double buffering");
 };
 
 // x_new[lane] = p[0] + sum_{r=1..MP} p[r] * x[r-1], x held one component per lane
@@ -739,232 +770,408 @@ __device__ __forceinline__ S hop(const S (&p)[MP + 1], S x, int lane) {
 // P from the map at m, z at zv)
 template <typename S, int MP, bool TRANS>
 __device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv, int j0) {
+    constexpr int RS = YGeo<S, MP>::RS;
     if constexpr (TRANS) {
+        // row j0+1 holds column j0 of P: 16-byte loads along it
+        constexpr int V = 16 / (int)sizeof(S);
+        const S *row = m + (j0 + 1) * RS;
 #pragma unroll
-        for (int k = 0; k < MP; ++k) p[k + 1] = m[(j0 + 1) * MP + k];
+        for (int k = 0; k < RS; k += V) {
+            if constexpr (sizeof(S) == 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(row + k);
+                if (k + 0 < MP) p[k + 1] = v.x;
+                if (k + 1 < MP) p[k + 2] = v.y;
+                if (k + 2 < MP) p[k + 3] = v.z;
+                if (k + 3 < MP) p[k + 4] = v.w;
+            } else {
+                const double2 v = *reinterpret_cast<const double2 *>(row + k);
+                if (k + 0 < MP) p[k + 1] = v.x;
+                if (k + 1 < MP) p[k + 2] = v.y;
+            }
+        }
         p[0] = zv[j0];
     } else {
 #pragma unroll
-        for (int r = 0; r <= MP; ++r) p[r] = m[r * MP + j0];
+        for (int r = 0; r <= MP; ++r) p[r] = m[r * RS + j0];
     }
 }
 
-// A warp's ring of `nslot` map slots filled by bulk copies.  Item i of the
-// warp's sequence goes to slot i % nslot; its map comes from `map` and, for
-// the adjoint, a z vector from `zvec`.  When the ring holds every item of the
-// sequence, everything is issued up front and no slot is reused.
-template <typename S, int MP> struct MapRing {
+// packed pair FMA (two IEEE fmas per instruction)
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long r, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Lanes that fold y into the composition: lane MP (idle otherwise) carries
+// the accumulated response y as one more column.  MP = 32 has no spare lane
+// and folds y by a separate hop chain.
+template <int MP> struct YLane {
+    static constexpr bool ON = MP < 32;
+};
+
+// col <- P col (+ y_c on lane MP when YLane is on) for the map at m: lane j
+// holds column j of the running product, acc[k] = sum_r P[k][r-1] col[r-1]
+// with rows of P read as 16-byte broadcasts; the sum runs in increasing r
+// for every k, after y_c[k] on the y lane
+template <typename S, int MP>
+__device__ __forceinline__ void compose_step(S (&col)[MP], const S *m, int lane) {
+    constexpr int RS = YGeo<S, MP>::RS;
+    const bool ylane = YLane<MP>::ON && lane == MP;
+    if constexpr (sizeof(S) == 4) {
+        constexpr int NP = (MP + 1) / 2;  // pairs covering k < MP
+        unsigned long long acc[NP];
+#pragma unroll
+        for (int q = 0; q + 1 < NP; q += 2) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(m + 2 * q);
+            acc[q] = ylane ? v.x : 0ull;
+            acc[q + 1] = ylane ? v.y : 0ull;
+        }
+        if constexpr (NP % 2 == 1) acc[NP - 1] = ylane ? *reinterpret_cast<const unsigned long long *>(m + 2 * (NP - 1)) : 0ull;
+#pragma unroll
+        for (int r = 1; r <= MP; ++r) {
+            const unsigned long long xx = pack2(col[r - 1], col[r - 1]);
+            const S *row = m + r * RS;
+#pragma unroll
+            for (int q = 0; q + 1 < NP; q += 2) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(row + 2 * q);
+                acc[q] = fma2(v.x, xx, acc[q]);
+                acc[q + 1] = fma2(v.y, xx, acc[q + 1]);
+            }
+            if constexpr (NP % 2 == 1)
+                acc[NP - 1] = fma2(*reinterpret_cast<const unsigned long long *>(row + 2 * (NP - 1)), xx, acc[NP - 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float lo, hi;
+            unpack2(acc[q], lo, hi);
+            col[2 * q] = lo;
+            if (2 * q + 1 < MP) col[2 * q + 1] = hi;
+        }
+    } else {
+        S acc[MP];
+#pragma unroll
+        for (int k = 0; k < MP; ++k) acc[k] = ylane ? m[k] : S(0);
+#pragma unroll
+        for (int r = 1; r <= MP; ++r) {
+            const S xr = col[r - 1];
+            const S *row = m + r * RS;
+#pragma unroll
+            for (int k = 0; k + 1 < MP; k += 2) {
+                const double2 v = *reinterpret_cast<const double2 *>(row + k);
+                acc[k] = fma(v.x, xr, acc[k]);
+                acc[k + 1] = fma(v.y, xr, acc[k + 1]);
+            }
+            if constexpr (MP % 2 == 1) acc[MP - 1] = fma(row[MP - 1], xr, acc[MP - 1]);
+        }
+#pragma unroll
+        for (int k = 0; k < MP; ++k) col[k] = acc[k];
+    }
+}
+
+// One hop with the state broadcast through shared memory: lane j < MP
+// publishes x_j in xb (RS entries, padding zero), then every lane reads the
+// whole state with 16-byte broadcasts.  xb alternates between two buffers
+// from hop to hop, so one barrier per hop suffices.
+template <typename S, int MP>
+__device__ __forceinline__ S hop_smem(const S (&p)[MP + 1], S *xb, S x, int lane) {
+    constexpr int RS = YGeo<S, MP>::RS;
+    constexpr int V = 16 / (int)sizeof(S);
+    if (lane < RS) xb[lane] = lane < MP ? x : S(0);
+    __syncwarp();
+    S a0 = p[0], a1 = S(0), a2 = S(0), a3 = S(0);
+#pragma unroll
+    for (int k = 0; k < RS; k += V) {
+        if constexpr (sizeof(S) == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(xb + k);
+            if (k + 0 < MP) a0 = fma(p[k + 1], v.x, a0);
+            if (k + 1 < MP) a1 = fma(p[k + 2], v.y, a1);
+            if (k + 2 < MP) a2 = fma(p[k + 3], v.z, a2);
+            if (k + 3 < MP) a3 = fma(p[k + 4], v.w, a3);
+        } else {
+            const double2 v = *reinterpret_cast<const double2 *>(xb + k);
+            if (k + 0 < MP) ((k / 2) % 2 == 0 ? a0 : a2) = fma(p[k + 1], v.x, (k / 2) % 2 == 0 ? a0 : a2);
+            if (k + 1 < MP) ((k / 2) % 2 == 0 ? a1 : a3) = fma(p[k + 2], v.y, (k / 2) % 2 == 0 ? a1 : a3);
+        }
+    }
+    return lane < MP ? (a0 + a1) + (a2 + a3) : S(0);
+}
+
+// A warp's map buffers: kScanDepth map slots and their z slots, filled by
+// bulk (TMA) copies of contiguous runs of maps, completing on one of two
+// mbarriers.  A run of up to kScanDepth maps arrives in one copy; a longer
+// run streams in batches of kScanDepth/2 through the two halves.
+template <typename S, int MP> struct ScanWarp {
     using SG = ScanGeo<S, MP>;
-    S *ring;
+    S *maps, *zs, *xb;
     uint64_t *bars;
-    int lane, nslot;
-    __device__ void init(unsigned char *base, int lane_, int nslot_) {
-        nslot = nslot_;
-        ring = reinterpret_cast<S *>(base);
-        bars = reinterpret_cast<uint64_t *>(base + (size_t)nslot * SG::SLOT * sizeof(S));
+    unsigned phase;  // bit h: parity of the next completion of bars[h]
+    int lane;
+    int *status;
+    __device__ void init(unsigned char *base, int lane_, int *status_) {
+        maps = reinterpret_cast<S *>(base);
+        zs = reinterpret_cast<S *>(base + SG::MAPS_BYTES);
+        bars = reinterpret_cast<uint64_t *>(base + SG::BAR_OFF);
+        xb = reinterpret_cast<S *>(base + SG::XB_OFF);
+        phase = 0;
         lane = lane_;
+        status = status_;
         if (lane == 0) {
-            for (int s = 0; s < nslot; ++s) mbar_init(bars + s, 1);
+            mbar_init(bars, 1);
+            mbar_init(bars + 1, 1);
             mbar_init_fence();
         }
         __syncwarp();
     }
-    __device__ void issue(int i, const S *map, const S *zvec) {
-        const int sl = i % nslot;
+    __device__ const S *map(int slot) const { return maps + slot * SG::YS; }
+    __device__ const S *zv(int slot) const { return zs + slot * SG::ZS; }
+    // n maps (and their z vectors) from memory into slots [slot0, slot0+n)
+    __device__ void issue(int slot0, int n, const S *map_src, const S *z_src, int bar) {
+        __syncwarp();  // every lane's reads of the slots are done
         if (lane == 0) {
-            const unsigned bytes = SG::YS * sizeof(S) + (zvec ? SG::ZS * sizeof(S) : 0);
-            mbar_arrive_expect_tx(bars + sl, bytes);
-            bulk_load(ring + sl * SG::SLOT, map, SG::YS * sizeof(S), bars + sl);
-            if (zvec) bulk_load(ring + sl * SG::SLOT + SG::YS, zvec, SG::ZS * sizeof(S), bars + sl);
+            const unsigned mb = (unsigned)(n * SG::YS * sizeof(S)), zb = z_src ? (unsigned)(n * SG::ZS * sizeof(S)) : 0u;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(bars + bar, mb + zb);
+            bulk_load(maps + slot0 * SG::YS, map_src, mb, bars + bar);
+            if (z_src) bulk_load(zs + slot0 * SG::ZS, z_src, zb, bars + bar);
         }
     }
-    // nullptr when the wait gave up; the copies still in flight (items
-    // i+1 .. issued-1) then get a bounded chance to land before the warp leaves
-    __device__ const S *wait(int i, int issued, int *status) {
-        const int sl = i % nslot;
-        if (!mbar_wait_warp(bars + sl, (i / nslot) & 1, kWaitLimit)) {
-            if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
-            for (int k = i + 1; k < issued; ++k) mbar_wait_warp(bars + k % nslot, (k / nslot) & 1, kWaitLimit);
-            return nullptr;
-        }
-        return ring + sl * SG::SLOT;
+    __device__ bool wait(int bar) {
+        const bool ok = mbar_wait_warp(bars + bar, (phase >> bar) & 1u, kWaitLimit);
+        phase ^= 1u << bar;
+        if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+        return ok;
     }
 };
-// bytes of a warp's ring of `nslot` slots (128-byte multiple)
-template <typename S, int MP> __host__ __device__ constexpr size_t ring_bytes(int nslot) {
-    return ((size_t(nslot) * ScanGeo<S, MP>::SLOT * sizeof(S) + size_t(nslot) * 8 + 127) / 128) * 128;
+
+// Runs step(i, map, z) for i = 0 .. n-1 along a contiguous run of n maps
+// (memory order from map_lo / z_lo; the chain visits it backwards when
+// REVR).  False when a copy never landed (status set; nothing in flight).
+template <typename S, int MP, bool REVR, typename Step>
+__device__ __forceinline__ bool run_maps(ScanWarp<S, MP> &W, const S *map_lo, const S *z_lo, int n, Step step) {
+    using SG = ScanGeo<S, MP>;
+    constexpr int D = kScanDepth, H = kScanDepth / 2;
+    if (n <= 0) return true;
+    if (n <= D) {
+        W.issue(0, n, map_lo, z_lo, 0);
+        if (!W.wait(0)) return false;
+        for (int i = 0; i < n; ++i) {
+            const int mi = REVR ? n - 1 - i : i;
+            step(i, W.map(mi), W.zv(mi));
+        }
+        return true;
+    }
+    const int nb = (n + H - 1) / H;
+    auto batch = [&](int j, int &mlo, int &cnt) {
+        const int c0 = j * H;
+        cnt = n - c0 < H ? n - c0 : H;
+        mlo = REVR ? n - c0 - cnt : c0;
+    };
+    auto issue = [&](int j) {
+        int mlo, cnt;
+        batch(j, mlo, cnt);
+        W.issue((j & 1) * H, cnt, map_lo + (size_t)mlo * SG::YS, z_lo ? z_lo + (size_t)mlo * SG::ZS : nullptr, j & 1);
+    };
+    issue(0);
+    issue(1);
+    for (int j = 0; j < nb; ++j) {
+        if (!W.wait(j & 1)) {
+            if (j + 1 < nb) W.wait((j + 1) & 1);  // the other half's copy, if any, is in flight
+            return false;
+        }
+        int mlo, cnt;
+        batch(j, mlo, cnt);
+        for (int k = 0; k < cnt; ++k) {
+            const int slot = (j & 1) * H + (REVR ? cnt - 1 - k : k);
+            step(j * H + k, W.map(slot), W.zv(slot));
+        }
+        if (j + 2 < nb) issue(j + 2);
+    }
+    return true;
 }
 
-constexpr int kScanWarps = 4;  // warps per block of k2_group / k2_expand
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
 
 template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(kScanWarps * 32)
-    k2_group(int64_t nC, int G2, int nG, int64_t n_items, int nslot, const S *__restrict__ Y,
-             const S *__restrict__ Z, S *__restrict__ GY, S *__restrict__ GZ, int *__restrict__ status) {
+    k2_scan(int M, int64_t nC, int G2, int nG, int B, const S *__restrict__ Y, const S *__restrict__ Z,
+            S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
+            S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status) {
     using SG = ScanGeo<S, MP>;
-    constexpr int YS = SG::YS, ZS = SG::ZS;
+    constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
     constexpr bool REV = MODE != CH_FWD;
     constexpr bool TRANS = MODE == CH_TRANS;
-    extern __shared__ __align__(128) unsigned char k2g_smem[];
+    extern __shared__ __align__(128) unsigned char k2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * kScanWarps + warp;  // b * nG + g
-    if (item >= n_items) return;
-    const int64_t b = item / nG;
-    const int g = (int)(item - b * nG);
-    MapRing<S, MP> R;
-    R.init(k2g_smem + (size_t)warp * ring_bytes<S, MP>(nslot), lane, nslot);
-    const int64_t c_lo = (int64_t)g * G2;
-    const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
-    auto chunk_at = [&](int i) -> int64_t { return b * nC + (REV ? c_lo + len - 1 - i : c_lo + i); };
-    int issued = 0;
-    auto issue = [&](int i) {
-        if (i < len) {
-            R.issue(i, Y + chunk_at(i) * YS, TRANS ? Z + chunk_at(i) * ZS : nullptr);
-            issued = i + 1;
-        }
-    };
-    for (int i = 0; i < nslot - 1 || (nslot >= len && i < len); ++i) issue(i);
+    const int64_t w0 = (int64_t)blockIdx.x * kScanWarps + warp;
+    const int64_t wstep = (int64_t)gridDim.x * kScanWarps;
+    const int64_t n_items = (int64_t)B * nG;
+    ScanWarp<S, MP> W;
+    W.init(k2_smem + (size_t)warp * SG::WARP_BYTES, lane, status);
+    S *xb = W.xb;
     const int j0 = lane < MP ? lane : 0;
-    if constexpr (TRANS) {
-        S zeta = S(0);
-        for (int i = 0; i < len; ++i) {
-            const S *m = R.wait(i, issued, status);
-            if (m == nullptr) return;
-            S p[MP + 1];
-            map_cols<S, MP, true>(p, m, m + YS, j0);
-            __syncwarp();
-            if (nslot < len) issue(i + nslot - 1);
-            zeta = hop<S, MP>(p, zeta, lane);
+    int nhop = 0;  // hops so far (selects the exchange buffer)
+
+    auto group_len = [&](int g) -> int {
+        const int64_t lo = (int64_t)g * G2;
+        return (int)((lo + G2 <= nC ? lo + G2 : nC) - lo);
+    };
+    // chunk of the group's i-th step along the chain
+    auto chunk_at = [&](int g, int len, int i) -> int64_t { return (int64_t)g * G2 + (REV ? len - 1 - i : i); };
+    // the group's chunk maps (and z vectors), lowest address first
+    auto group_maps = [&](int64_t b, int g) -> const S * { return Y + (b * nC + (int64_t)g * G2) * YS; };
+    auto group_zs = [&](int64_t b, int g) -> const S * { return TRANS ? Z + (b * nC + (int64_t)g * G2) * ZS : nullptr; };
+    auto hop_step = [&](const S *m, const S *z, S x) -> S {
+        S p[MP + 1];
+        map_cols<S, MP, TRANS>(p, m, z, j0);
+        return hop_smem<S, MP>(p, xb + ((nhop++) & 1) * RS, x, lane);
+    };
+    // bounded wait until signal b's counter reaches `target`: lane 0 polls
+    // with relaxed loads, then every lane takes one acquire load before
+    // reading what the count guards
+    auto wait_count = [&](int64_t b, unsigned target) -> bool {
+        bool ok = false;
+        for (int it = 0; it < kScanSpin && !ok; ++it) {
+            ok = __shfl_sync(0xffffffffu, lane == 0 ? (ld_relaxed(cnt + b * kCntStride) >= target) : false, 0);
+            if (!ok) __nanosleep(256);
         }
-        if (lane < MP) GZ[item * ZS + lane] = zeta;
-    } else {
-        // lane j < MP holds column j of the composed transfer (its response
-        // to a unit incoming component j+1); the accumulated response y is
-        // folded by a hop chain, one component per lane
-        S col[MP];
+        (void)ld_acquire(cnt + b * kCntStride);
+        if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT_SCAN);
+        return ok;
+    };
+    // make this warp's global stores visible (also to bulk copies) before
+    // bumping signal b's counter
+    auto publish = [&](int64_t b) {
+        fence_proxy_async_global();
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(cnt + b * kCntStride, 1u);
+    };
+
+    // ---- phase A: fold every group's chunk maps; the counter of signal b
+    // reaches nG when all its groups are done ----
+    for (int64_t item = w0; item < n_items; item += wstep) {
+        const int64_t b = item / nG;
+        const int g = (int)(item - b * nG);
+        const int len = group_len(g);
+        bool ok;
+        if constexpr (TRANS) {
+            S zeta = S(0);
+            ok = run_maps<S, MP, REV>(W, group_maps(b, g), group_zs(b, g), len,
+                                      [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
+            if (lane < ZS) GZ[item * ZS + lane] = lane < MP ? zeta : S(0);
+        } else {
+            // lane j < MP holds column j of the composed transfer (its response
+            // to a unit incoming component j+1); the accumulated response y
+            // rides on lane MP, or, for MP = 32, on a hop chain
+            S col[MP];
 #pragma unroll
-        for (int k = 0; k < MP; ++k) col[k] = (k == lane) ? S(1) : S(0);
-        S yv = S(0);
-        for (int i = 0; i < len; ++i) {
-            const S *m = R.wait(i, issued, status);
-            if (m == nullptr) return;
-            S p[MP + 1];
-            map_cols<S, MP, false>(p, m, nullptr, j0);
-            S acc[MP];
+            for (int k = 0; k < MP; ++k) col[k] = (k == lane) ? S(1) : S(0);
+            S yv = S(0);
+            ok = run_maps<S, MP, REV>(W, group_maps(b, g), nullptr, len, [&](int, const S *m, const S *) {
+                if constexpr (!YLane<MP>::ON) yv = hop_step(m, nullptr, yv);
+                compose_step<S, MP>(col, m, lane);
+            });
+            S *gy = GY + item * YS;
+            if constexpr (YLane<MP>::ON) {
+                // lane j < MP: row j+1 (column j of Phi_g); lane MP: row 0 (y_g)
+                if (lane <= MP) {
+                    S *row = gy + (lane == MP ? 0 : (lane + 1) * RS);
 #pragma unroll
-            for (int k = 0; k < MP; ++k) acc[k] = S(0);
+                    for (int k = 0; k < RS; ++k) row[k] = k < MP ? col[k] : S(0);
+                }
+            } else {
+                if (lane < RS) gy[lane] = lane < MP ? yv : S(0);
+                if (lane < MP) {
+                    S *row = gy + (lane + 1) * RS;
 #pragma unroll
-            for (int r = 1; r <= MP; ++r) {
-                const S xr = col[r - 1];
-                const S *row = m + r * MP;  // P[k][r-1] = m[r*MP + k]
-#pragma unroll
-                for (int k = 0; k < MP; k += 2) {
-                    if constexpr (sizeof(S) == 4) {
-                        const float2 v = *reinterpret_cast<const float2 *>(row + k);
-                        acc[k] = fma((S)v.x, xr, acc[k]);
-                        acc[k + 1] = fma((S)v.y, xr, acc[k + 1]);
-                    } else {
-                        acc[k] = fma(row[k], xr, acc[k]);
-                        acc[k + 1] = fma(row[k + 1], xr, acc[k + 1]);
-                    }
+                    for (int k = 0; k < RS; ++k) row[k] = k < MP ? col[k] : S(0);
                 }
             }
-            __syncwarp();
-            if (nslot < len) issue(i + nslot - 1);
-            yv = hop<S, MP>(p, yv, lane);
-#pragma unroll
-            for (int k = 0; k < MP; ++k) col[k] = acc[k];
         }
-        if (lane < MP) {
-            GY[item * YS + lane] = yv;
-#pragma unroll
-            for (int k = 0; k < MP; ++k) GY[item * YS + (lane + 1) * MP + k] = col[k];
-        }
+        if (!ok) return;
+        publish(b);
     }
-}
+    // With one item per warp whose group fits the buffers, they still hold
+    // that group's chunk maps (memory order, slots 0 .. len-1).
+    bool held = w0 < n_items && w0 + wstep >= n_items && group_len((int)(w0 % nG)) <= kScanDepth;
 
-template <typename S, int MP, int MODE>
-__global__ void __launch_bounds__(32)
-    k2_chain(int M, int nG, int nslot, const S *__restrict__ GY, const S *__restrict__ GZ, const S *__restrict__ zi,
-             S *__restrict__ GX, int *__restrict__ status) {
-    using SG = ScanGeo<S, MP>;
-    constexpr int YS = SG::YS, ZS = SG::ZS;
-    constexpr bool REV = MODE != CH_FWD;
-    constexpr bool TRANS = MODE == CH_TRANS;
-    extern __shared__ __align__(128) unsigned char k2c_smem[];
-    const int lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x;
-    MapRing<S, MP> R;
-    R.init(k2c_smem, lane, nslot);
-    auto gof = [&](int n) -> int64_t { return b * nG + (REV ? nG - 1 - n : n); };
-    int issued = 0;
-    auto issue = [&](int n) {
-        // the last group's map is not needed: nothing follows it
-        if (n < nG - 1) {
-            R.issue(n, GY + gof(n) * YS, TRANS ? GZ + gof(n) * ZS : nullptr);
-            issued = n + 1;
-        }
-    };
-    for (int n = 0; n < nslot - 1 || (nslot >= nG - 1 && n < nG - 1); ++n) issue(n);
-    const int j0 = lane < MP ? lane : 0;
-    S x = S(0);
-    if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
-    for (int n = 0; n < nG; ++n) {
-        if (lane < MP) GX[gof(n) * ZS + lane] = x;
-        if (n == nG - 1) break;
-        const S *m = R.wait(n, issued, status);
-        if (m == nullptr) return;
-        S p[MP + 1];
-        map_cols<S, MP, TRANS>(p, m, m + YS, j0);
-        __syncwarp();
-        if (nslot < nG - 1) issue(n + nslot - 1);
-        x = hop<S, MP>(p, x, lane);
+    // ---- phase B1: the warp owning group 0 of a signal chains that
+    // signal's group maps once, storing every group's incoming state in GX;
+    // its count then reaches nG + 1 ----
+    for (int64_t item = w0; item < n_items; item += wstep) {
+        const int64_t b = item / nG;
+        if (item - b * nG != 0) continue;
+        held = false;
+        if (!wait_count(b, (unsigned)nG)) return;
+        fence_proxy_async_global();  // the group maps are read by bulk copies
+        auto gidx = [&](int n) -> int64_t { return b * nG + (REV ? nG - 1 - n : n); };
+        S x = S(0);
+        if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
+        // groups 0 .. nG-2 along the chain: memory [b*nG, b*nG + nG-1)
+        // forward, [b*nG + 1, b*nG + nG) backward
+        const int64_t lo = b * nG + (REV ? 1 : 0);
+        const bool ok = run_maps<S, MP, REV>(W, GY + lo * YS, TRANS ? GZ + lo * ZS : nullptr, nG - 1,
+                                             [&](int n, const S *m, const S *z) {
+                                                 if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
+                                                 x = hop_step(m, z, x);
+                                             });
+        if (!ok) return;
+        if (lane < ZS) GX[gidx(nG - 1) * ZS + lane] = lane < MP ? x : S(0);
+        publish(b);
     }
-}
 
-template <typename S, int MP, int MODE>
-__global__ void __launch_bounds__(kScanWarps * 32)
-    k2_expand(int M, int64_t nC, int G2, int nG, int64_t n_items, int nslot, const S *__restrict__ Y,
-              const S *__restrict__ Z, const S *__restrict__ GX, S *__restrict__ X, S *__restrict__ ckpt,
-              int *__restrict__ status) {
-    using SG = ScanGeo<S, MP>;
-    constexpr int YS = SG::YS, ZS = SG::ZS;
-    constexpr bool REV = MODE != CH_FWD;
-    constexpr bool TRANS = MODE == CH_TRANS;
-    extern __shared__ __align__(128) unsigned char k2e_smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * kScanWarps + warp;  // b * nG + g
-    if (item >= n_items) return;
-    const int64_t b = item / nG;
-    const int g = (int)(item - b * nG);
-    MapRing<S, MP> R;
-    R.init(k2e_smem + (size_t)warp * ring_bytes<S, MP>(nslot), lane, nslot);
-    const int64_t c_lo = (int64_t)g * G2;
-    const int len = (int)((c_lo + G2 <= nC ? c_lo + G2 : nC) - c_lo);
-    auto chunk_at = [&](int i) -> int64_t { return REV ? c_lo + len - 1 - i : c_lo + i; };
-    int issued = 0;
-    auto issue = [&](int i) {
-        // the group's last chunk needs no map: nothing follows it in the group
-        if (i < len - 1) {
-            R.issue(i, Y + (b * nC + chunk_at(i)) * YS, TRANS ? Z + (b * nC + chunk_at(i)) * ZS : nullptr);
-            issued = i + 1;
+    // ---- phase B2: every group runs its chunks from its incoming state,
+    // writing each chunk's incoming state X (and the forward's checkpoints) ----
+    for (int64_t item = w0; item < n_items; item += wstep) {
+        const int64_t b = item / nG;
+        const int g = (int)(item - b * nG);
+        const int len = group_len(g);
+        if (!wait_count(b, (unsigned)nG + 1u)) return;
+        auto put = [&](int ci, S x) {
+            const int64_t q = b * nC + chunk_at(g, len, ci);
+            if (lane < MP) X[q * MP + lane] = x;
+            if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[q * M + lane] = x;
+        };
+        S x = lane < MP ? __ldcg(GX + item * ZS + lane) : S(0);
+        auto step = [&](int i, const S *m, const S *z) {
+            put(i, x);
+            x = hop_step(m, z, x);
+        };
+        if (held) {
+            // the group's maps are still in slots 0 .. len-1
+            for (int i = 0; i + 1 < len; ++i) {
+                const int mi = REV ? len - 1 - i : i;
+                step(i, W.map(mi), W.zv(mi));
+            }
+        } else {
+            // every map of the group but the last along the chain
+            const int64_t off = REV ? 1 : 0;
+            const S *zlo = TRANS ? group_zs(b, g) + off * ZS : nullptr;
+            if (!run_maps<S, MP, REV>(W, group_maps(b, g) + off * YS, zlo, len - 1, step)) return;
         }
-    };
-    for (int i = 0; i < nslot - 1 || (nslot >= len - 1 && i < len - 1); ++i) issue(i);
-    const int j0 = lane < MP ? lane : 0;
-    S x = lane < MP ? GX[item * ZS + lane] : S(0);
-    for (int i = 0; i < len; ++i) {
-        const int64_t c = chunk_at(i);
-        if (lane < MP) X[(b * nC + c) * MP + lane] = x;
-        if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[(b * nC + c) * M + lane] = x;
-        if (i == len - 1) break;
-        const S *m = R.wait(i, issued, status);
-        if (m == nullptr) return;
-        S p[MP + 1];
-        map_cols<S, MP, TRANS>(p, m, m + YS, j0);
-        __syncwarp();
-        if (nslot < len - 1) issue(i + nslot - 1);
-        x = hop<S, MP>(p, x, lane);
+        put(len - 1, x);
     }
 }
 
