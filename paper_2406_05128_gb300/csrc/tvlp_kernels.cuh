@@ -486,20 +486,31 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncwarp();
     }
-    // end states
+    // end states: the warp's CPW maps (consecutive in Y) are staged in its
+    // now idle stage ring, then written as one run of 16-byte stores
+    constexpr bool STAGED = (size_t)CPW * YS * sizeof(S) <= GE::RING_BYTES;
     const int64_t q = q0 + grp;
-    if (q < NQ) {
-        S *yq = Y + q * YS;
+    S *ys = STAGED ? a_buf : Y + q0 * YS;
+    if (STAGED || q < NQ) {
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int r = g * R + k;
             if (r <= MP) {
+                S *row = ys + grp * YS + r * RS;
 #pragma unroll
-                for (int j = 0; j < MP; ++j) yq[r * RS + j] = BWD ? h[k][j] : h[k][MP - 1 - j];
+                for (int j = 0; j < MP; ++j) row[j] = BWD ? h[k][j] : h[k][MP - 1 - j];
 #pragma unroll
-                for (int j = MP; j < RS; ++j) yq[r * RS + j] = S(0);
+                for (int j = MP; j < RS; ++j) row[j] = S(0);
             }
         }
+    }
+    if constexpr (STAGED) {
+        __syncwarp();
+        const int nq = (int)(NQ - q0 < CPW ? NQ - q0 : CPW);
+        const int n16 = (int)((size_t)nq * YS * sizeof(S) / 16);
+        const float4 *src = reinterpret_cast<const float4 *>(ys);
+        float4 *dst = reinterpret_cast<float4 *>(Y + q0 * YS);
+        for (int i = lane; i < n16; i += 32) dst[i] = src[i];
     }
 }
 
