@@ -1189,58 +1189,71 @@ __global__ void __launch_bounds__(kScanWarps * 32)
 // ---------------------------------------------------------------------------
 // Coefficient gradient (Eq. 12): ga[b][t][i-1] = -ge(b,t) * s(b, t-i), with
 // s(b, -j) = zi[b][j-1] (zero without zi).  A block owns TR rows of one
-// signal: it stages ge and the s window in shared memory, then writes its
-// TR*M outputs, one contiguous span, with 16-byte stores when aligned.
+// signal: it stages the s window in shared memory, builds its TR*M outputs
+// (one contiguous span) in a shared tile, one row per thread, and writes
+// the span with one bulk copy when it is 16-byte aligned.
 // ---------------------------------------------------------------------------
 template <typename S, int MP, bool EXACT> struct GradGeo {
     static constexpr int TR = 256;       // rows per block
     static constexpr int THREADS = 256;
 };
 
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store_commit_wait() {
+    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
 template <typename S, int MP, bool EXACT>
 __global__ void __launch_bounds__(256)
     k_grad_a(int64_t T, int M, int64_t tiles_per_signal, const S *__restrict__ ge, const S *__restrict__ s,
              const S *__restrict__ zi, S *__restrict__ ga) {
     constexpr int TR = GradGeo<S, MP, EXACT>::TR;
-    __shared__ S g_t[TR];
     __shared__ S s_t[TR + MP];
     const int64_t b = blockIdx.x / tiles_per_signal;
     const int64_t t0 = (blockIdx.x - b * tiles_per_signal) * (int64_t)TR;
     const int rows = (T - t0) < TR ? (int)(T - t0) : TR;
-    const int Mc = EXACT ? MP : M;
     for (int i = threadIdx.x; i < TR + MP; i += blockDim.x) {
         const int64_t t = t0 - MP + i;  // s_t[i] = s(t0 - MP + i)
         S v = S(0);
         if (t >= 0 && t < T) v = s[b * T + t];
         else if (t < 0 && zi != nullptr && -t <= M) v = zi[b * M + (-t - 1)];
         s_t[i] = v;
-        if (i < TR) g_t[i] = (i < rows) ? ge[b * T + t0 + i] : S(0);
     }
-    __syncthreads();
-    S *dst = ga + (b * T + t0) * (int64_t)Mc;
-    const int total = rows * Mc;
-    const bool vec = sizeof(S) == 4 && aligned16(dst);
-    if (vec) {
-        float4 *d4 = reinterpret_cast<float4 *>(dst);
-        const int n4 = total / 4;
-        for (int v = threadIdx.x; v < n4; v += blockDim.x) {
-            float o[4];
+    if constexpr (EXACT) {
+        // thread r computes row t0+r into a shared tile laid out like the
+        // output; the block's rows*MP outputs then leave as one bulk copy
+        __shared__ __align__(128) S tile[TR * MP];
+        const int r = threadIdx.x;
+        const S g = r < rows ? ge[b * T + t0 + r] : S(0);
+        __syncthreads();
+        if (r < rows) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int idx = 4 * v + e;
-                const int r = idx / Mc, i = idx - r * Mc;  // i = coefficient index - 1
-                o[e] = (float)(-g_t[r] * s_t[MP + r - (i + 1)]);
-            }
-            d4[v] = make_float4(o[0], o[1], o[2], o[3]);
+            for (int i = 0; i < MP; ++i) tile[r * MP + i] = -g * s_t[MP + r - 1 - i];
         }
-        for (int idx = 4 * n4 + threadIdx.x; idx < total; idx += blockDim.x) {
-            const int r = idx / Mc, i = idx - r * Mc;
-            dst[idx] = -g_t[r] * s_t[MP + r - (i + 1)];
+        fence_proxy_async();
+        __syncthreads();
+        S *dst = ga + (b * T + t0) * (int64_t)MP;
+        const unsigned bytes = (unsigned)(rows * MP * sizeof(S));
+        if (aligned16(dst) && bytes % 16 == 0) {
+            if (threadIdx.x == 0) {
+                bulk_store(dst, tile, bytes);
+                bulk_store_commit_wait();
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < rows * MP; idx += blockDim.x) dst[idx] = tile[idx];
         }
     } else {
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int r = idx / Mc, i = idx - r * Mc;
-            dst[idx] = -g_t[r] * s_t[MP + r - (i + 1)];
+        __shared__ S g_t[TR];
+        for (int i = threadIdx.x; i < TR; i += blockDim.x) g_t[i] = (i < rows) ? ge[b * T + t0 + i] : S(0);
+        __syncthreads();
+        S *dst = ga + (b * T + t0) * (int64_t)M;
+        for (int idx = threadIdx.x; idx < rows * M; idx += blockDim.x) {
+            const int rr = idx / M, i = idx - rr * M;  // i = coefficient index - 1
+            dst[idx] = -g_t[rr] * s_t[MP + rr - (i + 1)];
         }
     }
 }
