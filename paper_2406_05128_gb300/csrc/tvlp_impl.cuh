@@ -6,6 +6,7 @@
 namespace tvlp {
 
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per K1 block
+constexpr size_t kL2Keep = 80u << 20;        // bytes of `a` a pass keeps in L2 for the next
 constexpr int kMaxDevices = 64;
 
 template <typename S, int MP> using DefaultSumGeo = SumGeo<S, MP, Pack<MP>::G, Pack<MP>::R>;
@@ -49,6 +50,16 @@ template <typename S, int MP> struct Launch {
         return reinterpret_cast<unsigned *>(static_cast<char *>(ws) + ws_offset(p, sizeof(S), 7));
     }
 
+    // stages of the first kind in a pass: as many as keep about kL2Keep bytes
+    // of `a` in L2 for the next pass
+    static int l2_keep(const Problem &p) {
+        const int nblk = p.L / SRS < 255 ? p.L / SRS : 255;
+        const double bytes = (double)p.B * (double)p.T * (double)p.M * sizeof(S);
+        if (bytes <= (double)kL2Keep) return nblk;
+        const int k = (int)((double)nblk * (double)kL2Keep / bytes);
+        return k < 0 ? 0 : k;
+    }
+
     template <bool BWD>
     static cudaError_t summary(const Problem &p, const S *a, const S *u, S *Y, unsigned *cnt, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
@@ -59,8 +70,10 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         const int64_t per_block = (int64_t)W * GE::CPW;
         const int64_t grid = (p.NQ + per_block - 1) / per_block;
+        // the next pass (re-run or adjoint re-run) starts on this pass's first stages
+        const int l2 = l2_word(l2_keep(p), L2_LAST, L2_FIRST);
         kern<<<(unsigned)grid, 32 * W, smem, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Y, p.M == MP ? 1 : 0, cnt, p.B,
-                                                   p.status);
+                                                   l2, p.status);
         return cudaGetLastError();
     }
 
@@ -108,7 +121,7 @@ template <typename S, int MP> struct Launch {
 
     template <int MODE, bool EXACT>
     static cudaError_t rec_exact(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                                 S *gzi, int reverse, unsigned *cnt, cudaStream_t st) {
+                                 S *gzi, int reverse, unsigned *cnt, int l2, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         using RG = RecGeo<S, MP>;
         auto kern = k_rec<S, MP, EXACT, MODE>;
@@ -116,16 +129,17 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + 31) / 32;
         kern<<<(unsigned)grid, 32, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
-                                                   cnt, p.B, p.status);
+                                                   cnt, p.B, l2, p.status);
         return cudaGetLastError();
     }
 
-    // one recursion per chunk; `cnt`, when given, is zeroed for a scan that follows
+    // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
+    // follows; `l2` is the pass's L2 residency word (l2_word)
     template <int MODE>
     static cudaError_t rec(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                           S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr) {
-        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, st);
-        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, st);
+                           S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr, int l2 = 0) {
+        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, st);
+        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, st);
     }
 
     static cudaError_t grad_a(const Problem &p, const S *ge, const S *s, const S *zi, S *ga, cudaStream_t st) {
@@ -178,7 +192,11 @@ int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, 
     TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
     // the re-run walks the chunks in reverse so it starts on rows the
     // summary pass loaded last
-    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st)));
+    // reads the stages K1 kept first, streams the middle and keeps its last
+    // stages for an adjoint pass, which walks the chunks the other way
+    const int keep = LN::l2_keep(p), nblk = p.L / SRS;
+    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st, nullptr,
+                                                l2_word(keep, L2_FIRST, L2_FIRST, nblk - keep, L2_LAST))));
     return OK;
 }
 
@@ -201,14 +219,15 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
             // forward transfers P_c (and their group compositions) are in the
             // workspace: the adjoint needs one zero-state recursion per chunk,
             // then w_{c-1} = P_c^T w_c + z_c
-            TVLP_LAUNCH(k++,
-                        (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st, cnt)));
+            TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st, cnt,
+                                                         l2_word(LN::l2_keep(p), L2_LAST, L2_FIRST))));
             TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS>(p, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
         } else {
             TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, cnt, st)));
             TVLP_LAUNCH(k++, (LN::template scan<CH_BWD>(p, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt, st)));
         }
-        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st)));
+        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, nullptr,
+                                                      l2_word(0, L2_FIRST, L2_FIRST))));
     }
     if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(p, ge, s, zi, ga, st)));
     return OK;

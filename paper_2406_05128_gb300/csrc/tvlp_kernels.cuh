@@ -184,6 +184,37 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 }
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// L2 residency of the coefficient stages a pass reads.  Consecutive passes
+// over `a` reuse what L2 still holds from the previous one: a pass keeps the
+// stages the next pass reads first (evict_last) and streams the rest
+// (evict_first); the next pass reads the kept stages evict_first.  A launch
+// gets one word: in its own stage order, stages [0, head_n) use policy
+// `head`, stages [tail_from, ...) policy `tail`, the others policy `mid`
+// (L2_NORMAL: no hint).
+enum { L2_NORMAL = 0, L2_FIRST = 1, L2_LAST = 2 };
+__host__ __device__ constexpr int l2_word(int head_n, int head, int mid, int tail_from = 0xff, int tail = 0) {
+    return (head_n & 0xff) | ((tail_from & 0xff) << 8) | (head << 16) | (mid << 18) | (tail << 20);
+}
+__device__ __forceinline__ int l2_kind(int word, int stage) {
+    if (stage < (word & 0xff)) return (word >> 16) & 3;
+    if (stage >= ((word >> 8) & 0xff)) return (word >> 20) & 3;
+    return (word >> 18) & 3;
+}
+__device__ __forceinline__ void bulk_load_l2(void *dst, const void *src, unsigned bytes, uint64_t *bar, int kind) {
+    if (kind == L2_NORMAL) {
+        bulk_load(dst, src, bytes, bar);
+        return;
+    }
+    uint64_t pol;
+    if (kind == L2_LAST) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+    else asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
 constexpr int kWaitLimit = 1 << 18;  // mbarrier polls before a wait gives up (well under a second)
 
 // Load the MP coefficients of one shared-memory row (8-byte aligned for
@@ -293,7 +324,7 @@ __device__ __forceinline__ void slide(S (&h)[W]) {
 // ---------------------------------------------------------------------------
 template <typename S, int MP, typename GE, bool BWD>
 __device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int k,
-                                               int lane, int64_t my_base, int my_valid, bool exact) {
+                                               int lane, int64_t my_base, int my_valid, bool exact, int l2) {
     constexpr int CPW = GE::CPW;
     constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
     const int roff = BWD ? L - (k + 1) * SRS : k * SRS;  // chunk-local first row of the stage
@@ -307,7 +338,7 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *
     __syncwarp();
     if (tma_a) {
         fence_proxy_async();
-        bulk_load(a_st + lane * GE::CS, src_a, A_BYTES, bar);
+        bulk_load_l2(a_st + lane * GE::CS, src_a, A_BYTES, bar, l2_kind(l2, k));
     }
     // fallback chunk-stages
     unsigned slow = __ballot_sync(0xffffffffu, mine && !tma_a);
@@ -358,7 +389,7 @@ __device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__rest
 template <typename S, int MP, int G, int R, bool BWD>
 __global__ void __launch_bounds__(256, 1)
     k1_summary(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
-               S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt,
+               S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
                int *__restrict__ status) {
     using GE = SumGeo<S, MP, G, R>;
     constexpr int CPW = GE::CPW, NS = GE::NS, WIN = MP + SR;
@@ -413,7 +444,7 @@ __global__ void __launch_bounds__(256, 1)
     const S flag0 = (g == 0) ? S(1) : S(0);
 
     S uv[GE::UPL];
-    k1_issue_stage<S, MP, GE, BWD>(a_buf, bars, a, M, L, 0, lane, my_base, my_valid, exact);
+    k1_issue_stage<S, MP, GE, BWD>(a_buf, bars, a, M, L, 0, lane, my_base, my_valid, exact, l2);
     k1_load_inputs<S, MP, GE, BWD>(uv, u, L, 0, lane, my_base, my_valid);
 #pragma unroll
     for (int i = 0; i < GE::UPL; ++i)
@@ -425,7 +456,7 @@ __global__ void __launch_bounds__(256, 1)
         if (more) {
             // the other slot was consumed in the previous iteration
             k1_issue_stage<S, MP, GE, BWD>(a_buf + (slot ^ 1) * GE::A_STAGE, bars + (slot ^ 1), a, M, L, k + 1, lane,
-                                           my_base, my_valid, exact);
+                                           my_base, my_valid, exact, l2);
             k1_load_inputs<S, MP, GE, BWD>(uv, u, L, k + 1, lane, my_base, my_valid);
         } else {
             cp_async_commit();
@@ -545,7 +576,7 @@ template <typename S, int MP> struct RecGeo {
 
 template <typename S, int MP, bool EXACT, bool BWD>
 __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int s,
-                                                bool active, int64_t base, int n) {
+                                                bool active, int64_t base, int n, int l2) {
     constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
     const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
     int nv = n - roff;
@@ -558,7 +589,7 @@ __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S 
     __syncwarp();
     if (tma_a) {
         fence_proxy_async();
-        bulk_load(a_st, src_a, A_BYTES, bar);
+        bulk_load_l2(a_st, src_a, A_BYTES, bar, l2_kind(l2, s));
     } else if (EXACT) {
         for (int idx = 0; idx < SRS * MP; ++idx) {
             const bool v = idx < nv * MP;
@@ -586,7 +617,8 @@ template <typename S, int MP, bool EXACT, int MODE>
 __global__ void __launch_bounds__(32)
     k_rec(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
-          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int *__restrict__ status) {
+          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
+          int *__restrict__ status) {
     using RG = RecGeo<S, MP>;
     constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
@@ -641,7 +673,7 @@ __global__ void __launch_bounds__(32)
     }
     const int nblk = L / SRS;
     S ucur[SRS], unxt[SRS];
-    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n);
+    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n, l2);
     rec_load_inputs<S, BWD>(ucur, u, L, 0, active, base, n);
 #pragma unroll 1
     for (int s = 0; s < nblk; ++s) {
@@ -649,7 +681,7 @@ __global__ void __launch_bounds__(32)
         const bool more = s + 1 < nblk;
         if (more) {
             rec_issue_stage<S, MP, EXACT, BWD>(a_ring + (slot ^ 1) * RG::A_ST, bars + (slot ^ 1), a, M, L, s + 1, active,
-                                               base, n);
+                                               base, n, l2);
             rec_load_inputs<S, BWD>(unxt, u, L, s + 1, active, base, n);
         } else {
             cp_async_commit();
