@@ -127,7 +127,7 @@ template <typename S, int MP> struct Launch {
         auto kern = k_rec<S, MP, EXACT, MODE>;
         cudaError_t err = allow_smem(kern, RG::SMEM, done);
         if (err != cudaSuccess) return err;
-        const int64_t grid = (p.NQ + 31) / 32;
+        const int64_t grid = (p.NQ + kRecChunks - 1) / kRecChunks;
         kern<<<(unsigned)grid, 32, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
                                                    cnt, p.B, l2, p.status);
         return cudaGetLastError();

@@ -561,6 +561,8 @@ __global__ void __launch_bounds__(256, 1)
 // ---------------------------------------------------------------------------
 enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2 };
 
+constexpr int kRecChunks = 16;  // chunks per warp (lanes 0 .. kRecChunks-1 own one each)
+
 template <typename S, int MP> struct RecGeo {
     static constexpr int NS = 2;                                    // stages per lane ring
     static constexpr int A_ST = SRS * MP;                           // coefficient elements per lane-stage
@@ -568,7 +570,7 @@ template <typename S, int MP> struct RecGeo {
     // lane stride in words: an odd multiple of 4, so the 16-byte row loads of
     // a quarter warp hit distinct bank quads
     static constexpr int LW = ((RAW + 3) / 4) % 2 == 1 ? ((RAW + 3) / 4) * 4 : ((RAW + 3) / 4 + 1) * 4;
-    static constexpr size_t SMEM = size_t(32) * LW * 4 + NS * 8;
+    static constexpr size_t SMEM = size_t(kRecChunks) * LW * 4 + NS * 8;
     static_assert((A_ST * sizeof(S)) % 16 == 0, "16-byte lane stages");
     static_assert((LW * 4) % 16 == 0, "16-byte lane ring alignment");
     static_assert(NS * A_ST * sizeof(S) <= size_t(LW) * 4, "lane ring fits its stride");
@@ -576,7 +578,7 @@ template <typename S, int MP> struct RecGeo {
 
 template <typename S, int MP, bool EXACT, bool BWD>
 __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int s,
-                                                bool active, int64_t base, int n, int l2) {
+                                                bool active, int64_t base, int n, int l2, bool owner) {
     constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
     const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
     int nv = n - roff;
@@ -590,6 +592,8 @@ __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S 
     if (tma_a) {
         fence_proxy_async();
         bulk_load_l2(a_st, src_a, A_BYTES, bar, l2_kind(l2, s));
+    } else if (!owner) {
+        // no ring of its own: writes nothing
     } else if (EXACT) {
         for (int idx = 0; idx < SRS * MP; ++idx) {
             const bool v = idx < nv * MP;
@@ -628,11 +632,14 @@ __global__ void __launch_bounds__(32)
     if (scan_cnt != nullptr && blockIdx.x == 0)
         for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
-    const int64_t q = blk * 32 + lane;
-    const bool active = q < NQ;
-    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)lane * RG::LW * 4);  // [NS][SRS*MP]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)32 * RG::LW * 4);
-    if (!EXACT) {
+    // lanes past kRecChunks own no chunk; they read (and never write) the
+    // ring of lane lane % kRecChunks so every shared access stays in range
+    const bool owner = lane < kRecChunks;
+    const int64_t q = blk * kRecChunks + lane;
+    const bool active = owner && q < NQ;
+    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % kRecChunks) * RG::LW * 4);  // [NS][SRS*MP]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)kRecChunks * RG::LW * 4);
+    if (!EXACT && owner) {
         for (int j = 0; j < NS * RG::A_ST; ++j) a_ring[j] = S(0);
     }
     if (lane == 0) {
@@ -673,7 +680,7 @@ __global__ void __launch_bounds__(32)
     }
     const int nblk = L / SRS;
     S ucur[SRS], unxt[SRS];
-    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n, l2);
+    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n, l2, owner);
     rec_load_inputs<S, BWD>(ucur, u, L, 0, active, base, n);
 #pragma unroll 1
     for (int s = 0; s < nblk; ++s) {
@@ -681,7 +688,7 @@ __global__ void __launch_bounds__(32)
         const bool more = s + 1 < nblk;
         if (more) {
             rec_issue_stage<S, MP, EXACT, BWD>(a_ring + (slot ^ 1) * RG::A_ST, bars + (slot ^ 1), a, M, L, s + 1, active,
-                                               base, n, l2);
+                                               base, n, l2, owner);
             rec_load_inputs<S, BWD>(unxt, u, L, s + 1, active, base, n);
         } else {
             cp_async_commit();
