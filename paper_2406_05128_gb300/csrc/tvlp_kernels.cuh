@@ -473,7 +473,9 @@ __global__ void __launch_bounds__(256, 1)
         __syncwarp();
         const S *arow = a_buf + slot * GE::A_STAGE + grp * GE::CS;
         const S *urow = u_buf + slot * GE::U_STAGE + grp * SRS;
-#pragma unroll
+        // one SR-row block per iteration (kept rolled: the unrolled block is
+        // large and the instruction cache holds one)
+#pragma unroll 1
         for (int cb = 0; cb < SRS / SR; ++cb) {
             // forward: rows cb*SR + j; backward: the stage's rows in reverse
             const int rb = BWD ? (SRS / SR - 1 - cb) * SR : cb * SR;
