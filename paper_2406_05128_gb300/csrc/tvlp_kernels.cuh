@@ -184,6 +184,29 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 }
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Packed pairs of floats (two lanes of one register pair) and the packed
+// IEEE fma: fma.rn.f32x2 rounds each half exactly like fmaf.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(unsigned long long r) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(unsigned long long r) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+    return hi;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // L2 residency of the coefficient stages a pass reads.  Consecutive passes
 // over `a` reuse what L2 still holds from the previous one: a pass keeps the
 // stages the next pass reads first (evict_last) and streams the rest
@@ -430,16 +453,28 @@ __global__ void __launch_bounds__(256, 1)
     const int nblk = L / SRS;
 
     // forward window: h[k][MP - i] = s(t - i) at a block start; backward
-    // window: h[k][j - 1] = q_j at a block start
-    S h[R][WIN];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
+    // window: h[k][j - 1] = q_j at a block start.  For FP32 with an even R,
+    // recursions 2p and 2p+1 share one register pair per window entry (hp)
+    // and step together through packed fmas: they use the same coefficient.
+    constexpr bool PK = sizeof(S) == 4 && R % 2 == 0;
+    constexpr int RH = PK ? R / 2 : 1;
+    S h[PK ? 1 : R][PK ? 1 : WIN];
+    unsigned long long hp[RH][PK ? WIN : 1];
+    auto unit_of = [&](int k, int m) -> S {
         const int r = g * R + k;
+        const int unit = BWD ? r - 1 : MP - r;
+        return (r >= 1 && r <= MP && m == unit) ? S(1) : S(0);
+    };
+    if constexpr (PK) {
 #pragma unroll
-        for (int m = 0; m < WIN; ++m) {
-            const int unit = BWD ? r - 1 : MP - r;
-            h[k][m] = (r >= 1 && r <= MP && m == unit) ? S(1) : S(0);
-        }
+        for (int p2 = 0; p2 < RH; ++p2)
+#pragma unroll
+            for (int m = 0; m < WIN; ++m) hp[p2][m] = f2_pack((float)unit_of(2 * p2, m), (float)unit_of(2 * p2 + 1, m));
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int m = 0; m < WIN; ++m) h[k][m] = unit_of(k, m);
     }
     const S flag0 = (g == 0) ? S(1) : S(0);
 
@@ -485,7 +520,37 @@ __global__ void __launch_bounds__(256, 1)
                 S c[MP];
                 load_row_smem<S, MP>(c, arow + row * MP);
                 const S uu = flag0 * urow[row];
-                if constexpr (BWD) {
+                if constexpr (PK) {
+                    // the input drives recursion 0 only: the low half of pair 0
+                    const unsigned long long u0 = f2_pack((float)uu, 0.f);
+                    if constexpr (BWD) {
+                        const unsigned long long one = f2_pack(1.f, 1.f), zero = 0ull;
+                        unsigned long long yp[RH];
+#pragma unroll
+                        for (int p2 = 0; p2 < RH; ++p2) yp[p2] = f2_fma(one, hp[p2][j], p2 == 0 ? u0 : zero);
+#pragma unroll
+                        for (int i = 1; i < MP; ++i) {
+                            const unsigned long long nc = f2_pack(-(float)c[i - 1], -(float)c[i - 1]);
+#pragma unroll
+                            for (int p2 = 0; p2 < RH; ++p2) hp[p2][j + i] = f2_fma(nc, yp[p2], hp[p2][j + i]);
+                        }
+                        const unsigned long long nl = f2_pack(-(float)c[MP - 1], -(float)c[MP - 1]);
+#pragma unroll
+                        for (int p2 = 0; p2 < RH; ++p2) hp[p2][j + MP] = f2_fma(nl, yp[p2], zero);
+                    } else {
+                        unsigned long long accp[RH];
+#pragma unroll
+                        for (int p2 = 0; p2 < RH; ++p2) accp[p2] = p2 == 0 ? u0 : 0ull;
+#pragma unroll
+                        for (int i = MP; i >= 1; --i) {
+                            const unsigned long long nc = f2_pack(-(float)c[i - 1], -(float)c[i - 1]);
+#pragma unroll
+                            for (int p2 = 0; p2 < RH; ++p2) accp[p2] = f2_fma(nc, hp[p2][MP + j - i], accp[p2]);
+                        }
+#pragma unroll
+                        for (int p2 = 0; p2 < RH; ++p2) hp[p2][MP + j] = accp[p2];
+                    }
+                } else if constexpr (BWD) {
                     S y[R];
 #pragma unroll
                     for (int kk = 0; kk < R; ++kk) y[kk] = ((kk == 0) ? uu : S(0)) + h[kk][j];
@@ -507,8 +572,15 @@ __global__ void __launch_bounds__(256, 1)
                     for (int kk = 0; kk < R; ++kk) h[kk][MP + j] = acc[kk];
                 }
             }
+            if constexpr (PK) {
 #pragma unroll
-            for (int kk = 0; kk < R; ++kk) slide<S, MP, WIN>(h[kk]);
+                for (int p2 = 0; p2 < RH; ++p2)
+#pragma unroll
+                    for (int m = 0; m < MP; ++m) hp[p2][m] = hp[p2][m + SR];
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < R; ++kk) slide<S, MP, WIN>(h[kk]);
+            }
         }
         // park the next stage's input samples in the slot this iteration read
         // last time round (consumed before the previous iteration ended)
@@ -530,8 +602,12 @@ __global__ void __launch_bounds__(256, 1)
             const int r = g * R + k;
             if (r <= MP) {
                 S *row = ys + grp * YS + r * RS;
+                auto hv = [&](int m) -> S {
+                    if constexpr (PK) return (S)((k & 1) ? f2_hi(hp[k / 2][m]) : f2_lo(hp[k / 2][m]));
+                    else return h[k][m];
+                };
 #pragma unroll
-                for (int j = 0; j < MP; ++j) row[j] = BWD ? h[k][j] : h[k][MP - 1 - j];
+                for (int j = 0; j < MP; ++j) row[j] = BWD ? hv(j) : hv(MP - 1 - j);
 #pragma unroll
                 for (int j = MP; j < RS; ++j) row[j] = S(0);
             }
