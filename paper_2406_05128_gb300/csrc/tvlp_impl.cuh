@@ -16,6 +16,32 @@ template <typename S, int MP> inline int k1_warps_per_block() {
     return w > 8 ? 8 : (w < 1 ? 1 : w);
 }
 
+// Launch with programmatic stream serialization (the kernel may start while
+// the previous kernel on the stream finishes; see pdl_wait in the kernels),
+// optionally as a cooperative launch (all blocks resident).
+template <typename... Exp, typename... Act>
+inline cudaError_t launch(void (*kern)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool coop,
+                          Act &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+    if (coop) {
+        attr[n].id = cudaLaunchAttributeCooperative;
+        attr[n].val.cooperative = 1;
+        ++n;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Exp>(args)...);
+}
+
 // cudaFuncSetAttribute once per kernel and device.
 template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes, bool *done) {
     int dev = 0;
@@ -72,9 +98,8 @@ template <typename S, int MP> struct Launch {
         const int64_t grid = (p.NQ + per_block - 1) / per_block;
         // the next pass (re-run or adjoint re-run) starts on this pass's first stages
         const int l2 = l2_word(l2_keep(p), L2_LAST, L2_FIRST);
-        kern<<<(unsigned)grid, 32 * W, smem, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Y, p.M == MP ? 1 : 0, cnt, p.B,
-                                                   l2, p.status);
-        return cudaGetLastError();
+        return launch(kern, dim3((unsigned)grid), dim3(32 * W), smem, st, false, p.T, p.M, p.L, p.nC, p.NQ, a, u, Y,
+                      p.M == MP ? 1 : 0, cnt, p.B, l2, p.status);
     }
 
     // Two-level scan in one cooperative launch: as many blocks as the items
@@ -103,20 +128,8 @@ template <typename S, int MP> struct Launch {
         const int64_t items = (int64_t)p.B * p.nG;
         int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
         if (blocks > resident[dev]) blocks = resident[dev];
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)blocks);
-        cfg.blockDim = dim3(kScanWarps * 32);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        const int M = p.M, B = p.B, G2 = p.G2, nG = p.nG;
-        const int64_t nC = p.nC;
-        int *status = p.status;
-        return cudaLaunchKernelEx(&cfg, kern, M, nC, G2, nG, B, Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, status);
+        return launch(kern, dim3((unsigned)blocks), dim3(kScanWarps * 32), smem, st, true, p.M, p.nC, p.G2, p.nG, p.B,
+                      Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, p.status);
     }
 
     template <int MODE, bool EXACT>
@@ -128,9 +141,8 @@ template <typename S, int MP> struct Launch {
         cudaError_t err = allow_smem(kern, RG::SMEM, done);
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + kRecChunks - 1) / kRecChunks;
-        kern<<<(unsigned)grid, 32, RG::SMEM, st>>>(p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
-                                                   cnt, p.B, l2, p.status);
-        return cudaGetLastError();
+        return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin,
+                      zi, out, Zout, gzi, reverse, cnt, p.B, l2, p.status);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
@@ -148,11 +160,10 @@ template <typename S, int MP> struct Launch {
         const int64_t tiles = (p.T + TR - 1) / TR;
         const int64_t grid = tiles * p.B;
         if (p.M == MP)
-            k_grad_a<S, MP, true><<<(unsigned)grid, GradGeo<S, MP, true>::THREADS, 0, st>>>(p.T, p.M, tiles, ge, s, zi, ga);
-        else
-            k_grad_a<S, MP, false><<<(unsigned)grid, GradGeo<S, MP, false>::THREADS, 0, st>>>(p.T, p.M, tiles, ge, s, zi,
-                                                                                           ga);
-        return cudaGetLastError();
+            return launch(k_grad_a<S, MP, true>, dim3((unsigned)grid), dim3(GradGeo<S, MP, true>::THREADS), 0, st, false,
+                          p.T, p.M, tiles, ge, s, zi, ga);
+        return launch(k_grad_a<S, MP, false>, dim3((unsigned)grid), dim3(GradGeo<S, MP, false>::THREADS), 0, st, false,
+                      p.T, p.M, tiles, ge, s, zi, ga);
     }
 };
 

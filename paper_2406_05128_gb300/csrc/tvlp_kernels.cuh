@@ -184,6 +184,19 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 }
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Programmatic dependent launch.  The kernels of one call run back to back
+// on a stream; each may be launched before the previous one has finished.
+// pdl_wait() returns once the previous kernel has completed and its writes
+// are visible (immediately when launched without the attribute); only after
+// it does a kernel touch data the previous kernel writes or reads, and only
+// then does it let the next kernel launch (pdl_release), so that work a
+// kernel does before its wait overlaps its immediate predecessor alone.
+// Before the wait kernels only read the call's inputs (coefficients,
+// excitation, upstream gradient, and results of kernels two or more
+// launches back).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // Packed pairs of floats (two lanes of one register pair) and the packed
 // IEEE fma: fma.rn.f32x2 rounds each half exactly like fmaf.
 __device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
@@ -420,9 +433,6 @@ __global__ void __launch_bounds__(256, 1)
     extern __shared__ __align__(128) unsigned char k1_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    // the scan that follows counts finished groups per signal from zero
-    if (scan_cnt != nullptr && blockIdx.x == 0)
-        for (int i = threadIdx.x; i < n_cnt * kCntStride; i += blockDim.x) scan_cnt[i] = 0u;
     const int64_t q0 = ((int64_t)blockIdx.x * wpb + warp) * CPW;
     if (q0 >= NQ) return;
     const bool exact = exact_flag != 0;
@@ -481,6 +491,12 @@ __global__ void __launch_bounds__(256, 1)
     S uv[GE::UPL];
     k1_issue_stage<S, MP, GE, BWD>(a_buf, bars, a, M, L, 0, lane, my_base, my_valid, exact, l2);
     k1_load_inputs<S, MP, GE, BWD>(uv, u, L, 0, lane, my_base, my_valid);
+    pdl_wait();
+    pdl_release();
+    // the scan that follows counts finished groups per signal from zero
+    // (warp 0 of block 0 always owns chunks, so it is still here)
+    if (scan_cnt != nullptr && blockIdx.x == 0 && warp == 0)
+        for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
 #pragma unroll
     for (int i = 0; i < GE::UPL; ++i)
         if (lane + 32 * i < GE::U_STAGE) u_buf[lane + 32 * i] = uv[i];
@@ -706,9 +722,6 @@ __global__ void __launch_bounds__(32)
     constexpr bool BWD = MODE != FWD_RERUN;
     extern __shared__ __align__(128) unsigned char rec_smem[];
     const int lane = threadIdx.x & 31;
-    // a scan that follows counts finished groups per signal from zero
-    if (scan_cnt != nullptr && blockIdx.x == 0)
-        for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
     // lanes past kRecChunks own no chunk; they read (and never write) the
     // ring of lane lane % kRecChunks so every shared access stays in range
@@ -735,6 +748,15 @@ __global__ void __launch_bounds__(32)
         const int64_t rem = T - t0;
         n = rem < L ? (int)rem : L;
     }
+    const int nblk = L / SRS;
+    S ucur[SRS], unxt[SRS];
+    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n, l2, owner);
+    rec_load_inputs<S, BWD>(ucur, u, L, 0, active, base, n);
+    pdl_wait();
+    pdl_release();
+    // a scan that follows counts finished groups per signal from zero
+    if (scan_cnt != nullptr && blockIdx.x == 0)
+        for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     S h[WIN];
 #pragma unroll
     for (int m = 0; m < WIN; ++m) h[m] = S(0);
@@ -756,10 +778,6 @@ __global__ void __launch_bounds__(32)
             }
         }
     }
-    const int nblk = L / SRS;
-    S ucur[SRS], unxt[SRS];
-    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n, l2, owner);
-    rec_load_inputs<S, BWD>(ucur, u, L, 0, active, base, n);
 #pragma unroll 1
     for (int s = 0; s < nblk; ++s) {
         const int slot = s & 1;
@@ -1157,6 +1175,8 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     const int64_t n_items = (int64_t)B * nG;
     ScanWarp<S, MP> W;
     W.init(k2_smem + (size_t)warp * SG::WARP_BYTES, lane, status);
+    pdl_wait();
+    pdl_release();
     S *xb = W.xb;
     const int j0 = lane < MP ? lane : 0;
     int nhop = 0;  // hops so far (selects the exchange buffer)
@@ -1340,6 +1360,10 @@ __global__ void __launch_bounds__(256)
         else if (t < 0 && zi != nullptr && -t <= M) v = zi[b * M + (-t - 1)];
         s_t[i] = v;
     }
+    // s comes from the forward, two or more launches back; ge from the
+    // kernel just before this one
+    pdl_wait();
+    pdl_release();
     if constexpr (EXACT) {
         // thread r computes row t0+r into a shared tile laid out like the
         // output; the block's rows*MP outputs then leave as one bulk copy
