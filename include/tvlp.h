@@ -159,6 +159,36 @@ int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs,
                        void *stream);
 
 /*
+ * Adjoint from chunk checkpoints (the benchmark spec's chunk-state
+ * checkpointing; no counterpart in the paper): instead of the forward output
+ * s, the caller keeps the per-chunk incoming states `ckpt` that
+ * lp_tv_forward_* wrote (with the same `chunk`) and the excitation e.  The
+ * call first re-runs the forward pass of every chunk from its checkpoint
+ * into the caller's buffer `s` (bit for bit what the forward wrote), then
+ * computes ge, ga, gzi as lp_tv_backward_* with the chunked algorithm.
+ *   e    [B][T]     excitation of the forward                   (in)
+ *   ckpt [B][nC][M] incoming state of every chunk, from the forward (in)
+ *   s    [B][T]     scratch, holds the recomputed forward output  (out)
+ * Other arguments as lp_tv_backward_*; `flags` may be
+ * LP_BWD_REUSE_FORWARD when the workspace still holds that forward's maps.
+ * Memory kept between forward and backward is ckpt (M values per chunk:
+ * 0.55 B/sample at M=22, chunk 160) instead of s (4 B/sample).
+ */
+int lp_tv_backward_recompute_f32(int B, int64_t T, int M, const float *gs,
+                                 const float *a, const float *e,
+                                 const float *ckpt, const float *zi, float *s,
+                                 float *ge, float *ga, float *gzi, int chunk,
+                                 int flags, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+int lp_tv_backward_recompute_f64(int B, int64_t T, int M, const double *gs,
+                                 const double *a, const double *e,
+                                 const double *ckpt, const double *zi,
+                                 double *s, double *ge, double *ga,
+                                 double *gzi, int chunk, int flags,
+                                 void *workspace, size_t workspace_bytes,
+                                 void *stream);
+
+/*
  * Device status word of the current device: 0 while every bounded wait
  * inside the kernels completed, 1 once a shared-memory bulk-copy wait gave
  * up, 2 once a scan wait for other warps' results gave up (the kernel then

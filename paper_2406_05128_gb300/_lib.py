@@ -33,6 +33,7 @@ EXPORTS = (
     "lp_tv_workspace_bytes", "lp_tv_forward_f32", "lp_tv_forward_f64",
     "lp_tv_backward_f32", "lp_tv_backward_f64", "lp_tv_set_profile_events",
     "lp_tv_device_status", "lp_tv_forward_noalloc_f32",
+    "lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64",
 )
 
 LP_BWD_REUSE_FORWARD = 1
@@ -72,6 +73,10 @@ def _declare(lib):
     for name in ("lp_tv_backward_f32", "lp_tv_backward_f64"):
         f = getattr(lib, name)
         f.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]
+        f.restype = i32
+    for name in ("lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64"):
+        f = getattr(lib, name)
+        f.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
         f.restype = i32
     lib.lp_tv_forward_noalloc_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp]
     lib.lp_tv_forward_noalloc_f32.restype = i32
@@ -146,6 +151,14 @@ def lp_tv_backward(dtype: int, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, 
     """Raw backward call; pointers are ints (device addresses) or None."""
     fn = load().lp_tv_backward_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_backward_f64
     _check(fn(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, algo, flags, ws, ws_bytes, stream), "lp_tv_backward")
+
+
+def lp_tv_backward_recompute(dtype: int, B, T, M, gs, a, e, ckpt, zi, s, ge, ga, gzi, chunk, flags, ws, ws_bytes,
+                             stream):
+    """Raw backward from chunk checkpoints (s is recomputed into `s`)."""
+    fn = load().lp_tv_backward_recompute_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_backward_recompute_f64
+    _check(fn(B, T, M, gs, a, e, ckpt, zi, s, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream),
+           "lp_tv_backward_recompute")
 
 
 def lp_tv_forward_noalloc_f32(B, T, M, a, e, zi, s, stream):

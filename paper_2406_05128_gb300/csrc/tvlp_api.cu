@@ -96,6 +96,19 @@ template <> struct Dispatch<float> {
         }
         return EUNSUPPORTED;
     }
+    static int rerun(const Problem &p, const S *a, const S *e, const S *ck, const S *zi, S *s, cudaStream_t st) {
+        switch (p.MP) {
+            TVLP_CASE(2, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(4, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(8, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(12, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(16, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(22, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(30, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(32, rerun(p, a, e, ck, zi, s, st))
+        }
+        return EUNSUPPORTED;
+    }
     static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga, S *gzi,
                         int algo, int flags, void *ws, cudaStream_t st) {
         switch (p.MP) {
@@ -129,6 +142,16 @@ template <> struct Dispatch<double> {
             TVLP_CASE(8, forward(p, a, e, zi, s, ck, algo, ws, st))
             TVLP_CASE(12, forward(p, a, e, zi, s, ck, algo, ws, st))
             TVLP_CASE(16, forward(p, a, e, zi, s, ck, algo, ws, st))
+        }
+        return EUNSUPPORTED;
+    }
+    static int rerun(const Problem &p, const S *a, const S *e, const S *ck, const S *zi, S *s, cudaStream_t st) {
+        switch (p.MP) {
+            TVLP_CASE(2, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(4, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(8, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(12, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(16, rerun(p, a, e, ck, zi, s, st))
         }
         return EUNSUPPORTED;
     }
@@ -325,6 +348,30 @@ int backward_impl(int dtype, int B, int64_t T, int M, const S *gs, const S *a, c
     return Dispatch<S>::backward(p, gs, a, s, zi, ge, ga, gzi, algo, flags, ws, st);
 }
 
+
+// Backward from chunk checkpoints: s is recomputed into `s` from a, e and the
+// forward's per-chunk incoming states, then the adjoint runs as usual.
+template <typename S>
+int backward_recompute_impl(int dtype, int B, int64_t T, int M, const S *gs, const S *a, const S *e, const S *ckpt,
+                            const S *zi, S *s, S *ge, S *ga, S *gzi, int chunk, int flags, void *ws, size_t wsb,
+                            void *stream) {
+    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem(B, T, M, chunk, dtype, &p);
+    if (rc != LP_OK) return rc;
+    if (B == 0 || T == 0 || M == 0)  // no recursion: s = e
+        return backward_impl<S>(dtype, B, T, M, gs, a, e, zi, ge, ga, gzi, chunk, LP_ALGO_CHUNKED, flags, ws, wsb,
+                                stream);
+    if (e == nullptr || ckpt == nullptr || s == nullptr || a == nullptr) return LP_EINVAL;
+    if (!aligned(e, sizeof(S)) || !aligned(ckpt, sizeof(S)) || !aligned(s, sizeof(S)) || !aligned(a, 2 * sizeof(S)))
+        return LP_EALIGN;
+    if ((rc = check_workspace(p, dtype, LP_ALGO_CHUNKED, ws, wsb)) != LP_OK) return rc;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    if ((rc = Dispatch<S>::rerun(p, a, e, ckpt, zi, s, static_cast<cudaStream_t>(stream))) != LP_OK) return rc;
+    return backward_impl<S>(dtype, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, LP_ALGO_CHUNKED, flags, ws, wsb,
+                            stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -406,6 +453,21 @@ int lp_tv_device_status(int reset) {
         if (cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return LP_ECUDA;
     }
     return v;
+}
+
+int lp_tv_backward_recompute_f32(int B, int64_t T, int M, const float *gs, const float *a, const float *e,
+                                 const float *ckpt, const float *zi, float *s, float *ge, float *ga, float *gzi,
+                                 int chunk, int flags, void *workspace, size_t workspace_bytes, void *stream) {
+    return backward_recompute_impl<float>(LP_DTYPE_F32, B, T, M, gs, a, e, ckpt, zi, s, ge, ga, gzi, chunk, flags,
+                                          workspace, workspace_bytes, stream);
+}
+
+int lp_tv_backward_recompute_f64(int B, int64_t T, int M, const double *gs, const double *a, const double *e,
+                                 const double *ckpt, const double *zi, double *s, double *ge, double *ga,
+                                 double *gzi, int chunk, int flags, void *workspace, size_t workspace_bytes,
+                                 void *stream) {
+    return backward_recompute_impl<double>(LP_DTYPE_F64, B, T, M, gs, a, e, ckpt, zi, s, ge, ga, gzi, chunk, flags,
+                                           workspace, workspace_bytes, stream);
 }
 
 }  // extern "C"

@@ -134,7 +134,7 @@ template <typename S, int MP> struct Launch {
 
     template <int MODE, bool EXACT>
     static cudaError_t rec_exact(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                                 S *gzi, int reverse, unsigned *cnt, int l2, cudaStream_t st) {
+                                 S *gzi, int reverse, unsigned *cnt, int l2, int xs, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         using RG = RecGeo<S, MP>;
         auto kern = k_rec<S, MP, EXACT, MODE>;
@@ -142,16 +142,17 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + kRecChunks - 1) / kRecChunks;
         return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin,
-                      zi, out, Zout, gzi, reverse, cnt, p.B, l2, p.status);
+                      zi, out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
     // follows; `l2` is the pass's L2 residency word (l2_word)
     template <int MODE>
     static cudaError_t rec(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                           S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr, int l2 = 0) {
-        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, st);
-        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, st);
+                           S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr, int l2 = 0,
+                           int xs = MP) {
+        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
+        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
     }
 
     static cudaError_t grad_a(const Problem &p, const S *ge, const S *s, const S *zi, S *ga, cudaStream_t st) {
@@ -208,6 +209,15 @@ int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, 
     const int keep = LN::l2_keep(p), nblk = p.L / SRS;
     TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st, nullptr,
                                                 l2_word(keep, L2_FIRST, L2_FIRST, nblk - keep, L2_LAST))));
+    return OK;
+}
+
+template <typename S, int MP>
+int Impl<S, MP>::rerun(const Problem &p, const S *a, const S *e, const S *ckpt, const S *zi, S *s, cudaStream_t st) {
+    using LN = Launch<S, MP>;
+    // the forward's re-run pass from its stored chunk states: the same kernel
+    // on the same states, so s comes out bit for bit as the forward wrote it
+    TVLP_LAUNCH(0, (LN::template rec<FWD_RERUN>(p, a, e, ckpt, zi, s, nullptr, nullptr, 1, st, nullptr, 0, p.M)));
     return OK;
 }
 

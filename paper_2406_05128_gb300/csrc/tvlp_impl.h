@@ -35,6 +35,8 @@ template <typename S, int MP> struct Impl {
     static Shape shape();
     static int forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ckpt, int algo,
                        void *ws, cudaStream_t st);
+    // s from the chunk checkpoints of a chunked forward (same chunk length)
+    static int rerun(const Problem &p, const S *a, const S *e, const S *ckpt, const S *zi, S *s, cudaStream_t st);
     static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga,
                         S *gzi, int algo, int flags, void *ws, cudaStream_t st);
 };

@@ -645,7 +645,8 @@ __global__ void __launch_bounds__(256, 1)
 // coefficient rows; a full, aligned lane-stage arrives by one bulk copy
 // completing on the warp's per-stage mbarrier, others by cp.async with zero
 // fill.  Input samples are loaded into registers one stage ahead.
-//   FWD_RERUN: start from X[q] (or zi / zero), write s.
+//   FWD_RERUN: start from X[q] (or zi / zero), write s.  X rows have stride
+//              xs: MP for the scan's states, M for checkpoints.
 //   BWD_ZERO:  adjoint from zero state, store the end state to Z[q].
 //   BWD_RERUN: adjoint from W[q], write ge; chunk 0 also writes gzi.
 // A launch with one chunk per signal (L >= T) is the plain sequential filter.
@@ -715,7 +716,7 @@ template <typename S, int MP, bool EXACT, int MODE>
 __global__ void __launch_bounds__(32)
     k_rec(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
-          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
+          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
           int *__restrict__ status) {
     using RG = RecGeo<S, MP>;
     constexpr int NS = RG::NS, WIN = MP + SR;
@@ -766,15 +767,19 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
             for (int j = 1; j <= MP; ++j) {
                 S v = S(0);
-                if (Xin != nullptr) v = Xin[q * MP + (j - 1)];
-                else if (zi != nullptr && j <= M) v = zi[b * M + (j - 1)];
+                if (Xin != nullptr) {
+                    if (j - 1 < xs) v = Xin[q * xs + (j - 1)];
+                } else if (zi != nullptr && j <= M) {
+                    v = zi[b * M + (j - 1)];
+                }
                 h[MP - j] = v;
             }
         } else if constexpr (MODE == BWD_RERUN) {
             // h[j - 1] = q_j entering from the chunk's end
             if (Xin != nullptr) {
 #pragma unroll
-                for (int j = 0; j < MP; ++j) h[j] = Xin[q * MP + j];
+                for (int j = 0; j < MP; ++j)
+                    if (j < xs) h[j] = Xin[q * xs + j];
             }
         }
     }

@@ -111,33 +111,76 @@ def lp_tv_backward(gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = 
     return ge, ga, gzi
 
 
+def lp_tv_backward_recompute(gs, a, e, ckpt, zi=None, *, need_ga: bool = True, need_gzi: bool = True,
+                             chunk: int = 0, ws=None, reuse_forward: bool = False):
+    """Adjoint from chunk checkpoints: recomputes s from (a, e, ckpt) with
+    the forward's chunk length, then returns (ge, ga or None, gzi or None)."""
+    B, T, M = a.shape
+    dev = a.device
+    _check(a, "a", (B, T, M), a.dtype, dev)
+    _check(gs, "gs", (B, T), a.dtype, dev)
+    _check(e, "e", (B, T), a.dtype, dev)
+    _check(zi, "zi", (B, M), a.dtype, dev)
+    if ckpt is not None:
+        _check(ckpt, "ckpt", tuple(ckpt.shape), a.dtype, dev)
+    code = _dtype_code(a)
+    with torch.cuda.device(dev):
+        s = torch.empty((B, T), dtype=a.dtype, device=dev)
+        ge = torch.empty((B, T), dtype=a.dtype, device=dev)
+        ga = torch.empty((B, T, M), dtype=a.dtype, device=dev) if need_ga else None
+        gzi = torch.empty((B, M), dtype=a.dtype, device=dev) if need_gzi else None
+        if ws is None:
+            ws = workspace(B, T, M, chunk, a.dtype, dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward_recompute(code, B, T, M, _ptr(gs), _ptr(a), _ptr(e), _ptr(ckpt), _ptr(zi), _ptr(s),
+                                      _ptr(ge), _ptr(ga), _ptr(gzi), chunk, flags, _ptr(ws), ws.numel(),
+                                      _stream(dev))
+    return ge, ga, gzi
+
+
 class LPFunction(torch.autograd.Function):
     """Differentiable TV-LP filter: a non-differentiable fast kernel
     registered into the autograd graph with its adjoint (Sec. 2.2, Sec. 3.2).
-    The forward's workspace (its chunk transfer matrices) is kept for the
-    backward, which then runs one recursion per chunk."""
+
+    Default: the forward's output s and workspace (its chunk transfer
+    matrices) are kept for the backward, which then runs one recursion per
+    chunk.  With checkpoint=True only the per-chunk incoming states are kept
+    (M values per chunk instead of s and the maps); the backward recomputes
+    s from them and builds its own chunk maps."""
 
     @staticmethod
-    def forward(ctx, a, e, zi, chunk, algo):
+    def forward(ctx, a, e, zi, chunk, algo, checkpoint):
         a, e = a.contiguous(), e.contiguous()
         zi = zi.contiguous() if zi is not None else None
         B, T, M = a.shape
+        ctx.chunk, ctx.algo, ctx.checkpoint = chunk, algo, bool(checkpoint and algo == "chunked" and M > 0)
+        if ctx.checkpoint:
+            code = _dtype_code(a)
+            ctx.chunk = chunk or _lib.lp_tv_pick_chunk(B, T, M, code)
+            s, ck = lp_tv_forward(a, e, zi, chunk=ctx.chunk, algo=algo, ckpt=True)
+            ctx.save_for_backward(a, e, zi, ck)
+            return s
         ws = workspace(B, T, M, chunk, a.dtype, a.device)
         s = lp_tv_forward(a, e, zi, chunk=chunk, algo=algo, ws=ws)
         ctx.save_for_backward(a, s, zi, ws)
-        ctx.chunk, ctx.algo = chunk, algo
         return s
 
     @staticmethod
     def backward(ctx, gs):
-        a, s, zi, ws = ctx.saved_tensors
         need_a, need_e, need_zi = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
-        ge, ga, gzi = lp_tv_backward(gs.contiguous(), a, s, zi, need_ga=need_a,
-                                     need_gzi=need_zi and zi is not None, chunk=ctx.chunk, algo=ctx.algo,
-                                     ws=ws, reuse_forward=ctx.algo == "chunked")
-        return (ga if need_a else None, ge if need_e else None, gzi if need_zi else None, None, None)
+        if ctx.checkpoint:
+            a, e, zi, ck = ctx.saved_tensors
+            ge, ga, gzi = lp_tv_backward_recompute(gs.contiguous(), a, e, ck, zi, need_ga=need_a,
+                                                   need_gzi=need_zi and zi is not None, chunk=ctx.chunk)
+        else:
+            a, s, zi, ws = ctx.saved_tensors
+            ge, ga, gzi = lp_tv_backward(gs.contiguous(), a, s, zi, need_ga=need_a,
+                                         need_gzi=need_zi and zi is not None, chunk=ctx.chunk, algo=ctx.algo,
+                                         ws=ws, reuse_forward=ctx.algo == "chunked")
+        return (ga if need_a else None, ge if need_e else None, gzi if need_zi else None, None, None, None)
 
 
-def lp_filter(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked"):
-    """Differentiable s = LP_{a(t)}(e) with optional initial state zi."""
-    return LPFunction.apply(a, e, zi, chunk, algo)
+def lp_filter(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked", checkpoint: bool = False):
+    """Differentiable s = LP_{a(t)}(e) with optional initial state zi.
+    checkpoint=True keeps per-chunk states instead of s for the backward."""
+    return LPFunction.apply(a, e, zi, chunk, algo, checkpoint)
