@@ -189,6 +189,51 @@ int lp_tv_backward_recompute_f64(int B, int64_t T, int M, const double *gs,
                                  void *stream);
 
 /*
+ * Varlen batches (the benchmark spec's uneven batching; no counterpart in the
+ * paper): n signals of different lengths packed back to back, one call.
+ *   offsets [n+1]   DEVICE array, int64: signal b holds rows
+ *                   [offsets[b], offsets[b+1]); offsets[0] = 0,
+ *                   non-decreasing; `total` = offsets[n] (passed on the host
+ *                   for sizing).  A signal may be empty.
+ *   a [total][M], e / s / gs / ge [total], ga [total][M]  packed rows
+ *   zi / gzi [n][M]  per signal (NULL: zero state)
+ *   ckpt [nQ][M]     incoming state of every chunk, signals in order, each
+ *                    signal's chunks in order; nQ = sum_b ceil(len_b / L)
+ * Every signal is cut into chunks of `chunk` rows (0: picked from n and
+ * total/n; rounded up to a multiple of 16) from its own start, and its scan
+ * groups depend only on its own chunk count, so with a fixed `chunk` a
+ * signal's results do not depend on the rest of the batch (bit for bit).
+ * Coefficient rows start 16-byte aligned when offsets are even; odd offsets
+ * work but load through a slower path.  Algorithm: chunked only.  Returns
+ * and errors as the uniform calls; the workspace comes from
+ * lp_tv_workspace_bytes_varlen with the same (n, total, M, chunk, dtype).
+ */
+size_t lp_tv_workspace_bytes_varlen(int n, int64_t total, int M, int chunk,
+                                    int dtype);
+int lp_tv_forward_varlen_f32(int n, const int64_t *offsets, int64_t total,
+                             int M, const float *a, const float *e,
+                             const float *zi, float *s, float *ckpt,
+                             int chunk, void *workspace,
+                             size_t workspace_bytes, void *stream);
+int lp_tv_forward_varlen_f64(int n, const int64_t *offsets, int64_t total,
+                             int M, const double *a, const double *e,
+                             const double *zi, double *s, double *ckpt,
+                             int chunk, void *workspace,
+                             size_t workspace_bytes, void *stream);
+int lp_tv_backward_varlen_f32(int n, const int64_t *offsets, int64_t total,
+                              int M, const float *gs, const float *a,
+                              const float *s, const float *zi, float *ge,
+                              float *ga, float *gzi, int chunk, int flags,
+                              void *workspace, size_t workspace_bytes,
+                              void *stream);
+int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
+                              int M, const double *gs, const double *a,
+                              const double *s, const double *zi, double *ge,
+                              double *ga, double *gzi, int chunk, int flags,
+                              void *workspace, size_t workspace_bytes,
+                              void *stream);
+
+/*
  * Device status word of the current device: 0 while every bounded wait
  * inside the kernels completed, 1 once a shared-memory bulk-copy wait gave
  * up, 2 once a scan wait for other warps' results gave up (the kernel then

@@ -34,6 +34,8 @@ EXPORTS = (
     "lp_tv_backward_f32", "lp_tv_backward_f64", "lp_tv_set_profile_events",
     "lp_tv_device_status", "lp_tv_forward_noalloc_f32",
     "lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64",
+    "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
+    "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
 )
 
 LP_BWD_REUSE_FORWARD = 1
@@ -77,6 +79,16 @@ def _declare(lib):
     for name in ("lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64"):
         f = getattr(lib, name)
         f.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+        f.restype = i32
+    lib.lp_tv_workspace_bytes_varlen.argtypes = [i32, i64, i32, i32, i32]
+    lib.lp_tv_workspace_bytes_varlen.restype = sz
+    for name in ("lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64"):
+        f = getattr(lib, name)
+        f.argtypes = [i32, vp, i64, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+        f.restype = i32
+    for name in ("lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64"):
+        f = getattr(lib, name)
+        f.argtypes = [i32, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
         f.restype = i32
     lib.lp_tv_forward_noalloc_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp]
     lib.lp_tv_forward_noalloc_f32.restype = i32
@@ -159,6 +171,24 @@ def lp_tv_backward_recompute(dtype: int, B, T, M, gs, a, e, ckpt, zi, s, ge, ga,
     fn = load().lp_tv_backward_recompute_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_backward_recompute_f64
     _check(fn(B, T, M, gs, a, e, ckpt, zi, s, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream),
            "lp_tv_backward_recompute")
+
+
+def lp_tv_workspace_bytes_varlen(n, total, M, chunk=0, dtype=LP_DTYPE_F32):
+    return load().lp_tv_workspace_bytes_varlen(n, total, M, chunk, dtype)
+
+
+def lp_tv_forward_varlen(dtype: int, n, offsets, total, M, a, e, zi, s, ckpt, chunk, ws, ws_bytes, stream):
+    """Raw varlen forward; `offsets` is a device pointer to n+1 int64."""
+    fn = load().lp_tv_forward_varlen_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_forward_varlen_f64
+    _check(fn(n, offsets, total, M, a, e, zi, s, ckpt, chunk, ws, ws_bytes, stream), "lp_tv_forward_varlen")
+
+
+def lp_tv_backward_varlen(dtype: int, n, offsets, total, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_bytes,
+                          stream):
+    """Raw varlen backward; `offsets` is a device pointer to n+1 int64."""
+    fn = load().lp_tv_backward_varlen_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_backward_varlen_f64
+    _check(fn(n, offsets, total, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream),
+           "lp_tv_backward_varlen")
 
 
 def lp_tv_forward_noalloc_f32(B, T, M, a, e, zi, s, stream):

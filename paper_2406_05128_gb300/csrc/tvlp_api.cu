@@ -96,16 +96,17 @@ template <> struct Dispatch<float> {
         }
         return EUNSUPPORTED;
     }
-    static int rerun(const Problem &p, const S *a, const S *e, const S *ck, const S *zi, S *s, cudaStream_t st) {
+    static int rerun(const Problem &p, const S *a, const S *e, const S *ck, const S *zi, S *s, void *ws,
+                     cudaStream_t st) {
         switch (p.MP) {
-            TVLP_CASE(2, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(4, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(8, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(12, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(16, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(22, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(30, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(32, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(2, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(4, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(8, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(12, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(16, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(22, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(30, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(32, rerun(p, a, e, ck, zi, s, ws, st))
         }
         return EUNSUPPORTED;
     }
@@ -145,13 +146,14 @@ template <> struct Dispatch<double> {
         }
         return EUNSUPPORTED;
     }
-    static int rerun(const Problem &p, const S *a, const S *e, const S *ck, const S *zi, S *s, cudaStream_t st) {
+    static int rerun(const Problem &p, const S *a, const S *e, const S *ck, const S *zi, S *s, void *ws,
+                     cudaStream_t st) {
         switch (p.MP) {
-            TVLP_CASE(2, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(4, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(8, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(12, rerun(p, a, e, ck, zi, s, st))
-            TVLP_CASE(16, rerun(p, a, e, ck, zi, s, st))
+            TVLP_CASE(2, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(4, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(8, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(12, rerun(p, a, e, ck, zi, s, ws, st))
+            TVLP_CASE(16, rerun(p, a, e, ck, zi, s, ws, st))
         }
         return EUNSUPPORTED;
     }
@@ -256,6 +258,8 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
     p->M = M;
     p->MP = MP;
     p->status = nullptr;
+    p->off = nullptr;
+    p->items = 0;
     if (M == 0) {
         p->L = 0;
         p->nC = 0;
@@ -275,6 +279,40 @@ int make_problem(int B, int64_t T, int M, int chunk, int dtype, Problem *p) {
     while (G2 * G2 * 4 < p->nC) ++G2;
     p->G2 = (int)G2;
     p->nG = (int)ceil_div(p->nC > 0 ? p->nC : 1, G2);
+    p->items = (int64_t)B * p->nG;
+    return LP_OK;
+}
+
+// Varlen batch: n signals packed back to back, total rows in all, at device
+// offsets `off` [n+1].  Chunk and group counts are upper bounds (each signal
+// adds at most one partial chunk); the kernels read the exact ones from the
+// tables built at the start of every call.
+int make_problem_varlen(int n, int64_t total, int M, int chunk, int dtype, const int64_t *off, Problem *p) {
+    if (n < 0 || total < 0 || M < 0 || chunk < 0) return LP_EINVAL;
+    if (total >= (int64_t)INT_MAX / 2) return LP_EUNSUPPORTED;
+    const int MP = pad_order(M, dtype);
+    if (M > 0 && MP < 0) return LP_EUNSUPPORTED;
+    p->B = n;
+    p->T = total;
+    p->M = M;
+    p->MP = MP;
+    p->status = nullptr;
+    p->off = off;
+    p->nC = 0;
+    p->G2 = 0;
+    p->nG = 0;
+    if (M == 0 || n == 0) {
+        p->L = 0;
+        p->NQ = 0;
+        p->items = 0;
+        return LP_OK;
+    }
+    int L = chunk > 0 ? chunk : pick_chunk_impl(n, ceil_div(total, n), MP, dtype);
+    L = (int)(ceil_div(L, 16) * 16);
+    if (L <= 0) return LP_EINVAL;
+    p->L = L;
+    p->NQ = ceil_div(total, L) + n;
+    p->items = p->NQ;
     return LP_OK;
 }
 
@@ -367,9 +405,64 @@ int backward_recompute_impl(int dtype, int B, int64_t T, int M, const S *gs, con
         return LP_EALIGN;
     if ((rc = check_workspace(p, dtype, LP_ALGO_CHUNKED, ws, wsb)) != LP_OK) return rc;
     if ((p.status = status_word()) == nullptr) return LP_ECUDA;
-    if ((rc = Dispatch<S>::rerun(p, a, e, ckpt, zi, s, static_cast<cudaStream_t>(stream))) != LP_OK) return rc;
+    if ((rc = Dispatch<S>::rerun(p, a, e, ckpt, zi, s, ws, static_cast<cudaStream_t>(stream))) != LP_OK) return rc;
     return backward_impl<S>(dtype, B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, LP_ALGO_CHUNKED, flags, ws, wsb,
                             stream);
+}
+
+
+template <typename S>
+int forward_varlen_impl(int dtype, int n, const int64_t *off, int64_t total, int M, const S *a, const S *e,
+                        const S *zi, S *s, S *ckpt, int chunk, void *ws, size_t wsb, void *stream) {
+    Problem p;
+    int rc = make_problem_varlen(n, total, M, chunk, dtype, off, &p);
+    if (rc != LP_OK) return rc;
+    if (n == 0 || total == 0) return LP_OK;
+    if (off == nullptr || e == nullptr || s == nullptr || (M > 0 && a == nullptr)) return LP_EINVAL;
+    if (!aligned(off, 8) || !aligned(e, sizeof(S)) || !aligned(s, sizeof(S)) || !aligned(a, 2 * sizeof(S)) ||
+        !aligned(zi, sizeof(S)) || !aligned(ckpt, sizeof(S)))
+        return LP_EALIGN;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M == 0) {
+        if (cudaMemcpyAsync(s, e, (size_t)total * sizeof(S), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if ((rc = check_workspace(p, dtype, LP_ALGO_CHUNKED, ws, wsb)) != LP_OK) return rc;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    return Dispatch<S>::forward(p, a, e, zi, s, ckpt, LP_ALGO_CHUNKED, ws, st);
+}
+
+template <typename S>
+int backward_varlen_impl(int dtype, int n, const int64_t *off, int64_t total, int M, const S *gs, const S *a,
+                         const S *s, const S *zi, S *ge, S *ga, S *gzi, int chunk, int flags, void *ws, size_t wsb,
+                         void *stream) {
+    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem_varlen(n, total, M, chunk, dtype, off, &p);
+    if (rc != LP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return LP_OK;
+    if (total == 0) {
+        if (gzi != nullptr && M > 0 && cudaMemsetAsync(gzi, 0, (size_t)n * M * sizeof(S), st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if (off == nullptr || gs == nullptr || ge == nullptr || (M > 0 && a == nullptr) || (ga != nullptr && s == nullptr))
+        return LP_EINVAL;
+    if (!aligned(off, 8) || !aligned(gs, sizeof(S)) || !aligned(ge, sizeof(S)) || !aligned(a, 2 * sizeof(S)) ||
+        !aligned(s, sizeof(S)) || !aligned(zi, sizeof(S)) || !aligned(ga, sizeof(S)) || !aligned(gzi, sizeof(S)))
+        return LP_EALIGN;
+    if (M == 0) {
+        if (cudaMemcpyAsync(ge, gs, (size_t)total * sizeof(S), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if ((rc = check_workspace(p, dtype, LP_ALGO_CHUNKED, ws, wsb)) != LP_OK) return rc;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    // empty signals have no first chunk to write their (zero) gzi
+    if (gzi != nullptr && cudaMemsetAsync(gzi, 0, (size_t)n * M * sizeof(S), st) != cudaSuccess) return LP_ECUDA;
+    return Dispatch<S>::backward(p, gs, a, s, zi, ge, ga, gzi, LP_ALGO_CHUNKED, flags, ws, st);
 }
 
 }  // namespace
@@ -468,6 +561,43 @@ int lp_tv_backward_recompute_f64(int B, int64_t T, int M, const double *gs, cons
                                  void *stream) {
     return backward_recompute_impl<double>(LP_DTYPE_F64, B, T, M, gs, a, e, ckpt, zi, s, ge, ga, gzi, chunk, flags,
                                            workspace, workspace_bytes, stream);
+}
+
+size_t lp_tv_workspace_bytes_varlen(int n, int64_t total, int M, int chunk, int dtype) {
+    if (dtype != LP_DTYPE_F32 && dtype != LP_DTYPE_F64) return 0;
+    Problem p;
+    if (make_problem_varlen(n, total, M, chunk, dtype, nullptr, &p) != LP_OK) return 0;
+    p.off = reinterpret_cast<const int64_t *>(1);  // size the tables region too
+    return workspace_for(p, dtype);
+}
+
+int lp_tv_forward_varlen_f32(int n, const int64_t *offsets, int64_t total, int M, const float *a, const float *e,
+                             const float *zi, float *s, float *ckpt, int chunk, void *workspace,
+                             size_t workspace_bytes, void *stream) {
+    return forward_varlen_impl<float>(LP_DTYPE_F32, n, offsets, total, M, a, e, zi, s, ckpt, chunk, workspace,
+                                      workspace_bytes, stream);
+}
+
+int lp_tv_forward_varlen_f64(int n, const int64_t *offsets, int64_t total, int M, const double *a, const double *e,
+                             const double *zi, double *s, double *ckpt, int chunk, void *workspace,
+                             size_t workspace_bytes, void *stream) {
+    return forward_varlen_impl<double>(LP_DTYPE_F64, n, offsets, total, M, a, e, zi, s, ckpt, chunk, workspace,
+                                       workspace_bytes, stream);
+}
+
+int lp_tv_backward_varlen_f32(int n, const int64_t *offsets, int64_t total, int M, const float *gs, const float *a,
+                              const float *s, const float *zi, float *ge, float *ga, float *gzi, int chunk,
+                              int flags, void *workspace, size_t workspace_bytes, void *stream) {
+    return backward_varlen_impl<float>(LP_DTYPE_F32, n, offsets, total, M, gs, a, s, zi, ge, ga, gzi, chunk, flags,
+                                       workspace, workspace_bytes, stream);
+}
+
+int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total, int M, const double *gs,
+                              const double *a, const double *s, const double *zi, double *ge, double *ga,
+                              double *gzi, int chunk, int flags, void *workspace, size_t workspace_bytes,
+                              void *stream) {
+    return backward_varlen_impl<double>(LP_DTYPE_F64, n, offsets, total, M, gs, a, s, zi, ge, ga, gzi, chunk, flags,
+                                        workspace, workspace_bytes, stream);
 }
 
 }  // extern "C"

@@ -65,6 +65,24 @@ template <typename S, int MP> Shape Impl<S, MP>::shape() {
     return sh;
 }
 
+// The kernels' view of where a problem's chunks lie.
+inline Batch batch_of(const Problem &p, void *ws, size_t sz) {
+    Batch bt;
+    bt.T = p.T;
+    bt.nC = p.nC;
+    bt.G2 = p.G2;
+    bt.nG = p.nG;
+    bt.off = p.off;
+    bt.n = p.B;
+    bt.cstart = bt.gstart = nullptr;
+    if (p.off != nullptr) {
+        int *tab = reinterpret_cast<int *>(static_cast<char *>(ws) + ws_offset(p, sz, 8));
+        bt.cstart = tab;
+        bt.gstart = tab + p.B + 1;
+    }
+    return bt;
+}
+
 template <typename S, int MP> struct Launch {
     using GE = DefaultSumGeo<S, MP>;
 
@@ -80,14 +98,16 @@ template <typename S, int MP> struct Launch {
     // of `a` in L2 for the next pass
     static int l2_keep(const Problem &p) {
         const int nblk = p.L / SRS < 255 ? p.L / SRS : 255;
-        const double bytes = (double)p.B * (double)p.T * (double)p.M * sizeof(S);
+        const double rows = p.off != nullptr ? (double)p.T : (double)p.B * (double)p.T;
+        const double bytes = rows * (double)p.M * sizeof(S);
         if (bytes <= (double)kL2Keep) return nblk;
         const int k = (int)((double)nblk * (double)kL2Keep / bytes);
         return k < 0 ? 0 : k;
     }
 
     template <bool BWD>
-    static cudaError_t summary(const Problem &p, const S *a, const S *u, S *Y, unsigned *cnt, cudaStream_t st) {
+    static cudaError_t summary(const Problem &p, const Batch &bt, const S *a, const S *u, S *Y, unsigned *cnt,
+                               cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         const int W = k1_warps_per_block<S, MP>();
         const size_t smem = (size_t)W * GE::WARP_BYTES;
@@ -98,15 +118,15 @@ template <typename S, int MP> struct Launch {
         const int64_t grid = (p.NQ + per_block - 1) / per_block;
         // the next pass (re-run or adjoint re-run) starts on this pass's first stages
         const int l2 = l2_word(l2_keep(p), L2_LAST, L2_FIRST);
-        return launch(kern, dim3((unsigned)grid), dim3(32 * W), smem, st, false, p.T, p.M, p.L, p.nC, p.NQ, a, u, Y,
+        return launch(kern, dim3((unsigned)grid), dim3(32 * W), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Y,
                       p.M == MP ? 1 : 0, cnt, p.B, l2, p.status);
     }
 
     // Two-level scan in one cooperative launch: as many blocks as the items
     // need, at most as many as fit on the device at once.
     template <int MODE>
-    static cudaError_t scan(const Problem &p, const S *Y, const S *Z, S *GY, S *GZ, S *GX, const S *zi, S *X,
-                            S *ckpt, unsigned *cnt, cudaStream_t st) {
+    static cudaError_t scan(const Problem &p, const Batch &bt, const S *Y, const S *Z, S *GY, S *GZ, S *GX,
+                            const S *zi, S *X, S *ckpt, unsigned *cnt, cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         static int resident[kMaxDevices] = {};
         using SG = ScanGeo<S, MP>;
@@ -125,46 +145,49 @@ template <typename S, int MP> struct Launch {
             if (per_sm < 1) return cudaErrorInvalidConfiguration;
             resident[dev] = per_sm * sms;
         }
-        const int64_t items = (int64_t)p.B * p.nG;
+        const int64_t items = p.items;
         int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
         if (blocks > resident[dev]) blocks = resident[dev];
-        return launch(kern, dim3((unsigned)blocks), dim3(kScanWarps * 32), smem, st, true, p.M, p.nC, p.G2, p.nG, p.B,
-                      Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, p.status);
+        return launch(kern, dim3((unsigned)blocks), dim3(kScanWarps * 32), smem, st, true, bt, p.M, items, Y, Z, GY,
+                      GZ, GX, zi, X, ckpt, cnt, p.status);
     }
 
     template <int MODE, bool EXACT>
-    static cudaError_t rec_exact(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                                 S *gzi, int reverse, unsigned *cnt, int l2, int xs, cudaStream_t st) {
+    static cudaError_t rec_exact(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin,
+                                 const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
+                                 cudaStream_t st) {
         static bool done[kMaxDevices] = {};
         using RG = RecGeo<S, MP>;
         auto kern = k_rec<S, MP, EXACT, MODE>;
         cudaError_t err = allow_smem(kern, RG::SMEM, done);
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + kRecChunks - 1) / kRecChunks;
-        return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, p.T, p.M, p.L, p.nC, p.NQ, a, u, Xin,
-                      zi, out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status);
+        return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
+                      out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
     // follows; `l2` is the pass's L2 residency word (l2_word)
     template <int MODE>
-    static cudaError_t rec(const Problem &p, const S *a, const S *u, const S *Xin, const S *zi, S *out, S *Zout,
-                           S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr, int l2 = 0,
+    static cudaError_t rec(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin, const S *zi,
+                           S *out, S *Zout, S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr, int l2 = 0,
                            int xs = MP) {
-        if (p.M == MP) return rec_exact<MODE, true>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
-        return rec_exact<MODE, false>(p, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
+        if (p.M == MP) return rec_exact<MODE, true>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
+        return rec_exact<MODE, false>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
     }
 
-    static cudaError_t grad_a(const Problem &p, const S *ge, const S *s, const S *zi, S *ga, cudaStream_t st) {
+    static cudaError_t grad_a(const Problem &p, const Batch &bt, const S *ge, const S *s, const S *zi, S *ga,
+                              cudaStream_t st) {
         if ((int64_t)p.B * p.T * p.M == 0) return cudaSuccess;
         constexpr int TR = GradGeo<S, MP, true>::TR;
+        // uniform: tiles of TR rows per signal; varlen: tiles of TR packed rows
         const int64_t tiles = (p.T + TR - 1) / TR;
-        const int64_t grid = tiles * p.B;
+        const int64_t grid = p.off != nullptr ? tiles : tiles * p.B;
         if (p.M == MP)
             return launch(k_grad_a<S, MP, true>, dim3((unsigned)grid), dim3(GradGeo<S, MP, true>::THREADS), 0, st, false,
-                          p.T, p.M, tiles, ge, s, zi, ga);
+                          bt, p.M, tiles, ge, s, zi, ga);
         return launch(k_grad_a<S, MP, false>, dim3((unsigned)grid), dim3(GradGeo<S, MP, false>::THREADS), 0, st, false,
-                      p.T, p.M, tiles, ge, s, zi, ga);
+                      bt, p.M, tiles, ge, s, zi, ga);
     }
 };
 
@@ -187,37 +210,53 @@ inline Problem plain_problem(const Problem &p) {
         profile_mark(k_, true, st);                   \
     } while (0)
 
+// Varlen batches: the per-signal chunk and group tables, rebuilt at the
+// start of every call (a plain launch, so the tables are complete before the
+// next kernel starts).
+inline cudaError_t build_tables(const Problem &p, const Batch &bt, cudaStream_t st) {
+    if (p.off == nullptr) return cudaSuccess;
+    k_varlen_tables<<<1, kTableThreads, 0, st>>>(p.off, p.B, p.L, const_cast<int *>(bt.cstart),
+                                                 const_cast<int *>(bt.gstart));
+    return cudaGetLastError();
+}
+
 template <typename S, int MP>
 int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ckpt, int algo,
                          void *ws, cudaStream_t st) {
     using LN = Launch<S, MP>;
     if (algo == ALGO_PLAIN) {
-        TVLP_LAUNCH(0, (LN::template rec<FWD_RERUN>(plain_problem(p), a, e, nullptr, zi, s, nullptr, nullptr, 0, st)));
+        const Problem q = plain_problem(p);
+        TVLP_LAUNCH(0, (LN::template rec<FWD_RERUN>(q, batch_of(q, nullptr, sizeof(S)), a, e, nullptr, zi, s,
+                                                    nullptr, nullptr, 0, st)));
         return OK;
     }
+    const Batch bt = batch_of(p, ws, sizeof(S));
+    if (build_tables(p, bt, st) != cudaSuccess) return ECUDA;
     S *Y = LN::region(p, ws, 0);
     S *X = LN::region(p, ws, 1);
     S *GY = LN::region(p, ws, 4);
     S *GX = LN::region(p, ws, 6);
     unsigned *cnt = LN::counters(p, ws);
-    TVLP_LAUNCH(0, (LN::template summary<false>(p, a, e, Y, cnt, st)));
-    TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
-    // the re-run walks the chunks in reverse so it starts on rows the
-    // summary pass loaded last
-    // reads the stages K1 kept first, streams the middle and keeps its last
-    // stages for an adjoint pass, which walks the chunks the other way
+    TVLP_LAUNCH(0, (LN::template summary<false>(p, bt, a, e, Y, cnt, st)));
+    TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, bt, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
+    // the re-run reads the stages K1 kept first, streams the middle and
+    // keeps its last stages for an adjoint pass, which walks the chunks the
+    // other way
     const int keep = LN::l2_keep(p), nblk = p.L / SRS;
-    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, a, e, X, zi, s, nullptr, nullptr, 1, st, nullptr,
+    TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, bt, a, e, X, zi, s, nullptr, nullptr, 1, st, nullptr,
                                                 l2_word(keep, L2_FIRST, L2_FIRST, nblk - keep, L2_LAST))));
     return OK;
 }
 
 template <typename S, int MP>
-int Impl<S, MP>::rerun(const Problem &p, const S *a, const S *e, const S *ckpt, const S *zi, S *s, cudaStream_t st) {
+int Impl<S, MP>::rerun(const Problem &p, const S *a, const S *e, const S *ckpt, const S *zi, S *s, void *ws,
+                       cudaStream_t st) {
     using LN = Launch<S, MP>;
+    const Batch bt = batch_of(p, ws, sizeof(S));
+    if (build_tables(p, bt, st) != cudaSuccess) return ECUDA;
     // the forward's re-run pass from its stored chunk states: the same kernel
     // on the same states, so s comes out bit for bit as the forward wrote it
-    TVLP_LAUNCH(0, (LN::template rec<FWD_RERUN>(p, a, e, ckpt, zi, s, nullptr, nullptr, 1, st, nullptr, 0, p.M)));
+    TVLP_LAUNCH(0, (LN::template rec<FWD_RERUN>(p, bt, a, e, ckpt, zi, s, nullptr, nullptr, 1, st, nullptr, 0, p.M)));
     return OK;
 }
 
@@ -226,9 +265,12 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
                           S *gzi, int algo, int flags, void *ws, cudaStream_t st) {
     using LN = Launch<S, MP>;
     int k = 0;
+    const Problem q = algo == ALGO_PLAIN ? plain_problem(p) : p;
+    const Batch bt = batch_of(q, algo == ALGO_PLAIN ? nullptr : ws, sizeof(S));
     if (algo == ALGO_PLAIN) {
-        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(plain_problem(p), a, gs, nullptr, nullptr, ge, nullptr, gzi, 0, st)));
+        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(q, bt, a, gs, nullptr, nullptr, ge, nullptr, gzi, 0, st)));
     } else {
+        if (build_tables(p, bt, st) != cudaSuccess) return ECUDA;
         S *Y = LN::region(p, ws, 0);
         S *Z = LN::region(p, ws, 2);
         S *Wst = LN::region(p, ws, 3);
@@ -240,17 +282,19 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
             // forward transfers P_c (and their group compositions) are in the
             // workspace: the adjoint needs one zero-state recursion per chunk,
             // then w_{c-1} = P_c^T w_c + z_c
-            TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st, cnt,
-                                                         l2_word(LN::l2_keep(p), L2_LAST, L2_FIRST))));
-            TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS>(p, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
+            TVLP_LAUNCH(k++, (LN::template rec<BWD_ZERO>(p, bt, a, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st,
+                                                         cnt, l2_word(LN::l2_keep(p), L2_LAST, L2_FIRST))));
+            TVLP_LAUNCH(k++,
+                        (LN::template scan<CH_TRANS>(p, bt, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
         } else {
-            TVLP_LAUNCH(k++, (LN::template summary<true>(p, a, gs, Y, cnt, st)));
-            TVLP_LAUNCH(k++, (LN::template scan<CH_BWD>(p, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt, st)));
+            TVLP_LAUNCH(k++, (LN::template summary<true>(p, bt, a, gs, Y, cnt, st)));
+            TVLP_LAUNCH(k++,
+                        (LN::template scan<CH_BWD>(p, bt, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt, st)));
         }
-        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, nullptr,
+        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, bt, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, nullptr,
                                                       l2_word(0, L2_FIRST, L2_FIRST))));
     }
-    if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(p, ge, s, zi, ga, st)));
+    if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(q, bt, ge, s, zi, ga, st)));
     return OK;
 }
 

@@ -20,6 +20,12 @@ struct Problem {
     int64_t NQ;   // B * nC
     int G2;       // chunks per group of the two-level scan
     int nG;       // groups per signal
+    int64_t items;  // scan groups in the batch (varlen: an upper bound)
+    // varlen batches (off != nullptr): signals packed back to back, signal b
+    // at rows [off[b], off[b+1]) (device array, caller-owned); T is then the
+    // total row count, nC unused and NQ an upper bound of the chunk count;
+    // the prefix tables live in the workspace (region 8)
+    const int64_t *off;
     int *status;  // device status word (bounded waits record timeouts here)
 };
 
@@ -36,7 +42,8 @@ template <typename S, int MP> struct Impl {
     static int forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ckpt, int algo,
                        void *ws, cudaStream_t st);
     // s from the chunk checkpoints of a chunked forward (same chunk length)
-    static int rerun(const Problem &p, const S *a, const S *e, const S *ckpt, const S *zi, S *s, cudaStream_t st);
+    static int rerun(const Problem &p, const S *a, const S *e, const S *ckpt, const S *zi, S *s, void *ws,
+                     cudaStream_t st);
     static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga,
                         S *gzi, int algo, int flags, void *ws, cudaStream_t st);
 };
@@ -60,19 +67,25 @@ enum { BWD_REUSE_FORWARD = 1 };
 //   6 GX [B*nG][ZS]   incoming state of every group
 //   7 CNT [B][32]     scan progress per signal (unsigned, one 128-byte
 //                     line each), zeroed by the kernel before each scan
+//   8 TAB [2][B+1]    varlen: first chunk and first scan group of every
+//                     signal (int), built at the start of each call
+// Group regions hold p.items rows.
 inline size_t rs_elems(int MP, size_t sz) { return (((size_t)MP * sz + 15) / 16) * 16 / sz; }
 inline size_t ys_elems(int MP, size_t sz) { return (size_t)(MP + 1) * rs_elems(MP, sz); }
 inline size_t zs_elems(int MP, size_t sz) { return rs_elems(MP, sz); }
 inline size_t ws_offset(const Problem &p, size_t sz, int region) {
-    const size_t rows[8] = {(size_t)p.NQ * ys_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
+    const size_t items = (size_t)p.items;
+    const size_t tab = p.off != nullptr ? 2 * ((size_t)p.B + 1) * sizeof(int) : 0;
+    const size_t rows[9] = {(size_t)p.NQ * ys_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
                             (size_t)p.NQ * zs_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
-                            (size_t)p.B * p.nG * ys_elems(p.MP, sz), (size_t)p.B * p.nG * zs_elems(p.MP, sz),
-                            (size_t)p.B * p.nG * zs_elems(p.MP, sz), ((size_t)p.B * 32 * sizeof(unsigned) + sz - 1) / sz};
+                            items * ys_elems(p.MP, sz),            items * zs_elems(p.MP, sz),
+                            items * zs_elems(p.MP, sz),            ((size_t)p.B * 32 * sizeof(unsigned) + sz - 1) / sz,
+                            (tab + sz - 1) / sz};
     size_t off = 0;
     for (int r = 0; r < region; ++r) off += align256(rows[r] * sz);
     return off;
 }
-inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 8); }
+inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 9); }
 
 // Records the caller's profiling event for kernel k (begin or end) when a
 // hook is installed on this thread (lp_tv_set_profile_events).

@@ -345,6 +345,140 @@ __device__ __forceinline__ void slide(S (&h)[W]) {
 }
 
 // ---------------------------------------------------------------------------
+// Where a batch's chunks lie.  Uniform: n signals of T samples, signal b at
+// row b*T, nC chunks of L rows each.  Varlen (off != nullptr): signals packed
+// back to back, signal b at rows [off[b], off[b+1]); cstart[b] and gstart[b]
+// (prefix tables built by k_varlen_tables) number the first chunk and the
+// first scan group of signal b, with cstart[n], gstart[n] the totals.  Every
+// signal is cut into chunks of L rows from its own start, and its scan groups
+// hold group_size(nC_b) chunks, so a signal's results do not depend on the
+// rest of the batch.
+// ---------------------------------------------------------------------------
+struct Batch {
+    int64_t T;           // uniform: samples per signal
+    int64_t nC;          // uniform: chunks per signal
+    int G2, nG;          // uniform: chunks per scan group, groups per signal
+    const int64_t *off;  // varlen: [n+1] first row of every signal, or nullptr
+    const int *cstart;   // varlen: [n+1] first chunk of every signal
+    const int *gstart;   // varlen: [n+1] first scan group of every signal
+    int n;               // signals
+};
+
+// chunks per scan group for a signal of nC chunks: about sqrt(nC / 4)
+__host__ __device__ inline int group_size(int64_t nC) {
+    int g = 1;
+    while ((int64_t)g * g * 4 < nC) ++g;
+    return g;
+}
+
+// largest b in [0, n) with start[b] <= x (start non-decreasing, start[0] = 0)
+__device__ __forceinline__ int find_signal(const int *__restrict__ start, int n, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)__ldg(start + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// chunks in the batch (the host sizes grids for an upper bound)
+__device__ __forceinline__ int64_t batch_chunks(const Batch &bt, int64_t bound) {
+    if (bt.off == nullptr) return bound;
+    const int64_t n = __ldg(bt.cstart + bt.n);
+    return n < bound ? n : bound;
+}
+
+struct ChunkPos {
+    int64_t b, c;  // signal, chunk within the signal
+    int64_t base;  // row of the chunk's first sample
+    int valid;     // rows of the chunk inside the signal (<= L)
+};
+__device__ __forceinline__ ChunkPos chunk_pos(const Batch &bt, int64_t q, int L) {
+    ChunkPos p;
+    int64_t len;
+    if (bt.off == nullptr) {
+        p.b = q / bt.nC;
+        p.c = q - p.b * bt.nC;
+        p.base = p.b * bt.T + p.c * (int64_t)L;
+        len = bt.T;
+    } else {
+        p.b = find_signal(bt.cstart, bt.n, q);
+        p.c = q - __ldg(bt.cstart + p.b);
+        const int64_t o = __ldg(bt.off + p.b);
+        p.base = o + p.c * (int64_t)L;
+        len = __ldg(bt.off + p.b + 1) - o;
+    }
+    const int64_t rem = len - p.c * (int64_t)L;
+    p.valid = rem < 0 ? 0 : (rem < L ? (int)rem : L);
+    return p;
+}
+
+// Per-signal scan geometry: first chunk, chunks, first group, groups, group size.
+struct SigScan {
+    int64_t cbase, nC, gbase;
+    int nG, G2;
+};
+__device__ __forceinline__ SigScan sig_scan(const Batch &bt, int64_t b) {
+    SigScan r;
+    if (bt.off == nullptr) {
+        r.cbase = b * bt.nC;
+        r.nC = bt.nC;
+        r.gbase = b * bt.nG;
+        r.nG = bt.nG;
+        r.G2 = bt.G2;
+    } else {
+        r.cbase = __ldg(bt.cstart + b);
+        r.nC = __ldg(bt.cstart + b + 1) - r.cbase;
+        r.gbase = __ldg(bt.gstart + b);
+        r.nG = (int)(__ldg(bt.gstart + b + 1) - r.gbase);
+        r.G2 = group_size(r.nC);
+    }
+    return r;
+}
+
+// Builds the varlen prefix tables: one block; thread i handles a run of
+// consecutive signals, then the block scans the runs' totals.
+constexpr int kTableThreads = 1024;
+static __global__ void __launch_bounds__(kTableThreads)
+    k_varlen_tables(const int64_t *__restrict__ off, int n, int L, int *__restrict__ cstart, int *__restrict__ gstart) {
+    __shared__ long long sc[kTableThreads], sg[kTableThreads];
+    const int t = threadIdx.x;
+    const int per = (n + kTableThreads - 1) / kTableThreads;
+    const int lo = t * per, hi = (lo + per < n) ? lo + per : n;
+    long long nc = 0, ng = 0;
+    for (int b = lo; b < hi; ++b) {
+        const int64_t len = off[b + 1] - off[b];
+        const int64_t c = len > 0 ? (len + L - 1) / L : 0;
+        nc += c;
+        ng += c > 0 ? (c + group_size(c) - 1) / group_size(c) : 0;
+    }
+    sc[t] = nc;
+    sg[t] = ng;
+    __syncthreads();
+    for (int d = 1; d < kTableThreads; d <<= 1) {  // inclusive scan
+        const long long xc = t >= d ? sc[t - d] : 0, xg = t >= d ? sg[t - d] : 0;
+        __syncthreads();
+        sc[t] += xc;
+        sg[t] += xg;
+        __syncthreads();
+    }
+    long long c0 = sc[t] - nc, g0 = sg[t] - ng;  // exclusive
+    for (int b = lo; b < hi; ++b) {
+        cstart[b] = (int)c0;
+        gstart[b] = (int)g0;
+        const int64_t len = off[b + 1] - off[b];
+        const int64_t c = len > 0 ? (len + L - 1) / L : 0;
+        c0 += c;
+        g0 += c > 0 ? (c + group_size(c) - 1) / group_size(c) : 0;
+    }
+    if (t == kTableThreads - 1) {
+        cstart[n] = (int)sc[t];
+        gstart[n] = (int)sg[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K1: chunk summaries.
 // Flattened chunk index q = b*nC + c; chunk c of signal b covers samples
 // [c*L, c*L + L).  Each warp owns CPW consecutive chunks; lane (grp = lane/G,
@@ -424,7 +558,7 @@ __device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__rest
 
 template <typename S, int MP, int G, int R, bool BWD>
 __global__ void __launch_bounds__(256, 1)
-    k1_summary(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
+    k1_summary(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
                S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
                int *__restrict__ status) {
     using GE = SumGeo<S, MP, G, R>;
@@ -433,6 +567,8 @@ __global__ void __launch_bounds__(256, 1)
     extern __shared__ __align__(128) unsigned char k1_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
+    if (bt.off != nullptr) pdl_wait();  // the chunk tables come from the kernel before
+    NQ = batch_chunks(bt, NQ);
     const int64_t q0 = ((int64_t)blockIdx.x * wpb + warp) * CPW;
     if (q0 >= NQ) return;
     const bool exact = exact_flag != 0;
@@ -448,16 +584,13 @@ __global__ void __launch_bounds__(256, 1)
         mbar_init_fence();
     }
     __syncwarp();
-    // lane ch < CPW describes chunk q0 + ch: first row b*T + c*L, valid rows
+    // lane ch < CPW describes chunk q0 + ch: its first row and valid rows
     int64_t my_base = 0;
     int my_valid = 0;
     if (lane < CPW && q0 + lane < NQ) {
-        const int64_t q = q0 + lane;
-        const int64_t b = q / nC;
-        const int64_t t0 = (q - b * nC) * (int64_t)L;
-        my_base = b * T + t0;
-        const int64_t rem = T - t0;
-        my_valid = rem < L ? (int)rem : L;
+        const ChunkPos cp = chunk_pos(bt, q0 + lane, L);
+        my_base = cp.base;
+        my_valid = cp.valid;
     }
     const int grp = lane / G, g = lane % G;
     const int nblk = L / SRS;
@@ -714,7 +847,7 @@ __device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restric
 
 template <typename S, int MP, bool EXACT, int MODE>
 __global__ void __launch_bounds__(32)
-    k_rec(int64_t T, int M, int L, int64_t nC, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
+    k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
           S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
           int *__restrict__ status) {
@@ -728,6 +861,8 @@ __global__ void __launch_bounds__(32)
     // ring of lane lane % kRecChunks so every shared access stays in range
     const bool owner = lane < kRecChunks;
     const int64_t q = blk * kRecChunks + lane;
+    if (bt.off != nullptr) pdl_wait();  // the chunk tables come from a kernel before
+    NQ = batch_chunks(bt, NQ);
     const bool active = owner && q < NQ;
     S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % kRecChunks) * RG::LW * 4);  // [NS][SRS*MP]
     uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)kRecChunks * RG::LW * 4);
@@ -742,12 +877,11 @@ __global__ void __launch_bounds__(32)
     int64_t b = 0, c = 0, base = 0;
     int n = 0;
     if (active) {
-        b = q / nC;
-        c = q - b * nC;
-        const int64_t t0 = c * (int64_t)L;
-        base = b * T + t0;
-        const int64_t rem = T - t0;
-        n = rem < L ? (int)rem : L;
+        const ChunkPos cp = chunk_pos(bt, q, L);
+        b = cp.b;
+        c = cp.c;
+        base = cp.base;
+        n = cp.valid;
     }
     const int nblk = L / SRS;
     S ucur[SRS], unxt[SRS];
@@ -1166,7 +1300,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 
 template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(kScanWarps * 32)
-    k2_scan(int M, int64_t nC, int G2, int nG, int B, const S *__restrict__ Y, const S *__restrict__ Z,
+    k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
             S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
             S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status) {
     using SG = ScanGeo<S, MP>;
@@ -1177,7 +1311,11 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t)blockIdx.x * kScanWarps + warp;
     const int64_t wstep = (int64_t)gridDim.x * kScanWarps;
-    const int64_t n_items = (int64_t)B * nG;
+    int64_t n_items = items_bound;
+    if (bt.off != nullptr) {
+        const int64_t n = __ldg(bt.gstart + bt.n);
+        n_items = n < items_bound ? n : items_bound;
+    }
     ScanWarp<S, MP> W;
     W.init(k2_smem + (size_t)warp * SG::WARP_BYTES, lane, status);
     pdl_wait();
@@ -1186,15 +1324,27 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     const int j0 = lane < MP ? lane : 0;
     int nhop = 0;  // hops so far (selects the exchange buffer)
 
-    auto group_len = [&](int g) -> int {
-        const int64_t lo = (int64_t)g * G2;
-        return (int)((lo + G2 <= nC ? lo + G2 : nC) - lo);
+    // scan item -> (signal, group) and the signal's scan geometry
+    auto locate = [&](int64_t item, int64_t &b, int &g, SigScan &sg) {
+        b = bt.off == nullptr ? item / bt.nG : (int64_t)find_signal(bt.gstart, bt.n, item);
+        sg = sig_scan(bt, b);
+        g = (int)(item - sg.gbase);
     };
-    // chunk of the group's i-th step along the chain
-    auto chunk_at = [&](int g, int len, int i) -> int64_t { return (int64_t)g * G2 + (REV ? len - 1 - i : i); };
+    auto group_len = [&](const SigScan &sg, int g) -> int {
+        const int64_t lo = (int64_t)g * sg.G2;
+        return (int)((lo + sg.G2 <= sg.nC ? lo + sg.G2 : sg.nC) - lo);
+    };
+    // chunk (within the signal) of the group's i-th step along the chain
+    auto chunk_at = [&](const SigScan &sg, int g, int len, int i) -> int64_t {
+        return (int64_t)g * sg.G2 + (REV ? len - 1 - i : i);
+    };
     // the group's chunk maps (and z vectors), lowest address first
-    auto group_maps = [&](int64_t b, int g) -> const S * { return Y + (b * nC + (int64_t)g * G2) * YS; };
-    auto group_zs = [&](int64_t b, int g) -> const S * { return TRANS ? Z + (b * nC + (int64_t)g * G2) * ZS : nullptr; };
+    auto group_maps = [&](const SigScan &sg, int g) -> const S * {
+        return Y + (sg.cbase + (int64_t)g * sg.G2) * YS;
+    };
+    auto group_zs = [&](const SigScan &sg, int g) -> const S * {
+        return TRANS ? Z + (sg.cbase + (int64_t)g * sg.G2) * ZS : nullptr;
+    };
     auto hop_step = [&](const S *m, const S *z, S x) -> S {
         S p[MP + 1];
         map_cols<S, MP, TRANS>(p, m, z, j0);
@@ -1223,15 +1373,17 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     };
 
     // ---- phase A: fold every group's chunk maps; the counter of signal b
-    // reaches nG when all its groups are done ----
+    // reaches its group count when all its groups are done ----
     for (int64_t item = w0; item < n_items; item += wstep) {
-        const int64_t b = item / nG;
-        const int g = (int)(item - b * nG);
-        const int len = group_len(g);
+        int64_t b;
+        int g;
+        SigScan sg;
+        locate(item, b, g, sg);
+        const int len = group_len(sg, g);
         bool ok;
         if constexpr (TRANS) {
             S zeta = S(0);
-            ok = run_maps<S, MP, REV>(W, group_maps(b, g), group_zs(b, g), len,
+            ok = run_maps<S, MP, REV>(W, group_maps(sg, g), group_zs(sg, g), len,
                                       [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
             if (lane < ZS) GZ[item * ZS + lane] = lane < MP ? zeta : S(0);
         } else {
@@ -1242,7 +1394,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
 #pragma unroll
             for (int k = 0; k < MP; ++k) col[k] = (k == lane) ? S(1) : S(0);
             S yv = S(0);
-            ok = run_maps<S, MP, REV>(W, group_maps(b, g), nullptr, len, [&](int, const S *m, const S *) {
+            ok = run_maps<S, MP, REV>(W, group_maps(sg, g), nullptr, len, [&](int, const S *m, const S *) {
                 if constexpr (!YLane<MP>::ON) yv = hop_step(m, nullptr, yv);
                 compose_step<S, MP>(col, m, lane);
             });
@@ -1268,23 +1420,34 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     }
     // With one item per warp whose group fits the buffers, they still hold
     // that group's chunk maps (memory order, slots 0 .. len-1).
-    bool held = w0 < n_items && w0 + wstep >= n_items && group_len((int)(w0 % nG)) <= kScanDepth;
+    bool held = false;
+    if (w0 < n_items && w0 + wstep >= n_items) {
+        int64_t b;
+        int g;
+        SigScan sg;
+        locate(w0, b, g, sg);
+        held = group_len(sg, g) <= kScanDepth;
+    }
 
     // ---- phase B1: the warp owning group 0 of a signal chains that
     // signal's group maps once, storing every group's incoming state in GX;
-    // its count then reaches nG + 1 ----
+    // its count then reaches the group count + 1 ----
     for (int64_t item = w0; item < n_items; item += wstep) {
-        const int64_t b = item / nG;
-        if (item - b * nG != 0) continue;
+        int64_t b;
+        int g;
+        SigScan sg;
+        locate(item, b, g, sg);
+        if (g != 0) continue;
         held = false;
+        const int nG = sg.nG;
         if (!wait_count(b, (unsigned)nG)) return;
         fence_proxy_async_global();  // the group maps are read by bulk copies
-        auto gidx = [&](int n) -> int64_t { return b * nG + (REV ? nG - 1 - n : n); };
+        auto gidx = [&](int n) -> int64_t { return sg.gbase + (REV ? nG - 1 - n : n); };
         S x = S(0);
         if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
-        // groups 0 .. nG-2 along the chain: memory [b*nG, b*nG + nG-1)
-        // forward, [b*nG + 1, b*nG + nG) backward
-        const int64_t lo = b * nG + (REV ? 1 : 0);
+        // groups 0 .. nG-2 along the chain: the signal's group maps
+        // [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG) backward
+        const int64_t lo = sg.gbase + (REV ? 1 : 0);
         const bool ok = run_maps<S, MP, REV>(W, GY + lo * YS, TRANS ? GZ + lo * ZS : nullptr, nG - 1,
                                              [&](int n, const S *m, const S *z) {
                                                  if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
@@ -1298,12 +1461,14 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     // ---- phase B2: every group runs its chunks from its incoming state,
     // writing each chunk's incoming state X (and the forward's checkpoints) ----
     for (int64_t item = w0; item < n_items; item += wstep) {
-        const int64_t b = item / nG;
-        const int g = (int)(item - b * nG);
-        const int len = group_len(g);
-        if (!wait_count(b, (unsigned)nG + 1u)) return;
+        int64_t b;
+        int g;
+        SigScan sg;
+        locate(item, b, g, sg);
+        const int len = group_len(sg, g);
+        if (!wait_count(b, (unsigned)sg.nG + 1u)) return;
         auto put = [&](int ci, S x) {
-            const int64_t q = b * nC + chunk_at(g, len, ci);
+            const int64_t q = sg.cbase + chunk_at(sg, g, len, ci);
             if (lane < MP) X[q * MP + lane] = x;
             if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[q * M + lane] = x;
         };
@@ -1321,8 +1486,8 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         } else {
             // every map of the group but the last along the chain
             const int64_t off = REV ? 1 : 0;
-            const S *zlo = TRANS ? group_zs(b, g) + off * ZS : nullptr;
-            if (!run_maps<S, MP, REV>(W, group_maps(b, g) + off * YS, zlo, len - 1, step)) return;
+            const S *zlo = TRANS ? group_zs(sg, g) + off * ZS : nullptr;
+            if (!run_maps<S, MP, REV>(W, group_maps(sg, g) + off * YS, zlo, len - 1, step)) return;
         }
         put(len - 1, x);
     }
@@ -1349,40 +1514,77 @@ __device__ __forceinline__ void bulk_store_commit_wait() {
     asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
+// largest b in [0, n) with off[b] <= t (off non-decreasing, off[0] = 0)
+__device__ __forceinline__ int find_row_signal(const int64_t *__restrict__ off, int n, int64_t t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <typename S, int MP, bool EXACT>
 __global__ void __launch_bounds__(256)
-    k_grad_a(int64_t T, int M, int64_t tiles_per_signal, const S *__restrict__ ge, const S *__restrict__ s,
+    k_grad_a(Batch bt, int M, int64_t tiles_per_signal, const S *__restrict__ ge, const S *__restrict__ s,
              const S *__restrict__ zi, S *__restrict__ ga) {
     constexpr int TR = GradGeo<S, MP, EXACT>::TR;
     __shared__ S s_t[TR + MP];
-    const int64_t b = blockIdx.x / tiles_per_signal;
-    const int64_t t0 = (blockIdx.x - b * tiles_per_signal) * (int64_t)TR;
-    const int rows = (T - t0) < TR ? (int)(T - t0) : TR;
+    const bool varlen = bt.off != nullptr;
+    // uniform: the block owns rows [t0, t0+TR) of signal b, row r at b*T + t;
+    // varlen: the block owns packed rows [t0, t0+TR), each in its own signal
+    int64_t b = 0, t0, row0, nrows;
+    if (varlen) {
+        t0 = (int64_t)blockIdx.x * TR;
+        row0 = t0;
+        nrows = __ldg(bt.off + bt.n);
+    } else {
+        b = blockIdx.x / tiles_per_signal;
+        t0 = (blockIdx.x - b * tiles_per_signal) * (int64_t)TR;
+        row0 = b * bt.T + t0;
+        nrows = bt.T;
+    }
+    if (t0 >= nrows) return;
+    const int rows = (nrows - t0) < TR ? (int)(nrows - t0) : TR;
     for (int i = threadIdx.x; i < TR + MP; i += blockDim.x) {
-        const int64_t t = t0 - MP + i;  // s_t[i] = s(t0 - MP + i)
+        const int64_t t = t0 - MP + i;  // s_t[i] = s(t0 - MP + i), in the signal's rows (packed rows for varlen)
         S v = S(0);
-        if (t >= 0 && t < T) v = s[b * T + t];
-        else if (t < 0 && zi != nullptr && -t <= M) v = zi[b * M + (-t - 1)];
+        if (t >= 0 && t < nrows) v = s[row0 - t0 + t];
+        else if (!varlen && t < 0 && zi != nullptr && -t <= M) v = zi[b * M + (-t - 1)];
         s_t[i] = v;
     }
     // s comes from the forward, two or more launches back; ge from the
     // kernel just before this one
     pdl_wait();
     pdl_release();
+    // varlen: history before a row's own signal start is that signal's zi
+    auto hist = [&](int r, int i, int64_t rb, int64_t ro) -> S {
+        const int64_t tt = t0 + r - 1 - i;
+        if (!varlen || tt >= ro) return s_t[MP + r - 1 - i];
+        const int64_t j = ro - tt;  // s_b(-j) = zi[b][j-1]
+        return (zi != nullptr && j <= M) ? zi[rb * M + (j - 1)] : S(0);
+    };
     if constexpr (EXACT) {
         // thread r computes row t0+r into a shared tile laid out like the
         // output; the block's rows*MP outputs then leave as one bulk copy
         __shared__ __align__(128) S tile[TR * MP];
         const int r = threadIdx.x;
-        const S g = r < rows ? ge[b * T + t0 + r] : S(0);
+        const S g = r < rows ? ge[row0 + r] : S(0);
         __syncthreads();
         if (r < rows) {
+            if (varlen) {
+                const int64_t rb = find_row_signal(bt.off, bt.n, t0 + r), ro = __ldg(bt.off + rb);
 #pragma unroll
-            for (int i = 0; i < MP; ++i) tile[r * MP + i] = -g * s_t[MP + r - 1 - i];
+                for (int i = 0; i < MP; ++i) tile[r * MP + i] = -g * hist(r, i, rb, ro);
+            } else {
+#pragma unroll
+                for (int i = 0; i < MP; ++i) tile[r * MP + i] = -g * s_t[MP + r - 1 - i];
+            }
         }
         fence_proxy_async();
         __syncthreads();
-        S *dst = ga + (b * T + t0) * (int64_t)MP;
+        S *dst = ga + row0 * (int64_t)MP;
         const unsigned bytes = (unsigned)(rows * MP * sizeof(S));
         if (aligned16(dst) && bytes % 16 == 0) {
             if (threadIdx.x == 0) {
@@ -1394,12 +1596,19 @@ __global__ void __launch_bounds__(256)
         }
     } else {
         __shared__ S g_t[TR];
-        for (int i = threadIdx.x; i < TR; i += blockDim.x) g_t[i] = (i < rows) ? ge[b * T + t0 + i] : S(0);
+        __shared__ int64_t sig_t[TR], org_t[TR];
+        for (int i = threadIdx.x; i < TR; i += blockDim.x) {
+            g_t[i] = (i < rows) ? ge[row0 + i] : S(0);
+            if (varlen && i < rows) {
+                sig_t[i] = find_row_signal(bt.off, bt.n, t0 + i);
+                org_t[i] = __ldg(bt.off + sig_t[i]);
+            }
+        }
         __syncthreads();
-        S *dst = ga + (b * T + t0) * (int64_t)M;
+        S *dst = ga + row0 * (int64_t)M;
         for (int idx = threadIdx.x; idx < rows * M; idx += blockDim.x) {
             const int rr = idx / M, i = idx - rr * M;  // i = coefficient index - 1
-            dst[idx] = -g_t[rr] * s_t[MP + rr - (i + 1)];
+            dst[idx] = -g_t[rr] * (varlen ? hist(rr, i, sig_t[rr], org_t[rr]) : s_t[MP + rr - (i + 1)]);
         }
     }
 }

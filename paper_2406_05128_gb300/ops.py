@@ -138,6 +138,98 @@ def lp_tv_backward_recompute(gs, a, e, ckpt, zi=None, *, need_ga: bool = True, n
     return ge, ga, gzi
 
 
+# ---------------------------------------------------------------------------
+# Varlen batches: signals of different lengths packed back to back
+# ---------------------------------------------------------------------------
+class Packed:
+    """Signals packed back to back for the varlen calls.
+
+    rows [total] layout: signal b holds rows offsets[b] .. offsets[b] +
+    lengths[b]; offsets are rounded up to even rows (16-byte aligned
+    coefficient rows), the rows between signals are padding.  The library
+    sees each signal as rows [offsets[b], offsets[b+1]) -- a signal followed
+    by its padding, which comes after every real output and so leaves them
+    unchanged; its inputs are zero.
+    """
+
+    def __init__(self, lengths, device, align: int = 2):
+        self.lengths = [int(x) for x in lengths]
+        starts, pos = [], 0
+        for n in self.lengths:
+            starts.append(pos)
+            pos += n
+            pos += (-pos) % align
+        self.starts = starts
+        self.total = pos
+        self.n = len(self.lengths)
+        self.offsets = torch.tensor(starts + [pos], dtype=torch.int64, device=device)
+        self.device = device
+
+    def pack(self, xs, width=None, dtype=torch.float32):
+        """Concatenate per-signal tensors ([len] or [len, width]) into rows."""
+        shape = (self.total,) if width is None else (self.total, width)
+        out = torch.zeros(shape, dtype=dtype, device=self.device)
+        for x, st, n in zip(xs, self.starts, self.lengths):
+            out[st:st + n] = x
+        return out
+
+    def unpack(self, rows):
+        return [rows[st:st + n] for st, n in zip(self.starts, self.lengths)]
+
+
+def lp_tv_forward_varlen(packed: Packed, a, e, zi=None, *, chunk: int = 0, ckpt: bool = False, ws=None):
+    """Forward filter (Eq. 5) over a varlen batch: a [total, M], e [total],
+    zi [n, M] or None.  Returns s [total] (and the chunk checkpoints
+    [nQ, M] with ckpt=True)."""
+    total, M = a.shape
+    dev = a.device
+    _check(a, "a", (packed.total, M), a.dtype, dev)
+    _check(e, "e", (packed.total,), a.dtype, dev)
+    _check(zi, "zi", (packed.n, M), a.dtype, dev)
+    code = _dtype_code(a)
+    with torch.cuda.device(dev):
+        s = torch.empty((total,), dtype=a.dtype, device=dev)
+        ck = None
+        if ckpt:
+            L = chunk or _lib.lp_tv_pick_chunk(packed.n, -(-total // max(packed.n, 1)), M, code)
+            L = -(-L // 16) * 16
+            lens = (packed.offsets[1:] - packed.offsets[:-1]).tolist()
+            nq = sum(-(-x // L) for x in lens)
+            ck = torch.empty((nq, M), dtype=a.dtype, device=dev)
+        if ws is None:
+            nb = _lib.lp_tv_workspace_bytes_varlen(packed.n, total, M, chunk, code)
+            ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        _lib.lp_tv_forward_varlen(code, packed.n, packed.offsets.data_ptr(), total, M, _ptr(a), _ptr(e), _ptr(zi),
+                                  _ptr(s), _ptr(ck), chunk, _ptr(ws), ws.numel(), _stream(dev))
+    return (s, ck) if ckpt else s
+
+
+def lp_tv_backward_varlen(packed: Packed, gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = True,
+                          chunk: int = 0, ws=None, reuse_forward: bool = False):
+    """Adjoint (Eqs. 11-12) over a varlen batch: returns (ge [total],
+    ga [total, M] or None, gzi [n, M] or None)."""
+    total, M = a.shape
+    dev = a.device
+    _check(gs, "gs", (total,), a.dtype, dev)
+    _check(s, "s", (total,), a.dtype, dev)
+    _check(zi, "zi", (packed.n, M), a.dtype, dev)
+    code = _dtype_code(a)
+    if reuse_forward and ws is None:
+        raise ValueError("reuse_forward needs the forward's workspace")
+    with torch.cuda.device(dev):
+        ge = torch.empty((total,), dtype=a.dtype, device=dev)
+        ga = torch.empty((total, M), dtype=a.dtype, device=dev) if need_ga else None
+        gzi = torch.empty((packed.n, M), dtype=a.dtype, device=dev) if need_gzi else None
+        if ws is None:
+            nb = _lib.lp_tv_workspace_bytes_varlen(packed.n, total, M, chunk, code)
+            ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward_varlen(code, packed.n, packed.offsets.data_ptr(), total, M, _ptr(gs), _ptr(a), _ptr(s),
+                                   _ptr(zi), _ptr(ge), _ptr(ga), _ptr(gzi), chunk, flags, _ptr(ws), ws.numel(),
+                                   _stream(dev))
+    return ge, ga, gzi
+
+
 class LPFunction(torch.autograd.Function):
     """Differentiable TV-LP filter: a non-differentiable fast kernel
     registered into the autograd graph with its adjoint (Sec. 2.2, Sec. 3.2).
