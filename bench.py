@@ -60,8 +60,11 @@ def parse():
     ap.add_argument("--min-warmup-s", type=float, default=1.0, help="keep warming up at least this long")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--compare-plain", action="store_true", help="also time the plain one-thread-per-signal kernels")
+    ap.add_argument("--no-compare-plain", action="store_true",
+                    help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
+    ap.add_argument("--workload", choices=("headline", "uneven"), default="headline",
+                    help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders")
     return ap.parse_args()
 
 
@@ -360,7 +363,7 @@ def run_ours(args):
 
     # plain one-thread-per-signal comparator on the same GPU (context)
     plain = None
-    if args.compare_plain and args.algo == "chunked":
+    if not args.no_compare_plain and args.algo == "chunked":
         palgo = _lib.LP_ALGO_PLAIN
         pt = []
         for i in range(3 + 5):
@@ -375,7 +378,9 @@ def run_ours(args):
             if i >= 3:
                 pt.append(ev0.elapsed_time(ev1))
         plain = {"ms_per_step": round(statistics.mean(pt), 4),
-                 "value": round(B * T / (statistics.mean(pt) * 1e-3) / 1e6, 3), "unit": UNIT}
+                 "value": round(B * T / (statistics.mean(pt) * 1e-3) / 1e6, 3), "unit": UNIT,
+                 "speedup": round(statistics.mean(pt) / ms_per_step, 2),
+                 "what": "same step with LP_ALGO_PLAIN (one thread per signal, sequential in time), host launches"}
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -489,10 +494,133 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Uneven batch: 256 signals, lengths U[12000, 240000], orders from {16, 22,
+# 30}; one varlen call per order, forward + adjoint, as one CUDA graph
+# ---------------------------------------------------------------------------
+UNEVEN_N, UNEVEN_LO, UNEVEN_HI, UNEVEN_ORDERS = 256, 12000, 240000, (16, 22, 30)
+
+
+def run_uneven(args):
+    import torch
+
+    from paper_2406_05128_gb300 import _lib, autotune, inputs, ops
+
+    _lib.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(4)
+    lengths = rng.integers(UNEVEN_LO, UNEVEN_HI + 1, size=UNEVEN_N).tolist()
+    orders = rng.choice(UNEVEN_ORDERS, size=UNEVEN_N).tolist()
+    buckets = []
+    for M in UNEVEN_ORDERS:
+        idx = [k for k in range(UNEVEN_N) if orders[k] == M]
+        if not idx:
+            continue
+        lens = [lengths[k] for k in idx]
+        sig = inputs.signals_torch(lens, M, seed=1000 + M, gen="stable", device=dev)
+        pk = ops.Packed(lens, dev)
+        a = pk.pack([x[0] for x in sig], width=M)
+        e = pk.pack([x[1] for x in sig])
+        gs = pk.pack([x[2] for x in sig])
+        del sig
+        chunk, tried = autotune.tune_varlen(lens, M, device=dev, iters=5)
+        nb = _lib.lp_tv_workspace_bytes_varlen(pk.n, pk.total, M, chunk)
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        s = torch.empty_like(e)
+        ge = torch.empty_like(e)
+        ga = torch.empty_like(a)
+        buckets.append(dict(M=M, idx=idx, lens=lens, pk=pk, a=a, e=e, gs=gs, s=s, ge=ge, ga=ga, ws=ws, chunk=chunk,
+                            tried={str(k): round(v, 4) for k, v in tried.items()}))
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sp = torch.cuda.current_stream(dev).cuda_stream
+        for bk in buckets:
+            pk = bk["pk"]
+            _lib.lp_tv_forward_varlen(_lib.LP_DTYPE_F32, pk.n, pk.offsets.data_ptr(), pk.total, bk["M"],
+                                      bk["a"].data_ptr(), bk["e"].data_ptr(), None, bk["s"].data_ptr(), None,
+                                      bk["chunk"], bk["ws"].data_ptr(), bk["ws"].numel(), sp)
+            _lib.lp_tv_backward_varlen(_lib.LP_DTYPE_F32, pk.n, pk.offsets.data_ptr(), pk.total, bk["M"],
+                                       bk["gs"].data_ptr(), bk["a"].data_ptr(), bk["s"].data_ptr(), None,
+                                       bk["ge"].data_ptr(), bk["ga"].data_ptr(), None, bk["chunk"],
+                                       _lib.LP_BWD_REUSE_FORWARD, bk["ws"].data_ptr(), bk["ws"].numel(), sp)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True, external=True)
+    ev1 = torch.cuda.Event(enable_timing=True, external=True)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ev0.record()
+        step()
+        ev1.record()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t0 = time.perf_counter()
+    times = []
+    for _ in range(args.steps):
+        graph.replay()  # inputs are GBs, far beyond L2: no flush needed
+        stream.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    t1 = time.perf_counter()
+    sampler.stop()
+    ms = statistics.mean(times)
+    nsamp = sum(lengths)
+    # one call per signal, same chunk lengths (what batching replaces)
+    per_sig = []
+    for bk in buckets[:1]:
+        M, pk = bk["M"], bk["pk"]
+        ws1 = ops.workspace(1, max(bk["lens"]), M, bk["chunk"], torch.float32, dev)
+        for rep in range(3):
+            ev0.record(stream)
+            for k, T in enumerate(bk["lens"]):
+                st = pk.starts[k]
+                a1 = bk["a"][st:st + T].view(1, T, M)
+                e1 = bk["e"][st:st + T].view(1, T)
+                s1 = ops.lp_tv_forward(a1, e1, chunk=bk["chunk"], ws=ws1)
+                ops.lp_tv_backward(bk["gs"][st:st + T].view(1, T), a1, s1, chunk=bk["chunk"], ws=ws1,
+                                   reuse_forward=True, need_gzi=False)
+            ev1.record(stream)
+            stream.synchronize()
+            if rep:
+                per_sig.append(ev0.elapsed_time(ev1))
+        per_sig_rate = sum(bk["lens"]) / (statistics.mean(per_sig) * 1e-3) / 1e6
+    step_bytes = sum((12 * bk["M"] + 20) * sum(bk["lens"]) for bk in buckets)
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = step_bytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "fwd+bwd Msamples/s, uneven batch (varlen, one call per order, CUDA graph)",
+        "value": round(nsamp / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"uneven batch: {UNEVEN_N} signals, lengths U[{UNEVEN_LO}, {UNEVEN_HI}], "
+                               f"M from {list(UNEVEN_ORDERS)}, FP32, stable reflection generator, hop 120",
+                   "samples": nsamp,
+                   "buckets": [{"M": bk["M"], "signals": len(bk["lens"]), "samples": sum(bk["lens"]),
+                                "chunk": bk["chunk"], "autotune_ms": bk["tried"]} for bk in buckets],
+                   "l2": "inputs far beyond L2, no flush"},
+        "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "GB/s": round(gbs, 1),
+                          "frac_of_hbm": round(gbs / hbm, 4)},
+        "one_call_per_signal": {"bucket_M": buckets[0]["M"], "Msamples/s": round(per_sig_rate, 3),
+                                "what": "the same signals of one order, one uniform call each (host launches)"},
+        "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
     return run_ours(args)
 
 

@@ -141,3 +141,42 @@ def batched_headline(seed=2, gen="literal", B=32, T=48000, M=22):
     """B=32, T=48000 (2 s at 24 kHz), M=22, pulse train + 0.1 N(0,1)."""
     return make(f"batched B={B} T={T} M={M}", B, T, M, seed=seed, kmax=0.95,
                 gen=gen, excitation="pulse")
+
+
+# ---------------------------------------------------------------------------
+# The same recipe on the GPU, for workloads too large to draw on the host:
+# frame-rate reflection coefficients from a seeded numpy generator, then
+# linear upsampling and the step-up recursion as torch operations.  One
+# signal per entry of `lengths`; returns lists of per-signal tensors.
+# ---------------------------------------------------------------------------
+def signals_torch(lengths, M, *, seed, kmax=0.95, gen="stable", hop=HOP, device="cuda"):
+    """Per signal b of length T_b: a [T_b, M], e [T_b] (pulse train + 0.1
+    N(0,1)), gs [T_b] ~ N(0,1), all float32 on `device`."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    decay = 0.9 if gen == "stable" else 1.0
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = []
+    for T in lengths:
+        T = int(T)
+        k = torch.tensor(reflection_frames(rng, 1, n_frames(max(T, 1), hop), M, kmax, decay)[0], device=device)
+        t = torch.arange(T, device=device)
+        f = torch.div(t, hop, rounding_mode="floor")
+        w = ((t - f * hop).to(torch.float64) / hop)[:, None]
+        kt = k[f] * (1.0 - w) + k[f + 1] * w  # [T, M] float64
+        a = torch.zeros_like(kt)
+        for m in range(1, M + 1):
+            km = kt[:, m - 1:m]
+            prev = a[:, : m - 1].clone()
+            a[:, : m - 1] = prev + km * prev.flip(1)
+            a[:, m - 1] = kt[:, m - 1]
+        f0 = float(rng.uniform(100.0, 600.0))
+        phase = torch.cumsum(torch.full((T,), f0 / SAMPLE_RATE, dtype=torch.float64, device=device), 0)
+        wraps = torch.floor(phase)
+        prev = torch.cat([torch.zeros(1, dtype=torch.float64, device=device), wraps[:-1]])
+        e = (wraps > prev).to(torch.float64) + 0.1 * torch.randn(T, generator=g, dtype=torch.float64, device=device)
+        gs = torch.randn(T, generator=g, dtype=torch.float64, device=device)
+        out.append((a.float().contiguous(), e.float(), gs.float()))
+    return out

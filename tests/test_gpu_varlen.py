@@ -138,3 +138,26 @@ def test_varlen_checkpoints_match_uniform():
     _, cku = ops.lp_tv_forward(torch.tensor(w.a, device=DEV), torch.tensor(w.e, device=DEV), zi, chunk=chunk,
                                ckpt=True)
     assert torch.equal(ck, cku.reshape(-1, M))
+
+
+def test_uneven_full_length_sampled():
+    """Full lengths of the uneven workload (up to 240000 samples) at the
+    largest order, 30: inputs drawn on the GPU with the same recipe; the
+    longest and two other signals are checked against the oracle in full."""
+    M = 30
+    lengths = [240000, 12000, 150001, 99999, 200000, 12345]
+    sig_t = inputs.signals_torch(lengths, M, seed=55, gen="stable", device=DEV)
+    pk = ops.Packed(lengths, DEV)
+    a = pk.pack([x[0] for x in sig_t], width=M)
+    e = pk.pack([x[1] for x in sig_t])
+    gs = pk.pack([x[2] for x in sig_t])
+    s = ops.lp_tv_forward_varlen(pk, a, e)
+    ge, ga, _ = ops.lp_tv_backward_varlen(pk, gs, a, s, need_gzi=False)
+    torch.cuda.synchronize()
+    assert _lib.lp_tv_device_status() == 0
+    for k in (0, 2, 5):
+        an, en, gn = (x.cpu().numpy() for x in sig_t[k])
+        rs, rge, rga, _ = O.forward_backward(an[None], en[None], gn[None])
+        for name, x, r in (("s", pk.unpack(s)[k], rs), ("ge", pk.unpack(ge)[k], rge), ("ga", pk.unpack(ga)[k], rga)):
+            err = norm_err(x.cpu().numpy()[None], r)
+            assert err.max() <= TOL_F32, (name, k, err)
