@@ -10,7 +10,8 @@ coefficients k ~ U(-0.95, 0.95) per 120-sample frame, linearly interpolated
 per sample and stepped up to direct form; dL/ds ~ N(0,1).
 
 Metric: forward+backward Msamples/s (B*T samples per step, each counted
-once).  Per rank one JSON line is formed; rank 0 prints it.  Multi-GPU runs
+once), and the serving loop's p99 latency under Poisson arrivals (the
+"serving" object of the line; --workload serving runs it alone, longer).  Per rank one JSON line is formed; rank 0 prints it.  Multi-GPU runs
 are independent replicas (each rank its own batch, no collective on the data
 path): value = all ranks' samples / max-over-ranks time.
 
@@ -63,8 +64,13 @@ def parse():
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
-    ap.add_argument("--workload", choices=("headline", "uneven"), default="headline",
-                    help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders")
+    ap.add_argument("--workload", choices=("headline", "uneven", "serving"), default="headline",
+                    help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders; "
+                         "serving: the request loop under Poisson arrivals")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="measured seconds of the serving run (default 60 for --workload serving, 15 inside the "
+                         "headline line; 0 skips it there)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -473,6 +479,10 @@ def run_ours(args):
                          "FP64 sequential C oracle, one host thread per signal"}
 
     launches_per_step = len(names_f) + len(names_b)
+    serving = None
+    serve_s = 15.0 if args.serve_seconds is None else args.serve_seconds
+    if world == 1 and serve_s > 0:
+        serving = serving_run(serve_s, rate=args.serve_rate)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -484,7 +494,7 @@ def run_ours(args):
                          f"(mean step there {statistics.mean(prof_step_ms):.4f} ms)") if prof_step_ms
                         else "events around each kernel of the timed steps",
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks, "plain_gpu_kernel": plain, "source_hash": source_hash(),
+        "clocks": clocks, "plain_gpu_kernel": plain, "serving": serving, "source_hash": source_hash(),
         "region_wall_s": round(t_region1 - t_region0, 3),
     }
     print(json.dumps(line), flush=True)
@@ -615,12 +625,183 @@ def run_uneven(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Serving: Poisson arrivals, lognormal utterance lengths, 90% synthesis and
+# 10% adaptation (forward + adjoint) requests, continuous batching in the
+# library's serving loop; latency from arrival to results in host memory
+# ---------------------------------------------------------------------------
+SERVE_M, SERVE_MEDIAN, SERVE_SIGMA, SERVE_MAX, SERVE_ADAPT = 22, 72000, 0.6, 480000, 0.1
+SERVE_BUDGET = 20 << 30
+SERVE_POOL_ROWS = 1 << 22
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256):
+    """One serving run: `warmup_s` of arrivals not counted, then `seconds`
+    measured; then a burst of `burst` requests at once for the capacity.
+    Returns the summary dict."""
+    import torch
+
+    from paper_2406_05128_gb300 import autotune, inputs, serve
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    M = SERVE_M
+    # request payloads: windows of one long synthetic signal (pinned host)
+    sig = inputs.signals_torch([SERVE_POOL_ROWS], M, seed=seed, gen="stable", device=dev)[0]
+    a_pool, e_pool, gs_pool = (x.cpu().pin_memory() for x in sig)
+    del sig
+    torch.cuda.empty_cache()
+    chunk, _ = autotune.tune_varlen([SERVE_MEDIAN, 96000], M, device=dev, iters=5)
+    rng = np.random.default_rng(seed)
+
+    def draw():
+        T = int(min(SERVE_MAX, max(1, round(SERVE_MEDIAN * np.exp(SERVE_SIGMA * rng.standard_normal())))))
+        return T, int(rng.integers(0, SERVE_POOL_ROWS - T + 1)), bool(rng.random() < SERVE_ADAPT)
+
+    # page-locked output slots, reused once their request has completed
+    free_s = [torch.empty(SERVE_MAX, pin_memory=True) for _ in range(64)]
+    free_a = [(torch.empty(SERVE_MAX, pin_memory=True), torch.empty(SERVE_MAX, pin_memory=True),
+               torch.empty((SERVE_MAX, M), pin_memory=True)) for _ in range(12)]
+
+    srv = serve.Server(M, chunk=chunk, hbm_budget=SERVE_BUDGET)
+    recs = []
+
+    def collect():
+        for r in srv.poll():
+            measured, slot = r.tag
+            (free_a if r.kind == serve.ADAPT else free_s).append(slot)
+            if r.status != 0:
+                raise RuntimeError(f"serving request failed: status {r.status}")
+            if measured:
+                recs.append((r.kind, r.T, r.latency_ns))
+
+    def submit(T, o, adapt, t_arr, measured):
+        if adapt:
+            slot = free_a.pop() if free_a else (torch.empty(SERVE_MAX, pin_memory=True),
+                                                torch.empty(SERVE_MAX, pin_memory=True),
+                                                torch.empty((SERVE_MAX, M), pin_memory=True))
+            out = (slot[0][:T], slot[1][:T], slot[2][:T])
+            srv.submit(a_pool[o:o + T], e_pool[o:o + T], gs_pool[o:o + T], arrival_ns=t_arr, out=out,
+                       tag=(measured, slot))
+        else:
+            slot = free_s.pop() if free_s else torch.empty(SERVE_MAX, pin_memory=True)
+            srv.submit(a_pool[o:o + T], e_pool[o:o + T], arrival_ns=t_arr, out=slot[:T], tag=(measured, slot))
+
+    # arrival schedule on the server's clock
+    n_total = int(rate * (warmup_s + seconds) * 1.2) + 16
+    gaps = rng.exponential(1.0 / rate, size=n_total)
+    t_begin = serve.now_ns() + 20_000_000
+    arrivals = t_begin + np.cumsum(gaps * 1e9).astype(np.int64)
+    t_meas0 = t_begin + int(warmup_s * 1e9)
+    t_end = t_meas0 + int(seconds * 1e9)
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    srv.stats(reset=True)
+    late = []
+    w0 = time.perf_counter()
+    st_meas = None
+    for t_arr in arrivals:
+        if t_arr >= t_end:
+            break
+        if st_meas is None and t_arr >= t_meas0:
+            st_meas = srv.stats(reset=True)
+        T, o, adapt = draw()
+        while True:
+            now = serve.now_ns()
+            if now >= t_arr:
+                break
+            if t_arr - now > 2_000_000:
+                time.sleep((t_arr - now - 1_000_000) / 1e9)
+            collect()
+        late.append(serve.now_ns() - int(t_arr))
+        submit(T, o, adapt, int(t_arr), t_arr >= t_meas0)
+        collect()
+    srv.drain(timeout_s=120)
+    collect()
+    w1 = time.perf_counter()
+    sampler.stop()
+    st = srv.stats(reset=True)
+    # capacity: a burst of requests at once (closed loop)
+    burst_reqs = [draw() for _ in range(burst)]
+    outs = []
+    for T, o, adapt in burst_reqs:
+        outs.append((torch.empty(T, pin_memory=True), torch.empty(T, pin_memory=True),
+                     torch.empty((T, M), pin_memory=True)) if adapt else torch.empty(T, pin_memory=True))
+    tb0 = serve.now_ns()
+    for (T, o, adapt), out in zip(burst_reqs, outs):
+        if adapt:
+            srv.submit(a_pool[o:o + T], e_pool[o:o + T], gs_pool[o:o + T], out=out, tag=(False, None))
+        else:
+            srv.submit(a_pool[o:o + T], e_pool[o:o + T], out=out, tag=(False, None))
+    done = srv.drain(timeout_s=120)
+    tb1 = serve.now_ns()
+    st_burst = srv.stats()
+    srv.close()
+    lat_ms = [x[2] / 1e6 for x in recs]
+    lat_syn = [x[2] / 1e6 for x in recs if x[0] == serve.SYNTH]
+    lat_ad = [x[2] / 1e6 for x in recs if x[0] == serve.ADAPT]
+    samples = sum(x[1] for x in recs)
+    burst_samples = sum(x[0] for x in burst_reqs)
+    its = max(st["iterations"], 1)
+    return {
+        "workload": (f"Poisson arrivals {rate:g} req/s, lengths lognormal (median {SERVE_MEDIAN} = 3 s at 24 kHz, "
+                     f"sigma {SERVE_SIGMA}, max {SERVE_MAX}), M={M}, FP32, {int(100 * (1 - SERVE_ADAPT))}% "
+                     f"synthesis / {int(100 * SERVE_ADAPT)}% forward+backward adaptation, "
+                     f"{SERVE_BUDGET >> 30} GiB HBM budget, stable reflection generator, pinned host buffers"),
+        "measured_s": seconds, "warmup_s": warmup_s, "requests": len(recs),
+        "latency_ms": {"p50": _pct(lat_ms, 50), "p90": _pct(lat_ms, 90), "p99": _pct(lat_ms, 99),
+                       "p99.9": _pct(lat_ms, 99.9), "max": max(lat_ms) if lat_ms else None,
+                       "mean": statistics.mean(lat_ms) if lat_ms else None},
+        "latency_ms_synthesis": {"p50": _pct(lat_syn, 50), "p99": _pct(lat_syn, 99), "n": len(lat_syn)},
+        "latency_ms_adaptation": {"p50": _pct(lat_ad, 50), "p99": _pct(lat_ad, 99), "n": len(lat_ad)},
+        "latency_from": "scheduled arrival (server clock) to the request's last device-to-host copy seen complete",
+        "submit_late_ms_p99": _pct([x / 1e6 for x in late], 99),
+        "Msamples/s": round(samples / seconds / 1e6, 3),
+        "offered_Msamples/s": round(rate * SERVE_MEDIAN * float(np.exp(SERVE_SIGMA ** 2 / 2)) / 1e6, 3),
+        "iterations": st["iterations"], "synthesis_blocks_per_iteration": round(st["blocks"] / its, 3),
+        "adaptation_calls": st["adapt_calls"],
+        "max_signals_iteration": st["max_signals_iter"], "carried_blocks": st["carried_blocks"],
+        "overlapped_iterations": st["overlapped"], "max_waiting": st["max_waiting"],
+        "gpu_launches": st["kernel_launches"], "ring_peak_bytes": st["ring_peak"],
+        "device_bytes": st["device_bytes"], "chunk": st["chunk"], "block_rows": 96000, "max_inflight": 4,
+        "capacity": {"requests": burst, "samples": burst_samples,
+                     "Msamples/s": round(burst_samples / ((tb1 - tb0) * 1e-9) / 1e6, 3),
+                     "s": round((tb1 - tb0) * 1e-9, 4), "iterations": st_burst["iterations"],
+                     "max_signals_iteration": st_burst["max_signals_iter"], "completed": len(done),
+                     "what": "all requests submitted at once, until the last result is on the host"},
+        "wall_s": round(w1 - w0, 2), "clocks": sampler.summary(w0, w1),
+    }
+
+
+def run_serving(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    seconds = 60.0 if args.serve_seconds is None else args.serve_seconds
+    sv = serving_run(seconds, rate=args.serve_rate)
+    line = {
+        "metric": "serving p99 latency (ms) at Poisson arrivals, continuous batching", "value": sv["latency_ms"]["p99"],
+        "unit": "ms", "n_gpus": 1, "steps": sv["requests"], "warmup": sv["warmup_s"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving: " + sv.pop("workload"), "l2": "inputs arrive from host memory"},
+        "serving": sv, "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"], "source_hash": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -62,7 +62,8 @@ enum {
     LP_EWORKSPACE = -3,   /* workspace NULL, too small or misaligned      */
     LP_ECUDA = -4,        /* a CUDA launch or runtime call failed         */
     LP_EALIGN = -5,       /* a data pointer is not aligned to its type    */
-    LP_ETOOBIG = -6       /* problem too large for the fixed scratch      */
+    LP_ETOOBIG = -6,      /* problem too large for the fixed scratch      */
+    LP_ETIMEOUT = -7      /* a bounded host-side wait ended first         */
 };
 
 enum { LP_DTYPE_F32 = 0, LP_DTYPE_F64 = 1 };

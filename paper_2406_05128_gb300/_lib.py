@@ -1,4 +1,5 @@
-"""ctypes binding of libtvlp.so (the C ABI declared in include/tvlp.h).
+"""ctypes binding of libtvlp.so (the C ABI declared in include/tvlp.h and
+include/tvlp_serve.h).
 
 Argument marshalling only: every computation runs in the CUDA kernels of the
 shared library.  Importing this module does not load the library; the first
@@ -19,6 +20,7 @@ LP_EWORKSPACE = -3
 LP_ECUDA = -4
 LP_EALIGN = -5
 LP_ETOOBIG = -6
+LP_ETIMEOUT = -7
 LP_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 LP_DTYPE_F32 = 0
@@ -27,7 +29,7 @@ LP_DTYPE_F64 = 1
 LP_ALGO_CHUNKED = 0
 LP_ALGO_PLAIN = 1
 
-# Every function declared in include/tvlp.h.
+# Every function declared in include/*.h.
 EXPORTS = (
     "lp_strerror", "lp_version", "lp_tv_pick_chunk", "lp_tv_num_chunks",
     "lp_tv_workspace_bytes", "lp_tv_forward_f32", "lp_tv_forward_f64",
@@ -36,7 +38,31 @@ EXPORTS = (
     "lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64",
     "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
+    "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
+    "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
 )
+
+LP_SERVE_SYNTH = 0
+LP_SERVE_ADAPT = 1
+
+
+class ServeConfig(ctypes.Structure):
+    """lp_serve_config (include/tvlp_serve.h)."""
+    _fields_ = [("M", ctypes.c_int), ("chunk", ctypes.c_int), ("block_rows", ctypes.c_int64),
+                ("max_signals", ctypes.c_int), ("max_iter_rows", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int), ("hbm_budget", ctypes.c_uint64)]
+
+
+class ServeStats(ctypes.Structure):
+    """lp_serve_stats (include/tvlp_serve.h)."""
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "completed", "iterations", "synth_calls", "adapt_calls", "kernel_launches", "blocks",
+        "carried_blocks", "rows", "max_signals_iter", "max_waiting", "overlapped")] + \
+        [(n, ctypes.c_uint64) for n in ("device_bytes", "ring_bytes", "ring_peak")] + \
+        [("chunk", ctypes.c_int), ("error", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 LP_BWD_REUSE_FORWARD = 1
 
@@ -96,6 +122,22 @@ def _declare(lib):
     lib.lp_tv_device_status.restype = i32
     lib.lp_tv_set_profile_events.argtypes = [c.POINTER(vp), i32]
     lib.lp_tv_set_profile_events.restype = i32
+    lib.lp_serve_default_config.argtypes = [c.POINTER(ServeConfig)]
+    lib.lp_serve_default_config.restype = None
+    lib.lp_serve_create.argtypes = [c.POINTER(ServeConfig), c.POINTER(vp)]
+    lib.lp_serve_create.restype = i32
+    lib.lp_serve_destroy.argtypes = [vp]
+    lib.lp_serve_destroy.restype = i32
+    lib.lp_serve_submit.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp, vp, vp, i64]
+    lib.lp_serve_submit.restype = i32
+    lib.lp_serve_poll.argtypes = [vp, c.POINTER(i64), c.POINTER(i64), c.POINTER(i32), i32]
+    lib.lp_serve_poll.restype = i32
+    lib.lp_serve_drain.argtypes = [vp, i64]
+    lib.lp_serve_drain.restype = i32
+    lib.lp_serve_stats_get.argtypes = [vp, c.POINTER(ServeStats), i32]
+    lib.lp_serve_stats_get.restype = i32
+    lib.lp_serve_now_ns.argtypes = []
+    lib.lp_serve_now_ns.restype = i64
     return lib
 
 

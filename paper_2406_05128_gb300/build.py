@@ -1,8 +1,10 @@
 """Build the CUDA library libtvlp.so for sm_103a, in-tree.
 
 Each (scalar type, padded order) instantiation is its own translation unit,
-compiled in parallel with nvcc, then linked with the C ABI into one shared
-library: paper_2406_05128_gb300/_build/libtvlp.so.
+compiled in parallel with nvcc, then linked with the C ABI and the serving
+engine into one shared library: paper_2406_05128_gb300/_build/libtvlp.so.
+The serving loop's planner is also built alone with the host compiler
+(libtvlp_plan.so, no CUDA) for its CPU simulation.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtvlp.so")
+PLAN_LIB = os.path.join(BUILD, "libtvlp_plan.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
@@ -34,7 +37,7 @@ def nvcc() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "tvlp.h")]
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
 
 
 def _units():
@@ -46,6 +49,7 @@ def _units():
                           [f"-DTVLP_SCALAR={scalar}", f"-DTVLP_MP={mp}"]))
     units.append((os.path.join(CSRC, "tvlp_api.cu"), os.path.join(BUILD, "tvlp_api.o"), []))
     units.append((os.path.join(CSRC, "tvlp_noalloc.cu"), os.path.join(BUILD, "tvlp_noalloc.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_serve.cu"), os.path.join(BUILD, "tvlp_serve.o"), []))
     return units
 
 
@@ -69,6 +73,24 @@ def _compile(unit, verbose: bool, ptxas_v: bool):
     return res.stderr
 
 
+def build_plan(force: bool = False) -> str:
+    """The planner simulation library (host compiler only)."""
+    os.makedirs(BUILD, exist_ok=True)
+    src = os.path.join(CSRC, "serve_sim.cpp")
+    deps = [src, os.path.join(CSRC, "serve_plan.h")]
+    if force or _stale(PLAN_LIB, deps):
+        cxx = shutil.which("g++") or shutil.which("c++")
+        if cxx is None:
+            raise RuntimeError("no host C++ compiler found for libtvlp_plan.so")
+        tmp = PLAN_LIB + f".tmp{os.getpid()}"
+        cmd = [cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, src, "-o", tmp]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"host build of libtvlp_plan.so failed:\n{res.stderr}")
+        os.replace(tmp, PLAN_LIB)
+    return PLAN_LIB
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, jobs: int | None = None) -> str:
     """Compile every instantiation (in parallel) and link libtvlp.so."""
     os.makedirs(BUILD, exist_ok=True)
@@ -84,11 +106,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, job
     objs = [u[1] for u in _units()]
     if force or todo or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")
         os.replace(tmp, LIB)
+    build_plan(force)
     return LIB
 
 

@@ -1,10 +1,11 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports
-every function include/tvlp.h declares.  Host-only entry points (error
+every function include/*.h declares.  Host-only entry points (error
 strings, chunk and workspace queries, argument checks) are exercised; no
 call here launches a kernel."""
 from __future__ import annotations
 
 import ctypes
+import glob
 import os
 import re
 import shutil
@@ -12,7 +13,7 @@ import shutil
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "tvlp.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +26,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lp_\w+)\s*\(", text)))
 
@@ -43,7 +44,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_only_entry_points(lib):
     from paper_2406_05128_gb300 import _lib
     assert "sm_103a" in _lib.version()
-    for code in (0, -1, -2, -3, -4, -5):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert _lib.strerror(code)
     L = _lib.lp_tv_pick_chunk(32, 48000, 22)
     assert L > 0 and L % 16 == 0
@@ -67,3 +68,27 @@ def test_argument_errors_without_launching(lib):
     assert g(2, 10, 40, 8, 8, 8, None, 8, None, None, 0, 0, 0, None, 0, None) == _lib.LP_EUNSUPPORTED  # f64: M <= 16
     assert g(2, 10, 4, 16, 16, None, None, 16, 16, None, 0, 0, 0, None, 0, None) == _lib.LP_EINVAL  # ga needs s
     assert g(2, 10, 4, 16, 16, 16, None, 16, None, None, 0, 0, 4, None, 0, None) == _lib.LP_EINVAL  # bad flag
+
+
+def test_serve_host_only_entry_points(lib):
+    """Configuration checks of the serving loop run before any CUDA call."""
+    from paper_2406_05128_gb300 import _lib
+    cfg = _lib.ServeConfig()
+    lib.lp_serve_default_config(ctypes.byref(cfg))
+    assert (cfg.M, cfg.block_rows, cfg.max_signals, cfg.max_inflight) == (22, 96000, 256, 4)
+    assert cfg.hbm_budget == 20 << 30
+    h = ctypes.c_void_p()
+    for field, bad in (("M", 0), ("M", 33), ("max_signals", 0), ("max_inflight", 0), ("max_inflight", 17),
+                       ("block_rows", -2), ("max_iter_rows", 1)):
+        c = _lib.ServeConfig()
+        lib.lp_serve_default_config(ctypes.byref(c))
+        setattr(c, field, bad)
+        assert lib.lp_serve_create(ctypes.byref(c), ctypes.byref(h)) == _lib.LP_EINVAL, field
+    c = _lib.ServeConfig()
+    lib.lp_serve_default_config(ctypes.byref(c))
+    c.chunk = 256
+    c.hbm_budget = 64 << 20  # cannot hold one largest iteration of 4 M rows
+    assert lib.lp_serve_create(ctypes.byref(c), ctypes.byref(h)) == _lib.LP_ETOOBIG
+    assert lib.lp_serve_submit(None, 0, 0, 10, 8, 8, None, 8, None, None, 0) == _lib.LP_EINVAL
+    t0 = lib.lp_serve_now_ns()
+    assert lib.lp_serve_now_ns() >= t0 > 0
