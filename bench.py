@@ -193,10 +193,15 @@ class ClockSampler:
                 "power_w_max": max((num(r[2]) or 0) for r in loaded)}
 
 
+KERNEL_SOURCES = ("tvlp_kernels.cuh", "tvlp_impl.h", "tvlp_impl.cuh", "tvlp_inst.cu", "tvlp_api.cu")
+
+
 def source_hash():
+    """Hash of the sources the hot-path kernels are built from (the serving
+    engine and the planner are not part of it)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2406_05128_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
