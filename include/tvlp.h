@@ -235,6 +235,67 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
                               void *stream);
 
 /*
+ * Coefficients generated in the kernels instead of streamed (FP32, chunked
+ * algorithm; the per-sample coefficient preparation of Sec. 4.3 and the
+ * time-invariant filter of Sec. 2.2 / Eq. 2).  Every pass that would read
+ * a row a(t) computes it from a small input instead:
+ *
+ * Frames: k [B][F][M] reflection coefficients per frame, F = ceil(T/hop)+1,
+ *   k[(b*F + f)*M + m-1] = k_m of frame f of signal b.  Frame f is anchored
+ *   at sample f*hop and linearly interpolated to every sample,
+ *     k_m(t) = k_m[f] + w (k_m[f+1] - k_m[f]),  f = t / hop,
+ *     w = (t - f*hop) / hop,
+ *   then stepped up to the direct form of A(z) = 1 + sum_i a_i z^-i:
+ *     a^(m)_i = a^(m-1)_i + k_m a^(m-1)_{m-i} (i < m),  a^(m)_m = k_m,
+ *   and a(t) = a^(M).  The filter is Eq. 5 with that a(t).  The backward
+ *   returns ge (Eq. 11), gzi, and gk [B][F][M] = dL/dk: Eq. 12 taken
+ *   through the step-up and the interpolation (NULL: not computed).
+ * Time-invariant: a [B][M], one coefficient row per signal (Eq. 2).  The
+ *   backward returns ga [B][M] = sum_t dL/da(t) (Eq. 12 summed over time,
+ *   which is Eq. 3's two-filter gradient).
+ * Workspace: lp_tv_workspace_bytes_frames / _ti (the scan's workspace plus
+ * the gradient's scratch).  A forward leaves the chunk transfers in it for
+ * a backward with LP_BWD_REUSE_FORWARD, as for the streamed calls.  Other
+ * conventions, shapes and errors as for lp_tv_forward_f32 /
+ * lp_tv_backward_f32; hop >= 1.
+ *
+ * lp_tv_forward_frames_varlen_f32: varlen batches (offsets as for
+ * lp_tv_forward_varlen_f32) with frame_offsets [n] (DEVICE, int64): signal
+ * b's frames start at frame frame_offsets[b] of k, and it has
+ * ceil(len_b/hop)+1 of them.  Workspace: lp_tv_workspace_bytes_varlen.
+ */
+size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop,
+                                    int chunk);
+int lp_tv_forward_frames_f32(int B, int64_t T, int M, int hop,
+                             const float *k, const float *e,
+                             const float *zi, float *s, float *ckpt,
+                             int chunk, void *workspace,
+                             size_t workspace_bytes, void *stream);
+int lp_tv_backward_frames_f32(int B, int64_t T, int M, int hop,
+                              const float *gs, const float *k,
+                              const float *s, const float *zi, float *ge,
+                              float *gk, float *gzi, int chunk, int flags,
+                              void *workspace, size_t workspace_bytes,
+                              void *stream);
+int lp_tv_forward_frames_varlen_f32(int n, const int64_t *offsets,
+                                    int64_t total, int M, int hop,
+                                    const int64_t *frame_offsets,
+                                    const float *k, const float *e,
+                                    const float *zi, float *s, float *ckpt,
+                                    int chunk, void *workspace,
+                                    size_t workspace_bytes, void *stream);
+size_t lp_tv_workspace_bytes_ti(int B, int64_t T, int M, int chunk);
+int lp_tv_forward_ti_f32(int B, int64_t T, int M, const float *a,
+                         const float *e, const float *zi, float *s,
+                         float *ckpt, int chunk, void *workspace,
+                         size_t workspace_bytes, void *stream);
+int lp_tv_backward_ti_f32(int B, int64_t T, int M, const float *gs,
+                          const float *a, const float *s, const float *zi,
+                          float *ge, float *ga, float *gzi, int chunk,
+                          int flags, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+/*
  * Device status word of the current device: 0 while every bounded wait
  * inside the kernels completed, 1 once a shared-memory bulk-copy wait gave
  * up, 2 once a scan wait for other warps' results gave up (the kernel then

@@ -16,6 +16,11 @@ Parity status of each routine (see the tests under ``tests/test_oracle_*``):
             scipy.signal.lfilter, the IIR expansion of Eqs. 6-8, invariants.
   backward  pinned: dense transposed solve, finite differences, Eqs. 9-10,
             GOLF's time-invariant gradient (Eq. 3), adjoint identity.
+  coeffs    pinned: the Levinson recursion of scipy.linalg.solve_toeplitz,
+            the closed forms for M = 1, 2, frame anchors and midpoints,
+            minimum phase (roots inside the unit circle).
+  coeffs_adjoint  pinned: finite differences of <ga, a(k)> with respect to
+            every frame coefficient, closed forms for M = 1, 2.
 """
 from __future__ import annotations
 
@@ -58,6 +63,10 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.tvlp_oracle_forward_batch.restype = None
     lib.tvlp_oracle_backward_batch.argtypes = [i64, i64, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
     lib.tvlp_oracle_backward_batch.restype = None
+    lib.tvlp_oracle_coeffs_batch.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.tvlp_oracle_coeffs_batch.restype = None
+    lib.tvlp_oracle_coeffs_adjoint_batch.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    lib.tvlp_oracle_coeffs_adjoint_batch.restype = None
     return lib
 
 
@@ -129,3 +138,39 @@ def forward_backward(a, e, gs, zi=None, lib=None):
     s = forward(a, e, zi, lib=lib)
     ge, ga, gzi = backward(a, s, gs, zi, lib=lib)
     return s, ge, ga, gzi
+
+
+def n_frames(T: int, hop: int) -> int:
+    """Frames of a T-sample signal at this hop: ceil(T / hop) + 1."""
+    return -(-T // hop) + 1
+
+
+def coeffs(k, T, hop, lib=None):
+    """Sec. 4.3: per-sample direct-form coefficients a [B,T,M] (or [T,M])
+    from frame-rate reflection coefficients k [B,F,M] (or [F,M]), F =
+    ceil(T/hop)+1: linear interpolation, then the step-up recursion."""
+    lib = lib or _get()
+    k = _f64(k)
+    single = k.ndim == 2
+    if single:
+        k = k[None]
+    B, F, M = k.shape
+    assert F == n_frames(T, hop), (F, T, hop)
+    a = np.empty((B, T, M), np.float64)
+    lib.tvlp_oracle_coeffs_batch(B, T, M, hop, _ptr(k), _ptr(a))
+    return a[0] if single else a
+
+
+def coeffs_adjoint(k, ga, hop, lib=None):
+    """dL/dk [B,F,M] from dL/da [B,T,M] for the coefficients of coeffs()."""
+    lib = lib or _get()
+    k, ga = _f64(k), _f64(ga)
+    single = k.ndim == 2
+    if single:
+        k, ga = k[None], ga[None]
+    B, F, M = k.shape
+    T = ga.shape[1]
+    assert F == n_frames(T, hop) and ga.shape == (B, T, M)
+    gk = np.empty((B, F, M), np.float64)
+    lib.tvlp_oracle_coeffs_adjoint_batch(B, T, M, hop, _ptr(k), _ptr(ga), _ptr(gk))
+    return gk[0] if single else gk

@@ -23,6 +23,7 @@
  */
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 /* s(t - i) for the forward recursion, reading the initial state for t-i<0. */
 static double past_output(const double *s, const double *zi, int64_t t, int i)
@@ -113,4 +114,115 @@ void tvlp_oracle_backward_batch(int64_t B, int64_t T, int M, const double *a,
                              zi ? zi + b * M : NULL, gs + b * T, ge + b * T,
                              ga ? ga + b * T * M : NULL,
                              gzi ? gzi + b * M : NULL);
+}
+
+/*
+ * Sec. 4.3: per-sample coefficients from frame-rate reflection coefficients.
+ *   k  [F][M]  k[f*M + (m-1)] = k_m of frame f; frame f sits at sample f*hop
+ *              (F = ceil(T/hop) + 1 frames, so the last segment has an end)
+ * Linear interpolation between the two frames around t:
+ *   f = floor(t / hop), w = (t - f*hop) / hop,  k_m(t) = (1 - w) k_m[f] + w k_m[f+1]
+ * then the step-up recursion to the direct form of A(z) = 1 + sum a_i z^-i:
+ *   a^(m)_i = a^(m-1)_i + k_m a^(m-1)_{m-i}  (i = 1..m-1),   a^(m)_m = k_m,
+ * and a(t) = a^(M).  Orders up to TVLP_ORACLE_MAX_M.
+ */
+#define TVLP_ORACLE_MAX_M 64
+
+static double interp_k(const double *k, int M, int hop, int64_t t, int m)
+{
+    int64_t f = t / hop;
+    double w = (double)(t - f * hop) / (double)hop;
+    return (1.0 - w) * k[f * M + (m - 1)] + w * k[(f + 1) * M + (m - 1)];
+}
+
+/* A[m][i] = a^(m)_i for m = 0..M, i = 1..m (row m holds the order-m filter). */
+static void step_up(int M, const double *km, double A[][TVLP_ORACLE_MAX_M + 1])
+{
+    for (int m = 1; m <= M; ++m) {
+        for (int i = 1; i < m; ++i)
+            A[m][i] = A[m - 1][i] + km[m] * A[m - 1][m - i];
+        A[m][m] = km[m];
+    }
+}
+
+void tvlp_oracle_coeffs(int64_t T, int M, int hop, const double *k, double *a)
+{
+    double (*A)[TVLP_ORACLE_MAX_M + 1] = malloc(sizeof(double[TVLP_ORACLE_MAX_M + 1][TVLP_ORACLE_MAX_M + 1]));
+    double km[TVLP_ORACLE_MAX_M + 1] = {0.0};
+    for (int64_t t = 0; t < T; ++t) {
+        for (int m = 1; m <= M; ++m)
+            km[m] = interp_k(k, M, hop, t, m);
+        step_up(M, km, A);
+        for (int i = 1; i <= M; ++i)
+            a[t * M + (i - 1)] = A[M][i];
+    }
+    free(A);
+}
+
+/*
+ * dL/dk from dL/da (ga [T][M]) for the coefficients of tvlp_oracle_coeffs:
+ * the chain rule in forward mode.  For every sample the derivatives
+ * D[m][i][j] = d a^(m)_i / d k_j(t) follow the step-up term by term,
+ *   D[m][i][j] = D[m-1][i][j] + k_m D[m-1][m-i][j] + [j == m] a^(m-1)_{m-i}
+ *   D[m][m][j] = [j == m],
+ * then dL/dk_j(t) = sum_i ga_i(t) D[M][i][j], and the interpolation sends
+ * (1 - w) of it to frame f and w of it to frame f+1.  gk [F][M] is
+ * overwritten (F = ceil(T/hop) + 1).
+ */
+void tvlp_oracle_coeffs_adjoint(int64_t T, int M, int hop, const double *k,
+                                const double *ga, double *gk)
+{
+    double (*A)[TVLP_ORACLE_MAX_M + 1] = malloc(sizeof(double[TVLP_ORACLE_MAX_M + 1][TVLP_ORACLE_MAX_M + 1]));
+    double (*D)[TVLP_ORACLE_MAX_M + 1][TVLP_ORACLE_MAX_M + 1] =
+        malloc(sizeof(double[TVLP_ORACLE_MAX_M + 1][TVLP_ORACLE_MAX_M + 1][TVLP_ORACLE_MAX_M + 1]));
+    double km[TVLP_ORACLE_MAX_M + 1] = {0.0};
+    int64_t F = (T + hop - 1) / hop + 1;
+    for (int64_t x = 0; x < F * M; ++x)
+        gk[x] = 0.0;
+    for (int64_t t = 0; t < T; ++t) {
+        for (int m = 1; m <= M; ++m)
+            km[m] = interp_k(k, M, hop, t, m);
+        step_up(M, km, A);
+        for (int m = 1; m <= M; ++m) {
+            for (int j = 1; j <= M; ++j) {
+                for (int i = 1; i < m; ++i) {
+                    double d = D[m - 1][i][j] + km[m] * D[m - 1][m - i][j];
+                    if (j == m)
+                        d += A[m - 1][m - i];
+                    D[m][i][j] = d;
+                }
+                D[m][m][j] = (j == m) ? 1.0 : 0.0;
+            }
+        }
+        int64_t f = t / hop;
+        double w = (double)(t - f * hop) / (double)hop;
+        for (int j = 1; j <= M; ++j) {
+            double g = 0.0;
+            for (int i = 1; i <= M; ++i)
+                g += ga[t * M + (i - 1)] * D[M][i][j];
+            gk[f * M + (j - 1)] += (1.0 - w) * g;
+            gk[(f + 1) * M + (j - 1)] += w * g;
+        }
+    }
+    free(D);
+    free(A);
+}
+
+/* Batched forms of the coefficient routines: k [B][F][M], a / ga [B][T][M]. */
+void tvlp_oracle_coeffs_batch(int64_t B, int64_t T, int M, int hop,
+                              const double *k, double *a)
+{
+    int64_t F = (T + hop - 1) / hop + 1;
+    for (int64_t b = 0; b < B; ++b)
+        tvlp_oracle_coeffs(T, M, hop, k + b * F * M, a + b * T * M);
+}
+
+void tvlp_oracle_coeffs_adjoint_batch(int64_t B, int64_t T, int M, int hop,
+                                      const double *k, const double *ga,
+                                      double *gk)
+{
+    int64_t F = (T + hop - 1) / hop + 1;
+    for (int64_t b = 0; b < B; ++b)
+        tvlp_oracle_coeffs_adjoint(T, M, hop, k + b * F * M, ga + b * T * M,
+                                   gk + b * F * M);
 }

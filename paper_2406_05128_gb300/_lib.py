@@ -38,6 +38,8 @@ EXPORTS = (
     "lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64",
     "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
+    "lp_tv_workspace_bytes_frames", "lp_tv_forward_frames_f32", "lp_tv_backward_frames_f32",
+    "lp_tv_forward_frames_varlen_f32", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
     "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
 )
@@ -116,6 +118,20 @@ def _declare(lib):
         f = getattr(lib, name)
         f.argtypes = [i32, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
         f.restype = i32
+    lib.lp_tv_workspace_bytes_frames.argtypes = [i32, i64, i32, i32, i32]
+    lib.lp_tv_workspace_bytes_frames.restype = sz
+    lib.lp_tv_forward_frames_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+    lib.lp_tv_forward_frames_f32.restype = i32
+    lib.lp_tv_backward_frames_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+    lib.lp_tv_backward_frames_f32.restype = i32
+    lib.lp_tv_forward_frames_varlen_f32.argtypes = [i32, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+    lib.lp_tv_forward_frames_varlen_f32.restype = i32
+    lib.lp_tv_workspace_bytes_ti.argtypes = [i32, i64, i32, i32]
+    lib.lp_tv_workspace_bytes_ti.restype = sz
+    lib.lp_tv_forward_ti_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+    lib.lp_tv_forward_ti_f32.restype = i32
+    lib.lp_tv_backward_ti_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+    lib.lp_tv_backward_ti_f32.restype = i32
     lib.lp_tv_forward_noalloc_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp]
     lib.lp_tv_forward_noalloc_f32.restype = i32
     lib.lp_tv_device_status.argtypes = [i32]
@@ -244,3 +260,37 @@ def lp_tv_device_status(reset: bool = False) -> int:
     if rc < 0:
         raise LPError(rc, "lp_tv_device_status")
     return rc
+
+
+def lp_tv_workspace_bytes_frames(B, T, M, hop, chunk=0):
+    return load().lp_tv_workspace_bytes_frames(B, T, M, hop, chunk)
+
+
+def lp_tv_forward_frames(B, T, M, hop, k, e, zi, s, ckpt, chunk, ws, ws_bytes, stream):
+    _check(load().lp_tv_forward_frames_f32(B, T, M, hop, k, e, zi, s, ckpt, chunk, ws, ws_bytes, stream),
+           "lp_tv_forward_frames_f32")
+
+
+def lp_tv_backward_frames(B, T, M, hop, gs, k, s, zi, ge, gk, gzi, chunk, flags, ws, ws_bytes, stream):
+    _check(load().lp_tv_backward_frames_f32(B, T, M, hop, gs, k, s, zi, ge, gk, gzi, chunk, flags, ws, ws_bytes,
+                                            stream), "lp_tv_backward_frames_f32")
+
+
+def lp_tv_forward_frames_varlen(n, offsets, total, M, hop, frame_offsets, k, e, zi, s, ckpt, chunk, ws, ws_bytes,
+                                stream):
+    _check(load().lp_tv_forward_frames_varlen_f32(n, offsets, total, M, hop, frame_offsets, k, e, zi, s, ckpt, chunk,
+                                                  ws, ws_bytes, stream), "lp_tv_forward_frames_varlen_f32")
+
+
+def lp_tv_workspace_bytes_ti(B, T, M, chunk=0):
+    return load().lp_tv_workspace_bytes_ti(B, T, M, chunk)
+
+
+def lp_tv_forward_ti(B, T, M, a, e, zi, s, ckpt, chunk, ws, ws_bytes, stream):
+    _check(load().lp_tv_forward_ti_f32(B, T, M, a, e, zi, s, ckpt, chunk, ws, ws_bytes, stream),
+           "lp_tv_forward_ti_f32")
+
+
+def lp_tv_backward_ti(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream):
+    _check(load().lp_tv_backward_ti_f32(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream),
+           "lp_tv_backward_ti_f32")

@@ -124,6 +124,25 @@ template <> struct Dispatch<float> {
         }
         return EUNSUPPORTED;
     }
+#define TVLP_ALL_F32(CALL)                                                                            \
+    switch (p.MP) {                                                                                   \
+        TVLP_CASE(2, CALL) TVLP_CASE(4, CALL) TVLP_CASE(8, CALL) TVLP_CASE(12, CALL) TVLP_CASE(16, CALL) \
+        TVLP_CASE(22, CALL) TVLP_CASE(30, CALL) TVLP_CASE(32, CALL)                                   \
+    }                                                                                                 \
+    return EUNSUPPORTED;
+    static int forward_gen(const Problem &p, const CoefSrc &src, const S *e, const S *zi, S *s, S *ck, void *ws,
+                           cudaStream_t st) {
+        TVLP_ALL_F32(forward_gen(p, src, e, zi, s, ck, ws, st))
+    }
+    static int backward_gen(const Problem &p, const CoefSrc &src, const S *gs, const S *s, const S *zi, S *ge,
+                            S *gzi, int flags, void *ws, cudaStream_t st) {
+        TVLP_ALL_F32(backward_gen(p, src, gs, s, zi, ge, gzi, flags, ws, st))
+    }
+    static int grad_src(const Problem &p, const CoefSrc &src, const S *ge, const S *s, const S *zi, S *gk,
+                        void *scratch, cudaStream_t st) {
+        TVLP_ALL_F32(grad_src(p, src, ge, s, zi, gk, scratch, st))
+    }
+#undef TVLP_ALL_F32
 };
 
 template <> struct Dispatch<double> {
@@ -465,6 +484,120 @@ int backward_varlen_impl(int dtype, int n, const int64_t *off, int64_t total, in
     return Dispatch<S>::backward(p, gs, a, s, zi, ge, ga, gzi, LP_ALGO_CHUNKED, flags, ws, st);
 }
 
+
+// ---------------------------------------------------------------------------
+// Generated coefficients: time-invariant rows (SRC_CONST) and frame-rate
+// reflection coefficients (SRC_FRAMES).  FP32, chunked.
+// ---------------------------------------------------------------------------
+int64_t frames_of(int64_t T, int hop) { return ceil_div(T, hop) + 1; }
+
+// scratch of the coefficient gradient, after the scan workspace
+size_t grad_scratch_bytes(const Problem &p, int kind, int64_t F) {
+    if (p.M == 0 || p.T == 0 || p.B == 0) return 0;
+    if (kind == SRC_CONST) return align256((size_t)p.B * (size_t)ceil_div(p.T, 1024) * p.MP * sizeof(float));
+    return align256(2 * (size_t)p.B * (size_t)F * p.M * sizeof(float));
+}
+
+size_t gen_workspace_bytes(const Problem &p, int kind, int64_t F) {
+    return align256(workspace_for(p, LP_DTYPE_F32)) + grad_scratch_bytes(p, kind, F);
+}
+
+CoefSrc make_src(int kind, const float *k, int64_t F, int hop) {
+    CoefSrc c;
+    c.kind = kind;
+    c.k = k;
+    c.F = F;
+    c.hop = hop > 0 ? hop : 1;
+    c.inv_hop = 1.0f / (float)c.hop;
+    return c;
+}
+
+int forward_gen_impl(int kind, int B, int64_t T, int M, int hop, const float *k, const float *e, const float *zi,
+                     float *s, float *ckpt, int chunk, void *ws, size_t wsb, void *stream) {
+    if (kind == SRC_FRAMES && hop < 1) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem(B, T, M, chunk, LP_DTYPE_F32, &p);
+    if (rc != LP_OK) return rc;
+    if (B == 0 || T == 0) return LP_OK;
+    if (e == nullptr || s == nullptr || (M > 0 && k == nullptr)) return LP_EINVAL;
+    if (!aligned(e, 4) || !aligned(s, 4) || !aligned(k, 4) || !aligned(zi, 4) || !aligned(ckpt, 4)) return LP_EALIGN;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M == 0) {
+        if (cudaMemcpyAsync(s, e, (size_t)B * T * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    const int64_t F = kind == SRC_FRAMES ? frames_of(T, hop) : 1;
+    if (ws == nullptr || !aligned(ws, 256) || wsb < workspace_for(p, LP_DTYPE_F32)) return LP_EWORKSPACE;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    return Dispatch<float>::forward_gen(p, make_src(kind, k, F, hop), e, zi, s, ckpt, ws, st);
+}
+
+int backward_gen_impl(int kind, int B, int64_t T, int M, int hop, const float *gs, const float *k, const float *s,
+                      const float *zi, float *ge, float *gk, float *gzi, int chunk, int flags, void *ws, size_t wsb,
+                      void *stream) {
+    if (kind == SRC_FRAMES && hop < 1) return LP_EINVAL;
+    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem(B, T, M, chunk, LP_DTYPE_F32, &p);
+    if (rc != LP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B == 0 || (M == 0 && T == 0)) return LP_OK;
+    const int64_t F = kind == SRC_FRAMES ? frames_of(T, hop) : 1;
+    if (T == 0) {
+        // no samples: every gradient is zero
+        if (gzi != nullptr && cudaMemsetAsync(gzi, 0, (size_t)B * M * sizeof(float), st) != cudaSuccess)
+            return LP_ECUDA;
+        if (gk != nullptr && cudaMemsetAsync(gk, 0, (size_t)B * F * M * sizeof(float), st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if (gs == nullptr || ge == nullptr || (M > 0 && k == nullptr) || (gk != nullptr && s == nullptr))
+        return LP_EINVAL;
+    if (!aligned(gs, 4) || !aligned(ge, 4) || !aligned(k, 4) || !aligned(s, 4) || !aligned(zi, 4) ||
+        !aligned(gk, 4) || !aligned(gzi, 4))
+        return LP_EALIGN;
+    if (M == 0) {
+        if (cudaMemcpyAsync(ge, gs, (size_t)B * T * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if (ws == nullptr || !aligned(ws, 256) || wsb < (gk != nullptr ? gen_workspace_bytes(p, kind, F)
+                                                                    : workspace_for(p, LP_DTYPE_F32)))
+        return LP_EWORKSPACE;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    const CoefSrc src = make_src(kind, k, F, hop);
+    if ((rc = Dispatch<float>::backward_gen(p, src, gs, s, zi, ge, gzi, flags, ws, st)) != LP_OK) return rc;
+    if (gk == nullptr) return LP_OK;
+    void *scratch = static_cast<char *>(ws) + align256(workspace_for(p, LP_DTYPE_F32));
+    return Dispatch<float>::grad_src(p, src, ge, s, zi, gk, scratch, st);
+}
+
+int forward_frames_varlen_impl(int n, const int64_t *off, int64_t total, int M, int hop, const int64_t *foff,
+                               const float *k, const float *e, const float *zi, float *s, float *ckpt, int chunk,
+                               void *ws, size_t wsb, void *stream) {
+    if (hop < 1) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem_varlen(n, total, M, chunk, LP_DTYPE_F32, off, &p);
+    if (rc != LP_OK) return rc;
+    if (n == 0 || total == 0) return LP_OK;
+    if (off == nullptr || e == nullptr || s == nullptr || (M > 0 && (k == nullptr || foff == nullptr)))
+        return LP_EINVAL;
+    if (!aligned(off, 8) || !aligned(foff, 8) || !aligned(e, 4) || !aligned(s, 4) || !aligned(k, 4) ||
+        !aligned(zi, 4) || !aligned(ckpt, 4))
+        return LP_EALIGN;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M == 0) {
+        if (cudaMemcpyAsync(s, e, (size_t)total * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if ((rc = check_workspace(p, LP_DTYPE_F32, LP_ALGO_CHUNKED, ws, wsb)) != LP_OK) return rc;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    CoefSrc src = make_src(SRC_FRAMES, k, 0, hop);
+    src.foff = foff;
+    return Dispatch<float>::forward_gen(p, src, e, zi, s, ckpt, ws, st);
+}
 }  // namespace
 
 extern "C" {
@@ -599,6 +732,47 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total, int 
                               void *stream) {
     return backward_varlen_impl<double>(LP_DTYPE_F64, n, offsets, total, M, gs, a, s, zi, ge, ga, gzi, chunk, flags,
                                         workspace, workspace_bytes, stream);
+}
+
+size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop, int chunk) {
+    Problem p;
+    if (hop < 1 || make_problem(B, T, M, chunk, LP_DTYPE_F32, &p) != LP_OK) return 0;
+    return gen_workspace_bytes(p, SRC_FRAMES, frames_of(T, hop));
+}
+
+int lp_tv_forward_frames_f32(int B, int64_t T, int M, int hop, const float *k, const float *e, const float *zi,
+                             float *s, float *ckpt, int chunk, void *ws, size_t wsb, void *stream) {
+    return forward_gen_impl(SRC_FRAMES, B, T, M, hop, k, e, zi, s, ckpt, chunk, ws, wsb, stream);
+}
+
+int lp_tv_backward_frames_f32(int B, int64_t T, int M, int hop, const float *gs, const float *k, const float *s,
+                              const float *zi, float *ge, float *gk, float *gzi, int chunk, int flags, void *ws,
+                              size_t wsb, void *stream) {
+    return backward_gen_impl(SRC_FRAMES, B, T, M, hop, gs, k, s, zi, ge, gk, gzi, chunk, flags, ws, wsb, stream);
+}
+
+int lp_tv_forward_frames_varlen_f32(int n, const int64_t *offsets, int64_t total, int M, int hop,
+                                    const int64_t *frame_offsets, const float *k, const float *e, const float *zi,
+                                    float *s, float *ckpt, int chunk, void *ws, size_t wsb, void *stream) {
+    return forward_frames_varlen_impl(n, offsets, total, M, hop, frame_offsets, k, e, zi, s, ckpt, chunk, ws, wsb,
+                                      stream);
+}
+
+size_t lp_tv_workspace_bytes_ti(int B, int64_t T, int M, int chunk) {
+    Problem p;
+    if (make_problem(B, T, M, chunk, LP_DTYPE_F32, &p) != LP_OK) return 0;
+    return gen_workspace_bytes(p, SRC_CONST, 1);
+}
+
+int lp_tv_forward_ti_f32(int B, int64_t T, int M, const float *a, const float *e, const float *zi, float *s,
+                         float *ckpt, int chunk, void *ws, size_t wsb, void *stream) {
+    return forward_gen_impl(SRC_CONST, B, T, M, 0, a, e, zi, s, ckpt, chunk, ws, wsb, stream);
+}
+
+int lp_tv_backward_ti_f32(int B, int64_t T, int M, const float *gs, const float *a, const float *s, const float *zi,
+                          float *ge, float *ga, float *gzi, int chunk, int flags, void *ws, size_t wsb,
+                          void *stream) {
+    return backward_gen_impl(SRC_CONST, B, T, M, 0, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, wsb, stream);
 }
 
 }  // extern "C"

@@ -105,21 +105,21 @@ template <typename S, int MP> struct Launch {
         return k < 0 ? 0 : k;
     }
 
-    template <bool BWD>
+    template <bool BWD, int SRC = SRC_STREAM>
     static cudaError_t summary(const Problem &p, const Batch &bt, const S *a, const S *u, S *Y, unsigned *cnt,
-                               cudaStream_t st) {
+                               cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
         static bool done[kMaxDevices] = {};
         const int W = k1_warps_per_block<S, MP>();
         const size_t smem = (size_t)W * GE::WARP_BYTES;
-        auto kern = k1_summary<S, MP, GE::G, GE::R, BWD>;
+        auto kern = k1_summary<S, MP, GE::G, GE::R, BWD, SRC>;
         cudaError_t err = allow_smem(kern, smem, done);
         if (err != cudaSuccess) return err;
         const int64_t per_block = (int64_t)W * GE::CPW;
         const int64_t grid = (p.NQ + per_block - 1) / per_block;
         // the next pass (re-run or adjoint re-run) starts on this pass's first stages
-        const int l2 = l2_word(l2_keep(p), L2_LAST, L2_FIRST);
+        const int l2 = SRC == SRC_STREAM ? l2_word(l2_keep(p), L2_LAST, L2_FIRST) : 0;
         return launch(kern, dim3((unsigned)grid), dim3(32 * W), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Y,
-                      p.M == MP ? 1 : 0, cnt, p.B, l2, p.status);
+                      p.M == MP ? 1 : 0, cnt, p.B, l2, p.status, cs);
     }
 
     // Two-level scan in one cooperative launch: as many blocks as the items
@@ -152,18 +152,18 @@ template <typename S, int MP> struct Launch {
                       GZ, GX, zi, X, ckpt, cnt, p.status);
     }
 
-    template <int MODE, bool EXACT>
+    template <int MODE, bool EXACT, int SRC = SRC_STREAM>
     static cudaError_t rec_exact(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin,
                                  const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
         static bool done[kMaxDevices] = {};
         using RG = RecGeo<S, MP>;
-        auto kern = k_rec<S, MP, EXACT, MODE>;
+        auto kern = k_rec<S, MP, EXACT, MODE, SRC>;
         cudaError_t err = allow_smem(kern, RG::SMEM, done);
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + kRecChunks - 1) / kRecChunks;
         return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
-                      out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status);
+                      out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status, cs);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
@@ -174,6 +174,15 @@ template <typename S, int MP> struct Launch {
                            int xs = MP) {
         if (p.M == MP) return rec_exact<MODE, true>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
         return rec_exact<MODE, false>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
+    }
+
+    // the same with generated coefficient rows (rows are written whole, so
+    // the exact-order kernel serves every M)
+    template <int MODE, int SRC>
+    static cudaError_t rec_gen(const Problem &p, const Batch &bt, const S *u, const S *Xin, const S *zi, S *out,
+                               S *Zout, S *gzi, int reverse, cudaStream_t st, const CoefSrc &cs,
+                               unsigned *cnt = nullptr) {
+        return rec_exact<MODE, true, SRC>(p, bt, nullptr, u, Xin, zi, out, Zout, gzi, reverse, cnt, 0, MP, st, cs);
     }
 
     static cudaError_t grad_a(const Problem &p, const Batch &bt, const S *ge, const S *s, const S *zi, S *ga,
@@ -296,6 +305,113 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
     }
     if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(q, bt, ge, s, zi, ga, st)));
     return OK;
+}
+
+// Forward and adjoint with generated coefficient rows: the chunked path of
+// forward / backward with every pass over `a` taking its rows from the
+// source (SRC_CONST or SRC_FRAMES).  FP32 only.
+template <typename S, int MP, int SRC>
+int forward_gen_src(const Problem &p, const CoefSrc &src, const S *e, const S *zi, S *s, S *ckpt, void *ws,
+                    cudaStream_t st) {
+    using LN = Launch<S, MP>;
+    const Batch bt = batch_of(p, ws, sizeof(S));
+    if (build_tables(p, bt, st) != cudaSuccess) return ECUDA;
+    S *Y = LN::region(p, ws, 0);
+    S *X = LN::region(p, ws, 1);
+    S *GY = LN::region(p, ws, 4);
+    S *GX = LN::region(p, ws, 6);
+    unsigned *cnt = LN::counters(p, ws);
+    TVLP_LAUNCH(0, (LN::template summary<false, SRC>(p, bt, nullptr, e, Y, cnt, st, src)));
+    TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, bt, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
+    TVLP_LAUNCH(2, (LN::template rec_gen<FWD_RERUN, SRC>(p, bt, e, X, zi, s, nullptr, nullptr, 1, st, src)));
+    return OK;
+}
+
+template <typename S, int MP, int SRC>
+int backward_gen_src(const Problem &p, const CoefSrc &src, const S *gs, const S *zi, S *ge, S *gzi, int flags,
+                     void *ws, cudaStream_t st) {
+    using LN = Launch<S, MP>;
+    int k = 0;
+    const Batch bt = batch_of(p, ws, sizeof(S));
+    if (build_tables(p, bt, st) != cudaSuccess) return ECUDA;
+    S *Y = LN::region(p, ws, 0);
+    S *Z = LN::region(p, ws, 2);
+    S *Wst = LN::region(p, ws, 3);
+    S *GY = LN::region(p, ws, 4);
+    S *GZ = LN::region(p, ws, 5);
+    S *GX = LN::region(p, ws, 6);
+    unsigned *cnt = LN::counters(p, ws);
+    (void)zi;
+    if (flags & BWD_REUSE_FORWARD) {
+        TVLP_LAUNCH(k++, (LN::template rec_gen<BWD_ZERO, SRC>(p, bt, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st,
+                                                              src, cnt)));
+        TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS>(p, bt, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
+    } else {
+        TVLP_LAUNCH(k++, (LN::template summary<true, SRC>(p, bt, nullptr, gs, Y, cnt, st, src)));
+        TVLP_LAUNCH(k++, (LN::template scan<CH_BWD>(p, bt, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt,
+                                                    st)));
+    }
+    TVLP_LAUNCH(k++, (LN::template rec_gen<BWD_RERUN, SRC>(p, bt, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, src)));
+    return OK;
+}
+
+template <typename S, int MP>
+int Impl<S, MP>::forward_gen(const Problem &p, const CoefSrc &src, const S *e, const S *zi, S *s, S *ckpt, void *ws,
+                             cudaStream_t st) {
+    if constexpr (sizeof(S) != 4) {
+        return EUNSUPPORTED;
+    } else {
+        if (src.kind == SRC_CONST) return forward_gen_src<S, MP, SRC_CONST>(p, src, e, zi, s, ckpt, ws, st);
+        if (src.kind == SRC_FRAMES) return forward_gen_src<S, MP, SRC_FRAMES>(p, src, e, zi, s, ckpt, ws, st);
+        return EINVAL_;
+    }
+}
+
+template <typename S, int MP>
+int Impl<S, MP>::backward_gen(const Problem &p, const CoefSrc &src, const S *gs, const S *s, const S *zi, S *ge,
+                              S *gzi, int flags, void *ws, cudaStream_t st) {
+    (void)s;
+    if constexpr (sizeof(S) != 4) {
+        return EUNSUPPORTED;
+    } else {
+        if (src.kind == SRC_CONST) return backward_gen_src<S, MP, SRC_CONST>(p, src, gs, zi, ge, gzi, flags, ws, st);
+        if (src.kind == SRC_FRAMES)
+            return backward_gen_src<S, MP, SRC_FRAMES>(p, src, gs, zi, ge, gzi, flags, ws, st);
+        return EINVAL_;
+    }
+}
+
+template <typename S, int MP>
+int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, const S *s, const S *zi, S *gk,
+                          void *scratch, cudaStream_t st) {
+    if constexpr (sizeof(S) != 4) {
+        return EUNSUPPORTED;
+    } else {
+        if (p.off != nullptr) return EUNSUPPORTED;
+        float *sc = static_cast<float *>(scratch);
+        if (src.kind == SRC_CONST) {
+            const int64_t tiles = (p.T + kGradRows - 1) / kGradRows;
+            TVLP_LAUNCH(0, (launch(k_grad_const<MP>, dim3((unsigned)tiles, (unsigned)p.B), dim3(kGradThreads), 0, st,
+                                   false, p.T, p.M, tiles, ge, s, zi, sc)));
+            const int64_t n = (int64_t)p.B * p.M;
+            TVLP_LAUNCH(1, (launch(k_grad_const_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, p.B,
+                                   p.M, MP, tiles, sc, gk)));
+            return OK;
+        }
+        if (src.kind == SRC_FRAMES) {
+            using FG = FrameGradGeo<MP>;
+            const int64_t items = (int64_t)p.B * src.F;
+            const int64_t n = items * p.M;
+            float *lo = sc, *hi = sc + n;
+            TVLP_LAUNCH(0, (launch(k_grad_frames<MP>, dim3((unsigned)((items + FG::WARPS - 1) / FG::WARPS)),
+                                   dim3(32 * FG::WARPS), 0, st, false, p.B, p.T, p.M, src.F, src.hop, src.inv_hop,
+                                   src.k, ge, s, zi, lo, hi)));
+            TVLP_LAUNCH(1, (launch(k_grad_frames_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, n,
+                                   lo, hi, gk)));
+            return OK;
+        }
+        return EINVAL_;
+    }
 }
 
 #undef TVLP_LAUNCH

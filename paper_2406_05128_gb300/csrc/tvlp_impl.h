@@ -29,6 +29,26 @@ struct Problem {
     int *status;  // device status word (bounded waits record timeouts here)
 };
 
+// Where the streamed passes take the coefficient rows a(t) from.
+//   SRC_STREAM  read a [rows][M] from memory (the default path)
+//   SRC_CONST   one row per signal, k = a [signals][M]: the time-invariant
+//               filter of Eq. 2
+//   SRC_FRAMES  generated in the kernels from frame-rate reflection
+//               coefficients k [frames][M] (Sec. 4.3): frame f is anchored
+//               at sample f*hop, linearly interpolated to every sample, then
+//               stepped up to the direct form,
+//                 a^(m)_i = a^(m-1)_i + k_m a^(m-1)_{m-i} (i < m), a^(m)_m = k_m
+//               Signal b's frames start at frame foff[b] (varlen) or b*F.
+enum { SRC_STREAM = 0, SRC_CONST = 1, SRC_FRAMES = 2 };
+struct CoefSrc {
+    int kind = SRC_STREAM;
+    const float *k = nullptr;
+    const int64_t *foff = nullptr;  // varlen: first frame of every signal (device)
+    int64_t F = 0;                  // frames per signal (uniform batches)
+    int hop = 0;
+    float inv_hop = 0.f;
+};
+
 // Per-instantiation geometry the host needs before launching.
 struct Shape {
     int chunks_per_warp;   // K1 chunks held by one warp
@@ -46,6 +66,18 @@ template <typename S, int MP> struct Impl {
                      cudaStream_t st);
     static int backward(const Problem &p, const S *gs, const S *a, const S *s, const S *zi, S *ge, S *ga,
                         S *gzi, int algo, int flags, void *ws, cudaStream_t st);
+    // The chunked forward and adjoint with the coefficient rows generated in
+    // the kernels (src.kind SRC_CONST or SRC_FRAMES; FP32 only).  The
+    // adjoint writes ge and gzi; the coefficient gradient is grad_src.
+    static int forward_gen(const Problem &p, const CoefSrc &src, const S *e, const S *zi, S *s, S *ckpt, void *ws,
+                           cudaStream_t st);
+    static int backward_gen(const Problem &p, const CoefSrc &src, const S *gs, const S *s, const S *zi, S *ge,
+                            S *gzi, int flags, void *ws, cudaStream_t st);
+    // dL/d(source): SRC_CONST, gk [signals][M] = sum_t dL/da(t) (Eq. 12
+    // summed over time, Eq. 3); SRC_FRAMES, gk [frames][M] through the
+    // step-up and the interpolation.  `scratch` holds grad_src_scratch bytes.
+    static int grad_src(const Problem &p, const CoefSrc &src, const S *ge, const S *s, const S *zi, S *gk,
+                        void *scratch, cudaStream_t st);
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

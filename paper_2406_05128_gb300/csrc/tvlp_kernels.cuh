@@ -46,6 +46,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tvlp_impl.h"
+
 namespace tvlp {
 
 constexpr int SR = 8;    // rows per compute block (register window)
@@ -414,6 +416,61 @@ __device__ __forceinline__ ChunkPos chunk_pos(const Batch &bt, int64_t q, int L)
     return p;
 }
 
+// ---------------------------------------------------------------------------
+// Generated coefficient rows (CoefSrc, FP32).  gen_row writes a(t) of signal
+// b, sample t, as MP floats (zero past the order M, or for an invalid row).
+//   SRC_CONST:  the signal's one row k[b][0..M).
+//   SRC_FRAMES: k(t) = k[f] + w (k[f+1] - k[f]), f = t / hop,
+//               w = (t - f hop) / hop (Sec. 4.3: per-sample linear
+//               interpolation of the frame-rate reflection coefficients),
+//               then the step-up to the direct form of A(z) = 1 + sum a_i z^-i:
+//               a^(m)_i = a^(m-1)_i + k_m a^(m-1)_{m-i}, a^(m)_m = k_m.
+// ---------------------------------------------------------------------------
+template <int MP>
+__device__ __forceinline__ void stepup_row(float (&a)[MP], const float *__restrict__ k0,
+                                           const float *__restrict__ k1, float w, int M) {
+#pragma unroll
+    for (int m = 0; m < MP; ++m) a[m] = 0.f;
+#pragma unroll
+    for (int m = 1; m <= MP; ++m) {
+        float km = 0.f;
+        if (m <= M) {
+            const float x0 = __ldg(k0 + m - 1), x1 = __ldg(k1 + m - 1);
+            km = fmaf(w, x1 - x0, x0);
+        }
+        // pairs (i, m - i) read the old values of both
+#pragma unroll
+        for (int i = 1; 2 * i < m; ++i) {
+            const float lo = a[i - 1], hi = a[m - i - 1];
+            a[i - 1] = fmaf(km, hi, lo);
+            a[m - i - 1] = fmaf(km, lo, hi);
+        }
+        if (m % 2 == 0) a[m / 2 - 1] = fmaf(km, a[m / 2 - 1], a[m / 2 - 1]);
+        a[m - 1] = km;
+    }
+}
+
+template <int MP, int SRC>
+__device__ __forceinline__ void gen_row(const CoefSrc &cs, int M, int64_t b, int64_t t, bool valid, float *dst) {
+    float a[MP];
+    if (!valid) {
+#pragma unroll
+        for (int m = 0; m < MP; ++m) a[m] = 0.f;
+    } else if constexpr (SRC == SRC_CONST) {
+#pragma unroll
+        for (int m = 0; m < MP; ++m) a[m] = m < M ? __ldg(cs.k + b * M + m) : 0.f;
+    } else {
+        const int64_t f0 = cs.foff != nullptr ? __ldg(cs.foff + b) : b * cs.F;
+        const int64_t f = t / cs.hop;
+        const float w = (float)(t - f * cs.hop) * cs.inv_hop;
+        const float *k0 = cs.k + (f0 + f) * (int64_t)M;
+        stepup_row<MP>(a, k0, k0 + M, w, M);
+    }
+    // rows are MP floats (MP even): 8-byte stores
+#pragma unroll
+    for (int m = 0; m < MP; m += 2) *reinterpret_cast<float2 *>(dst + m) = make_float2(a[m], a[m + 1]);
+}
+
 // Per-signal scan geometry: first chunk, chunks, first group, groups, group size.
 struct SigScan {
     int64_t cbase, nC, gbase;
@@ -539,6 +596,27 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *
     cp_async_commit();
 }
 
+// Generated stage k (SRC_CONST / SRC_FRAMES): the warp writes the CPW x SRS
+// coefficient rows itself, then completes the stage's mbarrier phase with no
+// bytes in flight, so the consumer waits exactly as for a copied stage.
+template <int MP, typename GE, bool BWD, int SRC>
+__device__ __forceinline__ void k1_gen_stage(float *a_st, uint64_t *bar, const CoefSrc &cs, int M, int L, int k,
+                                             int lane, int64_t my_b, int64_t my_t0, int my_valid) {
+    constexpr int CPW = GE::CPW;
+    const int roff = BWD ? L - (k + 1) * SRS : k * SRS;
+#pragma unroll 1
+    for (int e = lane; e < CPW * SRS; e += 32) {
+        const int ch = e / SRS, r = e % SRS;
+        const int64_t b = __shfl_sync(0xffffffffu, my_b, ch);
+        const int64_t t0 = __shfl_sync(0xffffffffu, my_t0, ch);
+        const int valid = __shfl_sync(0xffffffffu, my_valid, ch);
+        gen_row<MP, SRC>(cs, M, b, t0 + roff + r, roff + r < valid, a_st + ch * GE::CS + r * MP);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar, 0u);
+    cp_async_commit();
+}
+
 // Input samples of stage k for the warp's chunks: element e = lane + 32*i
 // (i < UPL) is row e % SRS of chunk e / SRS; zero past the signal's end.
 template <typename S, int MP, typename GE, bool BWD>
@@ -556,11 +634,12 @@ __device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__rest
     }
 }
 
-template <typename S, int MP, int G, int R, bool BWD>
+template <typename S, int MP, int G, int R, bool BWD, int SRC = SRC_STREAM>
 __global__ void __launch_bounds__(256, 1)
     k1_summary(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
                S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
-               int *__restrict__ status) {
+               int *__restrict__ status, CoefSrc cs) {
+    static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
     using GE = SumGeo<S, MP, G, R>;
     constexpr int CPW = GE::CPW, NS = GE::NS, WIN = MP + SR;
     constexpr int RS = YGeo<S, MP>::RS, YS = YGeo<S, MP>::YS;
@@ -585,13 +664,24 @@ __global__ void __launch_bounds__(256, 1)
     }
     __syncwarp();
     // lane ch < CPW describes chunk q0 + ch: its first row and valid rows
-    int64_t my_base = 0;
+    int64_t my_base = 0, my_b = 0, my_t0 = 0;
     int my_valid = 0;
     if (lane < CPW && q0 + lane < NQ) {
         const ChunkPos cp = chunk_pos(bt, q0 + lane, L);
         my_base = cp.base;
         my_valid = cp.valid;
+        my_b = cp.b;
+        my_t0 = cp.c * (int64_t)L;
     }
+    // stage k of the coefficient rows into ring slot `slot`
+    auto stage = [&](int slot, int k) {
+        if constexpr (SRC == SRC_STREAM)
+            k1_issue_stage<S, MP, GE, BWD>(a_buf + slot * GE::A_STAGE, bars + slot, a, M, L, k, lane, my_base,
+                                           my_valid, exact, l2);
+        else
+            k1_gen_stage<MP, GE, BWD, SRC>(reinterpret_cast<float *>(a_buf + slot * GE::A_STAGE), bars + slot, cs, M,
+                                           L, k, lane, my_b, my_t0, my_valid);
+    };
     const int grp = lane / G, g = lane % G;
     const int nblk = L / SRS;
 
@@ -622,7 +712,7 @@ __global__ void __launch_bounds__(256, 1)
     const S flag0 = (g == 0) ? S(1) : S(0);
 
     S uv[GE::UPL];
-    k1_issue_stage<S, MP, GE, BWD>(a_buf, bars, a, M, L, 0, lane, my_base, my_valid, exact, l2);
+    if constexpr (SRC == SRC_STREAM) stage(0, 0);
     k1_load_inputs<S, MP, GE, BWD>(uv, u, L, 0, lane, my_base, my_valid);
     pdl_wait();
     pdl_release();
@@ -630,6 +720,8 @@ __global__ void __launch_bounds__(256, 1)
     // (warp 0 of block 0 always owns chunks, so it is still here)
     if (scan_cnt != nullptr && blockIdx.x == 0 && warp == 0)
         for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
+    // generated rows may read frames an earlier kernel wrote: after the wait
+    if constexpr (SRC != SRC_STREAM) stage(0, 0);
 #pragma unroll
     for (int i = 0; i < GE::UPL; ++i)
         if (lane + 32 * i < GE::U_STAGE) u_buf[lane + 32 * i] = uv[i];
@@ -639,8 +731,7 @@ __global__ void __launch_bounds__(256, 1)
         const bool more = k + 1 < nblk;
         if (more) {
             // the other slot was consumed in the previous iteration
-            k1_issue_stage<S, MP, GE, BWD>(a_buf + (slot ^ 1) * GE::A_STAGE, bars + (slot ^ 1), a, M, L, k + 1, lane,
-                                           my_base, my_valid, exact, l2);
+            stage(slot ^ 1, k + 1);
             k1_load_inputs<S, MP, GE, BWD>(uv, u, L, k + 1, lane, my_base, my_valid);
         } else {
             cp_async_commit();
@@ -837,6 +928,30 @@ __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S 
     cp_async_commit();
 }
 
+// Generated stage s (SRC_CONST / SRC_FRAMES) for all kRecChunks chunks of
+// the warp: all 32 lanes write rows (chunk e / SRS, row e % SRS) into the
+// owner lanes' rings, then the stage's mbarrier phase completes with no
+// bytes in flight.
+template <int MP, bool BWD, int SRC>
+__device__ __forceinline__ void rec_gen_stage(unsigned char *smem, int slot, uint64_t *bar, const CoefSrc &cs, int M,
+                                              int L, int s, int lane, int64_t b, int64_t t0, int n, bool active) {
+    using RG = RecGeo<float, MP>;
+    const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
+#pragma unroll 1
+    for (int e = lane; e < kRecChunks * SRS; e += 32) {
+        const int ch = e / SRS, r = e % SRS;
+        const int64_t bb = __shfl_sync(0xffffffffu, b, ch);
+        const int64_t tt = __shfl_sync(0xffffffffu, t0, ch);
+        const int nn = __shfl_sync(0xffffffffu, n, ch);
+        const bool act = __shfl_sync(0xffffffffu, active ? 1 : 0, ch) != 0;
+        float *ring = reinterpret_cast<float *>(smem + (size_t)ch * RG::LW * 4);
+        gen_row<MP, SRC>(cs, M, bb, tt + roff + r, act && roff + r < nn, ring + slot * RG::A_ST + r * MP);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar, 0u);
+    cp_async_commit();
+}
+
 template <typename S, bool BWD>
 __device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restrict__ u, int L, int s, bool active,
                                                 int64_t base, int n) {
@@ -845,12 +960,13 @@ __device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restric
     for (int r = 0; r < SRS; ++r) uv[r] = (active && roff + r < n) ? __ldg(u + base + roff + r) : S(0);
 }
 
-template <typename S, int MP, bool EXACT, int MODE>
+template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM>
 __global__ void __launch_bounds__(32)
     k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
           S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
-          int *__restrict__ status) {
+          int *__restrict__ status, CoefSrc cs) {
+    static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
     using RG = RecGeo<S, MP>;
     constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
@@ -884,14 +1000,22 @@ __global__ void __launch_bounds__(32)
         n = cp.valid;
     }
     const int nblk = L / SRS;
+    auto stage = [&](int slot, int s) {
+        if constexpr (SRC == SRC_STREAM)
+            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + slot * RG::A_ST, bars + slot, a, M, L, s, active, base, n, l2,
+                                               owner);
+        else
+            rec_gen_stage<MP, BWD, SRC>(rec_smem, slot, bars + slot, cs, M, L, s, lane, b, c * (int64_t)L, n, active);
+    };
     S ucur[SRS], unxt[SRS];
-    rec_issue_stage<S, MP, EXACT, BWD>(a_ring, bars, a, M, L, 0, active, base, n, l2, owner);
+    if constexpr (SRC == SRC_STREAM) stage(0, 0);
     rec_load_inputs<S, BWD>(ucur, u, L, 0, active, base, n);
     pdl_wait();
     pdl_release();
     // a scan that follows counts finished groups per signal from zero
     if (scan_cnt != nullptr && blockIdx.x == 0)
         for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
+    if constexpr (SRC != SRC_STREAM) stage(0, 0);
     S h[WIN];
 #pragma unroll
     for (int m = 0; m < WIN; ++m) h[m] = S(0);
@@ -922,8 +1046,7 @@ __global__ void __launch_bounds__(32)
         const int slot = s & 1;
         const bool more = s + 1 < nblk;
         if (more) {
-            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + (slot ^ 1) * RG::A_ST, bars + (slot ^ 1), a, M, L, s + 1, active,
-                                               base, n, l2, owner);
+            stage(slot ^ 1, s + 1);
             rec_load_inputs<S, BWD>(unxt, u, L, s + 1, active, base, n);
         } else {
             cp_async_commit();
@@ -1611,6 +1734,237 @@ __global__ void __launch_bounds__(256)
             dst[idx] = -g_t[rr] * (varlen ? hist(rr, i, sig_t[rr], org_t[rr]) : s_t[MP + rr - (i + 1)]);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Gradients with respect to generated coefficients (uniform batches, FP32).
+// Both start from Eq. 12, dL/da_i(t) = -ge(t) s(t-i) with s(t-i) = zi[i-t-1]
+// for t < i, and never store it.
+// ---------------------------------------------------------------------------
+constexpr int kGradRows = 1024;  // rows of one time-invariant gradient tile
+constexpr int kGradThreads = 128;
+
+// SRC_CONST (Eq. 3: the time-invariant gradient is Eq. 12 summed over time):
+// part[b][tile][i] = sum over the tile's rows t of ge(t) s(t-i-1) (the sign
+// is applied by k_grad_finish).  Threads (grp, i): grp = tid / 32 takes rows
+// grp, grp + 4, ... of the tile; the four groups are added in a fixed order.
+template <int MP>
+__global__ void __launch_bounds__(kGradThreads)
+    k_grad_const(int64_t T, int M, int64_t tiles, const float *__restrict__ ge, const float *__restrict__ s,
+                 const float *__restrict__ zi, float *__restrict__ part) {
+    __shared__ float sg[kGradRows];
+    __shared__ float ss[kGradRows + MP];
+    __shared__ float red[kGradThreads / 32][32];
+    const int64_t b = blockIdx.y, tile = blockIdx.x;
+    const int64_t t0 = tile * kGradRows;
+    const int tid = threadIdx.x;
+    pdl_wait();
+    pdl_release();
+    for (int r = tid; r < kGradRows + MP; r += kGradThreads) {
+        const int64_t t = t0 - MP + r;  // ss[r] = s(t0 - MP + r)
+        float v = 0.f;
+        if (t >= 0 && t < T) v = s[b * T + t];
+        else if (t < 0 && zi != nullptr && -t <= M) v = zi[b * M + (-t - 1)];
+        ss[r] = v;
+        if (r < kGradRows) sg[r] = (t0 + r < T) ? ge[b * T + t0 + r] : 0.f;
+    }
+    __syncthreads();
+    const int grp = tid / 32, i = tid % 32;
+    float acc = 0.f;
+    if (i < MP) {
+        for (int r = grp; r < kGradRows; r += kGradThreads / 32) acc = fmaf(sg[r], ss[MP + r - i - 1], acc);
+    }
+    red[grp][i] = acc;
+    __syncthreads();
+    if (tid < MP) {
+        float v = 0.f;
+#pragma unroll
+        for (int g = 0; g < kGradThreads / 32; ++g) v += red[g][tid];
+        part[(b * tiles + tile) * MP + tid] = v;
+    }
+}
+
+// gk[b][i] = -sum over tiles of part[b][tile][i], tiles in order.
+static __global__ void k_grad_const_finish(int B, int M, int MP, int64_t tiles, const float *__restrict__ part,
+                                    float *__restrict__ gk) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    pdl_wait();
+    pdl_release();
+    if (idx >= (int64_t)B * M) return;
+    const int64_t b = idx / M;
+    const int i = (int)(idx % M);
+    float v = 0.f;
+    for (int64_t t = 0; t < tiles; ++t) v += part[(b * tiles + t) * MP + i];
+    gk[idx] = -v;
+}
+
+// SRC_FRAMES: one warp per (signal, frame segment f), samples
+// t in [f hop, min((f+1) hop, T)).  Per sample, with G = dL/da(t):
+//   step-up reversed (m = M .. 1), with A^(m) the order-m coefficients:
+//     dL/dk_m(t) = G^(m)_m + sum_{i<m} G^(m)_i A^(m-1)_{m-i}
+//     G^(m-1)_j  = G^(m)_j + k_m G^(m)_{m-j}            (j < m)
+//   interpolation reversed: frame f gets (1 - w) dL/dk(t), frame f+1 gets
+//   w dL/dk(t).
+// A^(m) for the reverse sweep: the forward step-up keeps A at every SEG-th
+// order, and each segment of orders is recomputed from its checkpoint, so
+// everything stays in registers with compile-time indices.  The 32 lanes'
+// dL/dk(t) go through shared memory and are summed per coefficient in a
+// fixed order.  lo[b][f] and hi[b][f+1] receive the segment's two parts.
+template <int MP> struct FrameGradGeo {
+    static constexpr int SEG = 6;
+    static constexpr int NSEG = (MP + SEG - 1) / SEG;
+    static constexpr int WARPS = 4;
+};
+
+template <int MP>
+__device__ __forceinline__ void stepup_stage(float (&a)[MP], float km, int m) {
+    // m is a compile-time constant after unrolling
+#pragma unroll
+    for (int i = 1; 2 * i < MP + 1; ++i) {
+        if (2 * i < m) {
+            const float lo = a[i - 1], hi = a[m - i - 1];
+            a[i - 1] = fmaf(km, hi, lo);
+            a[m - i - 1] = fmaf(km, lo, hi);
+        }
+    }
+    if (m % 2 == 0) a[m / 2 - 1] = fmaf(km, a[m / 2 - 1], a[m / 2 - 1]);
+    a[m - 1] = km;
+}
+
+template <int MP>
+__global__ void __launch_bounds__(32 * FrameGradGeo<MP>::WARPS)
+    k_grad_frames(int B, int64_t T, int M, int64_t F, int hop, float inv_hop, const float *__restrict__ k,
+                  const float *__restrict__ ge, const float *__restrict__ s, const float *__restrict__ zi,
+                  float *__restrict__ lo_out, float *__restrict__ hi_out) {
+    using FG = FrameGradGeo<MP>;
+    constexpr int SEG = FG::SEG, NSEG = FG::NSEG;
+    __shared__ float gsh[FG::WARPS][32][MP + 1];
+    __shared__ float wsh[FG::WARPS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * FG::WARPS + warp;  // (b, f)
+    pdl_wait();
+    pdl_release();
+    if (item >= (int64_t)B * F) return;
+    const int64_t b = item / F, f = item % F;
+    const int64_t ts = f * hop, te = ts + hop < T ? ts + hop : T;
+    const float *k0 = k + (b * F + f) * (int64_t)M;
+    const float *k1 = f + 1 < F ? k0 + M : k0;
+    float lo_acc = 0.f, hi_acc = 0.f;  // lane m < M: coefficient m+1
+    for (int64_t base = ts; base < te; base += 32) {
+        const int64_t t = base + lane;
+        const bool valid = t < te;
+        float g[MP];  // G^(m) for the current m, g[i-1] = G_i
+        float w = 0.f;
+        if (valid) {
+            w = (float)(t - ts) * inv_hop;
+            const float gt = ge[b * T + t];
+#pragma unroll
+            for (int i = 1; i <= MP; ++i) {
+                float sv = 0.f;
+                if (i <= M) {
+                    const int64_t u = t - i;
+                    if (u >= 0) sv = s[b * T + u];
+                    else if (zi != nullptr) sv = zi[b * M + (-u - 1)];
+                }
+                g[i - 1] = -gt * sv;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < MP; ++i) g[i] = 0.f;
+        }
+        // k(t) and the forward step-up with checkpoints every SEG orders
+        float kt[MP];
+#pragma unroll
+        for (int m = 1; m <= MP; ++m) {
+            float km = 0.f;
+            if (m <= M) {
+                const float x0 = __ldg(k0 + m - 1), x1 = __ldg(k1 + m - 1);
+                km = fmaf(w, x1 - x0, x0);
+            }
+            kt[m - 1] = km;
+        }
+        float ck[NSEG][MP];
+        {
+            float a[MP];
+#pragma unroll
+            for (int i = 0; i < MP; ++i) a[i] = 0.f;
+#pragma unroll
+            for (int m = 1; m <= MP; ++m) {
+                if (m % SEG == 1) {
+#pragma unroll
+                    for (int i = 0; i < MP; ++i) ck[(m - 1) / SEG][i] = a[i];  // A^(m-1)
+                }
+                stepup_stage<MP>(a, kt[m - 1], m);
+            }
+        }
+        // dL/dk_m(t) goes straight to the warp's row of shared memory
+        float *gk = gsh[warp][lane];
+#pragma unroll
+        for (int j = NSEG - 1; j >= 0; --j) {
+            const int mlo = j * SEG;  // segment orders mlo+1 .. mhi
+            const int mhi = (j + 1) * SEG < MP ? (j + 1) * SEG : MP;
+            // A^(mlo) .. A^(mhi-1)
+            float seg[SEG][MP];
+#pragma unroll
+            for (int i = 0; i < MP; ++i) seg[0][i] = ck[j][i];
+#pragma unroll
+            for (int q = 1; q < SEG; ++q) {
+                if (mlo + q < mhi) {
+#pragma unroll
+                    for (int i = 0; i < MP; ++i) seg[q][i] = seg[q - 1][i];
+                    stepup_stage<MP>(seg[q], kt[mlo + q - 1], mlo + q);
+                }
+            }
+#pragma unroll
+            for (int q = SEG - 1; q >= 0; --q) {
+                const int m = mlo + q + 1;  // stage m uses A^(m-1) = seg[q]
+                if (m <= mhi) {
+                    float d = g[m - 1];
+#pragma unroll
+                    for (int i = 1; i < MP; ++i)
+                        if (i < m) d = fmaf(g[i - 1], seg[q][m - i - 1], d);
+                    gk[m - 1] = valid ? d : 0.f;
+                    const float km = kt[m - 1];
+#pragma unroll
+                    for (int jj = 1; 2 * jj < MP + 1; ++jj) {
+                        if (2 * jj < m) {
+                            const float x = g[jj - 1], y = g[m - jj - 1];
+                            g[jj - 1] = fmaf(km, y, x);
+                            g[m - jj - 1] = fmaf(km, x, y);
+                        }
+                    }
+                    if (m % 2 == 0) g[m / 2 - 1] = fmaf(km, g[m / 2 - 1], g[m / 2 - 1]);
+                }
+            }
+        }
+        wsh[warp][lane] = valid ? w : 0.f;
+        __syncwarp();
+        if (lane < MP) {
+            float l = 0.f, h = 0.f;
+            for (int r = 0; r < 32; ++r) {
+                const float v = gsh[warp][r][lane], wr = wsh[warp][r];
+                h = fmaf(wr, v, h);
+                l = fmaf(1.f - wr, v, l);
+            }
+            lo_acc += l;
+            hi_acc += h;
+        }
+        __syncwarp();
+    }
+    if (lane < M) {
+        lo_out[(b * F + f) * (int64_t)M + lane] = lo_acc;
+        if (f + 1 < F) hi_out[(b * F + f + 1) * (int64_t)M + lane] = hi_acc;
+        if (f == 0) hi_out[(b * F) * (int64_t)M + lane] = 0.f;
+    }
+}
+
+// gk = lo + hi, element by element.
+static __global__ void k_grad_frames_finish(int64_t n, const float *__restrict__ lo, const float *__restrict__ hi,
+                                     float *__restrict__ gk) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    pdl_wait();
+    pdl_release();
+    if (i < n) gk[i] = lo[i] + hi[i];
 }
 
 }  // namespace tvlp

@@ -276,3 +276,219 @@ def lp_filter(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked", checkpoin
     """Differentiable s = LP_{a(t)}(e) with optional initial state zi.
     checkpoint=True keeps per-chunk states instead of s for the backward."""
     return LPFunction.apply(a, e, zi, chunk, algo, checkpoint)
+
+
+# ---------------------------------------------------------------------------
+# Coefficients generated in the kernels (FP32): frame-rate reflection
+# coefficients (Sec. 4.3) or one time-invariant row per signal (Eq. 2)
+# ---------------------------------------------------------------------------
+def n_frames(T: int, hop: int) -> int:
+    """Frames of a T-sample signal at this hop: ceil(T / hop) + 1 (frame f
+    sits at sample f * hop, and the last segment has an end frame)."""
+    return -(-T // hop) + 1
+
+
+def _f32(t, name):
+    if t is not None and t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32 (generated coefficients are FP32)")
+
+
+def workspace_frames(B: int, T: int, M: int, hop: int, chunk: int = 0, device=None) -> torch.Tensor:
+    n = _lib.lp_tv_workspace_bytes_frames(B, T, M, hop, chunk)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+
+
+def workspace_ti(B: int, T: int, M: int, chunk: int = 0, device=None) -> torch.Tensor:
+    n = _lib.lp_tv_workspace_bytes_ti(B, T, M, chunk)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+
+
+def lp_tv_forward_frames(k, e, hop: int, zi=None, *, chunk: int = 0, ws=None):
+    """Eq. 5 with a(t) generated in the kernels from k [B, F, M] (frame-rate
+    reflection coefficients, F = ceil(T/hop)+1): interpolation per sample,
+    then the step-up.  e [B, T]; returns s [B, T]."""
+    B, F, M = k.shape
+    T = e.shape[1]
+    dev = k.device
+    _f32(k, "k")
+    _check(k, "k", (B, n_frames(T, hop), M), torch.float32, dev)
+    _check(e, "e", (B, T), torch.float32, dev)
+    _check(zi, "zi", (B, M), torch.float32, dev)
+    with torch.cuda.device(dev):
+        s = torch.empty((B, T), device=dev)
+        if ws is None:
+            ws = workspace_frames(B, T, M, hop, chunk, dev)
+        _lib.lp_tv_forward_frames(B, T, M, hop, _ptr(k), _ptr(e), _ptr(zi), _ptr(s), None, chunk, _ptr(ws),
+                                  ws.numel(), _stream(dev))
+    return s
+
+
+def lp_tv_backward_frames(gs, k, s, hop: int, zi=None, *, need_gk: bool = True, need_gzi: bool = True,
+                          chunk: int = 0, ws=None, reuse_forward: bool = False):
+    """Adjoint of lp_tv_forward_frames: (ge [B,T], gk [B,F,M] or None,
+    gzi [B,M] or None).  reuse_forward: ws holds the forward's transfers."""
+    B, F, M = k.shape
+    T = gs.shape[1]
+    dev = k.device
+    _check(gs, "gs", (B, T), torch.float32, dev)
+    _check(s, "s", (B, T), torch.float32, dev)
+    _check(zi, "zi", (B, M), torch.float32, dev)
+    with torch.cuda.device(dev):
+        ge = torch.empty((B, T), device=dev)
+        gk = torch.empty((B, F, M), device=dev) if need_gk else None
+        gzi = torch.empty((B, M), device=dev) if need_gzi else None
+        if ws is None:
+            ws = workspace_frames(B, T, M, hop, chunk, dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward_frames(B, T, M, hop, _ptr(gs), _ptr(k), _ptr(s), _ptr(zi), _ptr(ge), _ptr(gk),
+                                   _ptr(gzi), chunk, flags, _ptr(ws), ws.numel(), _stream(dev))
+    return ge, gk, gzi
+
+
+def lp_tv_forward_ti(a, e, zi=None, *, chunk: int = 0, ws=None):
+    """Time-invariant filter (Eq. 2): a [B, M], one row per signal; e [B, T]."""
+    B, M = a.shape
+    T = e.shape[1]
+    dev = a.device
+    _check(a, "a", (B, M), torch.float32, dev)
+    _check(e, "e", (B, T), torch.float32, dev)
+    _check(zi, "zi", (B, M), torch.float32, dev)
+    with torch.cuda.device(dev):
+        s = torch.empty((B, T), device=dev)
+        if ws is None:
+            ws = workspace_ti(B, T, M, chunk, dev)
+        _lib.lp_tv_forward_ti(B, T, M, _ptr(a), _ptr(e), _ptr(zi), _ptr(s), None, chunk, _ptr(ws), ws.numel(),
+                              _stream(dev))
+    return s
+
+
+def lp_tv_backward_ti(gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = True, chunk: int = 0,
+                      ws=None, reuse_forward: bool = False):
+    """Adjoint of lp_tv_forward_ti: (ge [B,T], ga [B,M] = sum_t dL/da(t)
+    (Eq. 3), gzi [B,M])."""
+    B, M = a.shape
+    T = gs.shape[1]
+    dev = a.device
+    _check(gs, "gs", (B, T), torch.float32, dev)
+    _check(s, "s", (B, T), torch.float32, dev)
+    with torch.cuda.device(dev):
+        ge = torch.empty((B, T), device=dev)
+        ga = torch.empty((B, M), device=dev) if need_ga else None
+        gzi = torch.empty((B, M), device=dev) if need_gzi else None
+        if ws is None:
+            ws = workspace_ti(B, T, M, chunk, dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward_ti(B, T, M, _ptr(gs), _ptr(a), _ptr(s), _ptr(zi), _ptr(ge), _ptr(ga), _ptr(gzi), chunk,
+                               flags, _ptr(ws), ws.numel(), _stream(dev))
+    return ge, ga, gzi
+
+
+class LPFramesFunction(torch.autograd.Function):
+    """Differentiable filter with in-kernel coefficients from frame-rate
+    reflection coefficients: gradients for k, e and zi."""
+
+    @staticmethod
+    def forward(ctx, k, e, zi, hop, chunk):
+        k, e = k.contiguous(), e.contiguous()
+        zi = zi.contiguous() if zi is not None else None
+        B, F, M = k.shape
+        ws = workspace_frames(B, e.shape[1], M, hop, chunk, k.device)
+        s = lp_tv_forward_frames(k, e, hop, zi, chunk=chunk, ws=ws)
+        ctx.hop, ctx.chunk = hop, chunk
+        ctx.save_for_backward(k, s, zi, ws)
+        return s
+
+    @staticmethod
+    def backward(ctx, gs):
+        k, s, zi, ws = ctx.saved_tensors
+        need_k, need_e, need_zi = ctx.needs_input_grad[:3]
+        ge, gk, gzi = lp_tv_backward_frames(gs.contiguous(), k, s, ctx.hop, zi, need_gk=need_k,
+                                            need_gzi=need_zi and zi is not None, chunk=ctx.chunk, ws=ws,
+                                            reuse_forward=True)
+        return (gk if need_k else None, ge if need_e else None, gzi if need_zi else None, None, None)
+
+
+def lp_filter_frames(k, e, hop: int, zi=None, *, chunk: int = 0):
+    """Differentiable s = LP_{a(k)}(e) with a(t) generated in the kernels
+    from frame-rate reflection coefficients k [B, ceil(T/hop)+1, M]."""
+    return LPFramesFunction.apply(k, e, zi, hop, chunk)
+
+
+class LPTIFunction(torch.autograd.Function):
+    """Differentiable time-invariant filter (Eq. 2) with GOLF's gradient (Eq. 3)."""
+
+    @staticmethod
+    def forward(ctx, a, e, zi, chunk):
+        a, e = a.contiguous(), e.contiguous()
+        zi = zi.contiguous() if zi is not None else None
+        B, M = a.shape
+        ws = workspace_ti(B, e.shape[1], M, chunk, a.device)
+        s = lp_tv_forward_ti(a, e, zi, chunk=chunk, ws=ws)
+        ctx.chunk = chunk
+        ctx.save_for_backward(a, s, zi, ws)
+        return s
+
+    @staticmethod
+    def backward(ctx, gs):
+        a, s, zi, ws = ctx.saved_tensors
+        need_a, need_e, need_zi = ctx.needs_input_grad[:3]
+        ge, ga, gzi = lp_tv_backward_ti(gs.contiguous(), a, s, zi, need_ga=need_a,
+                                        need_gzi=need_zi and zi is not None, chunk=ctx.chunk, ws=ws,
+                                        reuse_forward=True)
+        return (ga if need_a else None, ge if need_e else None, gzi if need_zi else None, None)
+
+
+def lp_filter_ti(a, e, zi=None, *, chunk: int = 0):
+    """Differentiable time-invariant all-pole filter, a [B, M]."""
+    return LPTIFunction.apply(a, e, zi, chunk)
+
+
+class PackedFrames:
+    """Frames of a varlen batch.  The library gives signal b the frames of
+    its whole slot of rows, [offsets[b], offsets[b+1]) of a Packed batch
+    (the signal and its pad row): ceil(slot/hop)+1 frames, packed back to
+    back from frame_offsets[b].  pack() repeats a signal's last frame where
+    its slot needs one more than the signal itself."""
+
+    def __init__(self, packed: Packed, hop: int):
+        self.hop = hop
+        ends = packed.starts[1:] + [packed.total]
+        self.slots = [e - st for st, e in zip(packed.starts, ends)]
+        self.counts = [n_frames(n, hop) for n in self.slots]
+        starts, pos = [], 0
+        for c in self.counts:
+            starts.append(pos)
+            pos += c
+        self.starts, self.total = starts, pos
+        self.offsets = torch.tensor(starts, dtype=torch.int64, device=packed.device)
+        self.device = packed.device
+
+    def pack(self, ks):
+        """ks: per signal [n_frames(len_b, hop), M]."""
+        rows = []
+        for k, c in zip(ks, self.counts):
+            k = k.reshape(k.shape[0], -1)
+            if k.shape[0] < c:
+                k = torch.cat([k, k[-1:].expand(c - k.shape[0], -1)])
+            rows.append(k[:c])
+        return torch.cat(rows).contiguous()
+
+
+def lp_tv_forward_frames_varlen(packed: Packed, frames: PackedFrames, k, e, zi=None, *, chunk: int = 0, ws=None):
+    """Varlen forward with generated coefficients: k [frames.total, M], e
+    [packed.total]; returns s [packed.total]."""
+    total = packed.total
+    M = k.shape[1]
+    dev = k.device
+    _check(k, "k", (frames.total, M), torch.float32, dev)
+    _check(e, "e", (total,), torch.float32, dev)
+    _check(zi, "zi", (packed.n, M), torch.float32, dev)
+    with torch.cuda.device(dev):
+        s = torch.empty((total,), device=dev)
+        if ws is None:
+            nb = _lib.lp_tv_workspace_bytes_varlen(packed.n, total, M, chunk, _lib.LP_DTYPE_F32)
+            ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        _lib.lp_tv_forward_frames_varlen(packed.n, packed.offsets.data_ptr(), total, M, frames.hop,
+                                         frames.offsets.data_ptr(), _ptr(k), _ptr(e), _ptr(zi), _ptr(s), None, chunk,
+                                         _ptr(ws), ws.numel(), _stream(dev))
+    return s

@@ -14,6 +14,7 @@ import subprocess
 import pytest
 
 import oracle as O
+from tests import test_oracle_coeff_pins as C
 from tests import test_oracle_pins as P
 
 SRC = open(os.path.join(os.path.dirname(O.__file__), "tvlp_oracle.c")).read()
@@ -46,6 +47,27 @@ MUTANTS = {
         ("acc -= ge[t] * a[t * M + (t + j - 1)];", "acc -= ge[t] * a[t * M + (j - 1)];"),
     "initial-state gradient stops one sample early":
         ("t <= (int64_t)(M - j) && t < T", "t < (int64_t)(M - j) && t < T"),
+    # coefficient preparation (Sec. 4.3) and its adjoint
+    "step-up pairs a coefficient with itself":
+        ("A[m][i] = A[m - 1][i] + km[m] * A[m - 1][m - i];", "A[m][i] = A[m - 1][i] + km[m] * A[m - 1][i];"),
+    "step-up sign flipped":
+        ("A[m][i] = A[m - 1][i] + km[m] * A[m - 1][m - i];", "A[m][i] = A[m - 1][i] - km[m] * A[m - 1][m - i];"),
+    "step-up drops the new reflection coefficient":
+        ("        A[m][m] = km[m];", "        A[m][m] = (m < M) ? km[m] : 0.0;"),
+    "interpolation weights swapped":
+        ("return (1.0 - w) * k[f * M + (m - 1)] + w * k[(f + 1) * M + (m - 1)];",
+         "return w * k[f * M + (m - 1)] + (1.0 - w) * k[(f + 1) * M + (m - 1)];"),
+    "interpolation anchored one frame late":
+        ("return (1.0 - w) * k[f * M + (m - 1)] + w * k[(f + 1) * M + (m - 1)];",
+         "return k[(f + 1) * M + (m - 1)];"),
+    "adjoint of the step-up drops the direct term":
+        ("                    if (j == m)\n                        d += A[m - 1][m - i];",
+         "                    if (j == m && m < 0)\n                        d += A[m - 1][m - i];"),
+    "adjoint of the step-up misses the pairing":
+        ("double d = D[m - 1][i][j] + km[m] * D[m - 1][m - i][j];", "double d = D[m - 1][i][j];"),
+    "adjoint of the interpolation swaps the weights":
+        ("            gk[f * M + (j - 1)] += (1.0 - w) * g;\n            gk[(f + 1) * M + (j - 1)] += w * g;",
+         "            gk[f * M + (j - 1)] += w * g;\n            gk[(f + 1) * M + (j - 1)] += (1.0 - w) * g;"),
 }
 
 PINS = [
@@ -60,6 +82,12 @@ PINS = [
     (P.test_golf_time_invariant_gradients, {"M": 5}),
     (P.test_adjoint_dot_product_identity, {}),
     (P.test_slicing_with_carried_state, {}),
+    (C.test_step_up_is_levinson, {"M": 8}),
+    (C.test_closed_forms_at_frame_anchors, {}),
+    (C.test_midpoint_is_the_step_up_of_the_mean_frame, {}),
+    (C.test_stable_reflection_coefficients_give_minimum_phase, {"M": 10}),
+    (C.test_adjoint_finite_differences, {"M": 3, "T": 13, "hop": 4}),
+    (C.test_adjoint_closed_form_m1, {}),
 ]
 
 
