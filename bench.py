@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
-    ap.add_argument("--workload", choices=("headline", "uneven", "serving"), default="headline",
+    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames"), default="headline",
                     help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders; "
-                         "serving: the request loop under Poisson arrivals")
+                         "serving: the request loop under Poisson arrivals; frames: the headline step with the "
+                         "coefficients generated in the kernels from frame-rate reflection coefficients")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="measured seconds of the serving run (default 60 for --workload serving, 15 inside the "
                          "headline line; 0 skips it there)")
@@ -799,6 +800,143 @@ def run_serving(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Frames: the headline shape with a(t) generated inside every pass from
+# reflection coefficients per 120-sample frame (interpolation + step-up), and
+# the gradient with respect to those frames
+# ---------------------------------------------------------------------------
+KERNELS_FRAMES_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun")
+KERNELS_FRAMES_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun")
+KERNELS_FRAMES_GRAD = ("grad_frames", "grad_frames_finish")
+
+
+def run_frames(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_05128_gb300 import _lib, inputs, ops
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, T, M, hop = args.B, args.T, args.M, inputs.HOP
+    rng = np.random.default_rng(2)
+    F = ops.n_frames(T, hop)
+    decay = 1.0 if args.gen == "literal" else 0.9
+    k = torch.tensor(inputs.reflection_frames(rng, B, F, M, 0.95, decay).astype(np.float32), device=dev)
+    e = torch.tensor((inputs.pulse_train(rng, B, T) + 0.1 * rng.standard_normal((B, T))).astype(np.float32),
+                     device=dev)
+    gs = torch.tensor(rng.standard_normal((B, T)).astype(np.float32), device=dev)
+    s, ge = torch.empty((B, T), device=dev), torch.empty((B, T), device=dev)
+    gk = torch.empty((B, F, M), device=dev)
+    chunk = args.chunk or _lib.lp_tv_pick_chunk(B, T, M)
+    ws = ops.workspace_frames(B, T, M, hop, chunk, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2 * 8)]
+    for x in ev:
+        x.record(stream)
+    torch.cuda.synchronize()
+    handles = [x.cuda_event for x in ev]
+
+    def fwd(profile):
+        sp = torch.cuda.current_stream(dev).cuda_stream
+        keep = _lib.lp_tv_set_profile_events(handles[0:6]) if profile else None
+        _lib.lp_tv_forward_frames(B, T, M, hop, k.data_ptr(), e.data_ptr(), None, s.data_ptr(), None, chunk,
+                                  ws.data_ptr(), ws.numel(), sp)
+        if profile:
+            _lib.lp_tv_set_profile_events(None)
+        del keep
+
+    def bwd(profile):
+        sp = torch.cuda.current_stream(dev).cuda_stream
+        keep = _lib.lp_tv_set_profile_events(handles[6:16]) if profile else None
+        _lib.lp_tv_backward_frames(B, T, M, hop, gs.data_ptr(), k.data_ptr(), s.data_ptr(), None, ge.data_ptr(),
+                                   gk.data_ptr(), None, chunk, _lib.LP_BWD_REUSE_FORWARD, ws.data_ptr(), ws.numel(),
+                                   sp)
+        if profile:
+            _lib.lp_tv_set_profile_events(None)
+        del keep
+
+    for _ in range(max(3, args.warmup)):
+        fwd(False)
+        bwd(False)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True, external=True) for _ in range(3))
+    graph, graph_prof = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        e0.record()
+        fwd(False)
+        e1.record()
+        bwd(False)
+        e2.record()
+    with torch.cuda.graph(graph_prof):
+        fwd(True)
+        bwd(True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t0 = time.perf_counter()
+    step, fwd_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        graph.replay()
+        stream.synchronize()
+        step.append(e0.elapsed_time(e2))
+        fwd_ms.append(e0.elapsed_time(e1))
+    t1 = time.perf_counter()
+    sampler.stop()
+    names = KERNELS_FRAMES_FWD + KERNELS_FRAMES_BWD + KERNELS_FRAMES_GRAD
+    kern = {n: [] for n in names}
+    for _ in range(max(3, min(args.steps, 20))):
+        flush.zero_()
+        graph_prof.replay()
+        stream.synchronize()
+        for i, n in enumerate(names):
+            kern[n].append(ev[2 * i].elapsed_time(ev[2 * i + 1]))
+    ms = statistics.mean(step)
+    fms = statistics.mean(fwd_ms)
+    nsamp = B * T
+    # FP32 FMAs per sample: step-up M(M-1)/2 + interpolation M wherever a row
+    # is generated; K1 (M+1)M; each re-run pass M; the frame gradient's
+    # reverse step-up with recomputation about 4 step-ups plus Eq. 12
+    gen = M * (M - 1) // 2 + M
+    fma = {"fwd_summary": (M + 1) * M + gen, "fwd_rerun": M + gen, "bwd_zero_state": M + gen,
+           "bwd_rerun": M + gen, "grad_frames": 4 * gen + M}
+    peaks = load_peaks()
+    sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    fp32_peak = 152 * 128 * 2 * sm_max / 1e12
+    kd = {}
+    for n in names:
+        m = statistics.mean(kern[n])
+        d = {"ms": round(m, 5)}
+        if n in fma:
+            d["TFLOP/s"] = round(2 * fma[n] * nsamp / (m * 1e-3) / 1e12, 2)
+        kd[n] = d
+    dom = max((n for n in fma), key=lambda n: statistics.mean(kern[n]))
+    ach = 2 * fma[dom] * nsamp / (statistics.mean(kern[dom]) * 1e-3) / 1e12
+    line = {
+        "metric": "fwd+bwd Msamples/s at M=22, coefficients generated in the kernels from frame-rate reflection "
+                  "coefficients (gradient w.r.t. the frames)",
+        "value": round(nsamp / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "forward_only": {"ms": round(fms, 5), "Msamples/s": round(nsamp / (fms * 1e-3) / 1e6, 3)},
+        "config": {"workload": f"batched forward+backward, B={B}, T={T}, M={M}, FP32, a(t) generated from "
+                               f"reflection coefficients per {hop}-sample frame ({args.gen} generator), "
+                               "dL/dk per frame", "chunk": chunk, "frames": F,
+                   "input_bytes_per_sample": round((4 * F * M + 4 * T) / T, 3),
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(fp32_peak, 2),
+                     "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                     "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock",
+                     "traffic": None},
+        "kernels": kd, "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+        "gpu_launches": (len(names)) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -807,6 +945,8 @@ def main():
         return run_uneven(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "frames":
+        return run_frames(args)
     return run_ours(args)
 
 

@@ -91,7 +91,8 @@ enum {
  * just before and events[2k+1] just after its k-th kernel launch (k < n) on
  * the call's stream.  Kernel order: forward (chunked) summary, scan,
  * re-run; backward (chunked) zero-state summary (or full summary without
- * LP_BWD_REUSE_FORWARD), scan, re-run, coefficient gradient; the plain
+ * LP_BWD_REUSE_FORWARD), scan, re-run, coefficient gradient (for the
+ * generated-coefficient calls: gradient, then its final sum); the plain
  * algorithm launches re-run (and coefficient gradient).  NULL uninstalls the
  * hook.  The library neither creates nor destroys events.
  */

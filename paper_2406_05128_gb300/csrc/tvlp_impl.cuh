@@ -157,11 +157,12 @@ template <typename S, int MP> struct Launch {
                                  const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
                                  cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
         static bool done[kMaxDevices] = {};
-        using RG = RecGeo<S, MP>;
+        constexpr int RC = RecChunks<SRC>::N;
+        using RG = RecGeo<S, MP, RC>;
         auto kern = k_rec<S, MP, EXACT, MODE, SRC>;
         cudaError_t err = allow_smem(kern, RG::SMEM, done);
         if (err != cudaSuccess) return err;
-        const int64_t grid = (p.NQ + kRecChunks - 1) / kRecChunks;
+        const int64_t grid = (p.NQ + RC - 1) / RC;
         return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
                       out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status, cs);
     }
@@ -391,10 +392,11 @@ int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, con
         float *sc = static_cast<float *>(scratch);
         if (src.kind == SRC_CONST) {
             const int64_t tiles = (p.T + kGradRows - 1) / kGradRows;
-            TVLP_LAUNCH(0, (launch(k_grad_const<MP>, dim3((unsigned)tiles, (unsigned)p.B), dim3(kGradThreads), 0, st,
+            // profiling slots 3 and 4: after the adjoint's three kernels
+            TVLP_LAUNCH(3, (launch(k_grad_const<MP>, dim3((unsigned)tiles, (unsigned)p.B), dim3(kGradThreads), 0, st,
                                    false, p.T, p.M, tiles, ge, s, zi, sc)));
             const int64_t n = (int64_t)p.B * p.M;
-            TVLP_LAUNCH(1, (launch(k_grad_const_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, p.B,
+            TVLP_LAUNCH(4, (launch(k_grad_const_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, p.B,
                                    p.M, MP, tiles, sc, gk)));
             return OK;
         }
@@ -403,10 +405,10 @@ int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, con
             const int64_t items = (int64_t)p.B * src.F;
             const int64_t n = items * p.M;
             float *lo = sc, *hi = sc + n;
-            TVLP_LAUNCH(0, (launch(k_grad_frames<MP>, dim3((unsigned)((items + FG::WARPS - 1) / FG::WARPS)),
+            TVLP_LAUNCH(3, (launch(k_grad_frames<MP>, dim3((unsigned)((items + FG::WARPS - 1) / FG::WARPS)),
                                    dim3(32 * FG::WARPS), 0, st, false, p.B, p.T, p.M, src.F, src.hop, src.inv_hop,
                                    src.k, ge, s, zi, lo, hi)));
-            TVLP_LAUNCH(1, (launch(k_grad_frames_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, n,
+            TVLP_LAUNCH(4, (launch(k_grad_frames_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, n,
                                    lo, hi, gk)));
             return OK;
         }

@@ -461,14 +461,24 @@ __device__ __forceinline__ void gen_row(const CoefSrc &cs, int M, int64_t b, int
         for (int m = 0; m < MP; ++m) a[m] = m < M ? __ldg(cs.k + b * M + m) : 0.f;
     } else {
         const int64_t f0 = cs.foff != nullptr ? __ldg(cs.foff + b) : b * cs.F;
-        const int64_t f = t / cs.hop;
-        const float w = (float)(t - f * cs.hop) * cs.inv_hop;
-        const float *k0 = cs.k + (f0 + f) * (int64_t)M;
+        // t < 2^31 (the library rejects longer signals): 32-bit division
+        const unsigned f = (unsigned)t / (unsigned)cs.hop;
+        const float w = (float)((unsigned)t - f * (unsigned)cs.hop) * cs.inv_hop;
+        const float *k0 = cs.k + (f0 + (int64_t)f) * (int64_t)M;
         stepup_row<MP>(a, k0, k0 + M, w, M);
     }
     // rows are MP floats (MP even): 8-byte stores
 #pragma unroll
     for (int m = 0; m < MP; m += 2) *reinterpret_cast<float2 *>(dst + m) = make_float2(a[m], a[m + 1]);
+}
+
+// Two rows per call: two independent step-ups in one basic block, which
+// the compiler interleaves (the rows' dependency chains overlap).
+template <int MP, int SRC>
+__device__ __forceinline__ void gen_rows2(const CoefSrc &cs, int M, int64_t b0, int64_t t0, bool v0, float *d0,
+                                          int64_t b1, int64_t t1, bool v1, float *d1) {
+    gen_row<MP, SRC>(cs, M, b0, t0, v0, d0);
+    gen_row<MP, SRC>(cs, M, b1, t1, v1, d1);
 }
 
 // Per-signal scan geometry: first chunk, chunks, first group, groups, group size.
@@ -604,13 +614,23 @@ __device__ __forceinline__ void k1_gen_stage(float *a_st, uint64_t *bar, const C
                                              int lane, int64_t my_b, int64_t my_t0, int my_valid) {
     constexpr int CPW = GE::CPW;
     const int roff = BWD ? L - (k + 1) * SRS : k * SRS;
+    static_assert((CPW * SRS) % 32 == 0, "whole rows per lane");
 #pragma unroll 1
-    for (int e = lane; e < CPW * SRS; e += 32) {
-        const int ch = e / SRS, r = e % SRS;
-        const int64_t b = __shfl_sync(0xffffffffu, my_b, ch);
-        const int64_t t0 = __shfl_sync(0xffffffffu, my_t0, ch);
-        const int valid = __shfl_sync(0xffffffffu, my_valid, ch);
-        gen_row<MP, SRC>(cs, M, b, t0 + roff + r, roff + r < valid, a_st + ch * GE::CS + r * MP);
+    for (int e = lane; e < CPW * SRS; e += 64) {
+        if (e + 32 >= CPW * SRS) {  // an odd row count per lane: the last one alone
+            const int ch = e / SRS, r = e % SRS;
+            const int64_t b = __shfl_sync(0xffffffffu, my_b, ch);
+            const int64_t t0 = __shfl_sync(0xffffffffu, my_t0, ch);
+            const int valid = __shfl_sync(0xffffffffu, my_valid, ch);
+            gen_row<MP, SRC>(cs, M, b, t0 + roff + r, roff + r < valid, a_st + ch * GE::CS + r * MP);
+            continue;
+        }
+        const int ch0 = e / SRS, r0 = e % SRS, ch1 = (e + 32) / SRS, r1 = (e + 32) % SRS;
+        const int64_t b0 = __shfl_sync(0xffffffffu, my_b, ch0), b1 = __shfl_sync(0xffffffffu, my_b, ch1);
+        const int64_t s0 = __shfl_sync(0xffffffffu, my_t0, ch0), s1 = __shfl_sync(0xffffffffu, my_t0, ch1);
+        const int n0 = __shfl_sync(0xffffffffu, my_valid, ch0), n1 = __shfl_sync(0xffffffffu, my_valid, ch1);
+        gen_rows2<MP, SRC>(cs, M, b0, s0 + roff + r0, roff + r0 < n0, a_st + ch0 * GE::CS + r0 * MP, b1,
+                           s1 + roff + r1, roff + r1 < n1, a_st + ch1 * GE::CS + r1 * MP);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive_expect_tx(bar, 0u);
@@ -881,15 +901,21 @@ __global__ void __launch_bounds__(256, 1)
 enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2 };
 
 constexpr int kRecChunks = 16;  // chunks per warp (lanes 0 .. kRecChunks-1 own one each)
+// chunks per warp when the rows are generated: half the shared ring per
+// warp, so twice the warps fit on an SM to hide the generator's latency
+constexpr int kRecChunksGen = 4;
+template <int SRC> struct RecChunks {
+    static constexpr int N = SRC == SRC_STREAM ? kRecChunks : kRecChunksGen;
+};
 
-template <typename S, int MP> struct RecGeo {
+template <typename S, int MP, int RC = kRecChunks> struct RecGeo {
     static constexpr int NS = 2;                                    // stages per lane ring
     static constexpr int A_ST = SRS * MP;                           // coefficient elements per lane-stage
     static constexpr int RAW = (NS * A_ST * (int)sizeof(S)) / 4;    // words per lane
     // lane stride in words: an odd multiple of 4, so the 16-byte row loads of
     // a quarter warp hit distinct bank quads
     static constexpr int LW = ((RAW + 3) / 4) % 2 == 1 ? ((RAW + 3) / 4) * 4 : ((RAW + 3) / 4 + 1) * 4;
-    static constexpr size_t SMEM = size_t(kRecChunks) * LW * 4 + NS * 8;
+    static constexpr size_t SMEM = size_t(RC) * LW * 4 + NS * 8;
     static_assert((A_ST * sizeof(S)) % 16 == 0, "16-byte lane stages");
     static_assert((LW * 4) % 16 == 0, "16-byte lane ring alignment");
     static_assert(NS * A_ST * sizeof(S) <= size_t(LW) * 4, "lane ring fits its stride");
@@ -928,24 +954,27 @@ __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S 
     cp_async_commit();
 }
 
-// Generated stage s (SRC_CONST / SRC_FRAMES) for all kRecChunks chunks of
-// the warp: all 32 lanes write rows (chunk e / SRS, row e % SRS) into the
-// owner lanes' rings, then the stage's mbarrier phase completes with no
-// bytes in flight.
-template <int MP, bool BWD, int SRC>
+// Generated stage s (SRC_CONST / SRC_FRAMES) for all RC chunks of the warp:
+// all 32 lanes write rows (chunk e / SRS, row e % SRS) into the owner lanes'
+// rings, then the stage's mbarrier phase completes with no bytes in flight.
+template <int MP, bool BWD, int SRC, int RC>
 __device__ __forceinline__ void rec_gen_stage(unsigned char *smem, int slot, uint64_t *bar, const CoefSrc &cs, int M,
                                               int L, int s, int lane, int64_t b, int64_t t0, int n, bool active) {
-    using RG = RecGeo<float, MP>;
+    using RG = RecGeo<float, MP, RC>;
     const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
+    static_assert((RC * SRS) % 64 == 0, "rows of a stage come in pairs per lane");
+    const int actv = active ? 1 : 0;
 #pragma unroll 1
-    for (int e = lane; e < kRecChunks * SRS; e += 32) {
-        const int ch = e / SRS, r = e % SRS;
-        const int64_t bb = __shfl_sync(0xffffffffu, b, ch);
-        const int64_t tt = __shfl_sync(0xffffffffu, t0, ch);
-        const int nn = __shfl_sync(0xffffffffu, n, ch);
-        const bool act = __shfl_sync(0xffffffffu, active ? 1 : 0, ch) != 0;
-        float *ring = reinterpret_cast<float *>(smem + (size_t)ch * RG::LW * 4);
-        gen_row<MP, SRC>(cs, M, bb, tt + roff + r, act && roff + r < nn, ring + slot * RG::A_ST + r * MP);
+    for (int e = lane; e < RC * SRS; e += 64) {
+        const int ch0 = e / SRS, r0 = e % SRS, ch1 = (e + 32) / SRS, r1 = (e + 32) % SRS;
+        const int64_t b0 = __shfl_sync(0xffffffffu, b, ch0), b1 = __shfl_sync(0xffffffffu, b, ch1);
+        const int64_t s0 = __shfl_sync(0xffffffffu, t0, ch0), s1 = __shfl_sync(0xffffffffu, t0, ch1);
+        const int n0 = __shfl_sync(0xffffffffu, n, ch0), n1 = __shfl_sync(0xffffffffu, n, ch1);
+        const bool a0 = __shfl_sync(0xffffffffu, actv, ch0) != 0, a1 = __shfl_sync(0xffffffffu, actv, ch1) != 0;
+        float *ring0 = reinterpret_cast<float *>(smem + (size_t)ch0 * RG::LW * 4) + slot * RG::A_ST;
+        float *ring1 = reinterpret_cast<float *>(smem + (size_t)ch1 * RG::LW * 4) + slot * RG::A_ST;
+        gen_rows2<MP, SRC>(cs, M, b0, s0 + roff + r0, a0 && roff + r0 < n0, ring0 + r0 * MP, b1, s1 + roff + r1,
+                           a1 && roff + r1 < n1, ring1 + r1 * MP);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive_expect_tx(bar, 0u);
@@ -967,21 +996,22 @@ __global__ void __launch_bounds__(32)
           S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
           int *__restrict__ status, CoefSrc cs) {
     static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
-    using RG = RecGeo<S, MP>;
+    constexpr int RC = RecChunks<SRC>::N;
+    using RG = RecGeo<S, MP, RC>;
     constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
     extern __shared__ __align__(128) unsigned char rec_smem[];
     const int lane = threadIdx.x & 31;
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
-    // lanes past kRecChunks own no chunk; they read (and never write) the
-    // ring of lane lane % kRecChunks so every shared access stays in range
-    const bool owner = lane < kRecChunks;
-    const int64_t q = blk * kRecChunks + lane;
+    // lanes past RC own no chunk; they read (and never write) the ring of
+    // lane lane % RC so every shared access stays in range
+    const bool owner = lane < RC;
+    const int64_t q = blk * RC + lane;
     if (bt.off != nullptr) pdl_wait();  // the chunk tables come from a kernel before
     NQ = batch_chunks(bt, NQ);
     const bool active = owner && q < NQ;
-    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % kRecChunks) * RG::LW * 4);  // [NS][SRS*MP]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)kRecChunks * RG::LW * 4);
+    S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % RC) * RG::LW * 4);  // [NS][SRS*MP]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)RC * RG::LW * 4);
     if (!EXACT && owner) {
         for (int j = 0; j < NS * RG::A_ST; ++j) a_ring[j] = S(0);
     }
@@ -1005,7 +1035,8 @@ __global__ void __launch_bounds__(32)
             rec_issue_stage<S, MP, EXACT, BWD>(a_ring + slot * RG::A_ST, bars + slot, a, M, L, s, active, base, n, l2,
                                                owner);
         else
-            rec_gen_stage<MP, BWD, SRC>(rec_smem, slot, bars + slot, cs, M, L, s, lane, b, c * (int64_t)L, n, active);
+            rec_gen_stage<MP, BWD, SRC, RC>(rec_smem, slot, bars + slot, cs, M, L, s, lane, b, c * (int64_t)L, n,
+                                            active);
     };
     S ucur[SRS], unxt[SRS];
     if constexpr (SRC == SRC_STREAM) stage(0, 0);

@@ -86,8 +86,8 @@ def test_frames_match_oracle(B, T, M, hop, chunk, reuse):
 
 
 def test_frames_headline_shape():
-    """B=32, T=48000, M=22, hop 120: every sample and every frame gradient
-    against the oracle."""
+    """B=32, T=48000, M=22, hop 120: every sample of s and ge, and every
+    frame gradient of two signals, against the oracle."""
     B, T, M, hop = 32, 48000, 22, 120
     k, e, gs, _ = _case(B, T, M, hop, seed=2, zi=False)
     kt, et, gst = _t(k), _t(e), _t(gs)
@@ -98,9 +98,11 @@ def test_frames_headline_shape():
     assert _lib.lp_tv_device_status() == 0
     a = O.coeffs(k, T, hop)
     rs, rge, rga, _ = O.forward_backward(a, e, gs)
-    rgk = O.coeffs_adjoint(k, rga, hop)
+    # the oracle's dL/dk is O(M^3) per sample: two signals
+    sel = [0, B - 1]
+    rgk = O.coeffs_adjoint(k[sel], rga[sel], hop)
     print("frames headline errors", _close("s", s.cpu().numpy(), rs), _close("ge", ge.cpu().numpy(), rge),
-          _close("gk", gk.cpu().numpy(), rgk))
+          _close("gk", gk.cpu().numpy()[sel], rgk))
 
 
 def test_frames_autograd_and_determinism():
@@ -150,7 +152,7 @@ def test_frames_varlen_forward():
 def test_time_invariant_matches_oracle(B, T, M, chunk):
     rng = np.random.default_rng(T + M)
     kc = inputs.reflection_frames(rng, B, 1, M, 0.95, 0.9)[:, 0]
-    a = np.stack([O.coeffs(kc[b][None], 1, 1)[0] for b in range(B)]).astype(np.float32)  # stable rows
+    a = np.stack([O.coeffs(np.stack([kc[b], kc[b]]), 1, 1)[0] for b in range(B)]).astype(np.float32)  # stable
     e = rng.standard_normal((B, T)).astype(np.float32)
     gs = rng.standard_normal((B, T)).astype(np.float32)
     zi = (0.1 * rng.standard_normal((B, M))).astype(np.float32)
@@ -167,7 +169,7 @@ def test_time_invariant_matches_oracle(B, T, M, chunk):
     _close("ga", ga.cpu().numpy(), rga.sum(axis=1))
     # autograd front end gives the same numbers
     at2 = _t(a).requires_grad_(True)
-    s2 = ops.lp_filter_ti(at2, et, zit)
+    s2 = ops.lp_filter_ti(at2, et, zit, chunk=chunk)
     s2.backward(gst)
     assert torch.equal(s2.detach(), s) and torch.equal(at2.grad, ga)
 
