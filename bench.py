@@ -72,6 +72,9 @@ def parse():
                     help="measured seconds of the serving run (default 60 for --workload serving, 15 inside the "
                          "headline line; 0 skips it there)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-frames", action="store_true",
+                    help="serving workload on a frames server (synthesis requests carry frame-rate reflection "
+                         "coefficients)")
     return ap.parse_args()
 
 
@@ -489,6 +492,9 @@ def run_ours(args):
     serve_s = 15.0 if args.serve_seconds is None else args.serve_seconds
     if world == 1 and serve_s > 0:
         serving = serving_run(serve_s, rate=args.serve_rate)
+        sf = serving_run(min(serve_s, 5.0), rate=args.serve_rate, frames=True)
+        serving["frames_server"] = {k: sf[k] for k in ("workload", "h2d_bytes_per_sample", "latency_ms",
+                                                       "Msamples/s", "capacity", "measured_s")}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -645,34 +651,50 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256):
+def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames=False):
     """One serving run: `warmup_s` of arrivals not counted, then `seconds`
     measured; then a burst of `burst` requests at once for the capacity.
-    Returns the summary dict."""
+    frames=True: a frames server (hop 120); every request is synthesis and
+    carries reflection coefficients per frame instead of a(t).  Returns the
+    summary dict."""
     import torch
 
     from paper_2406_05128_gb300 import autotune, inputs, serve
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    M = SERVE_M
+    M, hop = SERVE_M, inputs.HOP
+    adapt_frac = 0.0 if frames else SERVE_ADAPT
+    rng = np.random.default_rng(seed)
     # request payloads: windows of one long synthetic signal (pinned host)
-    sig = inputs.signals_torch([SERVE_POOL_ROWS], M, seed=seed, gen="stable", device=dev)[0]
-    a_pool, e_pool, gs_pool = (x.cpu().pin_memory() for x in sig)
-    del sig
+    if frames:
+        nf = SERVE_POOL_ROWS // hop + 1
+        k_pool = torch.from_numpy(inputs.reflection_frames(rng, 1, nf, M, 0.95, 0.9)[0].astype(np.float32))
+        a_pool = k_pool.pin_memory()
+        e_pool = torch.from_numpy(rng.standard_normal(SERVE_POOL_ROWS).astype(np.float32)).pin_memory()
+        gs_pool = None
+    else:
+        sig = inputs.signals_torch([SERVE_POOL_ROWS], M, seed=seed, gen="stable", device=dev)[0]
+        a_pool, e_pool, gs_pool = (x.cpu().pin_memory() for x in sig)
+        del sig
     torch.cuda.empty_cache()
     chunk, _ = autotune.tune_varlen([SERVE_MEDIAN, 96000], M, device=dev, iters=5)
-    rng = np.random.default_rng(seed)
 
     def draw():
         T = int(min(SERVE_MAX, max(1, round(SERVE_MEDIAN * np.exp(SERVE_SIGMA * rng.standard_normal())))))
-        return T, int(rng.integers(0, SERVE_POOL_ROWS - T + 1)), bool(rng.random() < SERVE_ADAPT)
+        o = int(rng.integers(0, (SERVE_POOL_ROWS - T) // hop + 1)) * hop  # on a frame anchor
+        return T, o, bool(rng.random() < adapt_frac)
+
+    def coef(o, T):
+        if frames:
+            return a_pool[o // hop:o // hop + (-(-T // hop) + 1)]
+        return a_pool[o:o + T]
 
     # page-locked output slots, reused once their request has completed
     free_s = [torch.empty(SERVE_MAX, pin_memory=True) for _ in range(64)]
     free_a = [(torch.empty(SERVE_MAX, pin_memory=True), torch.empty(SERVE_MAX, pin_memory=True),
                torch.empty((SERVE_MAX, M), pin_memory=True)) for _ in range(12)]
 
-    srv = serve.Server(M, chunk=chunk, hbm_budget=SERVE_BUDGET)
+    srv = serve.Server(M, chunk=chunk, hbm_budget=SERVE_BUDGET, hop=hop if frames else 0)
     recs = []
 
     def collect():
@@ -690,11 +712,11 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256):
                                                 torch.empty(SERVE_MAX, pin_memory=True),
                                                 torch.empty((SERVE_MAX, M), pin_memory=True))
             out = (slot[0][:T], slot[1][:T], slot[2][:T])
-            srv.submit(a_pool[o:o + T], e_pool[o:o + T], gs_pool[o:o + T], arrival_ns=t_arr, out=out,
+            srv.submit(coef(o, T), e_pool[o:o + T], gs_pool[o:o + T], arrival_ns=t_arr, out=out,
                        tag=(measured, slot))
         else:
             slot = free_s.pop() if free_s else torch.empty(SERVE_MAX, pin_memory=True)
-            srv.submit(a_pool[o:o + T], e_pool[o:o + T], arrival_ns=t_arr, out=slot[:T], tag=(measured, slot))
+            srv.submit(coef(o, T), e_pool[o:o + T], arrival_ns=t_arr, out=slot[:T], tag=(measured, slot))
 
     # arrival schedule on the server's clock
     n_total = int(rate * (warmup_s + seconds) * 1.2) + 16
@@ -738,9 +760,9 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256):
     tb0 = serve.now_ns()
     for (T, o, adapt), out in zip(burst_reqs, outs):
         if adapt:
-            srv.submit(a_pool[o:o + T], e_pool[o:o + T], gs_pool[o:o + T], out=out, tag=(False, None))
+            srv.submit(coef(o, T), e_pool[o:o + T], gs_pool[o:o + T], out=out, tag=(False, None))
         else:
-            srv.submit(a_pool[o:o + T], e_pool[o:o + T], out=out, tag=(False, None))
+            srv.submit(coef(o, T), e_pool[o:o + T], out=out, tag=(False, None))
     done = srv.drain(timeout_s=120)
     tb1 = serve.now_ns()
     st_burst = srv.stats()
@@ -753,9 +775,12 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256):
     its = max(st["iterations"], 1)
     return {
         "workload": (f"Poisson arrivals {rate:g} req/s, lengths lognormal (median {SERVE_MEDIAN} = 3 s at 24 kHz, "
-                     f"sigma {SERVE_SIGMA}, max {SERVE_MAX}), M={M}, FP32, {int(100 * (1 - SERVE_ADAPT))}% "
-                     f"synthesis / {int(100 * SERVE_ADAPT)}% forward+backward adaptation, "
-                     f"{SERVE_BUDGET >> 30} GiB HBM budget, stable reflection generator, pinned host buffers"),
+                     f"sigma {SERVE_SIGMA}, max {SERVE_MAX}), M={M}, FP32, {int(round(100 * (1 - adapt_frac)))}% "
+                     f"synthesis / {int(round(100 * adapt_frac))}% forward+backward adaptation, "
+                     f"{SERVE_BUDGET >> 30} GiB HBM budget, stable reflection generator, pinned host buffers"
+                     + (f"; requests carry reflection coefficients per {hop}-sample frame, a(t) generated in the "
+                        "kernels" if frames else "; requests carry a(t)")),
+        "h2d_bytes_per_sample": round((4 * M / hop if frames else 4 * M) + 4, 3),
         "measured_s": seconds, "warmup_s": warmup_s, "requests": len(recs),
         "latency_ms": {"p50": _pct(lat_ms, 50), "p90": _pct(lat_ms, 90), "p99": _pct(lat_ms, 99),
                        "p99.9": _pct(lat_ms, 99.9), "max": max(lat_ms) if lat_ms else None,
@@ -788,7 +813,7 @@ def run_serving(args):
     __graft_entry__.build()
     torch.cuda.set_device(0)
     seconds = 60.0 if args.serve_seconds is None else args.serve_seconds
-    sv = serving_run(seconds, rate=args.serve_rate)
+    sv = serving_run(seconds, rate=args.serve_rate, frames=args.serve_frames)
     line = {
         "metric": "serving p99 latency (ms) at Poisson arrivals, continuous batching", "value": sv["latency_ms"]["p99"],
         "unit": "ms", "n_gpus": 1, "steps": sv["requests"], "warmup": sv["warmup_s"], "higher_is_better": False,

@@ -52,7 +52,7 @@ class ServeConfig(ctypes.Structure):
     """lp_serve_config (include/tvlp_serve.h)."""
     _fields_ = [("M", ctypes.c_int), ("chunk", ctypes.c_int), ("block_rows", ctypes.c_int64),
                 ("max_signals", ctypes.c_int), ("max_iter_rows", ctypes.c_int64),
-                ("max_inflight", ctypes.c_int), ("hbm_budget", ctypes.c_uint64)]
+                ("max_inflight", ctypes.c_int), ("hbm_budget", ctypes.c_uint64), ("hop", ctypes.c_int)]
 
 
 class ServeStats(ctypes.Structure):

@@ -35,7 +35,11 @@ struct PlanConfig {
     int max_signals = 256;             // signals per call (each of the two calls)
     int64_t max_iter_rows = 4 << 20;   // packed rows per iteration, both calls together
     uint64_t ring_bytes = 0;           // device bytes for iteration regions
+    int hop = 0;                       // > 0: synthesis requests carry frames (block_rows a multiple of hop)
 };
+
+// Frames of `rows` samples at this hop: ceil(rows / hop) + 1.
+inline int64_t frames_of(int64_t rows, int hop) { return (rows + hop - 1) / hop + 1; }
 
 // The planner's view of one request; `user` belongs to the caller.
 struct Request {
@@ -54,6 +58,7 @@ struct Request {
 struct Block {
     Request *req = nullptr;
     int64_t row0 = 0, rows = 0, pos = 0;
+    int64_t fpos = 0;      // frames mode: first frame of the block in the call's frame rows
     bool carried = false;  // starts from a carried filter state
     bool last = false;     // the request's final block
 };
@@ -61,18 +66,20 @@ struct Block {
 inline int64_t padded(int64_t rows) { return rows + (rows & 1); }
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
-// Byte offsets of one iteration region: the synthesis call's a, e, s; the
-// adaptation call's a, e, gs, s, ge, ga; then the tables that go to the
-// device in one copy: both calls' row offsets and the indexes (into the
-// synthesis call) of the blocks whose request continues.
+// Byte offsets of one iteration region: the synthesis call's a (or, in
+// frames mode, its frame rows), e, s; the adaptation call's a, e, gs, s, ge,
+// ga; then the tables that go to the device in one copy: both calls' row
+// offsets, in frames mode the synthesis blocks' first frames, and the
+// indexes (into the synthesis call) of the blocks whose request continues.
 struct Layout {
     uint64_t a_f = 0, e_f = 0, s_f = 0;
     uint64_t a_a = 0, e_a = 0, gs_a = 0, s_a = 0, ge_a = 0, ga_a = 0;
-    uint64_t tab = 0, off_f = 0, off_a = 0, cont = 0, tab_bytes = 0;
+    uint64_t tab = 0, off_f = 0, off_a = 0, foff = 0, cont = 0, tab_bytes = 0;
     uint64_t bytes = 0;
 };
 
-inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont) {
+// frames_f < 0: streamed coefficient rows; >= 0: that many frame rows
+inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont, int64_t frames_f = -1) {
     Layout L;
     uint64_t p = 0;
     auto take = [&p](uint64_t nbytes) {
@@ -82,7 +89,7 @@ inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, in
     };
     const uint64_t rf = (uint64_t)rows_f, ra = (uint64_t)rows_a, m = (uint64_t)M;
     if (n_f > 0) {
-        L.a_f = take(rf * m * 4);
+        L.a_f = take((frames_f < 0 ? rf : (uint64_t)frames_f) * m * 4);
         L.e_f = take(rf * 4);
         L.s_f = take(rf * 4);
     }
@@ -97,7 +104,8 @@ inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, in
     L.tab = p;
     L.off_f = p;
     L.off_a = L.off_f + (uint64_t)(n_f + 1) * 8;
-    L.cont = L.off_a + (uint64_t)(n_a + 1) * 8;
+    L.foff = L.off_a + (uint64_t)(n_a + 1) * 8;
+    L.cont = L.foff + (frames_f < 0 ? 0 : (uint64_t)n_f * 8);
     L.tab_bytes = L.cont + (uint64_t)n_cont * 4 - L.tab;
     p = align256(L.cont + (uint64_t)n_cont * 4);
     L.bytes = p;
@@ -110,7 +118,7 @@ inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, in
 inline uint64_t max_region_bytes(const PlanConfig &c) {
     const Layout a = layout(c.M, c.max_iter_rows, 0, c.max_iter_rows, c.max_signals, 0);
     const Layout f = layout(c.M, c.max_iter_rows, c.max_signals, 0, 0, c.max_signals);
-    return std::max(a.bytes, f.bytes) + 2 * align256((uint64_t)(2 * c.max_signals + 2) * 8 + c.max_signals * 4);
+    return std::max(a.bytes, f.bytes) + 2 * align256((uint64_t)(3 * c.max_signals + 2) * 8 + c.max_signals * 4);
 }
 
 // FIFO ring of regions: allocated in iteration order, freed oldest first.
@@ -177,6 +185,7 @@ struct IterPlan {
     std::vector<int> cont;     // indexes into fwd of blocks whose request continues
     int n_carried = 0;         // fwd[0 .. n_carried) start from a carried state
     int64_t rows_f = 0, rows_a = 0;
+    int64_t frames_f = 0;  // frames mode: frame rows of the synthesis call
     Layout lay;
     uint64_t offset = 0;  // region offset in the ring
 };
@@ -198,6 +207,7 @@ class Planner {
     // Whether a request could ever be planned (alone, in an empty ring).
     bool admissible(int kind, int64_t T) const {
         if (T < 0) return false;
+        if (cfg_.hop > 0 && kind == ADAPT) return false;  // frames mode serves synthesis only
         const int64_t r = padded(first_rows(kind, T));
         if (r > cfg_.max_iter_rows) return false;
         const Layout L = kind == ADAPT ? layout(cfg_.M, 0, 0, r, 1, 0) : layout(cfg_.M, r, 1, 0, 0, 1);
@@ -224,21 +234,29 @@ class Planner {
             return b;
         };
         int n_cont_next = 0;
+        const bool frames = cfg_.hop > 0;
+        // frame rows a synthesis block needs (frames mode)
+        auto nfr = [&](int64_t rows) { return frames ? frames_of(padded(rows), cfg_.hop) : 0; };
         for (Request *r : cont_) {
             Block b = block_of(r);
             b.pos = P.rows_f;
+            b.fpos = P.frames_f;
             P.rows_f += padded(b.rows);
+            P.frames_f += nfr(b.rows);
             if (!b.last) ++n_cont_next;
             P.fwd.push_back(b);
         }
         P.n_carried = (int)P.fwd.size();
         uint64_t off = 0;
-        auto fits = [&](int64_t rf, int nf, int64_t ra, int na, int nc) {
+        auto lay_of = [&](int64_t rf, int nf, int64_t ra, int na, int nc, int64_t ff) {
+            return layout(cfg_.M, rf, nf, ra, na, nc, frames ? ff : -1);
+        };
+        auto fits = [&](int64_t rf, int nf, int64_t ra, int na, int nc, int64_t ff) {
             if (rf + ra > cfg_.max_iter_rows) return false;
             if (nf > cfg_.max_signals || na > cfg_.max_signals) return false;
-            return ring_.where(layout(cfg_.M, rf, nf, ra, na, nc).bytes, &off);
+            return ring_.where(lay_of(rf, nf, ra, na, nc, ff).bytes, &off);
         };
-        if (!P.fwd.empty() && !fits(P.rows_f, (int)P.fwd.size(), 0, 0, n_cont_next)) {
+        if (!P.fwd.empty() && !fits(P.rows_f, (int)P.fwd.size(), 0, 0, n_cont_next, P.frames_f)) {
             P = IterPlan();
             return false;
         }
@@ -248,15 +266,20 @@ class Planner {
             Block b = block_of(r);
             const int64_t pr = padded(b.rows);
             if (r->kind == ADAPT) {
-                if (!fits(P.rows_f, (int)P.fwd.size(), P.rows_a + pr, (int)P.adapt.size() + 1, n_cont_next)) break;
+                if (!fits(P.rows_f, (int)P.fwd.size(), P.rows_a + pr, (int)P.adapt.size() + 1, n_cont_next,
+                          P.frames_f))
+                    break;
                 b.pos = P.rows_a;
                 P.rows_a += pr;
                 P.adapt.push_back(b);
             } else {
                 const int nc = n_cont_next + (b.last ? 0 : 1);
-                if (!fits(P.rows_f + pr, (int)P.fwd.size() + 1, P.rows_a, (int)P.adapt.size(), nc)) break;
+                const int64_t ff = P.frames_f + nfr(b.rows);
+                if (!fits(P.rows_f + pr, (int)P.fwd.size() + 1, P.rows_a, (int)P.adapt.size(), nc, ff)) break;
                 b.pos = P.rows_f;
+                b.fpos = P.frames_f;
                 P.rows_f += pr;
+                P.frames_f = ff;
                 n_cont_next = nc;
                 P.fwd.push_back(b);
             }
@@ -264,7 +287,7 @@ class Planner {
         if (P.fwd.empty() && P.adapt.empty()) return false;
         // the last successful fits() sized exactly this layout, so the
         // allocation succeeds
-        P.lay = layout(cfg_.M, P.rows_f, (int)P.fwd.size(), P.rows_a, (int)P.adapt.size(), n_cont_next);
+        P.lay = lay_of(P.rows_f, (int)P.fwd.size(), P.rows_a, (int)P.adapt.size(), n_cont_next, P.frames_f);
         if (!ring_.alloc(P.lay.bytes, &P.offset)) {
             P = IterPlan();
             return false;

@@ -15,16 +15,17 @@ using namespace tvlp_serve;
 extern "C" {
 
 // Requests k = 0..n-1 arrive at step arrive[k] (non-decreasing), with length
-// T[k] and kind kind[k].  Writes one row of 8 int64 per block:
+// T[k] and kind kind[k]; hop > 0 plans a frames server.  Writes one row of 9
+// int64 per block:
 //   iteration, request, row0, rows, pos, call (0 synthesis, 1 adaptation),
-//   carried, last
+//   carried, last, fpos (first frame row in the call, frames mode)
 // and one row of 5 uint64 per iteration:
 //   step planned, step completed, ring offset, region bytes, ring bytes in use
 // Returns 0, -1 for bad arguments or a request no iteration can hold, -2
 // when an output array is too small, -3 when the loop stopped making
 // progress.
 int lp_plan_simulate(int M, int64_t block_rows, int max_signals, int64_t max_iter_rows, uint64_t ring_bytes,
-                     int lag, int n, const int64_t *T, const int *kind, const int64_t *arrive, int64_t cap_blocks,
+                     int hop, int lag, int n, const int64_t *T, const int *kind, const int64_t *arrive, int64_t cap_blocks,
                      int64_t *blocks, int64_t cap_iters, uint64_t *iters, int64_t *n_blocks, int64_t *n_iters) {
     if (M < 1 || max_signals < 1 || max_iter_rows < 2 || lag < 1 || n < 0 || n_blocks == nullptr ||
         n_iters == nullptr)
@@ -35,6 +36,7 @@ int lp_plan_simulate(int M, int64_t block_rows, int max_signals, int64_t max_ite
     c.max_signals = max_signals;
     c.max_iter_rows = max_iter_rows;
     c.ring_bytes = ring_bytes;
+    c.hop = hop;
     Planner P(c);
     std::vector<Request> req((size_t)n);
     for (int k = 0; k < n; ++k) {
@@ -76,7 +78,7 @@ int lp_plan_simulate(int M, int64_t block_rows, int max_signals, int64_t max_ite
             row[3] = it.lay.bytes;
             row[4] = P.ring().in_use();
             auto put = [&](const Block &b, int call) {
-                int64_t *o = blocks + nb * 8;
+                int64_t *o = blocks + nb * 9;
                 o[0] = ni;
                 o[1] = b.req->id;
                 o[2] = b.row0;
@@ -85,6 +87,7 @@ int lp_plan_simulate(int M, int64_t block_rows, int max_signals, int64_t max_ite
                 o[5] = call;
                 o[6] = b.carried;
                 o[7] = b.last;
+                o[8] = b.fpos;
                 ++nb;
                 if (b.last) ++finished;
             };
@@ -106,11 +109,13 @@ int lp_plan_simulate(int M, int64_t block_rows, int max_signals, int64_t max_ite
     return 0;
 }
 
-// The region layout of one iteration (serve_plan.h): 15 uint64 offsets
+// The region layout of one iteration (serve_plan.h; frames_f < 0 for
+// streamed rows): 15 uint64 offsets
 //   a_f e_f s_f a_a e_a gs_a s_a ge_a ga_a tab off_f off_a cont tab_bytes bytes
-int lp_plan_layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont, uint64_t *out) {
+int lp_plan_layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont, int64_t frames_f,
+                   uint64_t *out) {
     if (out == nullptr) return -1;
-    const Layout L = layout(M, rows_f, n_f, rows_a, n_a, n_cont);
+    const Layout L = layout(M, rows_f, n_f, rows_a, n_a, n_cont, frames_f);
     const uint64_t v[15] = {L.a_f, L.e_f, L.s_f, L.a_a, L.e_a, L.gs_a, L.s_a, L.ge_a, L.ga_a,
                             L.tab, L.off_f, L.off_a, L.cont, L.tab_bytes, L.bytes};
     for (int k = 0; k < 15; ++k) out[k] = v[k];

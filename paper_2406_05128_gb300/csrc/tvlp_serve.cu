@@ -144,6 +144,11 @@ int issue(Server &S, Iter &it) {
     for (int k = 0; k < na; ++k) off_a[k] = P.adapt[k].pos;
     off_a[na] = P.rows_a;
     for (int k = 0; k < nc; ++k) cont[k] = P.cont[k];
+    const int hop = S.cfg.hop;
+    if (hop > 0) {
+        int64_t *foff = reinterpret_cast<int64_t *>(tab + (L.foff - L.tab));
+        for (int k = 0; k < nf; ++k) foff[k] = P.fwd[k].fpos;
+    }
     SV_CUDA(cudaMemcpyAsync(base + L.tab, tab, L.tab_bytes, cudaMemcpyHostToDevice, S.s_in));
 
     auto put = [&](uint64_t dst, int64_t pos, const float *src, int64_t rows, size_t bytes_per_row, bool pad) {
@@ -158,6 +163,26 @@ int issue(Server &S, Iter &it) {
     };
     for (const Block &b : P.fwd) {
         const Rec *r = static_cast<const Rec *>(b.req->user);
+        if (hop > 0) {
+            // the block's frames: it starts on a frame anchor (block_rows is
+            // a multiple of hop), and a padded last block may need one frame
+            // more than the request has, which repeats its last frame
+            if (b.rows > 0) {
+                const int64_t f0 = b.row0 / hop, need = frames_of(padded(b.rows), hop);
+                const int64_t have = frames_of(r->req.T, hop) - f0;
+                const int64_t n = need < have ? need : have;
+                char *d = base + L.a_f + (size_t)b.fpos * rowb;
+                if (cudaMemcpyAsync(d, r->a + f0 * M, (size_t)n * rowb, cudaMemcpyHostToDevice, S.s_in) !=
+                    cudaSuccess)
+                    return fail(S, LP_ECUDA);
+                for (int64_t x = n; x < need; ++x)
+                    if (cudaMemcpyAsync(d + (size_t)x * rowb, r->a + (f0 + have - 1) * M, rowb,
+                                        cudaMemcpyHostToDevice, S.s_in) != cudaSuccess)
+                        return fail(S, LP_ECUDA);
+            }
+            if (!put(L.e_f, b.pos, r->e + b.row0, b.rows, sizeof(float), true)) return fail(S, LP_ECUDA);
+            continue;
+        }
         if (!put(L.a_f, b.pos, r->a + b.row0 * M, b.rows, rowb, true) ||
             !put(L.e_f, b.pos, r->e + b.row0, b.rows, sizeof(float), true))
             return fail(S, LP_ECUDA);
@@ -186,7 +211,14 @@ int issue(Server &S, Iter &it) {
     }
     const uint64_t it_no = S.iter_count;
     float *zi_cur = S.zi[it_no & 1], *zi_next = S.zi[(it_no + 1) & 1];
-    if (nf > 0) {
+    if (nf > 0 && hop > 0) {
+        SV_LP(lp_tv_forward_frames_varlen_f32(
+            nf, reinterpret_cast<const int64_t *>(base + L.off_f), P.rows_f, M, hop,
+            reinterpret_cast<const int64_t *>(base + L.foff), reinterpret_cast<const float *>(base + L.a_f),
+            reinterpret_cast<const float *>(base + L.e_f), zi_cur, reinterpret_cast<float *>(base + L.s_f), nullptr,
+            S.chunk, S.ws, S.ws_bytes, S.s_comp));
+        launches += kFwdKernels;
+    } else if (nf > 0) {
         SV_LP(lp_tv_forward_varlen_f32(nf, reinterpret_cast<const int64_t *>(base + L.off_f), P.rows_f, M,
                                        reinterpret_cast<const float *>(base + L.a_f),
                                        reinterpret_cast<const float *>(base + L.e_f), zi_cur,
@@ -356,6 +388,7 @@ void lp_serve_default_config(lp_serve_config *c) {
     c->max_iter_rows = int64_t(4) << 20;
     c->max_inflight = 4;
     c->hbm_budget = uint64_t(20) << 30;
+    c->hop = 0;
 }
 
 int64_t lp_serve_now_ns(void) { return steady_ns(); }
@@ -367,8 +400,14 @@ int lp_serve_create(const lp_serve_config *cfg, void **server) {
     if (c.M < 1 || c.M > 32 || c.chunk < 0 || c.block_rows < 0 || c.max_signals < 1 || c.max_iter_rows < 2 ||
         c.max_inflight < 1 || c.max_inflight > kMaxInflight)
         return LP_EINVAL;
+    if (c.hop < 0) return LP_EINVAL;
     if (c.block_rows > 0) {
         c.block_rows = std::max<int64_t>(padded(c.block_rows), padded(c.M));
+        if (c.hop > 0) {
+            // blocks start on frame anchors: a multiple of hop (and even)
+            const int64_t q = c.hop % 2 == 0 ? c.hop : 2 * (int64_t)c.hop;
+            c.block_rows = (c.block_rows + q - 1) / q * q;
+        }
         if (c.block_rows > c.max_iter_rows) return LP_EINVAL;
     }
     int chunk = c.chunk;
@@ -387,6 +426,7 @@ int lp_serve_create(const lp_serve_config *cfg, void **server) {
     pc.block_rows = c.block_rows;
     pc.max_signals = c.max_signals;
     pc.max_iter_rows = c.max_iter_rows;
+    pc.hop = c.hop;
     const uint64_t fixed = ws_b + 2 * zi_b;
     if (c.hbm_budget <= fixed) return LP_ETOOBIG;
     pc.ring_bytes = (c.hbm_budget - fixed) & ~uint64_t(255);
@@ -402,7 +442,7 @@ int lp_serve_create(const lp_serve_config *cfg, void **server) {
         return LP_ECUDA;
     }
     S->dev_bytes = fixed + pc.ring_bytes;
-    S->tab_slot_bytes = align256((uint64_t)(2 * c.max_signals + 2) * 8 + (uint64_t)c.max_signals * 4);
+    S->tab_slot_bytes = align256((uint64_t)(3 * c.max_signals + 2) * 8 + (uint64_t)c.max_signals * 4);
     bool ok = cudaMalloc(&S->dev, S->dev_bytes) == cudaSuccess;
     ok = ok && cudaHostAlloc(&S->tab_host, S->tab_slot_bytes * c.max_inflight, cudaHostAllocDefault) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&S->s_in, cudaStreamNonBlocking) == cudaSuccess;
@@ -440,6 +480,7 @@ int lp_serve_submit(void *server, int64_t id, int kind, int64_t T, const float *
     if (S == nullptr || T < 0 || (kind != LP_SERVE_SYNTH && kind != LP_SERVE_ADAPT)) return LP_EINVAL;
     if (T > 0 && (a == nullptr || e == nullptr || s == nullptr)) return LP_EINVAL;
     if (T > 0 && kind == LP_SERVE_ADAPT && (gs == nullptr || ge == nullptr || ga == nullptr)) return LP_EINVAL;
+    if (S->cfg.hop > 0 && kind == LP_SERVE_ADAPT) return LP_EUNSUPPORTED;
     if (!S->planner->admissible(kind, T)) return LP_ETOOBIG;
     Rec *r = new (std::nothrow) Rec();
     if (r == nullptr) return LP_ECUDA;

@@ -61,8 +61,8 @@ class Server:
     pick one chunk length for every call."""
 
     def __init__(self, M: int = 22, *, chunk: int = 0, block_rows: int = 96000, max_signals: int = 256,
-                 max_iter_rows: int = 4 << 20, max_inflight: int = 4, hbm_budget: int = 20 << 30, device=None,
-                 require_pinned: bool = True):
+                 max_iter_rows: int = 4 << 20, max_inflight: int = 4, hbm_budget: int = 20 << 30, hop: int = 0,
+                 device=None, require_pinned: bool = True):
         lib = _lib.load()
         self._lib = lib
         cfg = _lib.ServeConfig()
@@ -70,7 +70,9 @@ class Server:
         cfg.M, cfg.chunk, cfg.block_rows = M, chunk, block_rows
         cfg.max_signals, cfg.max_iter_rows, cfg.max_inflight, cfg.hbm_budget = (max_signals, max_iter_rows,
                                                                                 max_inflight, hbm_budget)
+        cfg.hop = hop
         self.M = M
+        self.hop = hop
         self.require_pinned = require_pinned
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if dev.type != "cuda":
@@ -88,15 +90,16 @@ class Server:
         self._pst = (ctypes.c_int * n)()
 
     def submit(self, a, e, gs=None, *, arrival_ns: int = 0, out=None, tag=None) -> Request:
-        """Queue one request.  a [T, M], e [T] (and gs [T] for adaptation)
-        are CPU float32 tensors; out optionally gives the output tensors
-        (s, or (s, ge, ga)).  Returns the Request, whose outputs are valid
-        once poll() has returned it."""
+        """Queue one request.  a [T, M] (a server with hop > 0: reflection
+        coefficients per frame, [ceil(T/hop)+1, M]), e [T] (and gs [T] for
+        adaptation) are CPU float32 tensors; out optionally gives the output
+        tensors (s, or (s, ge, ga)).  Returns the Request, whose outputs are
+        valid once poll() has returned it."""
         if self._h is None:
             raise RuntimeError("server is closed")
         T = e.shape[0] if isinstance(e, torch.Tensor) else -1
         _host(e, "e", (T,))
-        _host(a, "a", (T, self.M))
+        _host(a, "a", ((-(-T // self.hop) + 1) if self.hop > 0 else T, self.M))
         kind = ADAPT if gs is not None else SYNTH
         if gs is not None:
             _host(gs, "gs", (T,))

@@ -170,3 +170,42 @@ def test_rejects_what_no_iteration_holds():
         assert r.status == 0 and torch.equal(r.s, e)
         with pytest.raises(ValueError):
             srv.submit(torch.zeros((T, M)), torch.zeros(T))  # not page-locked
+
+
+def test_frames_server_alone_equals_mix_and_oracle():
+    """hop > 0: synthesis requests carry reflection coefficients per frame;
+    the kernels generate a(t).  Blocks of 4800 samples (40 frames) carry the
+    state; results are bit for bit the same alone and in the mix, and match
+    the oracle's Eq. 5 on the oracle's own interpolation and step-up."""
+    hop = 120
+    lengths = [4800, 0, 1, 17, 12000, 30001, 9600, 999, 20000, 121, 7000, 4799]
+    rng = np.random.default_rng(8)
+    reqs = []
+    for T in lengths:
+        k = inputs.reflection_frames(rng, 1, O.n_frames(T, hop), M, 0.95, 0.9)[0].astype(np.float32)
+        e = rng.standard_normal(T).astype(np.float32)
+        reqs.append((torch.from_numpy(k).pin_memory(), torch.from_numpy(e).pin_memory()))
+    cfg = dict(CFG, block_rows=4800, hop=hop)
+    with serve.Server(M, **cfg) as srv:
+        mix = []
+        for k, e in reqs:
+            mix.append(srv.submit(k, e))
+            time.sleep(float(rng.uniform(0, 3e-4)))
+        srv.drain(timeout_s=60)
+        st = srv.stats()
+        alone = []
+        for k, e in reqs:
+            alone.append(srv.submit(k, e))
+            srv.drain(timeout_s=60)
+        with pytest.raises(_lib.LPError) as ei:
+            srv.submit(reqs[0][0], reqs[0][1], reqs[0][1])
+        assert ei.value.code == _lib.LP_EUNSUPPORTED
+        assert _lib.lp_tv_device_status() == 0
+    assert st["carried_blocks"] > 0 and st["max_signals_iter"] > 1 and st["error"] == 0
+    for x, y, (k, e), T in zip(mix, alone, reqs, lengths):
+        assert x.status == 0 and np.array_equal(x.s.numpy(), y.s.numpy()), T
+        if T == 0:
+            continue
+        rs = O.forward(O.coeffs(k.numpy(), T, hop), e.numpy())
+        err = norm_err(x.s.numpy()[None], rs[None])
+        assert err.max() <= TOL_F32, (T, err)

@@ -29,9 +29,9 @@ from paper_2406_05128_gb300 import build
 def plan():
     lib = ctypes.CDLL(build.build_plan())
     i32, i64, u64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
-    lib.lp_plan_simulate.argtypes = [i32, i64, i32, i64, u64, i32, i32, vp, vp, vp, i64, vp, i64, vp, vp, vp]
+    lib.lp_plan_simulate.argtypes = [i32, i64, i32, i64, u64, i32, i32, i32, vp, vp, vp, i64, vp, i64, vp, vp, vp]
     lib.lp_plan_simulate.restype = i32
-    lib.lp_plan_layout.argtypes = [i32, i64, i32, i64, i32, i32, vp]
+    lib.lp_plan_layout.argtypes = [i32, i64, i32, i64, i32, i32, i64, vp]
     lib.lp_plan_layout.restype = i32
     lib.lp_plan_max_region_bytes.argtypes = [i32, i64, i32, i64]
     lib.lp_plan_max_region_bytes.restype = u64
@@ -39,33 +39,33 @@ def plan():
 
 
 def simulate(lib, T, kind, arrive, *, M=22, block_rows=4096, max_signals=8, max_iter_rows=1 << 16,
-             ring_bytes=None, lag=3):
+             ring_bytes=None, lag=3, hop=0):
     T = np.ascontiguousarray(T, dtype=np.int64)
     kind = np.ascontiguousarray(kind, dtype=np.int32)
     arrive = np.ascontiguousarray(arrive, dtype=np.int64)
     if ring_bytes is None:
         ring_bytes = 2 * lib.lp_plan_max_region_bytes(M, block_rows, max_signals, max_iter_rows)
     cap = int(4 * (T.sum() // max(block_rows, 1) + len(T)) + 64)
-    blocks = np.zeros((cap, 8), np.int64)
+    blocks = np.zeros((cap, 9), np.int64)
     iters = np.zeros((cap, 5), np.uint64)
     nb, ni = ctypes.c_int64(), ctypes.c_int64()
-    rc = lib.lp_plan_simulate(M, block_rows, max_signals, max_iter_rows, ring_bytes, lag, len(T), T.ctypes.data,
+    rc = lib.lp_plan_simulate(M, block_rows, max_signals, max_iter_rows, ring_bytes, hop, lag, len(T), T.ctypes.data,
                               kind.ctypes.data, arrive.ctypes.data, cap, blocks.ctypes.data, cap,
                               iters.ctypes.data, ctypes.byref(nb), ctypes.byref(ni))
     return rc, blocks[:nb.value], iters[:ni.value], ring_bytes
 
 
-def layout_bytes(lib, M, rf, nf, ra, na, nc):
+def layout_bytes(lib, M, rf, nf, ra, na, nc, frames_f=-1):
     out = np.zeros(15, np.uint64)
-    assert lib.lp_plan_layout(M, rf, nf, ra, na, nc, out.ctypes.data) == 0
+    assert lib.lp_plan_layout(M, rf, nf, ra, na, nc, frames_f, out.ctypes.data) == 0
     return out
 
 
-def check(lib, T, kind, blocks, iters, ring_bytes, *, M, block_rows, max_signals, max_iter_rows):
+def check(lib, T, kind, blocks, iters, ring_bytes, *, M, block_rows, max_signals, max_iter_rows, hop=0):
     n = len(T)
     # coverage, order, block sizes, carried flags
     per_req = {k: [] for k in range(n)}
-    for it, rq, row0, rows, pos, call, carried, last in blocks:
+    for it, rq, row0, rows, pos, call, carried, last, fpos in blocks:
         per_req[int(rq)].append((int(it), int(row0), int(rows), int(call), int(carried), int(last)))
     first_iter = []
     for k in range(n):
@@ -112,7 +112,15 @@ def check(lib, T, kind, blocks, iters, ring_bytes, *, M, block_rows, max_signals
         assert np.all(fw[ncar:, 6] == 0) if len(fw) else True
         prev_cont = [int(r[1]) for r in fw if r[7] == 0]
         nc = len(prev_cont)
-        lay = layout_bytes(lib, M, rows_f, len(fw), rows_a, len(ad), nc)
+        frames_f = -1
+        if hop > 0:
+            # blocks start on frame anchors; frame rows packed back to back
+            fpos = 0
+            for r in fw:
+                assert r[2] % hop == 0 and r[8] == fpos
+                fpos += -(-(int(r[3]) + int(r[3]) % 2) // hop) + 1
+            frames_f = fpos
+        lay = layout_bytes(lib, M, rows_f, len(fw), rows_a, len(ad), nc, frames_f)
         assert int(iters[i, 3]) == int(lay[14])
     # ring: in bounds, no overlap between regions alive at the same time
     for i in range(len(iters)):
@@ -206,6 +214,11 @@ def test_oversized_requests_rejected(plan):
 
 def test_layout_is_aligned_and_disjoint(plan):
     lay = layout_bytes(plan, 22, 1002, 3, 998, 2, 1)
+    # frames mode: the synthesis call holds 12 frame rows, and a frame-offset
+    # table sits between the row offsets and the continuing indexes
+    lf = layout_bytes(plan, 22, 1002, 3, 998, 2, 1, 12)
+    assert int(lf[1]) - int(lf[0]) >= 12 * 88 and int(lf[1]) < int(lay[1])
+    assert int(lf[12]) - int(lf[11]) == 3 * 8 + 3 * 8
     starts = [int(x) for x in lay[:9]] + [int(lay[9])]
     sizes = [1002 * 88, 1002 * 4, 1002 * 4, 998 * 88, 998 * 4, 998 * 4, 998 * 4, 998 * 4, 998 * 88]
     for s in starts:
@@ -215,3 +228,20 @@ def test_layout_is_aligned_and_disjoint(plan):
     # tables: off_f [4] int64, off_a [3] int64, cont [1] int32
     assert int(lay[11]) - int(lay[10]) == 4 * 8 and int(lay[12]) - int(lay[11]) == 3 * 8
     assert int(lay[13]) == 4 * 8 + 3 * 8 + 4 and int(lay[14]) >= int(lay[12]) + 4
+
+
+def test_frames_server_plan(plan):
+    """hop > 0: blocks start on frame anchors and carry their frame rows;
+    adaptation requests are not admissible."""
+    rng = np.random.default_rng(11)
+    n = 40
+    T = rng.integers(0, 20000, size=n)
+    kind = np.zeros(n, np.int32)
+    arrive = np.sort(rng.integers(0, 50, size=n))
+    cfg = dict(M=22, block_rows=4800, max_signals=6, max_iter_rows=1 << 15, hop=120)
+    rc, blocks, iters, ring = simulate(plan, T, kind, arrive, **cfg)
+    assert rc == 0
+    check(plan, T, kind, blocks, iters, ring, **cfg)
+    assert blocks[:, 6].sum() > 0
+    rc, *_ = simulate(plan, T[:3], np.array([0, 1, 0], np.int32), arrive[:3], **cfg)
+    assert rc == -1
