@@ -307,6 +307,18 @@ int lp_tv_backward_ti_f32(int B, int64_t T, int M, const float *gs,
 int lp_tv_device_status(int reset);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper).  Launches one
+ * warp on `stream` that runs one of the kernels' bounded waits on a
+ * condition nothing satisfies: which = 1, an mbarrier waiting for bulk-copy
+ * bytes that are never sent (no copy is issued); which = 2, a progress
+ * counter that nothing increments.  The wait gives up after the same limit
+ * the kernels use (well under a second), records status 1 or 2 in the
+ * device status word (lp_tv_device_status) and returns; the context stays
+ * usable.  LP_EINVAL for another `which`, LP_ECUDA if the launch fails.
+ */
+int lp_tv_selftest_wait(int which, void *stream);
+
+/*
  * Allocation-free forward filter (no counterpart in the paper; a service for
  * callers that cannot allocate device memory when they run the filter, such
  * as a real-time audio callback that must not wait on the CUDA allocator or

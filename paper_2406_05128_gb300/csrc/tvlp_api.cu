@@ -600,6 +600,10 @@ int forward_frames_varlen_impl(int n, const int64_t *off, int64_t total, int M, 
 }
 }  // namespace
 
+// The device status word of the current device, for the other translation
+// units of the library (nullptr if unavailable).
+int *tvlp::device_status_word() { return status_word(); }
+
 extern "C" {
 
 const char *lp_strerror(int code) {

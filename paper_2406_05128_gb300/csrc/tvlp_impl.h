@@ -123,4 +123,7 @@ inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 9)
 // hook is installed on this thread (lp_tv_set_profile_events).
 void profile_mark(int k, bool end, cudaStream_t st);
 
+// The device status word of the current device (nullptr if unavailable).
+int *device_status_word();
+
 }  // namespace tvlp

@@ -1452,6 +1452,21 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
 
+// Warp-collective bounded wait until *c >= target: lane 0 polls with relaxed
+// loads (sleeping between polls), then every lane takes one acquire load
+// before reading what the count guards.  After kScanSpin polls it records
+// DEV_TIMEOUT_SCAN and returns false.
+__device__ __forceinline__ bool wait_counter(const unsigned *c, unsigned target, int lane, int *status) {
+    bool ok = false;
+    for (int it = 0; it < kScanSpin && !ok; ++it) {
+        ok = __shfl_sync(0xffffffffu, lane == 0 ? (ld_relaxed(c) >= target) : false, 0);
+        if (!ok) __nanosleep(256);
+    }
+    (void)ld_acquire(c);
+    if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT_SCAN);
+    return ok;
+}
+
 template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(kScanWarps * 32)
     k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
@@ -1504,18 +1519,9 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         map_cols<S, MP, TRANS>(p, m, z, j0);
         return hop_smem<S, MP>(p, xb + ((nhop++) & 1) * RS, x, lane);
     };
-    // bounded wait until signal b's counter reaches `target`: lane 0 polls
-    // with relaxed loads, then every lane takes one acquire load before
-    // reading what the count guards
+    // bounded wait until signal b's counter reaches `target`
     auto wait_count = [&](int64_t b, unsigned target) -> bool {
-        bool ok = false;
-        for (int it = 0; it < kScanSpin && !ok; ++it) {
-            ok = __shfl_sync(0xffffffffu, lane == 0 ? (ld_relaxed(cnt + b * kCntStride) >= target) : false, 0);
-            if (!ok) __nanosleep(256);
-        }
-        (void)ld_acquire(cnt + b * kCntStride);
-        if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT_SCAN);
-        return ok;
+        return wait_counter(cnt + b * kCntStride, target, lane, status);
     };
     // make this warp's global stores visible (also to bulk copies) before
     // bumping signal b's counter

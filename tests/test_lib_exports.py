@@ -92,3 +92,9 @@ def test_serve_host_only_entry_points(lib):
     assert lib.lp_serve_submit(None, 0, 0, 10, 8, 8, None, 8, None, None, 0) == _lib.LP_EINVAL
     t0 = lib.lp_serve_now_ns()
     assert lib.lp_serve_now_ns() >= t0 > 0
+
+
+def test_selftest_rejects_unknown_wait_without_launching(lib):
+    from paper_2406_05128_gb300 import _lib
+    assert lib.lp_tv_selftest_wait(0, None) == _lib.LP_EINVAL
+    assert lib.lp_tv_selftest_wait(3, None) == _lib.LP_EINVAL
