@@ -64,10 +64,12 @@ def parse():
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
-    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames"), default="headline",
+    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train"), default="headline",
                     help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders; "
                          "serving: the request loop under Poisson arrivals; frames: the headline step with the "
-                         "coefficients generated in the kernels from frame-rate reflection coefficients")
+                         "coefficients generated in the kernels from frame-rate reflection coefficients; train: "
+                         "the harmonic-plus-noise training step (B=64, T=96000, two M=22 filters, MSS loss, "
+                         "chunk-state checkpointing)")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="measured seconds of the serving run (default 60 for --workload serving, 15 inside the "
                          "headline line; 0 skips it there)")
@@ -488,6 +490,7 @@ def run_ours(args):
                          "FP64 sequential C oracle, one host thread per signal"}
 
     launches_per_step = len(names_f) + len(names_b)
+    small = small_case_us() if world == 1 else None
     serving = None
     serve_s = 15.0 if args.serve_seconds is None else args.serve_seconds
     if world == 1 and serve_s > 0:
@@ -506,7 +509,8 @@ def run_ours(args):
                          f"(mean step there {statistics.mean(prof_step_ms):.4f} ms)") if prof_step_ms
                         else "events around each kernel of the timed steps",
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks, "plain_gpu_kernel": plain, "serving": serving, "source_hash": source_hash(),
+        "clocks": clocks, "plain_gpu_kernel": plain, "small_case": small, "serving": serving,
+        "source_hash": source_hash(),
         "region_wall_s": round(t_region1 - t_region0, 3),
     }
     print(json.dumps(line), flush=True)
@@ -962,6 +966,159 @@ def run_frames(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# C1: the small plain case, B=1, T=4800, M=16 (latency-bound: absolute us)
+# ---------------------------------------------------------------------------
+def small_case_us(reps=50):
+    import torch
+
+    from paper_2406_05128_gb300 import _lib, inputs
+
+    w = inputs.plain_small(seed=1, gen="literal")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    a, e, gs = (torch.from_numpy(x).to(dev) for x in (w.a, w.e, w.gs))
+    B, T, M = a.shape
+    s, ge, ga = torch.empty_like(e), torch.empty_like(e), torch.empty_like(a)
+    out = {"workload": "B=1, T=4800, M=16, FP32, k ~ U(-0.9, 0.9) per 120-sample frame, e ~ N(0,1), fwd+bwd"}
+    for name, algo in (("chunked", _lib.LP_ALGO_CHUNKED), ("plain", _lib.LP_ALGO_PLAIN)):
+        chunk = _lib.lp_tv_pick_chunk(B, T, M)
+        wsb = _lib.lp_tv_workspace_bytes(B, T, M, chunk)
+        ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if algo == _lib.LP_ALGO_CHUNKED else 0
+
+        def step():
+            sp = torch.cuda.current_stream(dev).cuda_stream
+            _lib.lp_tv_forward(_lib.LP_DTYPE_F32, B, T, M, a.data_ptr(), e.data_ptr(), None, s.data_ptr(), None,
+                               chunk, algo, ws.data_ptr(), ws.numel(), sp)
+            _lib.lp_tv_backward(_lib.LP_DTYPE_F32, B, T, M, gs.data_ptr(), a.data_ptr(), s.data_ptr(), None,
+                                ge.data_ptr(), ga.data_ptr(), None, chunk, algo, flags, ws.data_ptr(), ws.numel(), sp)
+
+        for _ in range(5):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = (torch.cuda.Event(enable_timing=True, external=True) for _ in range(2))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            e0.record()
+            step()
+            e1.record()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            g.replay()
+            torch.cuda.current_stream(dev).synchronize()
+            ts.append(e0.elapsed_time(e1) * 1000.0)
+        out[f"{name}_us"] = round(statistics.median(ts), 2)
+        out[f"{name}_chunk"] = chunk if algo == _lib.LP_ALGO_CHUNKED else None
+    return out
+
+
+# ---------------------------------------------------------------------------
+# C3: the harmonic-plus-noise training step, s = LP_{a_H}(pulse) +
+# LP_{a_C}(N(0,1)), both time-varying M=22, multi-resolution STFT L1 loss
+# against a fixed target, backward through torch.autograd, chunk-state
+# checkpointing on
+# ---------------------------------------------------------------------------
+TRAIN_B, TRAIN_T, TRAIN_M = 64, 96000, 22
+MSS_SIZES = (509, 1021, 2053)
+
+
+def mss_loss(x, y):
+    """Multi-resolution STFT L1 loss: L1 of linear and of log magnitudes,
+    Hann windows, hop n_fft/4 (the paper gives only the FFT sizes)."""
+    import torch
+    loss = 0.0
+    for n in MSS_SIZES:
+        win = torch.hann_window(n, device=x.device, dtype=x.dtype)
+        X = torch.stft(x, n, hop_length=n // 4, window=win, return_complex=True).abs()
+        Y = torch.stft(y, n, hop_length=n // 4, window=win, return_complex=True).abs()
+        loss = loss + (X - Y).abs().mean() + (torch.log(X + 1e-5) - torch.log(Y + 1e-5)).abs().mean()
+    return loss
+
+
+def run_train(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_05128_gb300 import inputs, ops
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, T, M = TRAIN_B, TRAIN_T, TRAIN_M
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+
+    def coeffs(seed):
+        sig = inputs.signals_torch([T] * B, M, seed=seed, gen="stable", device=dev)
+        return torch.stack([x[0] for x in sig]), torch.stack([x[1] for x in sig])
+
+    aH, eH = coeffs(21)      # harmonic filter, pulse-train excitation
+    aC, _ = coeffs(22)       # noise filter
+    eC = torch.randn((B, T), generator=gen, device=dev)
+    _, target = coeffs(23)   # a fixed target signal
+    aH.requires_grad_(True)
+    aC.requires_grad_(True)
+    g_lp = torch.randn((B, T), generator=gen, device=dev)
+
+    def step(checkpoint, loss_kind):
+        aH.grad = None
+        aC.grad = None
+        s = ops.lp_filter(aH, eH, checkpoint=checkpoint) + ops.lp_filter(aC, eC, checkpoint=checkpoint)
+        loss = mss_loss(s, target) if loss_kind == "mss" else (s * g_lp).sum()
+        loss.backward()
+
+    def timed(checkpoint, loss_kind, n):
+        for _ in range(max(3, args.warmup)):
+            step(checkpoint, loss_kind)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(n):
+            e0.record()
+            step(checkpoint, loss_kind)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        peak = torch.cuda.max_memory_allocated(dev) - base
+        return statistics.mean(ts), peak
+
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t0 = time.perf_counter()
+    ms, peak_ck = timed(True, "mss", args.steps)
+    t1 = time.perf_counter()
+    sampler.stop()
+    lp_ms, _ = timed(True, "lp", max(5, args.steps // 2))
+    ms_nock, peak_nock = timed(False, "mss", max(5, args.steps // 2))
+    nsamp = B * T
+    lp_bytes = 2 * (12 * M + 20) * nsamp
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": "harmonic-plus-noise training step Msamples/s (two M=22 TV-LP filters, MSS loss, checkpointing)",
+        "value": round(nsamp / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"s = LP_aH(pulse train + 0.1 N(0,1)) + LP_aC(N(0,1)), B={B}, T={T}, M={M}, FP32, "
+                               f"stable reflection generator, MSS L1 loss (FFT {list(MSS_SIZES)}, hop n/4, Hann) "
+                               "vs a fixed target, torch.autograd backward, chunk-state checkpointing on",
+                   "l2": "inputs far beyond L2 (2 x 540 MB of coefficients)"},
+        "lp_part": {"ms": round(lp_ms, 4), "what": "the same step with loss = <s, g> instead of the MSS loss: "
+                    "both filters forward, recompute from checkpoints and adjoint, plus the autograd overhead",
+                    "algorithmic_bytes": lp_bytes,
+                    "GB/s": round(lp_bytes / (lp_ms * 1e-3) / 1e9, 1),
+                    "frac_of_hbm": round(lp_bytes / (lp_ms * 1e-3) / 1e9 / hbm, 4)},
+        "stft_and_rest_ms": round(ms - lp_ms, 4),
+        "checkpointing": {"peak_extra_bytes_on": int(peak_ck), "peak_extra_bytes_off": int(peak_nock),
+                          "ms_per_step_off": round(ms_nock, 4)},
+        "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -972,6 +1129,8 @@ def main():
         return run_serving(args)
     if args.workload == "frames":
         return run_frames(args)
+    if args.workload == "train":
+        return run_train(args)
     return run_ours(args)
 
 
