@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--min-warmup-s", type=float, default=1.0, help="keep warming up at least this long")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-streams", type=int, default=1,
+                    help="copy streams per direction in the pipelined end-to-end measurement (each step's copies "
+                         "are split into that many parts)")
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
@@ -424,8 +427,82 @@ def run_ours(args):
             if i >= 2:
                 e2e_ms.append(ev0.elapsed_time(ev1))
         e2e_t = statistics.mean(e2e_ms)
-        e2e = {"value": round(B * T * world / (e2e_t * 1e-3) / 1e6, 4), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_t, 4)}
+        serial = {"value": round(B * T * world / (e2e_t * 1e-3) / 1e6, 4), "ms_per_step": round(e2e_t, 4),
+                  "what": "each step's copies in, kernels and copies out back to back on one stream"}
+        # pipelined: the copies in of step i+1, the kernels of step i and the
+        # copies out of step i-1 run at once on three streams, with two sets
+        # of device buffers; every step still copies its own inputs in and
+        # its own results out
+        sets = [dict(a=a, e=e, gs=gs, s=s, ge=ge, ga=ga)]
+        sets.append({k: torch.empty_like(v) for k, v in sets[0].items()})
+        s_in, s_cp, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+        ncs = max(1, args.e2e_streams)
+        s_in_x = [s_in] + [torch.cuda.Stream(dev) for _ in range(ncs - 1)]
+        s_out_x = [s_out] + [torch.cuda.Stream(dev) for _ in range(ncs - 1)]
+
+        def split_copy(streams, pairs, after):
+            """Copy (dst, src) pairs, each cut into len(streams) row ranges,
+            one range per stream; the extra streams wait for `after` first
+            and the first stream waits for all of them at the end."""
+            for st in streams[1:]:
+                st.wait_event(after)
+            for k, st in enumerate(streams):
+                with torch.cuda.stream(st):
+                    for dst, src in pairs:
+                        n = dst.numel()
+                        assert src.numel() == n
+                        d, s_ = dst.view(-1), src.view(-1)
+                        lo, hi = n * k // len(streams), n * (k + 1) // len(streams)
+                        d[lo:hi].copy_(s_[lo:hi], non_blocking=True)
+            for st in streams[1:]:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                streams[0].wait_event(ev)
+
+        def step_on(bf, st):
+            sp = st.cuda_stream
+            _lib.lp_tv_forward(_lib.LP_DTYPE_F32, B, T, M, bf["a"].data_ptr(), bf["e"].data_ptr(), None,
+                               bf["s"].data_ptr(), None, chunk, algo, ws.data_ptr(), ws.numel(), sp)
+            _lib.lp_tv_backward(_lib.LP_DTYPE_F32, B, T, M, bf["gs"].data_ptr(), bf["a"].data_ptr(),
+                                bf["s"].data_ptr(), None, bf["ge"].data_ptr(), bf["ga"].data_ptr(), None, chunk, algo,
+                                bwd_flags, ws.data_ptr(), ws.numel(), sp)
+
+        warm = 2
+        n_p = max(6, min(args.steps, 20))
+        ev_in = [torch.cuda.Event() for _ in range(warm + n_p)]
+        ev_cp = [torch.cuda.Event() for _ in range(warm + n_p)]
+        ev_out = [torch.cuda.Event() for _ in range(warm + n_p)]
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        for i in range(warm + n_p):
+            bf = sets[i % 2]
+            if i == warm:
+                p0.record(s_in)
+            if i >= 2:
+                s_in.wait_event(ev_cp[i - 2])  # step i-2 has read this set's inputs
+            mark = torch.cuda.Event()
+            mark.record(s_in)
+            split_copy(s_in_x, ((bf["a"], ha), (bf["e"], he), (bf["gs"], hgs)), mark)
+            ev_in[i].record(s_in)
+            s_cp.wait_event(ev_in[i])
+            if i >= 2:
+                s_cp.wait_event(ev_out[i - 2])  # this set's outputs of step i-2 are on the host
+            step_on(bf, s_cp)
+            ev_cp[i].record(s_cp)
+            s_out.wait_event(ev_cp[i])
+            split_copy(s_out_x, ((hs, bf["s"]), (hge, bf["ge"]), (hga, bf["ga"])), ev_cp[i])
+            ev_out[i].record(s_out)
+        p1.record(s_out)
+        torch.cuda.synchronize()
+        pipe_t = p0.elapsed_time(p1) / n_p
+        e2e = {"value": round(B * T * world / (pipe_t * 1e-3) / 1e6, 4), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(pipe_t, 4),
+               "steps": n_p, "what": "C ABI calls with pinned host buffers; every step copies its inputs in and its "
+                                     "results out inside the timed region, consecutive steps overlapped on three "
+                                     "streams",
+               "GB/s_h2d": round(h2d / (pipe_t * 1e-3) / 1e9, 1), "copy_streams_per_direction": ncs,
+               "serial": serial}
+        del sets
 
     clocks = None
     if sampler is not None:

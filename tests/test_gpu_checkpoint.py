@@ -178,3 +178,28 @@ def test_harmonic_plus_noise_training_step():
     for gaH, gaC in ((gaH0, gaC0), (gaH1, gaC1)):
         assert_close("ga_H", gaH, rgaH, TOL_F32)
         assert_close("ga_C", gaC, rgaC, TOL_F32)
+
+
+def test_training_shape_full_size_sampled():
+    """The differentiation workload at full size: B=64, T=96000, two M=22
+    filters through the checkpointed autograd op (the bench's launch
+    configuration); two signals of each filter against the oracle."""
+    B, T, M = 64, 96000, 22
+    sig_h = inputs.signals_torch([T] * B, M, seed=21, gen="stable", device=DEV)
+    sig_c = inputs.signals_torch([T] * B, M, seed=22, gen="stable", device=DEV)
+    aH = torch.stack([x[0] for x in sig_h]).requires_grad_(True)
+    aC = torch.stack([x[0] for x in sig_c]).requires_grad_(True)
+    eH = torch.stack([x[1] for x in sig_h])
+    eC = torch.stack([x[2] for x in sig_c])  # an N(0,1) excitation
+    g = torch.stack([x[2] for x in sig_h])
+    sH = ops.lp_filter(aH, eH, checkpoint=True)
+    sC = ops.lp_filter(aC, eC, checkpoint=True)
+    (sH + sC).backward(g)
+    torch.cuda.synchronize()
+    assert _lib.lp_tv_device_status() == 0
+    for a, e, s, ga in ((aH, eH, sH, aH.grad), (aC, eC, sC, aC.grad)):
+        for b in (0, B - 1):
+            an, en, gn = (x[b].detach().cpu().numpy()[None] for x in (a, e, g))
+            rs, rge, rga, _ = O.forward_backward(an, en, gn)
+            assert_close("s", s[b].detach().cpu().numpy()[None], rs, TOL_F32)
+            assert_close("ga", ga[b].cpu().numpy()[None], rga, TOL_F32)
