@@ -1002,6 +1002,63 @@ def run_frames(args):
     ms = statistics.mean(step)
     fms = statistics.mean(fwd_ms)
     nsamp = B * T
+    # end to end: every step copies k, e, gs in and s, ge, gk out (pinned host
+    # buffers); consecutive steps overlap on three streams, as for the
+    # streamed step
+    e2e = None
+    if not args.no_e2e:
+        hk, he, hgs = (x.cpu().pin_memory() for x in (k, e, gs))
+        hs, hge, hgk = (torch.empty(x.shape).pin_memory() for x in (s, ge, gk))
+        sets = [dict(k=k, e=e, gs=gs, s=s, ge=ge, gk=gk)]
+        sets.append({n_: torch.empty_like(v) for n_, v in sets[0].items()})
+        wss = [ws]
+        s_in, s_cp, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+
+        def step_on(bf, w_, st):
+            sp = st.cuda_stream
+            _lib.lp_tv_forward_frames(B, T, M, hop, bf["k"].data_ptr(), bf["e"].data_ptr(), None, bf["s"].data_ptr(),
+                                      None, chunk, w_.data_ptr(), w_.numel(), sp)
+            _lib.lp_tv_backward_frames(B, T, M, hop, bf["gs"].data_ptr(), bf["k"].data_ptr(), bf["s"].data_ptr(),
+                                       None, bf["ge"].data_ptr(), bf["gk"].data_ptr(), None, chunk,
+                                       _lib.LP_BWD_REUSE_FORWARD, w_.data_ptr(), w_.numel(), sp)
+
+        warm, n_p = 2, max(6, min(args.steps, 20))
+        ev_in = [torch.cuda.Event() for _ in range(warm + n_p)]
+        ev_cp = [torch.cuda.Event() for _ in range(warm + n_p)]
+        ev_out = [torch.cuda.Event() for _ in range(warm + n_p)]
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        for i in range(warm + n_p):
+            bf = sets[i % 2]
+            if i == warm:
+                p0.record(s_in)
+            if i >= 2:
+                s_in.wait_event(ev_cp[i - 2])
+            with torch.cuda.stream(s_in):
+                bf["k"].copy_(hk, non_blocking=True)
+                bf["e"].copy_(he, non_blocking=True)
+                bf["gs"].copy_(hgs, non_blocking=True)
+            ev_in[i].record(s_in)
+            s_cp.wait_event(ev_in[i])
+            if i >= 2:
+                s_cp.wait_event(ev_out[i - 2])
+            step_on(bf, wss[0], s_cp)
+            ev_cp[i].record(s_cp)
+            s_out.wait_event(ev_cp[i])
+            with torch.cuda.stream(s_out):
+                hs.copy_(bf["s"], non_blocking=True)
+                hge.copy_(bf["ge"], non_blocking=True)
+                hgk.copy_(bf["gk"], non_blocking=True)
+            ev_out[i].record(s_out)
+        p1.record(s_out)
+        torch.cuda.synchronize()
+        pt = p0.elapsed_time(p1) / n_p
+        h2d = (hk.numel() + he.numel() + hgs.numel()) * 4
+        d2h = (hs.numel() + hge.numel() + hgk.numel()) * 4
+        e2e = {"value": round(nsamp / (pt * 1e-3) / 1e6, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(pt, 4), "steps": n_p,
+               "what": "C ABI calls with pinned host buffers; every step copies k, e, gs in and s, ge, gk out inside "
+                       "the timed region, consecutive steps overlapped on three streams"}
     # FP32 FMAs per sample: step-up M(M-1)/2 + interpolation M wherever a row
     # is generated; K1 (M+1)M; each re-run pass M; the frame gradient's
     # reverse step-up with recomputation about 4 step-ups plus Eq. 12
@@ -1036,7 +1093,7 @@ def run_frames(args):
                      "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                      "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock",
                      "traffic": None},
-        "kernels": kd, "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+        "kernels": kd, "e2e": e2e, "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
         "gpu_launches": (len(names)) * args.steps,
     }
     print(json.dumps(line), flush=True)
