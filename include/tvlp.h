@@ -260,10 +260,13 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
  * conventions, shapes and errors as for lp_tv_forward_f32 /
  * lp_tv_backward_f32; hop >= 1.
  *
- * lp_tv_forward_frames_varlen_f32: varlen batches (offsets as for
- * lp_tv_forward_varlen_f32) with frame_offsets [n] (DEVICE, int64): signal
- * b's frames start at frame frame_offsets[b] of k, and it has
- * ceil(len_b/hop)+1 of them.  Workspace: lp_tv_workspace_bytes_varlen.
+ * lp_tv_forward_frames_varlen_f32 / lp_tv_backward_frames_varlen_f32:
+ * varlen batches (offsets as for lp_tv_forward_varlen_f32) with
+ * frame_offsets [n] (DEVICE, int64): signal b's frames start at frame
+ * frame_offsets[b] of k, and it has ceil(len_b/hop)+1 of them, len_b =
+ * offsets[b+1] - offsets[b]; total_frames = the rows of k (and of gk).
+ * Workspace: lp_tv_workspace_bytes_varlen for the forward (and a backward
+ * without gk), lp_tv_workspace_bytes_frames_varlen for a backward with gk.
  */
 size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop,
                                     int chunk);
@@ -285,6 +288,17 @@ int lp_tv_forward_frames_varlen_f32(int n, const int64_t *offsets,
                                     const float *zi, float *s, float *ckpt,
                                     int chunk, void *workspace,
                                     size_t workspace_bytes, void *stream);
+size_t lp_tv_workspace_bytes_frames_varlen(int n, int64_t total, int M,
+                                           int64_t total_frames, int chunk);
+int lp_tv_backward_frames_varlen_f32(int n, const int64_t *offsets,
+                                     int64_t total, int M, int hop,
+                                     const int64_t *frame_offsets,
+                                     int64_t total_frames, const float *gs,
+                                     const float *k, const float *s,
+                                     const float *zi, float *ge, float *gk,
+                                     float *gzi, int chunk, int flags,
+                                     void *workspace, size_t workspace_bytes,
+                                     void *stream);
 size_t lp_tv_workspace_bytes_ti(int B, int64_t T, int M, int chunk);
 int lp_tv_forward_ti_f32(int B, int64_t T, int M, const float *a,
                          const float *e, const float *zi, float *s,

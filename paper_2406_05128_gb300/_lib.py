@@ -39,7 +39,8 @@ EXPORTS = (
     "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
     "lp_tv_workspace_bytes_frames", "lp_tv_forward_frames_f32", "lp_tv_backward_frames_f32",
-    "lp_tv_forward_frames_varlen_f32", "lp_tv_selftest_wait", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
+    "lp_tv_forward_frames_varlen_f32", "lp_tv_selftest_wait", "lp_tv_workspace_bytes_frames_varlen",
+    "lp_tv_backward_frames_varlen_f32", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
     "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
 )
@@ -126,6 +127,11 @@ def _declare(lib):
     lib.lp_tv_backward_frames_f32.restype = i32
     lib.lp_tv_forward_frames_varlen_f32.argtypes = [i32, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.lp_tv_forward_frames_varlen_f32.restype = i32
+    lib.lp_tv_workspace_bytes_frames_varlen.argtypes = [i32, i64, i32, i64, i32]
+    lib.lp_tv_workspace_bytes_frames_varlen.restype = sz
+    lib.lp_tv_backward_frames_varlen_f32.argtypes = [i32, vp, i64, i32, i32, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32,
+                                                     i32, vp, sz, vp]
+    lib.lp_tv_backward_frames_varlen_f32.restype = i32
     lib.lp_tv_selftest_wait.argtypes = [i32, vp]
     lib.lp_tv_selftest_wait.restype = i32
     lib.lp_tv_workspace_bytes_ti.argtypes = [i32, i64, i32, i32]
@@ -296,3 +302,14 @@ def lp_tv_forward_ti(B, T, M, a, e, zi, s, ckpt, chunk, ws, ws_bytes, stream):
 def lp_tv_backward_ti(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream):
     _check(load().lp_tv_backward_ti_f32(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_bytes, stream),
            "lp_tv_backward_ti_f32")
+
+
+def lp_tv_workspace_bytes_frames_varlen(n, total, M, total_frames, chunk=0):
+    return load().lp_tv_workspace_bytes_frames_varlen(n, total, M, total_frames, chunk)
+
+
+def lp_tv_backward_frames_varlen(n, offsets, total, M, hop, frame_offsets, total_frames, gs, k, s, zi, ge, gk, gzi,
+                                 chunk, flags, ws, ws_bytes, stream):
+    _check(load().lp_tv_backward_frames_varlen_f32(n, offsets, total, M, hop, frame_offsets, total_frames, gs, k, s,
+                                                   zi, ge, gk, gzi, chunk, flags, ws, ws_bytes, stream),
+           "lp_tv_backward_frames_varlen_f32")

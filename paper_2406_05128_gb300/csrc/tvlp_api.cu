@@ -598,6 +598,52 @@ int forward_frames_varlen_impl(int n, const int64_t *off, int64_t total, int M, 
     src.foff = foff;
     return Dispatch<float>::forward_gen(p, src, e, zi, s, ckpt, ws, st);
 }
+
+// Varlen adjoint with frames: gk has total_frames rows (the packed frames).
+size_t frames_varlen_workspace_bytes(const Problem &p, int64_t total_frames) {
+    return align256(workspace_for(p, LP_DTYPE_F32)) + align256(2 * (size_t)total_frames * p.M * sizeof(float));
+}
+
+int backward_frames_varlen_impl(int n, const int64_t *off, int64_t total, int M, int hop, const int64_t *foff,
+                                int64_t total_frames, const float *gs, const float *k, const float *s,
+                                const float *zi, float *ge, float *gk, float *gzi, int chunk, int flags, void *ws,
+                                size_t wsb, void *stream) {
+    if (hop < 1 || total_frames < 0) return LP_EINVAL;
+    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    Problem p;
+    int rc = make_problem_varlen(n, total, M, chunk, LP_DTYPE_F32, off, &p);
+    if (rc != LP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return LP_OK;
+    if (total == 0 || M == 0) {
+        if (gzi != nullptr && M > 0 && cudaMemsetAsync(gzi, 0, (size_t)n * M * sizeof(float), st) != cudaSuccess)
+            return LP_ECUDA;
+        if (gk != nullptr && M > 0 &&
+            cudaMemsetAsync(gk, 0, (size_t)total_frames * M * sizeof(float), st) != cudaSuccess)
+            return LP_ECUDA;
+        if (M == 0 && total > 0 &&
+            cudaMemcpyAsync(ge, gs, (size_t)total * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return LP_ECUDA;
+        return LP_OK;
+    }
+    if (off == nullptr || foff == nullptr || gs == nullptr || ge == nullptr || k == nullptr ||
+        (gk != nullptr && s == nullptr))
+        return LP_EINVAL;
+    if (!aligned(off, 8) || !aligned(foff, 8) || !aligned(gs, 4) || !aligned(ge, 4) || !aligned(k, 4) ||
+        !aligned(s, 4) || !aligned(zi, 4) || !aligned(gk, 4) || !aligned(gzi, 4))
+        return LP_EALIGN;
+    const size_t need = gk != nullptr ? frames_varlen_workspace_bytes(p, total_frames) : workspace_for(p, LP_DTYPE_F32);
+    if (ws == nullptr || !aligned(ws, 256) || wsb < need) return LP_EWORKSPACE;
+    if ((p.status = status_word()) == nullptr) return LP_ECUDA;
+    CoefSrc src = make_src(SRC_FRAMES, k, total_frames, hop);
+    src.foff = foff;
+    // empty signals have no chunk to write their (zero) gzi
+    if (gzi != nullptr && cudaMemsetAsync(gzi, 0, (size_t)n * M * sizeof(float), st) != cudaSuccess) return LP_ECUDA;
+    if ((rc = Dispatch<float>::backward_gen(p, src, gs, s, zi, ge, gzi, flags, ws, st)) != LP_OK) return rc;
+    if (gk == nullptr) return LP_OK;
+    void *scratch = static_cast<char *>(ws) + align256(workspace_for(p, LP_DTYPE_F32));
+    return Dispatch<float>::grad_src(p, src, ge, s, zi, gk, scratch, st);
+}
 }  // namespace
 
 // The device status word of the current device, for the other translation
@@ -777,6 +823,21 @@ int lp_tv_backward_ti_f32(int B, int64_t T, int M, const float *gs, const float 
                           float *ge, float *ga, float *gzi, int chunk, int flags, void *ws, size_t wsb,
                           void *stream) {
     return backward_gen_impl(SRC_CONST, B, T, M, 0, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, wsb, stream);
+}
+
+size_t lp_tv_workspace_bytes_frames_varlen(int n, int64_t total, int M, int64_t total_frames, int chunk) {
+    Problem p;
+    if (total_frames < 0 || make_problem_varlen(n, total, M, chunk, LP_DTYPE_F32, nullptr, &p) != LP_OK) return 0;
+    p.off = reinterpret_cast<const int64_t *>(1);  // size the tables region too
+    return frames_varlen_workspace_bytes(p, total_frames);
+}
+
+int lp_tv_backward_frames_varlen_f32(int n, const int64_t *offsets, int64_t total, int M, int hop,
+                                     const int64_t *frame_offsets, int64_t total_frames, const float *gs,
+                                     const float *k, const float *s, const float *zi, float *ge, float *gk,
+                                     float *gzi, int chunk, int flags, void *ws, size_t wsb, void *stream) {
+    return backward_frames_varlen_impl(n, offsets, total, M, hop, frame_offsets, total_frames, gs, k, s, zi, ge, gk,
+                                       gzi, chunk, flags, ws, wsb, stream);
 }
 
 }  // extern "C"

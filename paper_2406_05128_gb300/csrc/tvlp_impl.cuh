@@ -388,9 +388,9 @@ int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, con
     if constexpr (sizeof(S) != 4) {
         return EUNSUPPORTED;
     } else {
-        if (p.off != nullptr) return EUNSUPPORTED;
         float *sc = static_cast<float *>(scratch);
         if (src.kind == SRC_CONST) {
+            if (p.off != nullptr) return EUNSUPPORTED;
             const int64_t tiles = (p.T + kGradRows - 1) / kGradRows;
             // profiling slots 3 and 4: after the adjoint's three kernels
             TVLP_LAUNCH(3, (launch(k_grad_const<MP>, dim3((unsigned)tiles, (unsigned)p.B), dim3(kGradThreads), 0, st,
@@ -402,12 +402,13 @@ int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, con
         }
         if (src.kind == SRC_FRAMES) {
             using FG = FrameGradGeo<MP>;
-            const int64_t items = (int64_t)p.B * src.F;
+            // varlen: src.F is the total number of packed frame rows
+            const int64_t items = p.off != nullptr ? src.F : (int64_t)p.B * src.F;
             const int64_t n = items * p.M;
             float *lo = sc, *hi = sc + n;
             TVLP_LAUNCH(3, (launch(k_grad_frames<MP>, dim3((unsigned)((items + FG::WARPS - 1) / FG::WARPS)),
                                    dim3(32 * FG::WARPS), 0, st, false, p.B, p.T, p.M, src.F, src.hop, src.inv_hop,
-                                   src.k, ge, s, zi, lo, hi)));
+                                   src.k, ge, s, zi, lo, hi, p.off, src.foff)));
             TVLP_LAUNCH(4, (launch(k_grad_frames_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, n,
                                    lo, hi, gk)));
             return OK;

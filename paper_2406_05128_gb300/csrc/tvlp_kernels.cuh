@@ -1868,24 +1868,56 @@ __device__ __forceinline__ void stepup_stage(float (&a)[MP], float km, int m) {
     a[m - 1] = km;
 }
 
+// Varlen batches (off != nullptr): items are the rows of the packed frame
+// array k [n_frames][M]; signal b owns rows [foff[b], foff[b+1]) (the last
+// up to n_frames) and samples [off[b], off[b+1]) of ge and s.
+__device__ __forceinline__ int find_frame_signal(const int64_t *__restrict__ foff, int n, int64_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(foff + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <int MP>
 __global__ void __launch_bounds__(32 * FrameGradGeo<MP>::WARPS)
     k_grad_frames(int B, int64_t T, int M, int64_t F, int hop, float inv_hop, const float *__restrict__ k,
                   const float *__restrict__ ge, const float *__restrict__ s, const float *__restrict__ zi,
-                  float *__restrict__ lo_out, float *__restrict__ hi_out) {
+                  float *__restrict__ lo_out, float *__restrict__ hi_out, const int64_t *__restrict__ off,
+                  const int64_t *__restrict__ foff) {
     using FG = FrameGradGeo<MP>;
     constexpr int SEG = FG::SEG, NSEG = FG::NSEG;
     __shared__ float gsh[FG::WARPS][32][MP + 1];
     __shared__ float wsh[FG::WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * FG::WARPS + warp;  // (b, f)
+    // uniform: item = b F + f, F frames per signal; varlen: F is the total
+    // frame count and item a row of the packed frames
+    const int64_t item = (int64_t)blockIdx.x * FG::WARPS + warp;
     pdl_wait();
     pdl_release();
-    if (item >= (int64_t)B * F) return;
-    const int64_t b = item / F, f = item % F;
-    const int64_t ts = f * hop, te = ts + hop < T ? ts + hop : T;
-    const float *k0 = k + (b * F + f) * (int64_t)M;
-    const float *k1 = f + 1 < F ? k0 + M : k0;
+    const int64_t n_items = off != nullptr ? F : (int64_t)B * F;
+    if (item >= n_items) return;
+    int64_t b, f, Fb, r0;  // signal, frame within it, its frames, its first row
+    int64_t Tb;             // its samples
+    if (off == nullptr) {
+        b = item / F;
+        f = item % F;
+        Fb = F;
+        r0 = b * T;
+        Tb = T;
+    } else {
+        b = find_frame_signal(foff, B, item);
+        const int64_t fb0 = __ldg(foff + b);
+        f = item - fb0;
+        Fb = (b + 1 < B ? __ldg(foff + b + 1) : F) - fb0;
+        r0 = __ldg(off + b);
+        Tb = __ldg(off + b + 1) - r0;
+    }
+    const int64_t ts = f * hop, te = ts + hop < Tb ? ts + hop : Tb;
+    const float *k0 = k + item * (int64_t)M;
+    const float *k1 = f + 1 < Fb ? k0 + M : k0;
     float lo_acc = 0.f, hi_acc = 0.f;  // lane m < M: coefficient m+1
     for (int64_t base = ts; base < te; base += 32) {
         const int64_t t = base + lane;
@@ -1894,13 +1926,13 @@ __global__ void __launch_bounds__(32 * FrameGradGeo<MP>::WARPS)
         float w = 0.f;
         if (valid) {
             w = (float)(t - ts) * inv_hop;
-            const float gt = ge[b * T + t];
+            const float gt = ge[r0 + t];
 #pragma unroll
             for (int i = 1; i <= MP; ++i) {
                 float sv = 0.f;
                 if (i <= M) {
                     const int64_t u = t - i;
-                    if (u >= 0) sv = s[b * T + u];
+                    if (u >= 0) sv = s[r0 + u];
                     else if (zi != nullptr) sv = zi[b * M + (-u - 1)];
                 }
                 g[i - 1] = -gt * sv;
@@ -1989,9 +2021,9 @@ __global__ void __launch_bounds__(32 * FrameGradGeo<MP>::WARPS)
         __syncwarp();
     }
     if (lane < M) {
-        lo_out[(b * F + f) * (int64_t)M + lane] = lo_acc;
-        if (f + 1 < F) hi_out[(b * F + f + 1) * (int64_t)M + lane] = hi_acc;
-        if (f == 0) hi_out[(b * F) * (int64_t)M + lane] = 0.f;
+        lo_out[item * (int64_t)M + lane] = lo_acc;
+        if (f + 1 < Fb) hi_out[(item + 1) * (int64_t)M + lane] = hi_acc;
+        if (f == 0) hi_out[item * (int64_t)M + lane] = 0.f;
     }
 }
 

@@ -492,3 +492,30 @@ def lp_tv_forward_frames_varlen(packed: Packed, frames: PackedFrames, k, e, zi=N
                                          frames.offsets.data_ptr(), _ptr(k), _ptr(e), _ptr(zi), _ptr(s), None, chunk,
                                          _ptr(ws), ws.numel(), _stream(dev))
     return s
+
+
+def lp_tv_backward_frames_varlen(packed: Packed, frames: PackedFrames, gs, k, s, zi=None, *, need_gk: bool = True,
+                                 need_gzi: bool = True, chunk: int = 0, ws=None, reuse_forward: bool = False):
+    """Varlen adjoint with generated coefficients: (ge [total], gk
+    [frames.total, M] or None, gzi [n, M] or None).  reuse_forward: ws holds
+    the forward's transfers (then size it with
+    lp_tv_workspace_bytes_frames_varlen)."""
+    total = packed.total
+    M = k.shape[1]
+    dev = k.device
+    _check(gs, "gs", (total,), torch.float32, dev)
+    _check(s, "s", (total,), torch.float32, dev)
+    _check(zi, "zi", (packed.n, M), torch.float32, dev)
+    with torch.cuda.device(dev):
+        ge = torch.empty((total,), device=dev)
+        gk = torch.empty((frames.total, M), device=dev) if need_gk else None
+        gzi = torch.empty((packed.n, M), device=dev) if need_gzi else None
+        if ws is None:
+            nb = _lib.lp_tv_workspace_bytes_frames_varlen(packed.n, total, M, frames.total, chunk)
+            ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward_frames_varlen(packed.n, packed.offsets.data_ptr(), total, M, frames.hop,
+                                          frames.offsets.data_ptr(), frames.total, _ptr(gs), _ptr(k), _ptr(s),
+                                          _ptr(zi), _ptr(ge), _ptr(gk), _ptr(gzi), chunk, flags, _ptr(ws),
+                                          ws.numel(), _stream(dev))
+    return ge, gk, gzi

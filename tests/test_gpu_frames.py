@@ -188,3 +188,43 @@ def test_generated_degenerate_shapes():
     assert torch.equal(s, e)
     with pytest.raises(_lib.LPError):
         _lib.lp_tv_forward_frames(2, T, 6, 0, k.data_ptr(), e.data_ptr(), None, s.data_ptr(), None, 0, None, 0, None)
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_frames_varlen_backward_matches_oracle(reuse):
+    """Varlen adjoint with generated coefficients: ge, gzi and dL/dk per
+    signal against the oracle; the padded slot's extra frame gets no
+    gradient beyond what the oracle gives the signal's own frames."""
+    M, hop, chunk = 22, 120, 96
+    lengths = [5000, 17, 1, 2400, 999, 240, 0, 3601]
+    rng = np.random.default_rng(41)
+    pk = ops.Packed(lengths, DEV)
+    pf = ops.PackedFrames(pk, hop)
+    ks = [inputs.reflection_frames(rng, 1, O.n_frames(n, hop), M, 0.95, 0.9)[0].astype(np.float32) for n in lengths]
+    es = [rng.standard_normal(n).astype(np.float32) for n in lengths]
+    gss = [rng.standard_normal(n).astype(np.float32) for n in lengths]
+    zis = (0.1 * rng.standard_normal((len(lengths), M))).astype(np.float32)
+    k = pf.pack([_t(x) for x in ks])
+    e, gs = pk.pack([_t(x) for x in es]), pk.pack([_t(x) for x in gss])
+    zi = _t(zis)
+    nb = _lib.lp_tv_workspace_bytes_frames_varlen(pk.n, pk.total, M, pf.total, chunk)
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=DEV)
+    s = ops.lp_tv_forward_frames_varlen(pk, pf, k, e, zi, chunk=chunk, ws=ws)
+    ge, gk, gzi = ops.lp_tv_backward_frames_varlen(pk, pf, gs, k, s, zi, chunk=chunk, ws=ws, reuse_forward=reuse)
+    torch.cuda.synchronize()
+    assert _lib.lp_tv_device_status() == 0
+    ge_u, s_u = pk.unpack(ge), pk.unpack(s)
+    for b, n in enumerate(lengths):
+        fb, cnt = pf.starts[b], ops.n_frames(n, hop)
+        gkb = gk[fb:fb + cnt].cpu().numpy()
+        if n == 0:
+            assert np.all(gkb == 0) and np.all(gzi[b].cpu().numpy() == 0)
+            continue
+        a = O.coeffs(ks[b], n, hop)
+        rs, rge, rga, rgzi = O.forward_backward(a[None], es[b][None], gss[b][None], zis[b][None])
+        rgk = O.coeffs_adjoint(ks[b], rga[0], hop)
+        _close("s", s_u[b].cpu().numpy()[None], rs)
+        _close("ge", ge_u[b].cpu().numpy()[None], rge)
+        _close("gk", gkb[None], rgk[None])
+        d = np.abs(gzi[b].cpu().numpy() - rgzi[0]).max() / np.abs(rge).max()
+        assert d <= TOL_F32
