@@ -573,8 +573,9 @@ def run_ours(args):
     if world == 1 and serve_s > 0:
         serving = serving_run(serve_s, rate=args.serve_rate)
         sf = serving_run(min(serve_s, 5.0), rate=args.serve_rate, frames=True)
-        serving["frames_server"] = {k: sf[k] for k in ("workload", "h2d_bytes_per_sample", "latency_ms",
-                                                       "Msamples/s", "capacity", "measured_s")}
+        serving["frames_server"] = {k: sf[k] for k in ("workload", "h2d_bytes_per_sample_synthesis", "latency_ms",
+                                                       "latency_ms_adaptation", "Msamples/s", "capacity",
+                                                       "measured_s")}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -744,7 +745,7 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
 
     dev = torch.device("cuda", torch.cuda.current_device())
     M, hop = SERVE_M, inputs.HOP
-    adapt_frac = 0.0 if frames else SERVE_ADAPT
+    adapt_frac = SERVE_ADAPT
     rng = np.random.default_rng(seed)
     # request payloads: windows of one long synthetic signal (pinned host)
     if frames:
@@ -752,7 +753,7 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
         k_pool = torch.from_numpy(inputs.reflection_frames(rng, 1, nf, M, 0.95, 0.9)[0].astype(np.float32))
         a_pool = k_pool.pin_memory()
         e_pool = torch.from_numpy(rng.standard_normal(SERVE_POOL_ROWS).astype(np.float32)).pin_memory()
-        gs_pool = None
+        gs_pool = torch.from_numpy(rng.standard_normal(SERVE_POOL_ROWS).astype(np.float32)).pin_memory()
     else:
         sig = inputs.signals_torch([SERVE_POOL_ROWS], M, seed=seed, gen="stable", device=dev)[0]
         a_pool, e_pool, gs_pool = (x.cpu().pin_memory() for x in sig)
@@ -770,10 +771,20 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
             return a_pool[o // hop:o // hop + (-(-T // hop) + 1)]
         return a_pool[o:o + T]
 
-    # page-locked output slots, reused once their request has completed
+    # page-locked output slots, reused once their request has completed; the
+    # coefficient gradient is dL/da per sample, or on a frames server dL/dk
+    # per frame
+    cg_max = SERVE_MAX // hop + 2 if frames else SERVE_MAX
+
+    def cg_rows(T):
+        return -(-T // hop) + 1 if frames else T
+
+    def new_a_slot():
+        return (torch.empty(SERVE_MAX, pin_memory=True), torch.empty(SERVE_MAX, pin_memory=True),
+                torch.empty((cg_max, M), pin_memory=True))
+
     free_s = [torch.empty(SERVE_MAX, pin_memory=True) for _ in range(64)]
-    free_a = [(torch.empty(SERVE_MAX, pin_memory=True), torch.empty(SERVE_MAX, pin_memory=True),
-               torch.empty((SERVE_MAX, M), pin_memory=True)) for _ in range(12)]
+    free_a = [new_a_slot() for _ in range(12)]
 
     srv = serve.Server(M, chunk=chunk, hbm_budget=SERVE_BUDGET, hop=hop if frames else 0)
     recs = []
@@ -789,10 +800,8 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
 
     def submit(T, o, adapt, t_arr, measured):
         if adapt:
-            slot = free_a.pop() if free_a else (torch.empty(SERVE_MAX, pin_memory=True),
-                                                torch.empty(SERVE_MAX, pin_memory=True),
-                                                torch.empty((SERVE_MAX, M), pin_memory=True))
-            out = (slot[0][:T], slot[1][:T], slot[2][:T])
+            slot = free_a.pop() if free_a else new_a_slot()
+            out = (slot[0][:T], slot[1][:T], slot[2][:cg_rows(T)])
             srv.submit(coef(o, T), e_pool[o:o + T], gs_pool[o:o + T], arrival_ns=t_arr, out=out,
                        tag=(measured, slot))
         else:
@@ -837,7 +846,7 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
     outs = []
     for T, o, adapt in burst_reqs:
         outs.append((torch.empty(T, pin_memory=True), torch.empty(T, pin_memory=True),
-                     torch.empty((T, M), pin_memory=True)) if adapt else torch.empty(T, pin_memory=True))
+                     torch.empty((cg_rows(T), M), pin_memory=True)) if adapt else torch.empty(T, pin_memory=True))
     tb0 = serve.now_ns()
     for (T, o, adapt), out in zip(burst_reqs, outs):
         if adapt:
@@ -861,7 +870,7 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
                      f"{SERVE_BUDGET >> 30} GiB HBM budget, stable reflection generator, pinned host buffers"
                      + (f"; requests carry reflection coefficients per {hop}-sample frame, a(t) generated in the "
                         "kernels" if frames else "; requests carry a(t)")),
-        "h2d_bytes_per_sample": round((4 * M / hop if frames else 4 * M) + 4, 3),
+        "h2d_bytes_per_sample_synthesis": round((4 * M / hop if frames else 4 * M) + 4, 3),
         "measured_s": seconds, "warmup_s": warmup_s, "requests": len(recs),
         "latency_ms": {"p50": _pct(lat_ms, 50), "p90": _pct(lat_ms, 90), "p99": _pct(lat_ms, 99),
                        "p99.9": _pct(lat_ms, 99.9), "max": max(lat_ms) if lat_ms else None,

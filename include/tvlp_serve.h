@@ -78,13 +78,14 @@ typedef struct lp_serve_config {
     int64_t max_iter_rows; /* packed rows per iteration, both calls           */
     int max_inflight;      /* iterations in flight, 1..16                     */
     uint64_t hbm_budget;   /* device bytes the server may hold                */
-    int hop;               /* 0: requests carry a [T][M].  > 0: synthesis
-                              requests carry reflection coefficients per frame
+    int hop;               /* 0: requests carry a [T][M].  > 0: requests
+                              carry reflection coefficients per frame
                               k [ceil(T/hop)+1][M] (as in
-                              lp_tv_forward_frames_f32) in place of a, and the
-                              kernels generate a(t); block_rows is rounded up
-                              to a multiple of hop; adaptation requests are
-                              rejected (LP_EUNSUPPORTED)                       */
+                              lp_tv_forward_frames_f32) in place of a, the
+                              kernels generate a(t), and an adaptation request
+                              receives dL/dk [ceil(T/hop)+1][M] in place of
+                              ga; block_rows is rounded up to a multiple of
+                              hop                                              */
 } lp_serve_config;
 
 typedef struct lp_serve_stats {
@@ -122,9 +123,8 @@ int lp_serve_destroy(void *server);
 /* Queue one request (never blocks on the GPU).  kind LP_SERVE_SYNTH needs
  * a, e, s (gs, ge, ga ignored); LP_SERVE_ADAPT needs all six.  T >= 0.
  * arrival_ns <= 0 stamps the arrival now.  With hop > 0, `a` points to the
- * request's frames.  Returns LP_EINVAL for a bad argument, LP_ETOOBIG for
- * a request no iteration can hold, LP_EUNSUPPORTED for an adaptation
- * request on a frames server. */
+ * request's frames and `ga` receives dL/dk per frame.  Returns LP_EINVAL
+ * for a bad argument, LP_ETOOBIG for a request no iteration can hold. */
 int lp_serve_submit(void *server, int64_t id, int kind, int64_t T,
                     const float *a, const float *e, const float *gs,
                     float *s, float *ge, float *ga, int64_t arrival_ns);

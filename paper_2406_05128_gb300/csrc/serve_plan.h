@@ -74,12 +74,15 @@ inline uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 struct Layout {
     uint64_t a_f = 0, e_f = 0, s_f = 0;
     uint64_t a_a = 0, e_a = 0, gs_a = 0, s_a = 0, ge_a = 0, ga_a = 0;
-    uint64_t tab = 0, off_f = 0, off_a = 0, foff = 0, cont = 0, tab_bytes = 0;
+    uint64_t tab = 0, off_f = 0, off_a = 0, foff = 0, foff_a = 0, cont = 0, tab_bytes = 0;
     uint64_t bytes = 0;
 };
 
-// frames_f < 0: streamed coefficient rows; >= 0: that many frame rows
-inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont, int64_t frames_f = -1) {
+// frames_f < 0: streamed coefficient rows; >= 0: frames mode, with frames_f
+// frame rows in the synthesis call and frames_a in the adaptation call (whose
+// a and ga regions then hold frames: k in, dL/dk out)
+inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont, int64_t frames_f = -1,
+                     int64_t frames_a = 0) {
     Layout L;
     uint64_t p = 0;
     auto take = [&p](uint64_t nbytes) {
@@ -93,19 +96,21 @@ inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, in
         L.e_f = take(rf * 4);
         L.s_f = take(rf * 4);
     }
+    const uint64_t rk = frames_f < 0 ? ra : (uint64_t)frames_a;  // coefficient rows of the adaptation call
     if (n_a > 0) {
-        L.a_a = take(ra * m * 4);
+        L.a_a = take(rk * m * 4);
         L.e_a = take(ra * 4);
         L.gs_a = take(ra * 4);
         L.s_a = take(ra * 4);
         L.ge_a = take(ra * 4);
-        L.ga_a = take(ra * m * 4);
+        L.ga_a = take(rk * m * 4);
     }
     L.tab = p;
     L.off_f = p;
     L.off_a = L.off_f + (uint64_t)(n_f + 1) * 8;
     L.foff = L.off_a + (uint64_t)(n_a + 1) * 8;
-    L.cont = L.foff + (frames_f < 0 ? 0 : (uint64_t)n_f * 8);
+    L.foff_a = L.foff + (frames_f < 0 ? 0 : (uint64_t)n_f * 8);
+    L.cont = L.foff_a + (frames_f < 0 ? 0 : (uint64_t)n_a * 8);
     L.tab_bytes = L.cont + (uint64_t)n_cont * 4 - L.tab;
     p = align256(L.cont + (uint64_t)n_cont * 4);
     L.bytes = p;
@@ -118,7 +123,7 @@ inline Layout layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, in
 inline uint64_t max_region_bytes(const PlanConfig &c) {
     const Layout a = layout(c.M, c.max_iter_rows, 0, c.max_iter_rows, c.max_signals, 0);
     const Layout f = layout(c.M, c.max_iter_rows, c.max_signals, 0, 0, c.max_signals);
-    return std::max(a.bytes, f.bytes) + 2 * align256((uint64_t)(3 * c.max_signals + 2) * 8 + c.max_signals * 4);
+    return std::max(a.bytes, f.bytes) + 2 * align256((uint64_t)(4 * c.max_signals + 2) * 8 + c.max_signals * 4);
 }
 
 // FIFO ring of regions: allocated in iteration order, freed oldest first.
@@ -186,6 +191,7 @@ struct IterPlan {
     int n_carried = 0;         // fwd[0 .. n_carried) start from a carried state
     int64_t rows_f = 0, rows_a = 0;
     int64_t frames_f = 0;  // frames mode: frame rows of the synthesis call
+    int64_t frames_a = 0;  // frames mode: frame rows of the adaptation call
     Layout lay;
     uint64_t offset = 0;  // region offset in the ring
 };
@@ -207,7 +213,6 @@ class Planner {
     // Whether a request could ever be planned (alone, in an empty ring).
     bool admissible(int kind, int64_t T) const {
         if (T < 0) return false;
-        if (cfg_.hop > 0 && kind == ADAPT) return false;  // frames mode serves synthesis only
         const int64_t r = padded(first_rows(kind, T));
         if (r > cfg_.max_iter_rows) return false;
         const Layout L = kind == ADAPT ? layout(cfg_.M, 0, 0, r, 1, 0) : layout(cfg_.M, r, 1, 0, 0, 1);
@@ -248,15 +253,15 @@ class Planner {
         }
         P.n_carried = (int)P.fwd.size();
         uint64_t off = 0;
-        auto lay_of = [&](int64_t rf, int nf, int64_t ra, int na, int nc, int64_t ff) {
-            return layout(cfg_.M, rf, nf, ra, na, nc, frames ? ff : -1);
+        auto lay_of = [&](int64_t rf, int nf, int64_t ra, int na, int nc, int64_t ff, int64_t fa) {
+            return layout(cfg_.M, rf, nf, ra, na, nc, frames ? ff : -1, fa);
         };
-        auto fits = [&](int64_t rf, int nf, int64_t ra, int na, int nc, int64_t ff) {
+        auto fits = [&](int64_t rf, int nf, int64_t ra, int na, int nc, int64_t ff, int64_t fa) {
             if (rf + ra > cfg_.max_iter_rows) return false;
             if (nf > cfg_.max_signals || na > cfg_.max_signals) return false;
-            return ring_.where(lay_of(rf, nf, ra, na, nc, ff).bytes, &off);
+            return ring_.where(lay_of(rf, nf, ra, na, nc, ff, fa).bytes, &off);
         };
-        if (!P.fwd.empty() && !fits(P.rows_f, (int)P.fwd.size(), 0, 0, n_cont_next, P.frames_f)) {
+        if (!P.fwd.empty() && !fits(P.rows_f, (int)P.fwd.size(), 0, 0, n_cont_next, P.frames_f, 0)) {
             P = IterPlan();
             return false;
         }
@@ -266,16 +271,20 @@ class Planner {
             Block b = block_of(r);
             const int64_t pr = padded(b.rows);
             if (r->kind == ADAPT) {
+                const int64_t fa = P.frames_a + nfr(b.rows);
                 if (!fits(P.rows_f, (int)P.fwd.size(), P.rows_a + pr, (int)P.adapt.size() + 1, n_cont_next,
-                          P.frames_f))
+                          P.frames_f, fa))
                     break;
                 b.pos = P.rows_a;
+                b.fpos = P.frames_a;
                 P.rows_a += pr;
+                P.frames_a = fa;
                 P.adapt.push_back(b);
             } else {
                 const int nc = n_cont_next + (b.last ? 0 : 1);
                 const int64_t ff = P.frames_f + nfr(b.rows);
-                if (!fits(P.rows_f + pr, (int)P.fwd.size() + 1, P.rows_a, (int)P.adapt.size(), nc, ff)) break;
+                if (!fits(P.rows_f + pr, (int)P.fwd.size() + 1, P.rows_a, (int)P.adapt.size(), nc, ff, P.frames_a))
+                    break;
                 b.pos = P.rows_f;
                 b.fpos = P.frames_f;
                 P.rows_f += pr;
@@ -287,7 +296,8 @@ class Planner {
         if (P.fwd.empty() && P.adapt.empty()) return false;
         // the last successful fits() sized exactly this layout, so the
         // allocation succeeds
-        P.lay = lay_of(P.rows_f, (int)P.fwd.size(), P.rows_a, (int)P.adapt.size(), n_cont_next, P.frames_f);
+        P.lay = lay_of(P.rows_f, (int)P.fwd.size(), P.rows_a, (int)P.adapt.size(), n_cont_next, P.frames_f,
+                       P.frames_a);
         if (!ring_.alloc(P.lay.bytes, &P.offset)) {
             P = IterPlan();
             return false;

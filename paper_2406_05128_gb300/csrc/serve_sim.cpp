@@ -113,9 +113,9 @@ int lp_plan_simulate(int M, int64_t block_rows, int max_signals, int64_t max_ite
 // streamed rows): 15 uint64 offsets
 //   a_f e_f s_f a_a e_a gs_a s_a ge_a ga_a tab off_f off_a cont tab_bytes bytes
 int lp_plan_layout(int M, int64_t rows_f, int n_f, int64_t rows_a, int n_a, int n_cont, int64_t frames_f,
-                   uint64_t *out) {
+                   int64_t frames_a, uint64_t *out) {
     if (out == nullptr) return -1;
-    const Layout L = layout(M, rows_f, n_f, rows_a, n_a, n_cont, frames_f);
+    const Layout L = layout(M, rows_f, n_f, rows_a, n_a, n_cont, frames_f, frames_a);
     const uint64_t v[15] = {L.a_f, L.e_f, L.s_f, L.a_a, L.e_a, L.gs_a, L.s_a, L.ge_a, L.ga_a,
                             L.tab, L.off_f, L.off_a, L.cont, L.tab_bytes, L.bytes};
     for (int k = 0; k < 15; ++k) out[k] = v[k];

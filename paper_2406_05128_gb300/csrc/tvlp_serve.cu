@@ -148,7 +148,26 @@ int issue(Server &S, Iter &it) {
     if (hop > 0) {
         int64_t *foff = reinterpret_cast<int64_t *>(tab + (L.foff - L.tab));
         for (int k = 0; k < nf; ++k) foff[k] = P.fwd[k].fpos;
+        int64_t *foff_a = reinterpret_cast<int64_t *>(tab + (L.foff_a - L.tab));
+        for (int k = 0; k < na; ++k) foff_a[k] = P.adapt[k].fpos;
     }
+    // a block's frames: it starts on a frame anchor (block_rows is a multiple
+    // of hop), and a padded block may need one frame more than the request
+    // has, which repeats the request's last frame
+    auto put_frames = [&](uint64_t dst, const Block &b, const Rec *r) {
+        if (b.rows <= 0) return true;
+        const int64_t f0 = b.row0 / hop, need = frames_of(padded(b.rows), hop);
+        const int64_t have = frames_of(r->req.T, hop) - f0;
+        const int64_t n = need < have ? need : have;
+        char *d = base + dst + (size_t)b.fpos * rowb;
+        if (cudaMemcpyAsync(d, r->a + f0 * M, (size_t)n * rowb, cudaMemcpyHostToDevice, S.s_in) != cudaSuccess)
+            return false;
+        for (int64_t x = n; x < need; ++x)
+            if (cudaMemcpyAsync(d + (size_t)x * rowb, r->a + (f0 + have - 1) * M, rowb, cudaMemcpyHostToDevice,
+                                S.s_in) != cudaSuccess)
+                return false;
+        return true;
+    };
     SV_CUDA(cudaMemcpyAsync(base + L.tab, tab, L.tab_bytes, cudaMemcpyHostToDevice, S.s_in));
 
     auto put = [&](uint64_t dst, int64_t pos, const float *src, int64_t rows, size_t bytes_per_row, bool pad) {
@@ -164,23 +183,8 @@ int issue(Server &S, Iter &it) {
     for (const Block &b : P.fwd) {
         const Rec *r = static_cast<const Rec *>(b.req->user);
         if (hop > 0) {
-            // the block's frames: it starts on a frame anchor (block_rows is
-            // a multiple of hop), and a padded last block may need one frame
-            // more than the request has, which repeats its last frame
-            if (b.rows > 0) {
-                const int64_t f0 = b.row0 / hop, need = frames_of(padded(b.rows), hop);
-                const int64_t have = frames_of(r->req.T, hop) - f0;
-                const int64_t n = need < have ? need : have;
-                char *d = base + L.a_f + (size_t)b.fpos * rowb;
-                if (cudaMemcpyAsync(d, r->a + f0 * M, (size_t)n * rowb, cudaMemcpyHostToDevice, S.s_in) !=
-                    cudaSuccess)
-                    return fail(S, LP_ECUDA);
-                for (int64_t x = n; x < need; ++x)
-                    if (cudaMemcpyAsync(d + (size_t)x * rowb, r->a + (f0 + have - 1) * M, rowb,
-                                        cudaMemcpyHostToDevice, S.s_in) != cudaSuccess)
-                        return fail(S, LP_ECUDA);
-            }
-            if (!put(L.e_f, b.pos, r->e + b.row0, b.rows, sizeof(float), true)) return fail(S, LP_ECUDA);
+            if (!put_frames(L.a_f, b, r) || !put(L.e_f, b.pos, r->e + b.row0, b.rows, sizeof(float), true))
+                return fail(S, LP_ECUDA);
             continue;
         }
         if (!put(L.a_f, b.pos, r->a + b.row0 * M, b.rows, rowb, true) ||
@@ -189,7 +193,8 @@ int issue(Server &S, Iter &it) {
     }
     for (const Block &b : P.adapt) {
         const Rec *r = static_cast<const Rec *>(b.req->user);
-        if (!put(L.a_a, b.pos, r->a, b.rows, rowb, true) || !put(L.e_a, b.pos, r->e, b.rows, sizeof(float), true) ||
+        const bool coef = hop > 0 ? put_frames(L.a_a, b, r) : put(L.a_a, b.pos, r->a, b.rows, rowb, true);
+        if (!coef || !put(L.e_a, b.pos, r->e, b.rows, sizeof(float), true) ||
             !put(L.gs_a, b.pos, r->gs, b.rows, sizeof(float), true))
             return fail(S, LP_ECUDA);
     }
@@ -201,13 +206,26 @@ int issue(Server &S, Iter &it) {
         auto *oa = reinterpret_cast<const int64_t *>(base + L.off_a);
         auto *a = reinterpret_cast<const float *>(base + L.a_a);
         auto *s = reinterpret_cast<float *>(base + L.s_a);
-        SV_LP(lp_tv_forward_varlen_f32(na, oa, P.rows_a, M, a, reinterpret_cast<const float *>(base + L.e_a), nullptr,
-                                       s, nullptr, S.chunk, S.ws, S.ws_bytes, S.s_comp));
-        SV_LP(lp_tv_backward_varlen_f32(na, oa, P.rows_a, M, reinterpret_cast<const float *>(base + L.gs_a), a, s,
-                                        nullptr, reinterpret_cast<float *>(base + L.ge_a),
-                                        reinterpret_cast<float *>(base + L.ga_a), nullptr, S.chunk,
-                                        LP_BWD_REUSE_FORWARD, S.ws, S.ws_bytes, S.s_comp));
-        launches += kFwdKernels + kBwdKernels;
+        auto *e = reinterpret_cast<const float *>(base + L.e_a);
+        auto *gs = reinterpret_cast<const float *>(base + L.gs_a);
+        auto *ge = reinterpret_cast<float *>(base + L.ge_a);
+        auto *ga = reinterpret_cast<float *>(base + L.ga_a);
+        if (hop > 0) {
+            // frames: a_a holds k, ga_a receives dL/dk
+            auto *fa = reinterpret_cast<const int64_t *>(base + L.foff_a);
+            SV_LP(lp_tv_forward_frames_varlen_f32(na, oa, P.rows_a, M, hop, fa, a, e, nullptr, s, nullptr, S.chunk, S.ws,
+                                                  S.ws_bytes, S.s_comp));
+            SV_LP(lp_tv_backward_frames_varlen_f32(na, oa, P.rows_a, M, hop, fa, P.frames_a, gs, a, s, nullptr, ge, ga,
+                                                   nullptr, S.chunk, LP_BWD_REUSE_FORWARD, S.ws, S.ws_bytes,
+                                                   S.s_comp));
+            launches += kFwdKernels + kBwdKernels + 1;
+        } else {
+            SV_LP(lp_tv_forward_varlen_f32(na, oa, P.rows_a, M, a, e, nullptr, s, nullptr, S.chunk, S.ws, S.ws_bytes,
+                                           S.s_comp));
+            SV_LP(lp_tv_backward_varlen_f32(na, oa, P.rows_a, M, gs, a, s, nullptr, ge, ga, nullptr, S.chunk,
+                                            LP_BWD_REUSE_FORWARD, S.ws, S.ws_bytes, S.s_comp));
+            launches += kFwdKernels + kBwdKernels;
+        }
     }
     const uint64_t it_no = S.iter_count;
     float *zi_cur = S.zi[it_no & 1], *zi_next = S.zi[(it_no + 1) & 1];
@@ -253,8 +271,11 @@ int issue(Server &S, Iter &it) {
     }
     for (const Block &b : P.adapt) {
         const Rec *r = static_cast<const Rec *>(b.req->user);
+        // dL/da rows, or in frames mode dL/dk for the request's own frames
+        const bool coef = hop > 0 ? (r->ga == nullptr || get(r->ga, L.ga_a, b.fpos, frames_of(r->req.T, hop), rowb))
+                                  : get(r->ga, L.ga_a, b.pos, b.rows, rowb);
         if (!get(r->s, L.s_a, b.pos, b.rows, sizeof(float)) || !get(r->ge, L.ge_a, b.pos, b.rows, sizeof(float)) ||
-            !get(r->ga, L.ga_a, b.pos, b.rows, rowb))
+            !coef)
             return fail(S, LP_ECUDA);
     }
     SV_CUDA(cudaEventRecord(S.ev_out[slot], S.s_out));
@@ -418,7 +439,12 @@ int lp_serve_create(const lp_serve_config *cfg, void **server) {
     }
     chunk = (chunk + 15) / 16 * 16;
 
-    const size_t ws = lp_tv_workspace_bytes_varlen(c.max_signals, c.max_iter_rows, c.M, chunk, LP_DTYPE_F32);
+    // frames mode: the adaptation call's dL/dk scratch too; a call's frame
+    // rows are at most rows/hop plus two per signal
+    const int64_t max_frames = c.hop > 0 ? c.max_iter_rows / c.hop + 2 * (int64_t)c.max_signals + 2 : 0;
+    const size_t ws = c.hop > 0 ? lp_tv_workspace_bytes_frames_varlen(c.max_signals, c.max_iter_rows, c.M, max_frames,
+                                                                      chunk)
+                                : lp_tv_workspace_bytes_varlen(c.max_signals, c.max_iter_rows, c.M, chunk, LP_DTYPE_F32);
     if (ws == 0) return LP_EUNSUPPORTED;
     const uint64_t ws_b = align256(ws), zi_b = align256((uint64_t)c.max_signals * c.M * sizeof(float));
     PlanConfig pc;
@@ -442,7 +468,7 @@ int lp_serve_create(const lp_serve_config *cfg, void **server) {
         return LP_ECUDA;
     }
     S->dev_bytes = fixed + pc.ring_bytes;
-    S->tab_slot_bytes = align256((uint64_t)(3 * c.max_signals + 2) * 8 + (uint64_t)c.max_signals * 4);
+    S->tab_slot_bytes = align256((uint64_t)(4 * c.max_signals + 2) * 8 + (uint64_t)c.max_signals * 4);
     bool ok = cudaMalloc(&S->dev, S->dev_bytes) == cudaSuccess;
     ok = ok && cudaHostAlloc(&S->tab_host, S->tab_slot_bytes * c.max_inflight, cudaHostAllocDefault) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&S->s_in, cudaStreamNonBlocking) == cudaSuccess;
@@ -480,7 +506,6 @@ int lp_serve_submit(void *server, int64_t id, int kind, int64_t T, const float *
     if (S == nullptr || T < 0 || (kind != LP_SERVE_SYNTH && kind != LP_SERVE_ADAPT)) return LP_EINVAL;
     if (T > 0 && (a == nullptr || e == nullptr || s == nullptr)) return LP_EINVAL;
     if (T > 0 && kind == LP_SERVE_ADAPT && (gs == nullptr || ge == nullptr || ga == nullptr)) return LP_EINVAL;
-    if (S->cfg.hop > 0 && kind == LP_SERVE_ADAPT) return LP_EUNSUPPORTED;
     if (!S->planner->admissible(kind, T)) return LP_ETOOBIG;
     Rec *r = new (std::nothrow) Rec();
     if (r == nullptr) return LP_ECUDA;

@@ -93,8 +93,9 @@ class Server:
         """Queue one request.  a [T, M] (a server with hop > 0: reflection
         coefficients per frame, [ceil(T/hop)+1, M]), e [T] (and gs [T] for
         adaptation) are CPU float32 tensors; out optionally gives the output
-        tensors (s, or (s, ge, ga)).  Returns the Request, whose outputs are
-        valid once poll() has returned it."""
+        tensors (s, or (s, ge, ga); on a frames server ga is dL/dk per
+        frame).  Returns the Request, whose outputs are valid once poll() has
+        returned it."""
         if self._h is None:
             raise RuntimeError("server is closed")
         T = e.shape[0] if isinstance(e, torch.Tensor) else -1
@@ -105,14 +106,16 @@ class Server:
             _host(gs, "gs", (T,))
         if self.require_pinned and T > 0 and not all(x.is_pinned() for x in (a, e) + ((gs,) if gs is not None else ())):
             raise ValueError("inputs must be page-locked (tensor.pin_memory()) so the copies overlap with compute")
+        # coefficient gradient rows: dL/da per sample, or dL/dk per frame
+        cg_rows = (-(-T // self.hop) + 1) if self.hop > 0 else T
         if out is None:
             s = torch.empty((T,), dtype=torch.float32, pin_memory=True)
             ge = torch.empty((T,), dtype=torch.float32, pin_memory=True) if kind == ADAPT else None
-            ga = torch.empty((T, self.M), dtype=torch.float32, pin_memory=True) if kind == ADAPT else None
+            ga = torch.empty((cg_rows, self.M), dtype=torch.float32, pin_memory=True) if kind == ADAPT else None
         elif kind == ADAPT:
             s, ge, ga = out
             _host(ge, "ge", (T,))
-            _host(ga, "ga", (T, self.M))
+            _host(ga, "ga", (cg_rows, self.M))
         else:
             s, ge, ga = (out[0] if isinstance(out, (tuple, list)) else out), None, None
         _host(s, "s", (T,))

@@ -173,39 +173,49 @@ def test_rejects_what_no_iteration_holds():
 
 
 def test_frames_server_alone_equals_mix_and_oracle():
-    """hop > 0: synthesis requests carry reflection coefficients per frame;
-    the kernels generate a(t).  Blocks of 4800 samples (40 frames) carry the
-    state; results are bit for bit the same alone and in the mix, and match
-    the oracle's Eq. 5 on the oracle's own interpolation and step-up."""
+    """hop > 0: requests carry reflection coefficients per frame and the
+    kernels generate a(t); adaptation requests get dL/dk per frame.  Blocks
+    of 4800 samples (40 frames) carry the state; results are bit for bit the
+    same alone and in the mix, and match the oracle's Eq. 5 / Eqs. 11-12 on
+    its own interpolation and step-up, with dL/dk by its chain rule."""
     hop = 120
-    lengths = [4800, 0, 1, 17, 12000, 30001, 9600, 999, 20000, 121, 7000, 4799]
+    lengths = [4800, 0, 1, 17, 12000, 30001, 9600, 999, 20000, 121, 7000, 4799, 2400, 5001]
+    kinds = [0, 0, 0, 1, 0, 1, 0, 1, 0, 0, 1, 0, 1, 0]
     rng = np.random.default_rng(8)
     reqs = []
-    for T in lengths:
+    for T, kind in zip(lengths, kinds):
         k = inputs.reflection_frames(rng, 1, O.n_frames(T, hop), M, 0.95, 0.9)[0].astype(np.float32)
         e = rng.standard_normal(T).astype(np.float32)
-        reqs.append((torch.from_numpy(k).pin_memory(), torch.from_numpy(e).pin_memory()))
+        gs = rng.standard_normal(T).astype(np.float32) if kind else None
+        reqs.append((torch.from_numpy(k).pin_memory(), torch.from_numpy(e).pin_memory(),
+                     None if gs is None else torch.from_numpy(gs).pin_memory()))
     cfg = dict(CFG, block_rows=4800, hop=hop)
     with serve.Server(M, **cfg) as srv:
         mix = []
-        for k, e in reqs:
-            mix.append(srv.submit(k, e))
+        for k, e, gs in reqs:
+            mix.append(srv.submit(k, e, gs))
             time.sleep(float(rng.uniform(0, 3e-4)))
         srv.drain(timeout_s=60)
         st = srv.stats()
         alone = []
-        for k, e in reqs:
-            alone.append(srv.submit(k, e))
+        for k, e, gs in reqs:
+            alone.append(srv.submit(k, e, gs))
             srv.drain(timeout_s=60)
-        with pytest.raises(_lib.LPError) as ei:
-            srv.submit(reqs[0][0], reqs[0][1], reqs[0][1])
-        assert ei.value.code == _lib.LP_EUNSUPPORTED
         assert _lib.lp_tv_device_status() == 0
-    assert st["carried_blocks"] > 0 and st["max_signals_iter"] > 1 and st["error"] == 0
-    for x, y, (k, e), T in zip(mix, alone, reqs, lengths):
-        assert x.status == 0 and np.array_equal(x.s.numpy(), y.s.numpy()), T
+    assert st["carried_blocks"] > 0 and st["max_signals_iter"] > 1 and st["adapt_calls"] > 0 and st["error"] == 0
+    for x, y, (k, e, gs), T in zip(mix, alone, reqs, lengths):
+        assert x.status == 0
+        for u, v in zip(_outputs(x), _outputs(y)):
+            assert np.array_equal(u, v), T
         if T == 0:
             continue
-        rs = O.forward(O.coeffs(k.numpy(), T, hop), e.numpy())
-        err = norm_err(x.s.numpy()[None], rs[None])
-        assert err.max() <= TOL_F32, (T, err)
+        a = O.coeffs(k.numpy(), T, hop)
+        if gs is None:
+            rs = O.forward(a, e.numpy())
+            assert norm_err(x.s.numpy()[None], rs[None]).max() <= TOL_F32, T
+        else:
+            rs, rge, rga, _ = O.forward_backward(a[None], e.numpy()[None], gs.numpy()[None])
+            rgk = O.coeffs_adjoint(k.numpy(), rga[0], hop)
+            for name, got, ref in (("s", x.s, rs), ("ge", x.ge, rge), ("gk", x.ga, rgk[None])):
+                err = norm_err(got.numpy().reshape(1, -1), ref.reshape(1, -1))
+                assert err.max() <= TOL_F32, (name, T, err)
