@@ -83,6 +83,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(total_ms, world, device):
+    """The slowest rank's timed total (all ranks call it together)."""
+    if world <= 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(samples_per_rank_step, world, steps, total_ms):
+    """Whole-job Msamples/s of independent replicas: every rank's samples
+    over the slowest rank's time."""
+    return samples_per_rank_step * world * steps / (total_ms * 1e-3) / 1e6
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -373,13 +390,9 @@ def run_ours(args):
             stream.synchronize()
             prof_step_ms.append(evp0.elapsed_time(evp1))
             record_kernels()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     ms_per_step = total_ms / args.steps
-    value = B * T * world * args.steps / (total_ms * 1e-3) / 1e6
+    value = replica_value(B * T, world, args.steps, total_ms)
 
     # plain one-thread-per-signal comparator on the same GPU (context)
     plain = None
