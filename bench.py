@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
+    ap.add_argument("--l2-set-aside-mb", type=int, default=0,
+                    help="persisting L2 for the passes' evict-last stages (this process's context; 0: none)")
     ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train"), default="headline",
                     help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders; "
                          "serving: the request loop under Poisson arrivals; frames: the headline step with the "
@@ -271,6 +273,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2406_05128_gb300 import _lib
 
+    l2_aside = _lib.lp_tv_l2_set_aside(args.l2_set_aside_mb << 20) if args.l2_set_aside_mb > 0 else 0
     w = workload(args, rank)
     B, T, M = w.a.shape
     a = torch.from_numpy(w.a).to(dev)
@@ -594,7 +597,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config(args, "flushed between timed steps (256 MiB write)") | {
-            "chunk": chunk, "launch": "host launches" if args.no_graph else "CUDA graph replay per step"},
+            "chunk": chunk, "launch": "host launches" if args.no_graph else "CUDA graph replay per step",
+            "l2_persisting_bytes": l2_aside},
         "roofline": roof, "step_roofline": step_roof, "kernels": kern_detail,
         "kernels_from": ("replays of the step graph with an event around each kernel, outside the timed region "
                          f"(mean step there {statistics.mean(prof_step_ms):.4f} ms)") if prof_step_ms

@@ -321,6 +321,19 @@ int lp_tv_backward_ti_f32(int B, int64_t T, int M, const float *gs,
 int lp_tv_device_status(int reset);
 
 /*
+ * L2 set-aside for the passes' evict-last stages (no counterpart in the
+ * paper).  Consecutive passes over `a` mark the stages the next pass reads
+ * first as evict-last (createpolicy L2::evict_last); the hardware keeps such
+ * lines in the persisting part of L2, which is 0 bytes unless the process
+ * sets it aside.  This sets the current context's persisting L2 size
+ * (cudaLimitPersistingL2CacheSize) to `bytes`, clipped to the device's
+ * maximum, and writes the size applied to *applied (may be NULL).  The
+ * limit belongs to this process's context and ends with it.  LP_ECUDA if a
+ * runtime call fails.
+ */
+int lp_tv_l2_set_aside(size_t bytes, size_t *applied);
+
+/*
  * Failure-detection self-test (no counterpart in the paper).  Launches one
  * warp on `stream` that runs one of the kernels' bounded waits on a
  * condition nothing satisfies: which = 1, an mbarrier waiting for bulk-copy

@@ -40,7 +40,7 @@ EXPORTS = (
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
     "lp_tv_workspace_bytes_frames", "lp_tv_forward_frames_f32", "lp_tv_backward_frames_f32",
     "lp_tv_forward_frames_varlen_f32", "lp_tv_selftest_wait", "lp_tv_workspace_bytes_frames_varlen",
-    "lp_tv_backward_frames_varlen_f32", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
+    "lp_tv_backward_frames_varlen_f32", "lp_tv_l2_set_aside", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
     "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
 )
@@ -132,6 +132,8 @@ def _declare(lib):
     lib.lp_tv_backward_frames_varlen_f32.argtypes = [i32, vp, i64, i32, i32, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32,
                                                      i32, vp, sz, vp]
     lib.lp_tv_backward_frames_varlen_f32.restype = i32
+    lib.lp_tv_l2_set_aside.argtypes = [sz, c.POINTER(sz)]
+    lib.lp_tv_l2_set_aside.restype = i32
     lib.lp_tv_selftest_wait.argtypes = [i32, vp]
     lib.lp_tv_selftest_wait.restype = i32
     lib.lp_tv_workspace_bytes_ti.argtypes = [i32, i64, i32, i32]
@@ -313,3 +315,11 @@ def lp_tv_backward_frames_varlen(n, offsets, total, M, hop, frame_offsets, total
     _check(load().lp_tv_backward_frames_varlen_f32(n, offsets, total, M, hop, frame_offsets, total_frames, gs, k, s,
                                                    zi, ge, gk, gzi, chunk, flags, ws, ws_bytes, stream),
            "lp_tv_backward_frames_varlen_f32")
+
+
+def lp_tv_l2_set_aside(nbytes: int) -> int:
+    """Set the current context's persisting L2 size (clipped to the device's
+    maximum); returns the size applied."""
+    got = ctypes.c_size_t()
+    _check(load().lp_tv_l2_set_aside(int(nbytes), ctypes.byref(got)), "lp_tv_l2_set_aside")
+    return got.value

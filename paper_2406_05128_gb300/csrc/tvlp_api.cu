@@ -840,4 +840,17 @@ int lp_tv_backward_frames_varlen_f32(int n, const int64_t *offsets, int64_t tota
                                        gzi, chunk, flags, ws, wsb, stream);
 }
 
+int lp_tv_l2_set_aside(size_t bytes, size_t *applied) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LP_ECUDA;
+    int max_bytes = 0;
+    if (cudaDeviceGetAttribute(&max_bytes, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess) return LP_ECUDA;
+    const size_t want = bytes > (size_t)max_bytes ? (size_t)max_bytes : bytes;
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) return LP_ECUDA;
+    size_t got = 0;
+    if (cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize) != cudaSuccess) return LP_ECUDA;
+    if (applied != nullptr) *applied = got;
+    return LP_OK;
+}
+
 }  // extern "C"
