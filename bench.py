@@ -69,12 +69,14 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
     ap.add_argument("--l2-set-aside-mb", type=int, default=0,
                     help="persisting L2 for the passes' evict-last stages (this process's context; 0: none)")
-    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train"), default="headline",
+    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train", "golf"),
+                    default="headline",
                     help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders; "
                          "serving: the request loop under Poisson arrivals; frames: the headline step with the "
                          "coefficients generated in the kernels from frame-rate reflection coefficients; train: "
                          "the harmonic-plus-noise training step (B=64, T=96000, two M=22 filters, MSS loss, "
-                         "chunk-state checkpointing)")
+                         "chunk-state checkpointing); golf: the source-filter synthesiser of Eq. 4 with "
+                         "synthetic parameters, trained end to end")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="measured seconds of the serving run (default 60 for --workload serving, 15 inside the "
                          "headline line; 0 skips it there)")
@@ -1279,6 +1281,91 @@ def run_train(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Source-filter synthesiser (Eq. 4, S = (G + N C) H) with synthetic
+# parameters: e = g(t) (pulse + noise * c), s = LP_{a(k)}(e) with a(t)
+# generated in the kernels from reflection coefficients per frame; the
+# frame gains, FIR taps and reflection coefficients are trained through the
+# MSS loss
+# ---------------------------------------------------------------------------
+GOLF_B, GOLF_T, GOLF_M, GOLF_K = 64, 48000, 22, 64
+
+
+def frame_interp(x, T, hop):
+    """x [B, F] per frame -> [B, T]: frame f at sample f*hop, linear between."""
+    import torch
+    t = torch.arange(T, device=x.device)
+    f = torch.div(t, hop, rounding_mode="floor")
+    w = ((t - f * hop).to(x.dtype) / hop)[None]
+    return x[:, f] * (1 - w) + x[:, f + 1] * w
+
+
+def run_golf(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_05128_gb300 import inputs, ops
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, T, M, K, hop = GOLF_B, GOLF_T, GOLF_M, GOLF_K, inputs.HOP
+    rng = np.random.default_rng(5)
+    F = ops.n_frames(T, hop)
+    k = torch.tensor(inputs.reflection_frames(rng, B, F, M, 0.95, 0.9).astype(np.float32), device=dev,
+                     requires_grad=True)
+    gain = torch.tensor((0.5 + rng.random((B, F))).astype(np.float32), device=dev, requires_grad=True)
+    c = torch.tensor((0.1 * rng.standard_normal((B, K))).astype(np.float32), device=dev, requires_grad=True)
+    pulse = torch.tensor(inputs.pulse_train(rng, B, T).astype(np.float32), device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    target = torch.tensor(inputs.pulse_train(rng, B, T).astype(np.float32), device=dev)
+    opt = torch.optim.Adam([k, gain, c], lr=1e-4)
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        noise = torch.randn((B, T), generator=gen, device=dev)
+        filt = torch.nn.functional.conv1d(torch.nn.functional.pad(noise[None], (K - 1, 0)), c.flip(1)[:, None],
+                                          groups=B)[0]
+        e = frame_interp(gain, T, hop) * (pulse + filt)
+        s = ops.lp_filter_frames(k, e, hop)
+        loss = mss_loss(s, target)
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            k.clamp_(-0.99, 0.99)  # keep every frame's filter stable
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ts = []
+    for _ in range(args.steps):
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    t1 = time.perf_counter()
+    sampler.stop()
+    ms = statistics.mean(ts)
+    line = {
+        "metric": "source-filter synthesiser training step Msamples/s (Eq. 4, coefficients from frames in the kernels)",
+        "value": round(B * T / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"S = (G + N C) H: e = g(t) (pulse train + N(0,1) * c), s = LP_a(k)(e); B={B}, T={T} "
+                               f"(2 s at 24 kHz), M={M}, hop {hop}, {K}-tap noise FIR per signal, gains and "
+                               "reflection coefficients per frame; MSS L1 loss, Adam step",
+                   "l2": "inputs beyond L2"},
+        "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1291,6 +1378,8 @@ def main():
         return run_frames(args)
     if args.workload == "train":
         return run_train(args)
+    if args.workload == "golf":
+        return run_golf(args)
     return run_ours(args)
 
 
