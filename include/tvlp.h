@@ -161,8 +161,8 @@ int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs,
                        void *stream);
 
 /*
- * Adjoint from chunk checkpoints (the benchmark spec's chunk-state
- * checkpointing; no counterpart in the paper): instead of the forward output
+ * Adjoint from chunk checkpoints (chunk-state checkpointing, a memory
+ * saving with no counterpart in the paper): instead of the forward output
  * s, the caller keeps the per-chunk incoming states `ckpt` that
  * lp_tv_forward_* wrote (with the same `chunk`) and the excitation e.  The
  * call first re-runs the forward pass of every chunk from its checkpoint
@@ -191,7 +191,7 @@ int lp_tv_backward_recompute_f64(int B, int64_t T, int M, const double *gs,
                                  void *stream);
 
 /*
- * Varlen batches (the benchmark spec's uneven batching; no counterpart in the
+ * Varlen batches (uneven batching of signals; no counterpart in the
  * paper): n signals of different lengths packed back to back, one call.
  *   offsets [n+1]   DEVICE array, int64: signal b holds rows
  *                   [offsets[b], offsets[b+1]); offsets[0] = 0,
