@@ -41,6 +41,9 @@ UNIT = "Msamples/s"
 WORKLOAD = "batched forward+backward time-varying LP, B=32, T=48000, M=22, FP32"
 KERNELS_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun")
 KERNELS_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun", "grad_a")
+# the chunked adjoint with LP_BWD_FUSED_GA at a compiled order: Eq. 12
+# inside the re-run
+KERNELS_BWD_FUSED = ("bwd_zero_state", "bwd_scan", "bwd_rerun_grad")
 KERNELS_PLAIN_FWD = ("plain_fwd",)
 KERNELS_PLAIN_BWD = ("plain_bwd", "grad_a")
 L2_FLUSH_BYTES = 256 << 20
@@ -67,6 +70,8 @@ def parse():
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
+    ap.add_argument("--fused-ga", action="store_true",
+                    help="the adjoint re-run writes dL/da itself instead of a pass of its own (LP_BWD_FUSED_GA)")
     ap.add_argument("--l2-set-aside-mb", type=int, default=0,
                     help="persisting L2 for the passes' evict-last stages (this process's context; 0: none)")
     ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train", "golf"),
@@ -274,6 +279,7 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2406_05128_gb300 import _lib
+    from paper_2406_05128_gb300.build import F32_ORDERS
 
     l2_aside = _lib.lp_tv_l2_set_aside(args.l2_set_aside_mb << 20) if args.l2_set_aside_mb > 0 else 0
     w = workload(args, rank)
@@ -292,8 +298,15 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     bwd_flags = _lib.LP_BWD_REUSE_FORWARD if args.algo == "chunked" else 0
+    if args.fused_ga and args.algo == "chunked":
+        bwd_flags |= _lib.LP_BWD_FUSED_GA
     names_f = KERNELS_FWD if args.algo == "chunked" else KERNELS_PLAIN_FWD
-    names_b = KERNELS_BWD if args.algo == "chunked" else KERNELS_PLAIN_BWD
+    if args.algo != "chunked":
+        names_b = KERNELS_PLAIN_BWD
+    elif not args.fused_ga or M not in F32_ORDERS:
+        names_b = KERNELS_BWD
+    else:
+        names_b = KERNELS_BWD_FUSED
     def timing_event():
         # external events are recorded by every replay of a captured graph
         try:
@@ -545,6 +558,8 @@ def run_ours(args):
     bytes_per_sample = {
         "fwd_summary": 4 * M + 4, "bwd_zero_state": 4 * M + 4,
         "fwd_rerun": 4 * M + 8, "bwd_rerun": 4 * M + 8, "grad_a": 4 * M + 8,
+        # a, gs and s in; ge and ga out
+        "bwd_rerun_grad": 8 * M + 12,
         "plain_fwd": 4 * M + 8, "plain_bwd": 4 * M + 8,
     }
     flops_per_sample = {"fwd_summary": 2 * (MP + 1) * MP}
@@ -600,6 +615,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config(args, "flushed between timed steps (256 MiB write)") | {
             "chunk": chunk, "launch": "host launches" if args.no_graph else "CUDA graph replay per step",
+            "ga": "separate pass" if names_b != KERNELS_BWD_FUSED else "written by the adjoint re-run",
             "l2_persisting_bytes": l2_aside},
         "roofline": roof, "step_roofline": step_roof, "kernels": kern_detail,
         "kernels_from": ("replays of the step graph with an event around each kernel, outside the timed region "

@@ -75,7 +75,15 @@ enum {
      * forward.  The adjoint's chunk transfer is their transpose (the
      * adjoint state is the gradient with respect to the forward state), so
      * the backward then runs one recursion per chunk instead of M+1. */
-    LP_BWD_REUSE_FORWARD = 1
+    LP_BWD_REUSE_FORWARD = 1,
+    /* The chunked adjoint re-run writes ga as it produces ge (one kernel
+     * and one pass over the rows instead of two), when M is one of the
+     * compiled orders; otherwise ga comes from a pass of its own over ge and
+     * s.  Both give the same bits.  At B=32, T=48000, M=22 on a GB300 the
+     * fused re-run takes 65 us against 32 + 27 us for the two kernels: its
+     * gradient rows leave through the same two-stage shared ring that
+     * prefetches the coefficients, which then runs shallower. */
+    LP_BWD_FUSED_GA = 2
 };
 
 /* Which kernels compute the recursion. */
@@ -91,7 +99,8 @@ enum {
  * just before and events[2k+1] just after its k-th kernel launch (k < n) on
  * the call's stream.  Kernel order: forward (chunked) summary, scan,
  * re-run; backward (chunked) zero-state summary (or full summary without
- * LP_BWD_REUSE_FORWARD), scan, re-run, coefficient gradient (for the
+ * LP_BWD_REUSE_FORWARD), scan, re-run, coefficient gradient (none when the
+ * re-run writes ga itself, see LP_BWD_FUSED_GA; for the
  * generated-coefficient calls: gradient, then its final sum); the plain
  * algorithm launches re-run (and coefficient gradient).  NULL uninstalls the
  * hook.  The library neither creates nor destroys events.
@@ -147,7 +156,7 @@ int lp_tv_forward_f64(int B, int64_t T, int M, const double *a, const double *e,
  *   ge   [B][T]     dL/de                                       (out)
  *   ga   [B][T][M]  dL/da_i(t) = -ge(t) s(t-i), or NULL         (out)
  *   gzi  [B][M]     dL/ds(-j), or NULL                          (out)
- *   flags           0 or LP_BWD_REUSE_FORWARD
+ *   flags           0, LP_BWD_REUSE_FORWARD, LP_BWD_FUSED_GA (or both)
  * `s` may be NULL only when `ga` is NULL.
  */
 int lp_tv_backward_f32(int B, int64_t T, int M, const float *gs, const float *a,
@@ -171,8 +180,9 @@ int lp_tv_backward_f64(int B, int64_t T, int M, const double *gs,
  *   e    [B][T]     excitation of the forward                   (in)
  *   ckpt [B][nC][M] incoming state of every chunk, from the forward (in)
  *   s    [B][T]     scratch, holds the recomputed forward output  (out)
- * Other arguments as lp_tv_backward_*; `flags` may be
- * LP_BWD_REUSE_FORWARD when the workspace still holds that forward's maps.
+ * Other arguments as lp_tv_backward_*; `flags` may hold
+ * LP_BWD_REUSE_FORWARD (when the workspace still holds that forward's maps)
+ * and LP_BWD_FUSED_GA.
  * Memory kept between forward and backward is ckpt (M values per chunk:
  * 0.55 B/sample at M=22, chunk 160) instead of s (4 B/sample).
  */

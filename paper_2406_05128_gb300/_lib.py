@@ -68,6 +68,7 @@ class ServeStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 LP_BWD_REUSE_FORWARD = 1
+LP_BWD_FUSED_GA = 2
 
 
 class LPLibraryMissing(RuntimeError):

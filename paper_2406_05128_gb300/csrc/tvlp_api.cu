@@ -378,7 +378,7 @@ template <typename S>
 int backward_impl(int dtype, int B, int64_t T, int M, const S *gs, const S *a, const S *s, const S *zi, S *ge,
                   S *ga, S *gzi, int chunk, int algo, int flags, void *ws, size_t wsb, void *stream) {
     if (algo != LP_ALGO_CHUNKED && algo != LP_ALGO_PLAIN) return LP_EINVAL;
-    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    if ((flags & ~(LP_BWD_REUSE_FORWARD | LP_BWD_FUSED_GA)) != 0) return LP_EINVAL;
     Problem p;
     int rc = make_problem(B, T, M, chunk, dtype, &p);
     if (rc != LP_OK) return rc;
@@ -412,7 +412,7 @@ template <typename S>
 int backward_recompute_impl(int dtype, int B, int64_t T, int M, const S *gs, const S *a, const S *e, const S *ckpt,
                             const S *zi, S *s, S *ge, S *ga, S *gzi, int chunk, int flags, void *ws, size_t wsb,
                             void *stream) {
-    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    if ((flags & ~(LP_BWD_REUSE_FORWARD | LP_BWD_FUSED_GA)) != 0) return LP_EINVAL;
     Problem p;
     int rc = make_problem(B, T, M, chunk, dtype, &p);
     if (rc != LP_OK) return rc;
@@ -456,7 +456,7 @@ template <typename S>
 int backward_varlen_impl(int dtype, int n, const int64_t *off, int64_t total, int M, const S *gs, const S *a,
                          const S *s, const S *zi, S *ge, S *ga, S *gzi, int chunk, int flags, void *ws, size_t wsb,
                          void *stream) {
-    if ((flags & ~LP_BWD_REUSE_FORWARD) != 0) return LP_EINVAL;
+    if ((flags & ~(LP_BWD_REUSE_FORWARD | LP_BWD_FUSED_GA)) != 0) return LP_EINVAL;
     Problem p;
     int rc = make_problem_varlen(n, total, M, chunk, dtype, off, &p);
     if (rc != LP_OK) return rc;

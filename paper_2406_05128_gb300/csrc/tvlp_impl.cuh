@@ -155,16 +155,18 @@ template <typename S, int MP> struct Launch {
     template <int MODE, bool EXACT, int SRC = SRC_STREAM>
     static cudaError_t rec_exact(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin,
                                  const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
-                                 cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
+                                 cudaStream_t st, const CoefSrc &cs = CoefSrc(), const S *sfw = nullptr,
+                                 S *ga = nullptr) {
         static bool done[kMaxDevices] = {};
         constexpr int RC = RecChunks<SRC>::N;
         using RG = RecGeo<S, MP, RC>;
         auto kern = k_rec<S, MP, EXACT, MODE, SRC>;
-        cudaError_t err = allow_smem(kern, RG::SMEM, done);
+        constexpr size_t smem = MODE == BWD_GRAD ? RG::SMEM_GA : RG::SMEM;
+        cudaError_t err = allow_smem(kern, smem, done);
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + RC - 1) / RC;
-        return launch(kern, dim3((unsigned)grid), dim3(32), RG::SMEM, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
-                      out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status, cs);
+        return launch(kern, dim3((unsigned)grid), dim3(32), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
+                      out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status, cs, sfw, ga);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
@@ -175,6 +177,13 @@ template <typename S, int MP> struct Launch {
                            int xs = MP) {
         if (p.M == MP) return rec_exact<MODE, true>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
         return rec_exact<MODE, false>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
+    }
+
+    // the adjoint re-run that also writes Eq. 12's ga (M == MP only)
+    static cudaError_t rec_grad(const Problem &p, const Batch &bt, const S *a, const S *gs, const S *Win, const S *zi,
+                                const S *s, S *ge, S *ga, S *gzi, cudaStream_t st, int l2) {
+        return rec_exact<BWD_GRAD, true>(p, bt, a, gs, Win, zi, ge, nullptr, gzi, 1, nullptr, l2, MP, st, CoefSrc(), s,
+                                         ga);
     }
 
     // the same with generated coefficient rows (rows are written whole, so
@@ -277,6 +286,9 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
     int k = 0;
     const Problem q = algo == ALGO_PLAIN ? plain_problem(p) : p;
     const Batch bt = batch_of(q, algo == ALGO_PLAIN ? nullptr : ws, sizeof(S));
+    // on request (chunked, exact rows): Eq. 12 inside the adjoint re-run;
+    // otherwise a separate pass over ge and s
+    const bool fused_ga = ga != nullptr && algo != ALGO_PLAIN && p.M == MP && (flags & BWD_FUSED_GA);
     if (algo == ALGO_PLAIN) {
         TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(q, bt, a, gs, nullptr, nullptr, ge, nullptr, gzi, 0, st)));
     } else {
@@ -301,10 +313,15 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
             TVLP_LAUNCH(k++,
                         (LN::template scan<CH_BWD>(p, bt, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt, st)));
         }
-        TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, bt, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, nullptr,
-                                                      l2_word(0, L2_FIRST, L2_FIRST))));
+        if (fused_ga) {
+            // the re-run writes ga as it goes (Eq. 12 from its own ge)
+            TVLP_LAUNCH(k++, (LN::rec_grad(p, bt, a, gs, Wst, zi, s, ge, ga, gzi, st, l2_word(0, L2_FIRST, L2_FIRST))));
+        } else {
+            TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, bt, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st,
+                                                          nullptr, l2_word(0, L2_FIRST, L2_FIRST))));
+        }
     }
-    if (ga != nullptr) TVLP_LAUNCH(k, (LN::grad_a(q, bt, ge, s, zi, ga, st)));
+    if (ga != nullptr && !fused_ga) TVLP_LAUNCH(k, (LN::grad_a(q, bt, ge, s, zi, ga, st)));
     return OK;
 }
 

@@ -85,7 +85,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Status codes (mirror include/tvlp.h).
 enum { OK = 0, EINVAL_ = -1, EUNSUPPORTED = -2, EWORKSPACE = -3, ECUDA = -4, EALIGN = -5 };
 enum { ALGO_CHUNKED = 0, ALGO_PLAIN = 1 };
-enum { BWD_REUSE_FORWARD = 1 };
+enum { BWD_REUSE_FORWARD = 1, BWD_FUSED_GA = 2 };
 
 // Workspace regions (each 256-byte aligned), in elements of the scalar
 // (RS = MP padded to 16 bytes, YS = (MP+1)*RS, ZS = RS):

@@ -185,6 +185,21 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
         : "memory");
 }
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+// 1-D bulk store shared -> global in the issuing thread's bulk groups
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// the thread's stores have finished reading their shared source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// the thread's stores are complete in global memory
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_store_commit_wait() {
+    bulk_commit();
+    bulk_wait_all();
+}
 
 // Programmatic dependent launch.  The kernels of one call run back to back
 // on a stream; each may be launched before the previous one has finished.
@@ -304,6 +319,28 @@ __device__ __forceinline__ void load_pair_smem(S (&c0)[MP], S (&c1)[MP], const S
     for (int i = 0; i < MP; ++i) {
         c0[i] = v[i];
         c1[i] = v[MP + i];
+    }
+}
+
+// Eq. 12 for two consecutive rows r0, r0 + 1 into shared memory (16-byte
+// aligned pair): row r gets -g_r s(t_r - 1 - i), i < MP, where sv[MP + r - 1
+// - i] holds s(t_r - 1 - i).
+template <typename S, int MP, int NV>
+__device__ __forceinline__ void store_ga_pair(S *rows, S g0, S g1, const S (&sv)[NV], int r0) {
+    S v[2 * MP];
+#pragma unroll
+    for (int i = 0; i < MP; ++i) {
+        v[i] = -g0 * sv[MP + r0 - 1 - i];
+        v[MP + i] = -g1 * sv[MP + r0 - i];
+    }
+    if constexpr (sizeof(S) == 4) {
+        float4 *p = reinterpret_cast<float4 *>(rows);
+#pragma unroll
+        for (int i = 0; i < MP / 2; ++i) p[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+        double2 *p = reinterpret_cast<double2 *>(rows);
+#pragma unroll
+        for (int i = 0; i < MP; ++i) p[i] = make_double2(v[2 * i], v[2 * i + 1]);
     }
 }
 
@@ -893,12 +930,16 @@ __global__ void __launch_bounds__(256, 1)
 //              xs: MP for the scan's states, M for checkpoints.
 //   BWD_ZERO:  adjoint from zero state, store the end state to Z[q].
 //   BWD_RERUN: adjoint from W[q], write ge; chunk 0 also writes gzi.
+//   BWD_GRAD:  BWD_RERUN that also writes Eq. 12's ga(t) = -ge(t) s(t-i)
+//              (exact rows only, M == MP).  The adjoint uses row a(t) up at
+//              step t, so the lane writes ga(t) over it in its ring and the
+//              finished stage leaves by one bulk store.
 // A launch with one chunk per signal (L >= T) is the plain sequential filter.
 // With `reverse` set, warps walk the chunks from the end, so a pass right
 // after another over the same rows starts with the rows that pass loaded
 // last (most likely still in L2).
 // ---------------------------------------------------------------------------
-enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2 };
+enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2, BWD_GRAD = 3 };
 
 constexpr int kRecChunks = 16;  // chunks per warp (lanes 0 .. kRecChunks-1 own one each)
 // chunks per warp when the rows are generated: half the shared ring per
@@ -916,6 +957,9 @@ template <typename S, int MP, int RC = kRecChunks> struct RecGeo {
     // a quarter warp hit distinct bank quads
     static constexpr int LW = ((RAW + 3) / 4) % 2 == 1 ? ((RAW + 3) / 4) * 4 : ((RAW + 3) / 4 + 1) * 4;
     static constexpr size_t SMEM = size_t(RC) * LW * 4 + NS * 8;
+    // BWD_GRAD: plus one lane-stage that the lanes without a chunk read
+    // (owners write gradient rows over their own rings as they go)
+    static constexpr size_t SMEM_GA = SMEM + size_t(A_ST) * sizeof(S);
     static_assert((A_ST * sizeof(S)) % 16 == 0, "16-byte lane stages");
     static_assert((LW * 4) % 16 == 0, "16-byte lane ring alignment");
     static_assert(NS * A_ST * sizeof(S) <= size_t(LW) * 4, "lane ring fits its stride");
@@ -994,12 +1038,15 @@ __global__ void __launch_bounds__(32)
     k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
           S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
-          int *__restrict__ status, CoefSrc cs) {
+          int *__restrict__ status, CoefSrc cs, const S *__restrict__ sfw, S *__restrict__ ga) {
     static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
     constexpr int RC = RecChunks<SRC>::N;
     using RG = RecGeo<S, MP, RC>;
     constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
+    constexpr bool GA = MODE == BWD_GRAD;  // also Eq. 12, from s (sfw) and zi
+    constexpr bool RERUN_B = MODE == BWD_RERUN || GA;
+    static_assert(!GA || (EXACT && SRC == SRC_STREAM), "fused gradient rows need exact streamed rows");
     extern __shared__ __align__(128) unsigned char rec_smem[];
     const int lane = threadIdx.x & 31;
     const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
@@ -1012,6 +1059,8 @@ __global__ void __launch_bounds__(32)
     const bool active = owner && q < NQ;
     S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % RC) * RG::LW * 4);  // [NS][SRS*MP]
     uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)RC * RG::LW * 4);
+    // BWD_GRAD: lanes without a chunk read this never-written stage instead
+    const S *idle_rows = reinterpret_cast<const S *>(rec_smem + (size_t)RC * RG::LW * 4 + NS * 8);
     if (!EXACT && owner) {
         for (int j = 0; j < NS * RG::A_ST; ++j) a_ring[j] = S(0);
     }
@@ -1063,7 +1112,7 @@ __global__ void __launch_bounds__(32)
                 }
                 h[MP - j] = v;
             }
-        } else if constexpr (MODE == BWD_RERUN) {
+        } else if constexpr (RERUN_B) {
             // h[j - 1] = q_j entering from the chunk's end
             if (Xin != nullptr) {
 #pragma unroll
@@ -1076,6 +1125,8 @@ __global__ void __launch_bounds__(32)
     for (int s = 0; s < nblk; ++s) {
         const int slot = s & 1;
         const bool more = s + 1 < nblk;
+        // the other slot's gradient rows (stage s - 1) have left shared memory
+        if constexpr (GA) bulk_wait_read();
         if (more) {
             stage(slot ^ 1, s + 1);
             rec_load_inputs<S, BWD>(unxt, u, L, s + 1, active, base, n);
@@ -1083,14 +1134,34 @@ __global__ void __launch_bounds__(32)
             cp_async_commit();
         }
         cp_async_wait<1>();
+        // sv[k] = s(roff - MP + k) in chunk rows: the forward output (zi
+        // before the signal's start) that Eq. 12 pairs with the stage's rows
+        constexpr int NV = GA ? SRS + MP - 1 : 1;
+        S sv[NV];
+        if constexpr (GA) {
+            const int roff = L - (s + 1) * SRS;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const int l = roff - MP + k;
+                const int64_t t = c * (int64_t)L + l;  // time in the signal
+                S v = S(0);
+                if (active && l < n) {
+                    if (t >= 0) v = __ldg(sfw + base + l);
+                    else if (zi != nullptr) v = __ldg(zi + b * M + (-t - 1));
+                }
+                sv[k] = v;
+            }
+        }
         if (!mbar_wait_warp(bars + slot, (s >> 1) & 1, kWaitLimit)) {
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
             if (more) mbar_wait_warp(bars + (slot ^ 1), ((s + 1) >> 1) & 1, kWaitLimit);
             cp_async_wait<0>();
+            if constexpr (GA) bulk_wait_all();
             return;
         }
         __syncwarp();
-        const S *ar = a_ring + slot * RG::A_ST;
+        S *ar = a_ring + slot * RG::A_ST;
+        const S *ar_read = (GA && !owner) ? idle_rows : ar;
         const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
 #pragma unroll
         for (int cb = 0; cb < SRS / SR; ++cb) {
@@ -1102,7 +1173,7 @@ __global__ void __launch_bounds__(32)
                 const int p = BWD ? SR / 2 - 1 - pr : pr;
                 const int r0 = rb + 2 * p;
                 S c0[MP], c1[MP];
-                load_pair_smem<S, MP>(c0, c1, ar + r0 * MP);
+                load_pair_smem<S, MP>(c0, c1, ar_read + r0 * MP);
                 if constexpr (MODE == FWD_RERUN) {
                     const S y0 = fwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * p);
                     const S y1 = fwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * p + 1);
@@ -1111,19 +1182,38 @@ __global__ void __launch_bounds__(32)
                 } else {
                     const S y1 = bwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * pr);
                     const S y0 = bwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * pr + 1);
-                    if constexpr (MODE == BWD_RERUN) {
+                    if constexpr (RERUN_B) {
                         if (roff + r0 + 1 < n) out[base + roff + r0 + 1] = y1;
                         if (roff + r0 < n) out[base + roff + r0] = y0;
                     }
+                    // both rows are in registers and no other lane reads
+                    // this ring: its rows take ga
+                    if constexpr (GA)
+                        if (active) store_ga_pair<S, MP>(ar + r0 * MP, y0, y1, sv, r0);
                 }
             }
             slide<S, MP, WIN>(h);
+        }
+        if constexpr (GA) {
+            if (active) {
+                int nv = n - roff;
+                nv = nv < 0 ? 0 : (nv > SRS ? SRS : nv);
+                S *dst = ga + (base + roff) * (int64_t)MP;
+                if (nv == SRS && aligned16(dst)) {
+                    fence_proxy_async();
+                    bulk_store(dst, ar, (unsigned)(SRS * MP * sizeof(S)));
+                } else {
+                    for (int i = 0; i < nv * MP; ++i) dst[i] = ar[i];
+                }
+            }
+            bulk_commit();
         }
 #pragma unroll
         for (int r = 0; r < SRS; ++r) ucur[r] = unxt[r];
         __syncwarp();
     }
     cp_async_wait<0>();
+    if constexpr (GA) bulk_wait_all();
     if (!active) return;
     if constexpr (MODE == BWD_ZERO) {
         // adjoint zero-state summaries use the 16-byte stride of the scan's z
@@ -1131,7 +1221,7 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
         for (int j = 0; j < MP; ++j) Zout[q * ZS + j] = h[j];
     }
-    if constexpr (MODE == BWD_RERUN) {
+    if constexpr (RERUN_B) {
         if (gzi != nullptr && c == 0) {
 #pragma unroll
             for (int j = 0; j < MP; ++j)
@@ -1664,15 +1754,6 @@ template <typename S, int MP, bool EXACT> struct GradGeo {
     static constexpr int TR = 256;       // rows per block
     static constexpr int THREADS = 256;
 };
-
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_store_commit_wait() {
-    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group 0;\n" ::: "memory");
-}
 
 // largest b in [0, n) with off[b] <= t (off non-decreasing, off[0] = 0)
 __device__ __forceinline__ int find_row_signal(const int64_t *__restrict__ off, int n, int64_t t) {

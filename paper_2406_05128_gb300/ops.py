@@ -82,13 +82,18 @@ def lp_tv_forward(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked", ckpt:
     return (s, ck) if ckpt else s
 
 
+def _bwd_flags(reuse_forward: bool, fused_ga: bool) -> int:
+    return (_lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0) | (_lib.LP_BWD_FUSED_GA if fused_ga else 0)
+
+
 def lp_tv_backward(gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = True, chunk: int = 0,
-                   algo: str = "chunked", ws=None, reuse_forward: bool = False):
+                   algo: str = "chunked", ws=None, reuse_forward: bool = False, fused_ga: bool = False):
     """Adjoint (Eqs. 11-12): returns (ge [B,T], ga [B,T,M] or None, gzi [B,M] or None).
 
     reuse_forward=True requires `ws` to be the workspace the forward call on
     the same `a` (and chunk) filled; the adjoint then reuses its chunk
-    transfer matrices.
+    transfer matrices.  fused_ga=True has the adjoint re-run write ga
+    instead of a pass of its own (same results).
     """
     B, T, M = a.shape
     dev = a.device
@@ -105,14 +110,14 @@ def lp_tv_backward(gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = 
         gzi = torch.empty((B, M), dtype=a.dtype, device=dev) if need_gzi else None
         if ws is None:
             ws = workspace(B, T, M, chunk, a.dtype, dev)
-        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        flags = _bwd_flags(reuse_forward, fused_ga)
         _lib.lp_tv_backward(code, B, T, M, _ptr(gs), _ptr(a), _ptr(s), _ptr(zi), _ptr(ge), _ptr(ga), _ptr(gzi),
                             chunk, _ALGOS[algo], flags, _ptr(ws), ws.numel(), _stream(dev))
     return ge, ga, gzi
 
 
 def lp_tv_backward_recompute(gs, a, e, ckpt, zi=None, *, need_ga: bool = True, need_gzi: bool = True,
-                             chunk: int = 0, ws=None, reuse_forward: bool = False):
+                             chunk: int = 0, ws=None, reuse_forward: bool = False, fused_ga: bool = False):
     """Adjoint from chunk checkpoints: recomputes s from (a, e, ckpt) with
     the forward's chunk length, then returns (ge, ga or None, gzi or None)."""
     B, T, M = a.shape
@@ -131,7 +136,7 @@ def lp_tv_backward_recompute(gs, a, e, ckpt, zi=None, *, need_ga: bool = True, n
         gzi = torch.empty((B, M), dtype=a.dtype, device=dev) if need_gzi else None
         if ws is None:
             ws = workspace(B, T, M, chunk, a.dtype, dev)
-        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        flags = _bwd_flags(reuse_forward, fused_ga)
         _lib.lp_tv_backward_recompute(code, B, T, M, _ptr(gs), _ptr(a), _ptr(e), _ptr(ckpt), _ptr(zi), _ptr(s),
                                       _ptr(ge), _ptr(ga), _ptr(gzi), chunk, flags, _ptr(ws), ws.numel(),
                                       _stream(dev))
@@ -205,7 +210,7 @@ def lp_tv_forward_varlen(packed: Packed, a, e, zi=None, *, chunk: int = 0, ckpt:
 
 
 def lp_tv_backward_varlen(packed: Packed, gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = True,
-                          chunk: int = 0, ws=None, reuse_forward: bool = False):
+                          chunk: int = 0, ws=None, reuse_forward: bool = False, fused_ga: bool = False):
     """Adjoint (Eqs. 11-12) over a varlen batch: returns (ge [total],
     ga [total, M] or None, gzi [n, M] or None)."""
     total, M = a.shape
@@ -223,7 +228,7 @@ def lp_tv_backward_varlen(packed: Packed, gs, a, s, zi=None, *, need_ga: bool = 
         if ws is None:
             nb = _lib.lp_tv_workspace_bytes_varlen(packed.n, total, M, chunk, code)
             ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
-        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        flags = _bwd_flags(reuse_forward, fused_ga)
         _lib.lp_tv_backward_varlen(code, packed.n, packed.offsets.data_ptr(), total, M, _ptr(gs), _ptr(a), _ptr(s),
                                    _ptr(zi), _ptr(ge), _ptr(ga), _ptr(gzi), chunk, flags, _ptr(ws), ws.numel(),
                                    _stream(dev))
