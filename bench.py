@@ -526,12 +526,39 @@ def run_ours(args):
         p1.record(s_out)
         torch.cuda.synchronize()
         pipe_t = p0.elapsed_time(p1) / n_p
+        # the floor of the pipelined step: the same copies in and out alone,
+        # both directions at once, no kernels
+        link_ms = []
+        for r in range(4):
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            l0.record(s_in)
+            s_out.wait_event(l0)
+            bf = sets[r % 2]
+            with torch.cuda.stream(s_in):
+                for dst, src in ((bf["a"], ha), (bf["e"], he), (bf["gs"], hgs)):
+                    dst.copy_(src, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                for dst, src in ((hs, bf["s"]), (hge, bf["ge"]), (hga, bf["ga"])):
+                    dst.copy_(src, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(s_out)
+            s_in.wait_event(done)
+            l1.record(s_in)
+            torch.cuda.synchronize()
+            if r >= 1:
+                link_ms.append(l0.elapsed_time(l1))
+        link_t = statistics.mean(link_ms)
         e2e = {"value": round(B * T * world / (pipe_t * 1e-3) / 1e6, 4), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(pipe_t, 4),
                "steps": n_p, "what": "C ABI calls with pinned host buffers; every step copies its inputs in and its "
                                      "results out inside the timed region, consecutive steps overlapped on three "
                                      "streams",
                "GB/s_h2d": round(h2d / (pipe_t * 1e-3) / 1e9, 1), "copy_streams_per_direction": ncs,
+               "link": {"ms_per_step": round(link_t, 4), "frac": round(link_t / pipe_t, 3),
+                        "GB/s_each_way": round(h2d / (link_t * 1e-3) / 1e9, 1),
+                        "what": "the step's copies in and out alone, both directions at once, no kernels: the "
+                                "floor of the pipelined step on this host link"},
                "serial": serial}
         del sets
 
