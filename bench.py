@@ -635,7 +635,7 @@ def run_ours(args):
         sf = serving_run(min(serve_s, 5.0), rate=args.serve_rate, frames=True)
         serving["frames_server"] = {k: sf[k] for k in ("workload", "h2d_bytes_per_sample_synthesis", "latency_ms",
                                                        "latency_ms_adaptation", "Msamples/s", "capacity",
-                                                       "measured_s")}
+                                                       "measured_s", "host_link_h2d_GBs")}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -877,6 +877,22 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
     arrivals = t_begin + np.cumsum(gaps * 1e9).astype(np.int64)
     t_meas0 = t_begin + int(warmup_s * 1e9)
     t_end = t_meas0 + int(seconds * 1e9)
+    def h2d_rate():
+        """Host-to-device GB/s of a 128 MiB pinned copy (mean of 3), the
+        link the requests' payloads cross, probed around the window."""
+        hb = torch.empty(128 << 20, dtype=torch.uint8, pin_memory=True)
+        db = torch.empty(128 << 20, dtype=torch.uint8, device=dev)
+        ts = []
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            db.copy_(hb, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return round(hb.numel() / (statistics.mean(ts[1:]) * 1e-3) / 1e9, 1)
+
+    link_before = h2d_rate()
     sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
     srv.stats(reset=True)
     late = []
@@ -919,6 +935,7 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
     tb1 = serve.now_ns()
     st_burst = srv.stats()
     srv.close()
+    link_after = h2d_rate()
     lat_ms = [x[2] / 1e6 for x in recs]
     lat_syn = [x[2] / 1e6 for x in recs if x[0] == serve.SYNTH]
     lat_ad = [x[2] / 1e6 for x in recs if x[0] == serve.ADAPT]
@@ -955,6 +972,10 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
                      "max_signals_iteration": st_burst["max_signals_iter"], "completed": len(done),
                      "what": "all requests submitted at once, until the last result is on the host"},
         "wall_s": round(w1 - w0, 2), "clocks": sampler.summary(w0, w1),
+        "host_link_h2d_GBs": {"before": link_before, "after": link_after,
+                              "what": "128 MiB pinned host-to-device copy just before the arrivals and after the "
+                                      "capacity burst; the requests' payloads cross this link, which the box's "
+                                      "other jobs share"},
     }
 
 
