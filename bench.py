@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain one-thread-per-signal kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch every step from the host instead of a CUDA graph")
+    ap.add_argument("--no-row-cache", action="store_true",
+                    help="frames workload: generate a(t) in every pass instead of keeping the first pass's rows in "
+                         "the workspace")
     ap.add_argument("--fused-ga", action="store_true",
                     help="the adjoint re-run writes dL/da itself instead of a pass of its own (LP_BWD_FUSED_GA)")
     ap.add_argument("--l2-set-aside-mb", type=int, default=0,
@@ -194,6 +197,19 @@ class ClockSampler:
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+        # nvidia-smi takes a moment to print its first line
+        t = time.perf_counter()
+        while self.proc is not None and not self.rows and time.perf_counter() - t < 3.0:
+            time.sleep(0.01)
+
+    def loaded(self, fn, seconds=1.0):
+        """Run fn() (one untimed step, synchronised) for `seconds` so that the
+        clock samples see the GPU under this workload's load before its timed
+        steps; returns the start of that window for summary()."""
+        t = time.perf_counter()
+        while time.perf_counter() - t < seconds:
+            fn()
+        return t
 
     def _read(self):
         for line in self.proc.stdout:
@@ -727,6 +743,7 @@ def run_uneven(args):
         graph.replay()
     torch.cuda.synchronize()
     sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t_load = sampler.loaded(lambda: (graph.replay(), stream.synchronize()))
     t0 = time.perf_counter()
     times = []
     for _ in range(args.steps):
@@ -775,7 +792,7 @@ def run_uneven(args):
                           "frac_of_hbm": round(gbs / hbm, 4)},
         "one_call_per_signal": {"bucket_M": buckets[0]["M"], "Msamples/s": round(per_sig_rate, 3),
                                 "what": "the same signals of one order, one uniform call each (host launches)"},
-        "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+        "clocks": sampler.summary(t_load, t1), "source_hash": source_hash(),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -1028,7 +1045,7 @@ def run_frames(args):
     s, ge = torch.empty((B, T), device=dev), torch.empty((B, T), device=dev)
     gk = torch.empty((B, F, M), device=dev)
     chunk = args.chunk or _lib.lp_tv_pick_chunk(B, T, M)
-    ws = ops.workspace_frames(B, T, M, hop, chunk, dev)
+    ws = ops.workspace_frames(B, T, M, hop, chunk, dev, cache_rows=not args.no_row_cache)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2 * 8)]
@@ -1073,6 +1090,7 @@ def run_frames(args):
         bwd(True)
     torch.cuda.synchronize()
     sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t_load = sampler.loaded(lambda: (flush.zero_(), graph.replay(), stream.synchronize()))
     t0 = time.perf_counter()
     step, fwd_ms = [], []
     for _ in range(args.steps):
@@ -1154,9 +1172,15 @@ def run_frames(args):
     # FP32 FMAs per sample: step-up M(M-1)/2 + interpolation M wherever a row
     # is generated; K1 (M+1)M; each re-run pass M; the frame gradient's
     # reverse step-up with recomputation about 4 step-ups plus Eq. 12
+    # with the row cache the three later passes stream the rows the summary
+    # pass kept (4M bytes per sample) instead of generating them
+    from paper_2406_05128_gb300.build import F32_ORDERS
+    cached = not args.no_row_cache and M in F32_ORDERS
     gen = M * (M - 1) // 2 + M
-    fma = {"fwd_summary": (M + 1) * M + gen, "fwd_rerun": M + gen, "bwd_zero_state": M + gen,
-           "bwd_rerun": M + gen, "grad_frames": 4 * gen + M}
+    gen_later = 0 if cached else gen
+    fma = {"fwd_summary": (M + 1) * M + gen, "fwd_rerun": M + gen_later, "bwd_zero_state": M + gen_later,
+           "bwd_rerun": M + gen_later, "grad_frames": 4 * gen + M}
+    streamed_bytes = {"fwd_rerun": 4 * M + 8, "bwd_zero_state": 4 * M + 4, "bwd_rerun": 4 * M + 8} if cached else {}
     peaks = load_peaks()
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     fp32_peak = 152 * 128 * 2 * sm_max / 1e12
@@ -1166,6 +1190,8 @@ def run_frames(args):
         d = {"ms": round(m, 5)}
         if n in fma:
             d["TFLOP/s"] = round(2 * fma[n] * nsamp / (m * 1e-3) / 1e12, 2)
+        if n in streamed_bytes:
+            d["GB/s"] = round(streamed_bytes[n] * nsamp / (m * 1e-3) / 1e9, 1)
         kd[n] = d
     dom = max((n for n in fma), key=lambda n: statistics.mean(kern[n]))
     ach = 2 * fma[dom] * nsamp / (statistics.mean(kern[dom]) * 1e-3) / 1e12
@@ -1179,13 +1205,16 @@ def run_frames(args):
         "config": {"workload": f"batched forward+backward, B={B}, T={T}, M={M}, FP32, a(t) generated from "
                                f"reflection coefficients per {hop}-sample frame ({args.gen} generator), "
                                "dL/dk per frame", "chunk": chunk, "frames": F,
+                   "row_cache": ({"bytes": B * T * M * 4, "what": "the summary pass keeps the generated rows in the "
+                                                                  "workspace; the re-run and adjoint passes stream "
+                                                                  "them"} if cached else None),
                    "input_bytes_per_sample": round((4 * F * M + 4 * T) / T, 3),
                    "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(fp32_peak, 2),
                      "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                      "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock",
                      "traffic": None},
-        "kernels": kd, "e2e": e2e, "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+        "kernels": kd, "e2e": e2e, "clocks": sampler.summary(t_load, t1), "source_hash": source_hash(),
         "gpu_launches": (len(names)) * args.steps,
     }
     print(json.dumps(line), flush=True)
@@ -1403,6 +1432,7 @@ def run_golf(args):
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t_load = sampler.loaded(lambda: (step(), torch.cuda.synchronize()))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     ts = []
@@ -1424,7 +1454,7 @@ def run_golf(args):
                                f"(2 s at 24 kHz), M={M}, hop {hop}, {K}-tap noise FIR per signal, gains and "
                                "reflection coefficients per frame; MSS L1 loss, Adam step",
                    "l2": "inputs beyond L2"},
-        "clocks": sampler.summary(t0, t1), "source_hash": source_hash(),
+        "clocks": sampler.summary(t_load, t1), "source_hash": source_hash(),
     }
     print(json.dumps(line), flush=True)
     return 0

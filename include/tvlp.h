@@ -270,6 +270,16 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
  * conventions, shapes and errors as for lp_tv_forward_f32 /
  * lp_tv_backward_f32; hop >= 1.
  *
+ * Row cache (frames, uniform batches): with a workspace of at least
+ * lp_tv_workspace_bytes_frames_cached bytes and M one of the compiled
+ * orders (2, 4, 8, 12, 16, 22, 30, 32), the forward's first pass also
+ * writes every generated row a(t) into the workspace (4*M bytes per
+ * sample), and its re-run streams them instead of generating them again.
+ * A backward with LP_BWD_REUSE_FORWARD on that workspace streams them too:
+ * that flag promises the workspace still holds what the forward on the
+ * same k left in it.  Results are the same bits either way.  For other M,
+ * lp_tv_workspace_bytes_frames_cached equals lp_tv_workspace_bytes_frames.
+ *
  * lp_tv_forward_frames_varlen_f32 / lp_tv_backward_frames_varlen_f32:
  * varlen batches (offsets as for lp_tv_forward_varlen_f32) with
  * frame_offsets [n] (DEVICE, int64): signal b's frames start at frame
@@ -280,6 +290,8 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
  */
 size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop,
                                     int chunk);
+size_t lp_tv_workspace_bytes_frames_cached(int B, int64_t T, int M, int hop,
+                                           int chunk);
 int lp_tv_forward_frames_f32(int B, int64_t T, int M, int hop,
                              const float *k, const float *e,
                              const float *zi, float *s, float *ckpt,

@@ -38,7 +38,7 @@ EXPORTS = (
     "lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64",
     "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
-    "lp_tv_workspace_bytes_frames", "lp_tv_forward_frames_f32", "lp_tv_backward_frames_f32",
+    "lp_tv_workspace_bytes_frames", "lp_tv_workspace_bytes_frames_cached", "lp_tv_forward_frames_f32", "lp_tv_backward_frames_f32",
     "lp_tv_forward_frames_varlen_f32", "lp_tv_selftest_wait", "lp_tv_workspace_bytes_frames_varlen",
     "lp_tv_backward_frames_varlen_f32", "lp_tv_l2_set_aside", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
@@ -122,6 +122,8 @@ def _declare(lib):
         f.restype = i32
     lib.lp_tv_workspace_bytes_frames.argtypes = [i32, i64, i32, i32, i32]
     lib.lp_tv_workspace_bytes_frames.restype = sz
+    lib.lp_tv_workspace_bytes_frames_cached.argtypes = [i32, i64, i32, i32, i32]
+    lib.lp_tv_workspace_bytes_frames_cached.restype = sz
     lib.lp_tv_forward_frames_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.lp_tv_forward_frames_f32.restype = i32
     lib.lp_tv_backward_frames_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
@@ -275,6 +277,10 @@ def lp_tv_device_status(reset: bool = False) -> int:
 
 def lp_tv_workspace_bytes_frames(B, T, M, hop, chunk=0):
     return load().lp_tv_workspace_bytes_frames(B, T, M, hop, chunk)
+
+
+def lp_tv_workspace_bytes_frames_cached(B, T, M, hop, chunk=0):
+    return load().lp_tv_workspace_bytes_frames_cached(B, T, M, hop, chunk)
 
 
 def lp_tv_forward_frames(B, T, M, hop, k, e, zi, s, ckpt, chunk, ws, ws_bytes, stream):

@@ -502,6 +502,18 @@ size_t gen_workspace_bytes(const Problem &p, int kind, int64_t F) {
     return align256(workspace_for(p, LP_DTYPE_F32)) + grad_scratch_bytes(p, kind, F);
 }
 
+// frames, M one of the compiled orders: the generated-row cache after the
+// gradient's scratch (0: no cache for this problem)
+size_t row_cache_bytes(const Problem &p, int kind) {
+    if (kind != SRC_FRAMES || p.M != p.MP || p.M == 0) return 0;
+    return align256((size_t)p.B * (size_t)p.T * p.MP * sizeof(float));
+}
+float *row_cache(const Problem &p, int kind, int64_t F, void *ws, size_t wsb) {
+    const size_t off = gen_workspace_bytes(p, kind, F), n = row_cache_bytes(p, kind);
+    if (n == 0 || wsb < off + n) return nullptr;
+    return reinterpret_cast<float *>(static_cast<char *>(ws) + off);
+}
+
 CoefSrc make_src(int kind, const float *k, int64_t F, int hop) {
     CoefSrc c;
     c.kind = kind;
@@ -530,7 +542,9 @@ int forward_gen_impl(int kind, int B, int64_t T, int M, int hop, const float *k,
     const int64_t F = kind == SRC_FRAMES ? frames_of(T, hop) : 1;
     if (ws == nullptr || !aligned(ws, 256) || wsb < workspace_for(p, LP_DTYPE_F32)) return LP_EWORKSPACE;
     if ((p.status = status_word()) == nullptr) return LP_ECUDA;
-    return Dispatch<float>::forward_gen(p, make_src(kind, k, F, hop), e, zi, s, ckpt, ws, st);
+    CoefSrc src = make_src(kind, k, F, hop);
+    src.cache = row_cache(p, kind, F, ws, wsb);
+    return Dispatch<float>::forward_gen(p, src, e, zi, s, ckpt, ws, st);
 }
 
 int backward_gen_impl(int kind, int B, int64_t T, int M, int hop, const float *gs, const float *k, const float *s,
@@ -566,7 +580,10 @@ int backward_gen_impl(int kind, int B, int64_t T, int M, int hop, const float *g
                                                                     : workspace_for(p, LP_DTYPE_F32)))
         return LP_EWORKSPACE;
     if ((p.status = status_word()) == nullptr) return LP_ECUDA;
-    const CoefSrc src = make_src(kind, k, F, hop);
+    CoefSrc src = make_src(kind, k, F, hop);
+    // the rows the forward cached in this workspace (used with
+    // LP_BWD_REUSE_FORWARD only)
+    src.cache = row_cache(p, kind, F, ws, wsb);
     if ((rc = Dispatch<float>::backward_gen(p, src, gs, s, zi, ge, gzi, flags, ws, st)) != LP_OK) return rc;
     if (gk == nullptr) return LP_OK;
     void *scratch = static_cast<char *>(ws) + align256(workspace_for(p, LP_DTYPE_F32));
@@ -788,6 +805,12 @@ size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop, int chunk)
     Problem p;
     if (hop < 1 || make_problem(B, T, M, chunk, LP_DTYPE_F32, &p) != LP_OK) return 0;
     return gen_workspace_bytes(p, SRC_FRAMES, frames_of(T, hop));
+}
+
+size_t lp_tv_workspace_bytes_frames_cached(int B, int64_t T, int M, int hop, int chunk) {
+    Problem p;
+    if (hop < 1 || make_problem(B, T, M, chunk, LP_DTYPE_F32, &p) != LP_OK) return 0;
+    return gen_workspace_bytes(p, SRC_FRAMES, frames_of(T, hop)) + row_cache_bytes(p, SRC_FRAMES);
 }
 
 int lp_tv_forward_frames_f32(int B, int64_t T, int M, int hop, const float *k, const float *e, const float *zi,

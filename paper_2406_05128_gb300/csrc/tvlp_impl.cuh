@@ -341,7 +341,16 @@ int forward_gen_src(const Problem &p, const CoefSrc &src, const S *e, const S *z
     unsigned *cnt = LN::counters(p, ws);
     TVLP_LAUNCH(0, (LN::template summary<false, SRC>(p, bt, nullptr, e, Y, cnt, st, src)));
     TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, bt, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
-    TVLP_LAUNCH(2, (LN::template rec_gen<FWD_RERUN, SRC>(p, bt, e, X, zi, s, nullptr, nullptr, 1, st, src)));
+    if (src.cache != nullptr) {
+        // the summary pass left every generated row in the cache: stream it
+        const int keep = LN::l2_keep(p), nblk = p.L / SRS;
+        TVLP_LAUNCH(2, (LN::template rec_exact<FWD_RERUN, true>(p, bt, src.cache, e, X, zi, s, nullptr, nullptr, 1,
+                                                                nullptr, l2_word(keep, L2_FIRST, L2_FIRST,
+                                                                                 nblk - keep, L2_LAST),
+                                                                MP, st)));
+    } else {
+        TVLP_LAUNCH(2, (LN::template rec_gen<FWD_RERUN, SRC>(p, bt, e, X, zi, s, nullptr, nullptr, 1, st, src)));
+    }
     return OK;
 }
 
@@ -360,7 +369,14 @@ int backward_gen_src(const Problem &p, const CoefSrc &src, const S *gs, const S 
     S *GX = LN::region(p, ws, 6);
     unsigned *cnt = LN::counters(p, ws);
     (void)zi;
-    if (flags & BWD_REUSE_FORWARD) {
+    // the forward's cached rows (valid with its workspace only)
+    const S *rows = (flags & BWD_REUSE_FORWARD) ? src.cache : nullptr;
+    if (rows != nullptr) {
+        TVLP_LAUNCH(k++, (LN::template rec_exact<BWD_ZERO, true>(p, bt, rows, gs, nullptr, nullptr, nullptr, Z, nullptr,
+                                                                 0, cnt, l2_word(LN::l2_keep(p), L2_LAST, L2_FIRST),
+                                                                 MP, st)));
+        TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS>(p, bt, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
+    } else if (flags & BWD_REUSE_FORWARD) {
         TVLP_LAUNCH(k++, (LN::template rec_gen<BWD_ZERO, SRC>(p, bt, gs, nullptr, nullptr, nullptr, Z, nullptr, 0, st,
                                                               src, cnt)));
         TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS>(p, bt, Y, Z, GY, GZ, GX, nullptr, Wst, nullptr, cnt, st)));
@@ -369,7 +385,13 @@ int backward_gen_src(const Problem &p, const CoefSrc &src, const S *gs, const S 
         TVLP_LAUNCH(k++, (LN::template scan<CH_BWD>(p, bt, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt,
                                                     st)));
     }
-    TVLP_LAUNCH(k++, (LN::template rec_gen<BWD_RERUN, SRC>(p, bt, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, src)));
+    if (rows != nullptr) {
+        TVLP_LAUNCH(k++, (LN::template rec_exact<BWD_RERUN, true>(p, bt, rows, gs, Wst, nullptr, ge, nullptr, gzi, 1,
+                                                                  nullptr, l2_word(0, L2_FIRST, L2_FIRST), MP, st)));
+    } else {
+        TVLP_LAUNCH(k++,
+                    (LN::template rec_gen<BWD_RERUN, SRC>(p, bt, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, src)));
+    }
     return OK;
 }
 

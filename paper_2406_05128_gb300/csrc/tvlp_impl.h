@@ -47,6 +47,10 @@ struct CoefSrc {
     int64_t F = 0;                  // frames per signal (uniform batches)
     int hop = 0;
     float inv_hop = 0.f;
+    // SRC_FRAMES, M == MP: the forward's summary pass also writes every
+    // generated row here ([rows][MP], rows in the order of `a`), and the
+    // later passes stream them instead of generating them again
+    float *cache = nullptr;
 };
 
 // Per-instantiation geometry the host needs before launching.

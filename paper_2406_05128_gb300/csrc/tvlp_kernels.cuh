@@ -194,6 +194,10 @@ __device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 // the thread's stores have finished reading their shared source
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// the thread's stores but its newest group have read their shared source
+__device__ __forceinline__ void bulk_wait_read_prev() {
+    asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+}
 // the thread's stores are complete in global memory
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_store_commit_wait() {
@@ -674,6 +678,39 @@ __device__ __forceinline__ void k1_gen_stage(float *a_st, uint64_t *bar, const C
     cp_async_commit();
 }
 
+// Generated stage k (forward) of the warp's chunks out to the row cache:
+// one bulk store per full, aligned chunk-stage, coalesced plain stores for
+// the rest; every lane then commits one bulk group, so a later
+// bulk_wait_read_prev() in each lane waits for this stage's store only once
+// the next one has been issued.
+template <int MP, typename GE>
+__device__ __forceinline__ void k1_cache_stage(float *__restrict__ cache, const float *a_st, int k, int lane,
+                                               int64_t my_base, int my_valid) {
+    constexpr int CPW = GE::CPW;
+    constexpr unsigned BYTES = SRS * MP * sizeof(float);
+    const int roff = k * SRS;
+    int nvalid = my_valid - roff;
+    nvalid = nvalid < 0 ? 0 : (nvalid > SRS ? SRS : nvalid);
+    const bool mine = lane < CPW;
+    float *dst = cache + (my_base + roff) * (int64_t)MP;
+    const bool bulk = mine && nvalid == SRS && aligned16(dst);
+    // the generated rows (written by every lane) before the async proxy reads them
+    fence_proxy_async();
+    __syncwarp();
+    if (bulk) bulk_store(dst, a_st + lane * GE::CS, BYTES);
+    unsigned slow = __ballot_sync(0xffffffffu, mine && !bulk && nvalid > 0);
+    while (slow) {
+        const int ch = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const int64_t base = __shfl_sync(0xffffffffu, my_base, ch);
+        const int nv = __shfl_sync(0xffffffffu, nvalid, ch);
+        float *d = cache + (base + roff) * (int64_t)MP;
+        const float *src = a_st + ch * GE::CS;
+        for (int idx = lane; idx < nv * MP; idx += 32) d[idx] = src[idx];
+    }
+    bulk_commit();
+}
+
 // Input samples of stage k for the warp's chunks: element e = lane + 32*i
 // (i < UPL) is row e % SRS of chunk e / SRS; zero past the signal's end.
 template <typename S, int MP, typename GE, bool BWD>
@@ -735,9 +772,13 @@ __global__ void __launch_bounds__(256, 1)
         if constexpr (SRC == SRC_STREAM)
             k1_issue_stage<S, MP, GE, BWD>(a_buf + slot * GE::A_STAGE, bars + slot, a, M, L, k, lane, my_base,
                                            my_valid, exact, l2);
-        else
-            k1_gen_stage<MP, GE, BWD, SRC>(reinterpret_cast<float *>(a_buf + slot * GE::A_STAGE), bars + slot, cs, M,
-                                           L, k, lane, my_b, my_t0, my_valid);
+        else {
+            float *st_rows = reinterpret_cast<float *>(a_buf + slot * GE::A_STAGE);
+            // the slot's rows of two stages back have left for the cache
+            if (!BWD && cs.cache != nullptr) bulk_wait_read_prev();
+            k1_gen_stage<MP, GE, BWD, SRC>(st_rows, bars + slot, cs, M, L, k, lane, my_b, my_t0, my_valid);
+            if (!BWD && cs.cache != nullptr) k1_cache_stage<MP, GE>(cs.cache, st_rows, k, lane, my_base, my_valid);
+        }
     };
     const int grp = lane / G, g = lane % G;
     const int nblk = L / SRS;
@@ -800,6 +841,7 @@ __global__ void __launch_bounds__(256, 1)
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
             if (more) mbar_wait_warp(bars + (slot ^ 1), ((k + 1) >> 1) & 1, kWaitLimit);
             cp_async_wait<0>();
+            if (SRC != SRC_STREAM && cs.cache != nullptr) bulk_wait_all();
             return;
         }
         __syncwarp();
@@ -888,6 +930,8 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncwarp();
     }
+    // the ring's last rows have left for the cache before it is reused
+    if (SRC != SRC_STREAM && cs.cache != nullptr) bulk_wait_all();
     // end states: the warp's CPW maps (consecutive in Y) are staged in its
     // now idle stage ring, then written as one run of 16-byte stores
     constexpr bool STAGED = (size_t)CPW * YS * sizeof(S) <= GE::RING_BYTES;

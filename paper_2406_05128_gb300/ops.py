@@ -298,8 +298,13 @@ def _f32(t, name):
         raise TypeError(f"{name} must be float32 (generated coefficients are FP32)")
 
 
-def workspace_frames(B: int, T: int, M: int, hop: int, chunk: int = 0, device=None) -> torch.Tensor:
-    n = _lib.lp_tv_workspace_bytes_frames(B, T, M, hop, chunk)
+def workspace_frames(B: int, T: int, M: int, hop: int, chunk: int = 0, device=None,
+                     cache_rows: bool = False) -> torch.Tensor:
+    """Workspace of the frames calls.  cache_rows=True adds room for the
+    generated rows (4*M bytes per sample, compiled orders only): the
+    forward's first pass keeps them and the later passes stream them."""
+    size = _lib.lp_tv_workspace_bytes_frames_cached if cache_rows else _lib.lp_tv_workspace_bytes_frames
+    n = size(B, T, M, hop, chunk)
     return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
 
 
@@ -393,11 +398,11 @@ class LPFramesFunction(torch.autograd.Function):
     reflection coefficients: gradients for k, e and zi."""
 
     @staticmethod
-    def forward(ctx, k, e, zi, hop, chunk):
+    def forward(ctx, k, e, zi, hop, chunk, cache_rows):
         k, e = k.contiguous(), e.contiguous()
         zi = zi.contiguous() if zi is not None else None
         B, F, M = k.shape
-        ws = workspace_frames(B, e.shape[1], M, hop, chunk, k.device)
+        ws = workspace_frames(B, e.shape[1], M, hop, chunk, k.device, cache_rows=cache_rows)
         s = lp_tv_forward_frames(k, e, hop, zi, chunk=chunk, ws=ws)
         ctx.hop, ctx.chunk = hop, chunk
         ctx.save_for_backward(k, s, zi, ws)
@@ -410,13 +415,16 @@ class LPFramesFunction(torch.autograd.Function):
         ge, gk, gzi = lp_tv_backward_frames(gs.contiguous(), k, s, ctx.hop, zi, need_gk=need_k,
                                             need_gzi=need_zi and zi is not None, chunk=ctx.chunk, ws=ws,
                                             reuse_forward=True)
-        return (gk if need_k else None, ge if need_e else None, gzi if need_zi else None, None, None)
+        return (gk if need_k else None, ge if need_e else None, gzi if need_zi else None, None, None, None)
 
 
-def lp_filter_frames(k, e, hop: int, zi=None, *, chunk: int = 0):
+def lp_filter_frames(k, e, hop: int, zi=None, *, chunk: int = 0, cache_rows: bool = True):
     """Differentiable s = LP_{a(k)}(e) with a(t) generated in the kernels
-    from frame-rate reflection coefficients k [B, ceil(T/hop)+1, M]."""
-    return LPFramesFunction.apply(k, e, zi, hop, chunk)
+    from frame-rate reflection coefficients k [B, ceil(T/hop)+1, M].
+    cache_rows: keep the generated rows in the workspace between forward
+    and backward (4*M bytes per sample) so that only the first pass
+    generates them."""
+    return LPFramesFunction.apply(k, e, zi, hop, chunk, cache_rows)
 
 
 class LPTIFunction(torch.autograd.Function):

@@ -85,13 +85,44 @@ def test_frames_match_oracle(B, T, M, hop, chunk, reuse):
     assert d.max() <= TOL_F32
 
 
+@pytest.mark.parametrize("B,T,M,hop,chunk", CASES)
+@pytest.mark.parametrize("reuse", [True, False])
+def test_frames_row_cache_same_bits(B, T, M, hop, chunk, reuse):
+    """With the cached workspace, the forward's first pass keeps every
+    generated row and the later passes stream them: the same bits as
+    generating them in every pass, and the kept rows are the oracle's a(t)."""
+    k, e, gs, zi = _case(B, T, M, hop, seed=B * 5 + T + M)
+    kt, et, gst, zit = _t(k), _t(e), _t(gs), _t(zi)
+    got = []
+    for cache in (False, True):
+        ws = ops.workspace_frames(B, T, M, hop, chunk, DEV, cache_rows=cache)
+        s = ops.lp_tv_forward_frames(kt, et, hop, zit, chunk=chunk, ws=ws)
+        ge, gk, gzi = ops.lp_tv_backward_frames(gst, kt, s, hop, zit, chunk=chunk, ws=ws, reuse_forward=reuse)
+        torch.cuda.synchronize()
+        assert _lib.lp_tv_device_status() == 0
+        got.append([x.cpu().numpy() for x in (s, ge, gk, gzi)])
+        if cache:
+            n0 = _lib.lp_tv_workspace_bytes_frames(B, T, M, hop, chunk)
+            n1 = _lib.lp_tv_workspace_bytes_frames_cached(B, T, M, hop, chunk)
+            if M in (2, 4, 8, 12, 16, 22, 30, 32):
+                assert n1 >= n0 + B * T * M * 4
+                rows = ws[n0:n0 + B * T * M * 4].view(torch.float32).reshape(B, T, M).cpu().numpy()
+                ref = O.coeffs(k, T, hop)
+                err = np.abs(rows - ref).max() / max(np.abs(ref).max(), 1e-30)
+                assert err <= TOL_F32, err
+            else:
+                assert n1 == n0  # padded orders keep no cache
+    for x, y in zip(*got):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+
+
 def test_frames_headline_shape():
-    """B=32, T=48000, M=22, hop 120: every sample of s and ge, and every
-    frame gradient of two signals, against the oracle."""
+    """B=32, T=48000, M=22, hop 120, with the row cache: every sample of s
+    and ge, and every frame gradient of two signals, against the oracle."""
     B, T, M, hop = 32, 48000, 22, 120
     k, e, gs, _ = _case(B, T, M, hop, seed=2, zi=False)
     kt, et, gst = _t(k), _t(e), _t(gs)
-    ws = ops.workspace_frames(B, T, M, hop, 0, DEV)
+    ws = ops.workspace_frames(B, T, M, hop, 0, DEV, cache_rows=True)
     s = ops.lp_tv_forward_frames(kt, et, hop, chunk=0, ws=ws)
     ge, gk, _ = ops.lp_tv_backward_frames(gst, kt, s, hop, need_gzi=False, ws=ws, reuse_forward=True)
     torch.cuda.synchronize()
