@@ -54,6 +54,22 @@ def test_host_only_entry_points(lib):
     assert _lib.lp_tv_workspace_bytes(2, 10, 40) == 0  # order above 32
 
 
+def test_frames_row_cache_sizes(lib):
+    """The cached frames workspace adds 4*M bytes per sample (256-aligned)
+    for the compiled orders and nothing for padded ones."""
+    from paper_2406_05128_gb300 import _lib
+    for B, T, M, hop in ((32, 48000, 22, 120), (3, 1237, 16, 120), (2, 999, 13, 7), (1, 50, 8, 120)):
+        n0 = _lib.lp_tv_workspace_bytes_frames(B, T, M, hop)
+        n1 = _lib.lp_tv_workspace_bytes_frames_cached(B, T, M, hop)
+        assert n0 > 0
+        if M in (2, 4, 8, 12, 16, 22, 30, 32):
+            assert n1 == n0 + ((B * T * M * 4 + 255) // 256) * 256
+        else:
+            assert n1 == n0
+    assert _lib.lp_tv_workspace_bytes_frames_cached(2, 100, 4, 0) == 0  # hop < 1
+    assert _lib.lp_tv_workspace_bytes_frames_cached(2, 100, 40, 10) == 0  # order above 32
+
+
 def test_argument_errors_without_launching(lib):
     from paper_2406_05128_gb300 import _lib
     f = lib.lp_tv_forward_f32
@@ -68,6 +84,8 @@ def test_argument_errors_without_launching(lib):
     assert g(2, 10, 40, 8, 8, 8, None, 8, None, None, 0, 0, 0, None, 0, None) == _lib.LP_EUNSUPPORTED  # f64: M <= 16
     assert g(2, 10, 4, 16, 16, None, None, 16, 16, None, 0, 0, 0, None, 0, None) == _lib.LP_EINVAL  # ga needs s
     assert g(2, 10, 4, 16, 16, 16, None, 16, None, None, 0, 0, 4, None, 0, None) == _lib.LP_EINVAL  # bad flag
+    # LP_BWD_FUSED_GA is accepted (then the missing workspace is the error)
+    assert g(2, 10, 4, 16, 16, 16, None, 16, 16, None, 0, 0, 3, None, 0, None) == _lib.LP_EWORKSPACE
 
 
 def test_serve_host_only_entry_points(lib):
