@@ -63,7 +63,8 @@ enum {
     LP_ECUDA = -4,        /* a CUDA launch or runtime call failed         */
     LP_EALIGN = -5,       /* a data pointer is not aligned to its type    */
     LP_ETOOBIG = -6,      /* problem too large for the fixed scratch      */
-    LP_ETIMEOUT = -7      /* a bounded host-side wait ended first         */
+    LP_ETIMEOUT = -7,     /* a bounded host-side wait ended first         */
+    LP_ENONFINITE = -8    /* lp_tv_check_finite_*: an inf or NaN found    */
 };
 
 enum { LP_DTYPE_F32 = 0, LP_DTYPE_F64 = 1 };
@@ -91,6 +92,22 @@ enum {
     LP_ALGO_CHUNKED = 0, /* chunked parallel scan (default, fast path)  */
     LP_ALGO_PLAIN = 1    /* one thread per signal, sequential in time   */
 };
+
+/*
+ * Non-finite check: one pass over x [n] (DEVICE memory) on `stream`.
+ * Returns LP_ENONFINITE if any element is an infinity or NaN, LP_OK if
+ * none is (or n == 0), LP_EINVAL for x NULL with n > 0, LP_EALIGN for x
+ * not aligned to its type.  The recursions carry a non-finite value to every
+ * later sample of its signal, and a filter with a pole outside the unit
+ * circle overflows FP32 to inf (the literal |k| <= 0.95 generator at M=22
+ * does so in long signals).  So a caller checks a, e, gs before a call,
+ * and s, ge, ga after one, when its inputs are not known to be finite and
+ * stable.  The call synchronises `stream` (it reads the result back) and
+ * so cannot be captured in a graph.  Up to 64 checks may run at once from
+ * different threads or streams.
+ */
+int lp_tv_check_finite_f32(const float *x, size_t n, void *stream);
+int lp_tv_check_finite_f64(const double *x, size_t n, void *stream);
 
 /*
  * Per-kernel timing hook.  `events` points to 2*n cudaEvent_t handles

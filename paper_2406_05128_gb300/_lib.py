@@ -21,6 +21,7 @@ LP_ECUDA = -4
 LP_EALIGN = -5
 LP_ETOOBIG = -6
 LP_ETIMEOUT = -7
+LP_ENONFINITE = -8
 LP_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 LP_DTYPE_F32 = 0
@@ -38,7 +39,8 @@ EXPORTS = (
     "lp_tv_backward_recompute_f32", "lp_tv_backward_recompute_f64",
     "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
-    "lp_tv_workspace_bytes_frames", "lp_tv_workspace_bytes_frames_cached", "lp_tv_forward_frames_f32", "lp_tv_backward_frames_f32",
+    "lp_tv_workspace_bytes_frames", "lp_tv_workspace_bytes_frames_cached", "lp_tv_forward_frames_f32",
+    "lp_tv_check_finite_f32", "lp_tv_check_finite_f64", "lp_tv_backward_frames_f32",
     "lp_tv_forward_frames_varlen_f32", "lp_tv_selftest_wait", "lp_tv_workspace_bytes_frames_varlen",
     "lp_tv_backward_frames_varlen_f32", "lp_tv_l2_set_aside", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
@@ -124,6 +126,9 @@ def _declare(lib):
     lib.lp_tv_workspace_bytes_frames.restype = sz
     lib.lp_tv_workspace_bytes_frames_cached.argtypes = [i32, i64, i32, i32, i32]
     lib.lp_tv_workspace_bytes_frames_cached.restype = sz
+    for name in ("lp_tv_check_finite_f32", "lp_tv_check_finite_f64"):
+        getattr(lib, name).argtypes = [vp, sz, vp]
+        getattr(lib, name).restype = i32
     lib.lp_tv_forward_frames_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.lp_tv_forward_frames_f32.restype = i32
     lib.lp_tv_backward_frames_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
@@ -281,6 +286,17 @@ def lp_tv_workspace_bytes_frames(B, T, M, hop, chunk=0):
 
 def lp_tv_workspace_bytes_frames_cached(B, T, M, hop, chunk=0):
     return load().lp_tv_workspace_bytes_frames_cached(B, T, M, hop, chunk)
+
+
+def lp_tv_check_finite(dtype: int, x, n, stream) -> bool:
+    """True if the n values at device address x are all finite (synchronises
+    the stream); raises on any other error."""
+    fn = load().lp_tv_check_finite_f32 if dtype == LP_DTYPE_F32 else load().lp_tv_check_finite_f64
+    rc = fn(x, n, stream)
+    if rc == LP_ENONFINITE:
+        return False
+    _check(rc, "lp_tv_check_finite")
+    return True
 
 
 def lp_tv_forward_frames(B, T, M, hop, k, e, zi, s, ckpt, chunk, ws, ws_bytes, stream):

@@ -51,6 +51,7 @@ def _units():
     units.append((os.path.join(CSRC, "tvlp_noalloc.cu"), os.path.join(BUILD, "tvlp_noalloc.o"), []))
     units.append((os.path.join(CSRC, "tvlp_serve.cu"), os.path.join(BUILD, "tvlp_serve.o"), []))
     units.append((os.path.join(CSRC, "tvlp_selftest.cu"), os.path.join(BUILD, "tvlp_selftest.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_check.cu"), os.path.join(BUILD, "tvlp_check.o"), []))
     return units
 
 

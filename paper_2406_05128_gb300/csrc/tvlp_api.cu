@@ -679,6 +679,7 @@ const char *lp_strerror(int code) {
         case LP_EALIGN: return "data pointer not aligned to its element type";
         case LP_ETOOBIG: return "problem needs more scratch than the fixed no-allocation array holds";
         case LP_ETIMEOUT: return "a bounded wait ended before its condition held";
+        case LP_ENONFINITE: return "an infinity or NaN was found";
     }
     return "unknown error code";
 }

@@ -49,6 +49,15 @@ def _stream(device):
     return torch.cuda.current_stream(device).cuda_stream
 
 
+def all_finite(t: torch.Tensor) -> bool:
+    """True if every element of the CUDA tensor t (float32 or float64,
+    contiguous) is finite: one pass in the library's check kernel, then a
+    synchronisation of the current stream (lp_tv_check_finite_*)."""
+    _check(t, "t", tuple(t.shape), t.dtype, t.device)
+    with torch.cuda.device(t.device):
+        return _lib.lp_tv_check_finite(_dtype_code(t), t.data_ptr(), t.numel(), _stream(t.device))
+
+
 def workspace(B: int, T: int, M: int, chunk: int = 0, dtype=torch.float32, device=None) -> torch.Tensor:
     """Workspace tensor (uint8) sized for one forward or backward call."""
     code = _lib.LP_DTYPE_F32 if dtype == torch.float32 else _lib.LP_DTYPE_F64

@@ -44,8 +44,14 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_only_entry_points(lib):
     from paper_2406_05128_gb300 import _lib
     assert "sm_103a" in _lib.version()
-    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert _lib.strerror(code)
+    assert "unknown" not in _lib.strerror(_lib.LP_ENONFINITE).lower()
+    # argument checks of the non-finite check come before any CUDA call
+    assert lib.lp_tv_check_finite_f32(None, 0, None) == _lib.LP_OK
+    assert lib.lp_tv_check_finite_f32(None, 5, None) == _lib.LP_EINVAL
+    assert lib.lp_tv_check_finite_f32(2, 5, None) == _lib.LP_EALIGN
+    assert lib.lp_tv_check_finite_f64(4, 5, None) == _lib.LP_EALIGN
     L = _lib.lp_tv_pick_chunk(32, 48000, 22)
     assert L > 0 and L % 16 == 0
     assert _lib.lp_tv_num_chunks(48000, 22, L) == -(-48000 // L)
