@@ -157,6 +157,22 @@ def oracle_time(w, steps, warmup):
     return B * T / dt / 1e6, cores, dt
 
 
+def oracle_single_core(w, reps=3):
+    """The oracle on one host thread: forward + adjoint of the first signal,
+    best of `reps` (Msamples/s)."""
+    import oracle
+    T = w.a.shape[1]
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        s = oracle.forward(w.a[0], w.e[0])
+        oracle.backward(w.a[0], s, w.gs[0])
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return {"value": round(T / best / 1e6, 4), "unit": UNIT, "cores": 1,
+            "sample": f"one signal of {T} samples (M={w.a.shape[2]}) fwd+bwd on one thread, best of {reps}"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -171,7 +187,8 @@ def run_reference(args):
         "config": config(args, "n/a (host CPU)"),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"full batch {w.a.shape[0]}x{w.a.shape[1]} (M={w.a.shape[2]}) per step, "
-                                   "sequential FP64 C oracle, one thread per signal"},
+                                   "sequential FP64 C oracle, one thread per signal",
+                         "single_core": oracle_single_core(w)},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -640,7 +657,8 @@ def run_ours(args):
         cv, cores, cdt = oracle_time(w, steps=3, warmup=1)
         cpu = {"value": round(cv, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"full batch {B}x{T} (M={M}) fwd+bwd, 3 timed passes after 1 warm-up, "
-                         "FP64 sequential C oracle, one host thread per signal"}
+                         "FP64 sequential C oracle, one host thread per signal",
+               "single_core": oracle_single_core(w)}
 
     launches_per_step = len(names_f) + len(names_b)
     small = small_case_us() if world == 1 else None
