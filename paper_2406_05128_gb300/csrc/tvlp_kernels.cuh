@@ -1306,17 +1306,36 @@ constexpr int kScanWarps = 4;       // warps per block
 constexpr int kScanDepth = 10;      // map slots per warp ring
 constexpr int kScanSpin = 1 << 19;  // counter polls (~250 ns each) before a wait gives up
 
+// Group composition on the tensor cores (FP32 data, MP >= 8): the running
+// product R (MP x MP, with the accumulated response y as column MP) lives
+// in a shared tile of KP rows (the product's rows, padded to the k-steps of
+// an m16n8k8 MMA) and NP columns (MP+1 padded to n-tiles), row stride ST.
+template <int MP> struct MmaGeo {
+    static constexpr int KP = 8 * ((MP + 7) / 8);
+    static constexpr int NP = 8 * ((MP + 1 + 7) / 8);
+    // ST = 8 or 24 mod 32: the B-fragment loads (4 rows x 8 columns) and
+    // the A loads hit 32 distinct banks
+    static constexpr int ST = NP % 16 == 8 ? NP : NP + 8;
+};
+template <typename S, int MP> struct UseMma {
+    static constexpr bool ON = sizeof(S) == 4 && MP >= 8;
+};
+
 template <typename S, int MP> struct ScanGeo {
     static constexpr int RS = YGeo<S, MP>::RS;
     static constexpr int YS = YGeo<S, MP>::YS;
     static constexpr int ZS = RS;         // a z vector: MP values padded to 16 bytes
-    // per warp: kScanDepth map slots, kScanDepth z slots, two mbarriers and
-    // two state-exchange buffers of RS values
+    // per warp: kScanDepth map slots, kScanDepth z slots, two mbarriers,
+    // two state-exchange buffers of RS values, and (FP32) the tile of the
+    // running product of the tensor-core composition
     static constexpr size_t MAPS_BYTES = size_t(kScanDepth) * YS * sizeof(S);
     static constexpr size_t ZS_BYTES = size_t(kScanDepth) * ZS * sizeof(S);
     static constexpr size_t BAR_OFF = MAPS_BYTES + ZS_BYTES;
     static constexpr size_t XB_OFF = BAR_OFF + 16;
-    static constexpr size_t WARP_BYTES = ((XB_OFF + 2 * RS * sizeof(S) + 127) / 128) * 128;
+    static constexpr size_t R_OFF = ((XB_OFF + 2 * RS * sizeof(S) + 15) / 16) * 16;
+    static constexpr size_t R_BYTES =
+        UseMma<S, MP>::ON ? size_t(MmaGeo<MP>::KP) * MmaGeo<MP>::ST * sizeof(float) : 0;
+    static constexpr size_t WARP_BYTES = ((R_OFF + R_BYTES + 127) / 128) * 128;
     static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte maps");
     static_assert(BAR_OFF % 16 == 0 && WARP_BYTES % 128 == 0, "aligned warp slices");
     static_assert(RS <= 32, "a padded row fits the lanes of a warp");
@@ -1367,6 +1386,84 @@ __device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv
 #pragma unroll
         for (int r = 0; r <= MP; ++r) p[r] = m[r * RS + j0];
     }
+}
+
+// TF32 tensor-core MMA, D += A B, m16n8k8, A row-major, B column-major.
+// Fragments (g = lane / 4, t = lane % 4): a0 (g, t), a1 (g+8, t), a2 (g, t+4),
+// a3 (g+8, t+4); b0 (t, g), b1 (t+4, g); d0 (g, 2t), d1 (g, 2t+1),
+// d2 (g+8, 2t), d3 (g+8, 2t+1).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// x = hi + lo with hi, lo TF32 (round to nearest, ties away): the products
+// hi*hi + hi*lo + lo*hi carry x's value to within about 2^-21 of it
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float r = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// One composition step on the tensor cores: R <- P R, with y <- P y + y_c in
+// column MP, for the chunk map at m (Y[0][k] = y_c[k], Y[r][k] = P[k][r-1]).
+// Three TF32 products per k-step (the hi/lo split of both operands) keep
+// the result within a few FP32 ulps of the FP32 composition.
+template <int MP>
+__device__ __forceinline__ void compose_mma(float *rs, const float *m, int lane) {
+    using MG = MmaGeo<MP>;
+    constexpr int RS = YGeo<float, MP>::RS, ST = MG::ST;
+    constexpr int MT = (MP + 15) / 16, KT = MG::KP / 8, NT = MG::NP / 8;
+    const int g = lane >> 2, t = lane & 3;
+    unsigned bh[KT][NT][2], bl[KT][NT][2];
+#pragma unroll
+    for (int kk = 0; kk < KT; ++kk)
+#pragma unroll
+        for (int nn = 0; nn < NT; ++nn)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) split_tf32(rs[(t + 4 * h + 8 * kk) * ST + g + 8 * nn], bh[kk][nn][h], bl[kk][nn][h]);
+    float d[MT][NT][4];
+#pragma unroll
+    for (int mm = 0; mm < MT; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < NT; ++nn)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = g + 8 * (q >> 1) + 16 * mm, col = 2 * t + (q & 1) + 8 * nn;
+                d[mm][nn][q] = (col == MP && row < MP) ? m[row] : 0.f;
+            }
+#pragma unroll
+    for (int mm = 0; mm < MT; ++mm)
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+            // A = P: element (k, r) at Y[r+1][k]
+            unsigned ah[4], al[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = g + 8 * (q & 1) + 16 * mm, col = t + 4 * (q >> 1) + 8 * kk;
+                const float x = (row < MP && col < MP) ? m[(col + 1) * RS + row] : 0.f;
+                split_tf32(x, ah[q], al[q]);
+            }
+#pragma unroll
+            for (int nn = 0; nn < NT; ++nn) {
+                mma_tf32(d[mm][nn], al, bh[kk][nn]);
+                mma_tf32(d[mm][nn], ah, bl[kk][nn]);
+                mma_tf32(d[mm][nn], ah, bh[kk][nn]);
+            }
+        }
+    __syncwarp();  // every lane has read R before it is overwritten
+#pragma unroll
+    for (int mm = 0; mm < MT; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < NT; ++nn)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = g + 8 * (q >> 1) + 16 * mm, col = 2 * t + (q & 1) + 8 * nn;
+                if (row < MG::KP) rs[row * ST + col] = d[mm][nn][q];
+            }
+    __syncwarp();
 }
 
 // packed pair FMA (two IEEE fmas per instruction)
@@ -1485,6 +1582,7 @@ __device__ __forceinline__ S hop_smem(const S (&p)[MP + 1], S *xb, S x, int lane
 template <typename S, int MP> struct ScanWarp {
     using SG = ScanGeo<S, MP>;
     S *maps, *zs, *xb;
+    float *rs;  // tensor-core composition tile (FP32 only)
     uint64_t *bars;
     unsigned phase;  // bit h: parity of the next completion of bars[h]
     int lane;
@@ -1494,6 +1592,7 @@ template <typename S, int MP> struct ScanWarp {
         zs = reinterpret_cast<S *>(base + SG::MAPS_BYTES);
         bars = reinterpret_cast<uint64_t *>(base + SG::BAR_OFF);
         xb = reinterpret_cast<S *>(base + SG::XB_OFF);
+        rs = reinterpret_cast<float *>(base + SG::R_OFF);
         phase = 0;
         lane = lane_;
         status = status_;
@@ -1680,6 +1779,24 @@ __global__ void __launch_bounds__(kScanWarps * 32)
             ok = run_maps<S, MP, REV>(W, group_maps(sg, g), group_zs(sg, g), len,
                                       [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
             if (lane < ZS) GZ[item * ZS + lane] = lane < MP ? zeta : S(0);
+        } else if constexpr (UseMma<S, MP>::ON) {
+            // the running product in the warp's tile, starting from the
+            // identity (y = 0); each map left-multiplies it on the tensor cores
+            using MG = MmaGeo<MP>;
+            float *rs = W.rs;
+            for (int idx = lane; idx < MG::KP * MG::ST; idx += 32) {
+                const int r = idx / MG::ST, j = idx - r * MG::ST;
+                rs[idx] = (r == j && j < MP) ? 1.f : 0.f;
+            }
+            __syncwarp();
+            ok = run_maps<S, MP, REV>(W, group_maps(sg, g), nullptr, len,
+                                      [&](int, const S *m, const S *) { compose_mma<MP>(rs, m, lane); });
+            // row 0 of the group map: y_g (column MP); row j+1: column j of Phi_g
+            S *gy = GY + item * YS;
+            for (int idx = lane; idx < (MP + 1) * RS; idx += 32) {
+                const int r = idx / RS, k = idx - r * RS;
+                gy[idx] = k < MP ? rs[k * MG::ST + (r == 0 ? MP : r - 1)] : S(0);
+            }
         } else {
             // lane j < MP holds column j of the composed transfer (its response
             // to a unit incoming component j+1); the accumulated response y
