@@ -203,12 +203,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id):
+    def __init__(self, gpu_id, interval_ms=50):
         self.rows = []
         self.proc = None
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+                 str(int(interval_ms)),
                  "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -665,8 +666,8 @@ def run_ours(args):
     serving = None
     serve_s = 15.0 if args.serve_seconds is None else args.serve_seconds
     if world == 1 and serve_s > 0:
-        serving = serving_run(serve_s, rate=args.serve_rate)
-        sf = serving_run(min(serve_s, 5.0), rate=args.serve_rate, frames=True)
+        serving = serving_in_own_process(serve_s, args.serve_rate)
+        sf = serving_in_own_process(min(serve_s, 5.0), args.serve_rate, frames=True)
         serving["frames_server"] = {k: sf[k] for k in ("workload", "h2d_bytes_per_sample_synthesis", "latency_ms",
                                                        "latency_ms_adaptation", "Msamples/s", "capacity",
                                                        "measured_s", "host_link_h2d_GBs")}
@@ -880,8 +881,12 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
         return (torch.empty(SERVE_MAX, pin_memory=True), torch.empty(SERVE_MAX, pin_memory=True),
                 torch.empty((cg_max, M), pin_memory=True))
 
-    free_s = [torch.empty(SERVE_MAX, pin_memory=True) for _ in range(64)]
-    free_a = [new_a_slot() for _ in range(12)]
+    # enough page-locked slots that none is allocated while requests are
+    # timed (an allocation of page-locked memory stalls the host thread);
+    # any that still is gets counted
+    free_s = [torch.empty(SERVE_MAX, pin_memory=True) for _ in range(128)]
+    free_a = [new_a_slot() for _ in range(16)]
+    allocs = [0]
 
     srv = serve.Server(M, chunk=chunk, hbm_budget=SERVE_BUDGET, hop=hop if frames else 0)
     recs = []
@@ -897,12 +902,18 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
 
     def submit(T, o, adapt, t_arr, measured):
         if adapt:
-            slot = free_a.pop() if free_a else new_a_slot()
+            if not free_a:
+                allocs[0] += measured
+                free_a.append(new_a_slot())
+            slot = free_a.pop()
             out = (slot[0][:T], slot[1][:T], slot[2][:cg_rows(T)])
             srv.submit(coef(o, T), e_pool[o:o + T], gs_pool[o:o + T], arrival_ns=t_arr, out=out,
                        tag=(measured, slot))
         else:
-            slot = free_s.pop() if free_s else torch.empty(SERVE_MAX, pin_memory=True)
+            if not free_s:
+                allocs[0] += measured
+                free_s.append(torch.empty(SERVE_MAX, pin_memory=True))
+            slot = free_s.pop()
             srv.submit(coef(o, T), e_pool[o:o + T], arrival_ns=t_arr, out=slot[:T], tag=(measured, slot))
 
     # arrival schedule on the server's clock
@@ -928,7 +939,9 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
         return round(hb.numel() / (statistics.mean(ts[1:]) * 1e-3) / 1e9, 1)
 
     link_before = h2d_rate()
-    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    # clocks every 500 ms: each nvidia-smi query goes through the driver
+    # that the request loop is using
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid), interval_ms=500)
     srv.stats(reset=True)
     late = []
     w0 = time.perf_counter()
@@ -993,6 +1006,7 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
         "latency_ms_adaptation": {"p50": _pct(lat_ad, 50), "p99": _pct(lat_ad, 99), "n": len(lat_ad)},
         "latency_from": "scheduled arrival (server clock) to the request's last device-to-host copy seen complete",
         "submit_late_ms_p99": _pct([x / 1e6 for x in late], 99),
+        "slots_allocated_while_timed": allocs[0],
         "Msamples/s": round(samples / seconds / 1e6, 3),
         "offered_Msamples/s": round(rate * SERVE_MEDIAN * float(np.exp(SERVE_SIGMA ** 2 / 2)) / 1e6, 3),
         "iterations": st["iterations"], "synthesis_blocks_per_iteration": round(st["blocks"] / its, 3),
@@ -1012,6 +1026,23 @@ def serving_run(seconds, *, rate=200.0, warmup_s=2.0, seed=11, burst=256, frames
                                       "capacity burst; the requests' payloads cross this link, which the box's "
                                       "other jobs share"},
     }
+
+
+def serving_in_own_process(seconds, rate, frames=False):
+    """The serving summary from `bench.py --workload serving` in a process of
+    its own, as a server runs: in the process that has just run the headline
+    step it measured slower on some boxes, for a reason not found."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "serving", "--serve-seconds", str(seconds),
+           "--serve-rate", str(rate)] + (["--serve-frames"] if frames else [])
+    res = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    if res.returncode != 0 or not lines:
+        raise RuntimeError(f"serving run failed (exit {res.returncode}): {res.stderr[-2000:]}")
+    line = json.loads(lines[-1])
+    sv = line["serving"]
+    sv["workload"] = line["config"]["workload"].split(": ", 1)[1]
+    sv["process"] = "own (bench.py --workload serving" + (" --serve-frames" if frames else "") + ")"
+    return sv
 
 
 def run_serving(args):
