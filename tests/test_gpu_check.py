@@ -50,7 +50,7 @@ def test_empty_and_large_values():
 
 def test_forward_output_matches_numpy():
     """A forward on the literal |k| <= 0.95 generator at M=22: whatever the
-    draw does, the check equals numpy's verdict on the output; the stable
+    draw does, the check agrees with numpy on the output; the stable
     generator's output is finite."""
     for gen in ("literal", "stable"):
         w = inputs.make("chk", 4, 48000, 22, seed=2, gen=gen, excitation="pulse")
