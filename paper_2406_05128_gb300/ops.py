@@ -255,20 +255,23 @@ class LPFunction(torch.autograd.Function):
     s from them and builds its own chunk maps."""
 
     @staticmethod
-    def forward(ctx, a, e, zi, chunk, algo, checkpoint):
+    def forward(ctx, a, e, zi, chunk, algo, checkpoint, check=False):
         a, e = a.contiguous(), e.contiguous()
         zi = zi.contiguous() if zi is not None else None
         B, T, M = a.shape
         ctx.chunk, ctx.algo, ctx.checkpoint = chunk, algo, bool(checkpoint and algo == "chunked" and M > 0)
+        ctx.check = check
         if ctx.checkpoint:
             code = _dtype_code(a)
             ctx.chunk = chunk or _lib.lp_tv_pick_chunk(B, T, M, code)
             s, ck = lp_tv_forward(a, e, zi, chunk=ctx.chunk, algo=algo, ckpt=True)
             ctx.save_for_backward(a, e, zi, ck)
-            return s
-        ws = workspace(B, T, M, chunk, a.dtype, a.device)
-        s = lp_tv_forward(a, e, zi, chunk=chunk, algo=algo, ws=ws)
-        ctx.save_for_backward(a, s, zi, ws)
+        else:
+            ws = workspace(B, T, M, chunk, a.dtype, a.device)
+            s = lp_tv_forward(a, e, zi, chunk=chunk, algo=algo, ws=ws)
+            ctx.save_for_backward(a, s, zi, ws)
+        if check:
+            _raise_if_nonfinite(s, "s")
         return s
 
     @staticmethod
@@ -283,13 +286,27 @@ class LPFunction(torch.autograd.Function):
             ge, ga, gzi = lp_tv_backward(gs.contiguous(), a, s, zi, need_ga=need_a,
                                          need_gzi=need_zi and zi is not None, chunk=ctx.chunk, algo=ctx.algo,
                                          ws=ws, reuse_forward=ctx.algo == "chunked")
-        return (ga if need_a else None, ge if need_e else None, gzi if need_zi else None, None, None, None)
+        if ctx.check:
+            for name, g in (("dL/de", ge), ("dL/da", ga), ("dL/dzi", gzi)):
+                if g is not None:
+                    _raise_if_nonfinite(g, name)
+        return (ga if need_a else None, ge if need_e else None, gzi if need_zi else None, None, None, None, None)
 
 
-def lp_filter(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked", checkpoint: bool = False):
+def _raise_if_nonfinite(t, name):
+    if not all_finite(t):
+        raise FloatingPointError(f"{name} holds an infinity or NaN (LP_ENONFINITE): a filter with a pole outside "
+                                 "the unit circle, or a non-finite input")
+
+
+def lp_filter(a, e, zi=None, *, chunk: int = 0, algo: str = "chunked", checkpoint: bool = False,
+              check: bool = False):
     """Differentiable s = LP_{a(t)}(e) with optional initial state zi.
-    checkpoint=True keeps per-chunk states instead of s for the backward."""
-    return LPFunction.apply(a, e, zi, chunk, algo, checkpoint)
+    checkpoint=True keeps per-chunk states instead of s for the backward.
+    check=True raises FloatingPointError when s, or a gradient in the
+    backward, holds an infinity or NaN (one extra pass and a stream
+    synchronisation per tensor)."""
+    return LPFunction.apply(a, e, zi, chunk, algo, checkpoint, check)
 
 
 # ---------------------------------------------------------------------------

@@ -62,3 +62,20 @@ def test_forward_output_matches_numpy():
         if gen == "stable":
             assert expect
         assert ops.all_finite(a) and ops.all_finite(e)
+
+
+def test_lp_filter_check_raises_on_overflow_and_passes_when_stable():
+    """ops.lp_filter(check=True): a filter with a pole outside the unit
+    circle overflows and raises; a stable one runs forward and backward."""
+    T, M = 4000, 2
+    a = torch.zeros((1, T, M), device=DEV)
+    a[..., 0] = -2.5  # s(t) = e(t) + 2.5 s(t-1): grows as 2.5^t
+    e = torch.ones((1, T), device=DEV)
+    with pytest.raises(FloatingPointError):
+        ops.lp_filter(a, e, check=True)
+    w = inputs.make("chk2", 2, 3000, 16, seed=4, gen="stable")
+    a2 = torch.tensor(w.a, device=DEV, requires_grad=True)
+    e2 = torch.tensor(w.e, device=DEV, requires_grad=True)
+    s = ops.lp_filter(a2, e2, check=True)
+    s.sum().backward()
+    assert ops.all_finite(a2.grad) and ops.all_finite(e2.grad)
