@@ -304,6 +304,10 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
  * offsets[b+1] - offsets[b]; total_frames = the rows of k (and of gk).
  * Workspace: lp_tv_workspace_bytes_varlen for the forward (and a backward
  * without gk), lp_tv_workspace_bytes_frames_varlen for a backward with gk.
+ * lp_tv_workspace_bytes_frames_varlen_cached adds the row cache described
+ * above (4*M bytes per packed row, compiled orders): the varlen forward
+ * keeps its generated rows in such a workspace, and a backward with
+ * LP_BWD_REUSE_FORWARD on it streams them.
  */
 size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop,
                                     int chunk);
@@ -329,6 +333,9 @@ int lp_tv_forward_frames_varlen_f32(int n, const int64_t *offsets,
                                     size_t workspace_bytes, void *stream);
 size_t lp_tv_workspace_bytes_frames_varlen(int n, int64_t total, int M,
                                            int64_t total_frames, int chunk);
+size_t lp_tv_workspace_bytes_frames_varlen_cached(int n, int64_t total, int M,
+                                                  int64_t total_frames,
+                                                  int chunk);
 int lp_tv_backward_frames_varlen_f32(int n, const int64_t *offsets,
                                      int64_t total, int M, int hop,
                                      const int64_t *frame_offsets,

@@ -40,7 +40,7 @@ EXPORTS = (
     "lp_tv_workspace_bytes_varlen", "lp_tv_forward_varlen_f32", "lp_tv_forward_varlen_f64",
     "lp_tv_backward_varlen_f32", "lp_tv_backward_varlen_f64",
     "lp_tv_workspace_bytes_frames", "lp_tv_workspace_bytes_frames_cached", "lp_tv_forward_frames_f32",
-    "lp_tv_check_finite_f32", "lp_tv_check_finite_f64", "lp_tv_backward_frames_f32",
+    "lp_tv_check_finite_f32", "lp_tv_check_finite_f64", "lp_tv_workspace_bytes_frames_varlen_cached", "lp_tv_backward_frames_f32",
     "lp_tv_forward_frames_varlen_f32", "lp_tv_selftest_wait", "lp_tv_workspace_bytes_frames_varlen",
     "lp_tv_backward_frames_varlen_f32", "lp_tv_l2_set_aside", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
@@ -137,6 +137,8 @@ def _declare(lib):
     lib.lp_tv_forward_frames_varlen_f32.restype = i32
     lib.lp_tv_workspace_bytes_frames_varlen.argtypes = [i32, i64, i32, i64, i32]
     lib.lp_tv_workspace_bytes_frames_varlen.restype = sz
+    lib.lp_tv_workspace_bytes_frames_varlen_cached.argtypes = [i32, i64, i32, i64, i32]
+    lib.lp_tv_workspace_bytes_frames_varlen_cached.restype = sz
     lib.lp_tv_backward_frames_varlen_f32.argtypes = [i32, vp, i64, i32, i32, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32,
                                                      i32, vp, sz, vp]
     lib.lp_tv_backward_frames_varlen_f32.restype = i32
@@ -331,6 +333,10 @@ def lp_tv_backward_ti(B, T, M, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws, ws_b
 
 def lp_tv_workspace_bytes_frames_varlen(n, total, M, total_frames, chunk=0):
     return load().lp_tv_workspace_bytes_frames_varlen(n, total, M, total_frames, chunk)
+
+
+def lp_tv_workspace_bytes_frames_varlen_cached(n, total, M, total_frames, chunk=0):
+    return load().lp_tv_workspace_bytes_frames_varlen_cached(n, total, M, total_frames, chunk)
 
 
 def lp_tv_backward_frames_varlen(n, offsets, total, M, hop, frame_offsets, total_frames, gs, k, s, zi, ge, gk, gzi,

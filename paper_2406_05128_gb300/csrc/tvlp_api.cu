@@ -514,6 +514,15 @@ float *row_cache(const Problem &p, int kind, int64_t F, void *ws, size_t wsb) {
     return reinterpret_cast<float *>(static_cast<char *>(ws) + off);
 }
 
+// Varlen frames, M one of the compiled orders: the generated-row cache
+// ([total][MP]) starts right after the scan workspace.  The varlen forward
+// does not know the frame count, so here the gradient's scratch follows the
+// cache (when the workspace holds both) instead of preceding it.
+size_t varlen_cache_bytes(const Problem &p) {
+    if (p.M != p.MP || p.M == 0) return 0;
+    return align256((size_t)p.T * p.MP * sizeof(float));  // p.T: packed rows
+}
+
 CoefSrc make_src(int kind, const float *k, int64_t F, int hop) {
     CoefSrc c;
     c.kind = kind;
@@ -613,6 +622,8 @@ int forward_frames_varlen_impl(int n, const int64_t *off, int64_t total, int M, 
     if ((p.status = status_word()) == nullptr) return LP_ECUDA;
     CoefSrc src = make_src(SRC_FRAMES, k, 0, hop);
     src.foff = foff;
+    const size_t base = align256(workspace_for(p, LP_DTYPE_F32)), cb = varlen_cache_bytes(p);
+    if (cb > 0 && wsb >= base + cb) src.cache = reinterpret_cast<float *>(static_cast<char *>(ws) + base);
     return Dispatch<float>::forward_gen(p, src, e, zi, s, ckpt, ws, st);
 }
 
@@ -656,9 +667,15 @@ int backward_frames_varlen_impl(int n, const int64_t *off, int64_t total, int M,
     src.foff = foff;
     // empty signals have no chunk to write their (zero) gzi
     if (gzi != nullptr && cudaMemsetAsync(gzi, 0, (size_t)n * M * sizeof(float), st) != cudaSuccess) return LP_ECUDA;
+    // the forward's cached rows, when the workspace holds them and the
+    // gradient's scratch after them
+    const size_t base = align256(workspace_for(p, LP_DTYPE_F32)), cb = varlen_cache_bytes(p);
+    const size_t sb = gk != nullptr ? align256(2 * (size_t)total_frames * p.M * sizeof(float)) : 0;
+    const bool cached = cb > 0 && (flags & LP_BWD_REUSE_FORWARD) && wsb >= base + cb + sb;
+    if (cached) src.cache = reinterpret_cast<float *>(static_cast<char *>(ws) + base);
     if ((rc = Dispatch<float>::backward_gen(p, src, gs, s, zi, ge, gzi, flags, ws, st)) != LP_OK) return rc;
     if (gk == nullptr) return LP_OK;
-    void *scratch = static_cast<char *>(ws) + align256(workspace_for(p, LP_DTYPE_F32));
+    void *scratch = static_cast<char *>(ws) + base + (cached ? cb : 0);
     return Dispatch<float>::grad_src(p, src, ge, s, zi, gk, scratch, st);
 }
 }  // namespace
@@ -854,6 +871,13 @@ size_t lp_tv_workspace_bytes_frames_varlen(int n, int64_t total, int M, int64_t 
     if (total_frames < 0 || make_problem_varlen(n, total, M, chunk, LP_DTYPE_F32, nullptr, &p) != LP_OK) return 0;
     p.off = reinterpret_cast<const int64_t *>(1);  // size the tables region too
     return frames_varlen_workspace_bytes(p, total_frames);
+}
+
+size_t lp_tv_workspace_bytes_frames_varlen_cached(int n, int64_t total, int M, int64_t total_frames, int chunk) {
+    Problem p;
+    if (total_frames < 0 || make_problem_varlen(n, total, M, chunk, LP_DTYPE_F32, nullptr, &p) != LP_OK) return 0;
+    p.off = reinterpret_cast<const int64_t *>(1);  // size the tables region too
+    return frames_varlen_workspace_bytes(p, total_frames) + varlen_cache_bytes(p);
 }
 
 int lp_tv_backward_frames_varlen_f32(int n, const int64_t *offsets, int64_t total, int M, int hop,

@@ -259,3 +259,49 @@ def test_frames_varlen_backward_matches_oracle(reuse):
         _close("gk", gkb[None], rgk[None])
         d = np.abs(gzi[b].cpu().numpy() - rgzi[0]).max() / np.abs(rge).max()
         assert d <= TOL_F32
+
+
+@pytest.mark.parametrize("M", [22, 13])
+def test_frames_varlen_row_cache_same_bits(M):
+    """Varlen frames with the cached workspace: the forward keeps its rows
+    and the adjoint (reusing the forward) streams them; the same bits as the
+    uncached workspace, and the kept rows are the oracle's a(t).  M=13 is a
+    padded order: no cache, the same workspace size."""
+    hop, chunk = 120, 96
+    lengths = [5000, 17, 1, 2400, 999, 240, 0, 3601]
+    rng = np.random.default_rng(43)
+    pk = ops.Packed(lengths, DEV)
+    pf = ops.PackedFrames(pk, hop)
+    ks = [inputs.reflection_frames(rng, 1, O.n_frames(n, hop), M, 0.95, 0.9)[0].astype(np.float32) for n in lengths]
+    k = pf.pack([_t(x) for x in ks])
+    e = pk.pack([_t(rng.standard_normal(n).astype(np.float32)) for n in lengths])
+    gs = pk.pack([_t(rng.standard_normal(n).astype(np.float32)) for n in lengths])
+    zi = _t((0.1 * rng.standard_normal((len(lengths), M))).astype(np.float32))
+    n0 = _lib.lp_tv_workspace_bytes_frames_varlen(pk.n, pk.total, M, pf.total, chunk)
+    n1 = _lib.lp_tv_workspace_bytes_frames_varlen_cached(pk.n, pk.total, M, pf.total, chunk)
+    nscan = _lib.lp_tv_workspace_bytes_varlen(pk.n, pk.total, M, chunk)
+    if M == 13:
+        assert n1 == n0
+    else:
+        assert n1 >= n0 + pk.total * M * 4
+    got = []
+    for nb in (n0, n1):
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=DEV)
+        s = ops.lp_tv_forward_frames_varlen(pk, pf, k, e, zi, chunk=chunk, ws=ws)
+        ge, gk, gzi = ops.lp_tv_backward_frames_varlen(pk, pf, gs, k, s, zi, chunk=chunk, ws=ws,
+                                                       reuse_forward=True)
+        torch.cuda.synchronize()
+        assert _lib.lp_tv_device_status() == 0
+        got.append([x.cpu().numpy() for x in (s, ge, gk, gzi)])
+        if nb == n1 and M == 22:
+            base = ((nscan + 255) // 256) * 256
+            rows = ws[base:base + pk.total * M * 4].view(torch.float32).reshape(pk.total, M).cpu().numpy()
+            for b, n in enumerate(lengths):
+                if n == 0:
+                    continue
+                o = int(pk.offsets[b].item())
+                ref = O.coeffs(ks[b][None], n, hop)[0]
+                err = np.abs(rows[o:o + n] - ref).max() / max(np.abs(ref).max(), 1e-30)
+                assert err <= TOL_F32, (b, err)
+    for x, y in zip(*got):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
