@@ -74,6 +74,17 @@ def test_frames_row_cache_sizes(lib):
             assert n1 == n0
     assert _lib.lp_tv_workspace_bytes_frames_cached(2, 100, 4, 0) == 0  # hop < 1
     assert _lib.lp_tv_workspace_bytes_frames_cached(2, 100, 40, 10) == 0  # order above 32
+    # varlen: the cache adds 4*M bytes per packed row (256-aligned) on top of
+    # the workspace of a backward with dL/dk
+    for n, total, M, frames in ((8, 12258, 22, 110), (3, 4000, 16, 40), (5, 999, 13, 30)):
+        n0 = _lib.lp_tv_workspace_bytes_frames_varlen(n, total, M, frames)
+        n1 = _lib.lp_tv_workspace_bytes_frames_varlen_cached(n, total, M, frames)
+        assert n0 > 0
+        if M in (2, 4, 8, 12, 16, 22, 30, 32):
+            assert n1 == n0 + ((total * M * 4 + 255) // 256) * 256
+        else:
+            assert n1 == n0
+    assert _lib.lp_tv_workspace_bytes_frames_varlen_cached(2, 100, 4, -1) == 0  # negative frame count
 
 
 def test_argument_errors_without_launching(lib):
