@@ -41,6 +41,7 @@ _lib = None
 # -ffp-contract=off: no fused multiply-add, so the x86 and aarch64 builds
 # round identically.
 CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off"]
+LDLIBS = ["-lm"]
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +50,7 @@ def build(force: bool = False) -> str:
     stale = (not os.path.exists(_SO)) or os.path.getmtime(_SO) < os.path.getmtime(_SRC)
     if force or stale:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp], check=True)
+        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, *LDLIBS], check=True)
         os.replace(tmp, _SO)
     return _SO
 
@@ -67,6 +68,10 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.tvlp_oracle_coeffs_batch.restype = None
     lib.tvlp_oracle_coeffs_adjoint_batch.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, dp, dp, dp]
     lib.tvlp_oracle_coeffs_adjoint_batch.restype = None
+    lib.tvlp_oracle_framewise_frames.argtypes = [i64, ctypes.c_int]
+    lib.tvlp_oracle_framewise_frames.restype = i64
+    lib.tvlp_oracle_framewise_batch.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+    lib.tvlp_oracle_framewise_batch.restype = None
     return lib
 
 
@@ -174,3 +179,27 @@ def coeffs_adjoint(k, ga, hop, lib=None):
     gk = np.empty((B, F, M), np.float64)
     lib.tvlp_oracle_coeffs_adjoint_batch(B, T, M, hop, _ptr(k), _ptr(ga), _ptr(gk))
     return gk[0] if single else gk
+
+
+def framewise_frames(T: int, hop: int) -> int:
+    """Frames of the frame-wise approximation: ceil(T / hop) + 3."""
+    return -(-T // hop) + 3
+
+
+def framewise(af, e, gs=None, hop=120, lib=None):
+    """Frame-wise approximation of Eq. 5 with 75 % overlap-add (Sec. 3.2,
+    Sec. 4) and, with gs, its adjoint.
+
+    af: [B,F,M] direct-form coefficients per frame, F = framewise_frames(T, hop);
+    e, gs: [B,T].  Returns s [B,T], or (s, ge [B,T], gaf [B,F,M]) with gs.
+    """
+    lib = lib or _get()
+    af, e, gs = _f64(af), _f64(e), _f64(gs)
+    B, F, M = af.shape
+    T = e.shape[1]
+    assert F == framewise_frames(T, hop) and e.shape == (B, T)
+    s = np.empty((B, T), np.float64)
+    ge = np.empty((B, T), np.float64) if gs is not None else None
+    gaf = np.empty((B, F, M), np.float64) if gs is not None else None
+    lib.tvlp_oracle_framewise_batch(B, T, M, hop, _ptr(af), _ptr(e), _ptr(gs), _ptr(s), _ptr(ge), _ptr(gaf))
+    return s if gs is None else (s, ge, gaf)

@@ -21,6 +21,7 @@
  * Sample count: the paper indexes samples 0..T (T+1 samples, Sec. 2.2);
  * here a signal has T samples indexed 0..T-1.
  */
+#include <math.h>
 #include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -225,4 +226,120 @@ void tvlp_oracle_coeffs_adjoint_batch(int64_t B, int64_t T, int M, int hop,
     for (int64_t b = 0; b < B; ++b)
         tvlp_oracle_coeffs_adjoint(T, M, hop, k + b * F * M, ga + b * T * M,
                                    gk + b * F * M);
+}
+
+/*
+ * Frame-wise approximation of Eq. 5 (Sec. 3.2, the method of the earlier
+ * GOLF work that the sample-wise filter replaces; Sec. 4 uses 75 % overlap).
+ * The signal is cut into frames of N = 4*hop samples, one every hop
+ * samples; frame f covers samples t_f .. t_f + N - 1 with t_f = (f - 3)*hop,
+ * so with F = ceil(T/hop) + 3 frames every sample lies in exactly four.
+ * Each frame:
+ *   u_f(n) = w(n) e(t_f + n)                  (e = 0 outside 0..T-1)
+ *   y_f(n) = u_f(n) - sum_{i=1..M} af_i y_f(n-i),  y_f(n < 0) = 0
+ * i.e. the time-invariant filter of Eq. 2 with the frame's coefficients
+ * af [F][M], run from zero state over the frame; the outputs overlap-add:
+ *   s(t) = sum_f y_f(t - t_f)   over the frames with 0 <= t - t_f < N.
+ * w(n) = (1 - cos(2 pi n / N)) / 4, a periodic Hann window scaled so that
+ * the four windows over any sample sum to one.  (The paper states the
+ * per-frame filtering and the overlap; frame length, window and where it
+ * is applied are this build's reading.)
+ * y [F][N] may be NULL; it receives the frame outputs.
+ */
+static double ff_window(int64_t n, int64_t N)
+{
+    return 0.25 * (1.0 - cos(2.0 * 3.14159265358979323846 * (double)n / (double)N));
+}
+
+int64_t tvlp_oracle_framewise_frames(int64_t T, int hop)
+{
+    return (T + hop - 1) / hop + 3;
+}
+
+void tvlp_oracle_framewise_forward(int64_t T, int M, int hop, const double *af,
+                                   const double *e, double *s, double *y)
+{
+    const int64_t N = 4 * (int64_t)hop;
+    const int64_t F = tvlp_oracle_framewise_frames(T, hop);
+    double *yf = malloc(sizeof(double) * (size_t)N);
+    for (int64_t t = 0; t < T; ++t)
+        s[t] = 0.0;
+    for (int64_t f = 0; f < F; ++f) {
+        const int64_t t0 = (f - 3) * hop;
+        for (int64_t n = 0; n < N; ++n) {
+            const int64_t t = t0 + n;
+            double acc = (t >= 0 && t < T) ? ff_window(n, N) * e[t] : 0.0;
+            for (int i = 1; i <= M; ++i)
+                if (n - i >= 0)
+                    acc -= af[f * M + (i - 1)] * yf[n - i];
+            yf[n] = acc;
+            if (t >= 0 && t < T)
+                s[t] += acc;
+            if (y)
+                y[f * N + n] = acc;
+        }
+    }
+    free(yf);
+}
+
+/*
+ * Its adjoint for dL/ds = gs: the overlap-add hands every frame
+ * g_f(n) = gs(t_f + n); Eq. 11 with the frame's constant coefficients runs
+ * backwards over the frame from a zero state past its end,
+ *   gu_f(n) = g_f(n) - sum_{i=1..M} af_i gu_f(n+i),  gu_f(n >= N) = 0,
+ * the window and the framing send it back to the excitation,
+ *   ge(t) = sum_f w(t - t_f) gu_f(t - t_f),
+ * and Eq. 12 summed over the frame (Eq. 3) gives the frame's coefficients
+ *   gaf_i = -sum_n gu_f(n) y_f(n - i),  y_f(n < 0) = 0.
+ * y [F][N] are the forward's frame outputs.
+ */
+void tvlp_oracle_framewise_backward(int64_t T, int M, int hop, const double *af,
+                                    const double *y, const double *gs,
+                                    double *ge, double *gaf)
+{
+    const int64_t N = 4 * (int64_t)hop;
+    const int64_t F = tvlp_oracle_framewise_frames(T, hop);
+    double *gu = malloc(sizeof(double) * (size_t)N);
+    for (int64_t t = 0; t < T; ++t)
+        ge[t] = 0.0;
+    for (int64_t f = 0; f < F; ++f) {
+        const int64_t t0 = (f - 3) * hop;
+        for (int64_t n = N - 1; n >= 0; --n) {
+            const int64_t t = t0 + n;
+            double acc = (t >= 0 && t < T) ? gs[t] : 0.0;
+            for (int i = 1; i <= M; ++i)
+                if (n + i < N)
+                    acc -= af[f * M + (i - 1)] * gu[n + i];
+            gu[n] = acc;
+            if (t >= 0 && t < T)
+                ge[t] += ff_window(n, N) * acc;
+        }
+        for (int i = 1; i <= M; ++i) {
+            double g = 0.0;
+            for (int64_t n = i; n < N; ++n)
+                g -= gu[n] * y[f * N + (n - i)];
+            gaf[f * M + (i - 1)] = g;
+        }
+    }
+    free(gu);
+}
+
+/* Batched: af / gaf [B][F][M], e / s / gs / ge [B][T], y [B][F][N]. */
+void tvlp_oracle_framewise_batch(int64_t B, int64_t T, int M, int hop,
+                                 const double *af, const double *e,
+                                 const double *gs, double *s, double *ge,
+                                 double *gaf)
+{
+    const int64_t N = 4 * (int64_t)hop;
+    const int64_t F = tvlp_oracle_framewise_frames(T, hop);
+    double *y = malloc(sizeof(double) * (size_t)(F * N));
+    for (int64_t b = 0; b < B; ++b) {
+        tvlp_oracle_framewise_forward(T, M, hop, af + b * F * M, e + b * T,
+                                      s + b * T, y);
+        if (gs)
+            tvlp_oracle_framewise_backward(T, M, hop, af + b * F * M, y,
+                                           gs + b * T, ge + b * T,
+                                           gaf + b * F * M);
+    }
+    free(y);
 }

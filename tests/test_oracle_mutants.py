@@ -15,6 +15,7 @@ import pytest
 
 import oracle as O
 from tests import test_oracle_coeff_pins as C
+from tests import test_oracle_framewise_pins as FW
 from tests import test_oracle_pins as P
 
 SRC = open(os.path.join(os.path.dirname(O.__file__), "tvlp_oracle.c")).read()
@@ -68,6 +69,18 @@ MUTANTS = {
     "adjoint of the interpolation swaps the weights":
         ("            gk[f * M + (j - 1)] += (1.0 - w) * g;\n            gk[(f + 1) * M + (j - 1)] += w * g;",
          "            gk[f * M + (j - 1)] += w * g;\n            gk[(f + 1) * M + (j - 1)] += (1.0 - w) * g;"),
+    # frame-wise overlap-add approximation
+    "frame-wise window not scaled to sum to one":
+        ("return 0.25 * (1.0 - cos(", "return 0.5 * (1.0 - cos("),
+    "frame-wise frames start one hop late":
+        ("const int64_t t0 = (f - 3) * hop;\n        for (int64_t n = 0; n < N; ++n) {",
+         "const int64_t t0 = (f - 2) * hop;\n        for (int64_t n = 0; n < N; ++n) {"),
+    "frame-wise filter drops the order-M term":
+        ("                if (n - i >= 0)\n                    acc -= af", "                if (n - i >= 0 && i < M)\n                    acc -= af"),
+    "frame-wise adjoint without the window":
+        ("ge[t] += ff_window(n, N) * acc;", "ge[t] += acc;"),
+    "frame-wise coefficient gradient lag off by one":
+        ("g -= gu[n] * y[f * N + (n - i)];", "g -= gu[n] * y[f * N + (n - i + 1)];"),
 }
 
 PINS = [
@@ -88,6 +101,11 @@ PINS = [
     (C.test_stable_reflection_coefficients_give_minimum_phase, {"M": 10}),
     (C.test_adjoint_finite_differences, {"M": 3, "T": 13, "hop": 4}),
     (C.test_adjoint_closed_form_m1, {}),
+    (FW.test_zero_coefficients_identity, {}),
+    (FW.test_frames_are_lfilter, {"M": 4}),
+    (FW.test_m1_impulse_closed_form, {}),
+    (FW.test_adjoint_finite_differences, {}),
+    (FW.test_adjoint_dot_product_identity, {}),
 ]
 
 
@@ -96,7 +114,7 @@ def _build_mutant(tmp_path, name, old, new):
     src = tmp_path / "mutant.c"
     src.write_text(SRC.replace(old, new, 1))
     so = tmp_path / "libmutant.so"
-    subprocess.run(["gcc", *O.CFLAGS, str(src), "-o", str(so)], check=True)
+    subprocess.run(["gcc", *O.CFLAGS, str(src), "-o", str(so), *O.LDLIBS], check=True)
     return O.load_library(str(so))
 
 
