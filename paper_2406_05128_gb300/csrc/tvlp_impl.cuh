@@ -1,5 +1,7 @@
 // Host launchers of the time-varying LP kernels for one (scalar, MP) pair.
 #pragma once
+#include <atomic>
+
 #include "tvlp_impl.h"
 #include "tvlp_kernels.cuh"
 
@@ -42,15 +44,17 @@ inline cudaError_t launch(void (*kern)(Exp...), dim3 grid, dim3 block, size_t sm
     return cudaLaunchKernelEx(&cfg, kern, static_cast<Exp>(args)...);
 }
 
-// cudaFuncSetAttribute once per kernel and device.
-template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes, bool *done) {
+// cudaFuncSetAttribute once per kernel and device.  Host threads may race
+// on the first call: the flags are atomics, and setting the same attribute
+// twice is harmless.
+template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<bool> *done) {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (done[dev]) return cudaSuccess;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (err == cudaSuccess) done[dev] = true;
+    if (err == cudaSuccess) done[dev].store(true, std::memory_order_release);
     return err;
 }
 
@@ -108,7 +112,7 @@ template <typename S, int MP> struct Launch {
     template <bool BWD, int SRC = SRC_STREAM>
     static cudaError_t summary(const Problem &p, const Batch &bt, const S *a, const S *u, S *Y, unsigned *cnt,
                                cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
-        static bool done[kMaxDevices] = {};
+        static std::atomic<bool> done[kMaxDevices] = {};
         const int W = k1_warps_per_block<S, MP>();
         const size_t smem = (size_t)W * GE::WARP_BYTES;
         auto kern = k1_summary<S, MP, GE::G, GE::R, BWD, SRC>;
@@ -119,16 +123,20 @@ template <typename S, int MP> struct Launch {
         // the next pass (re-run or adjoint re-run) starts on this pass's first stages
         const int l2 = SRC == SRC_STREAM ? l2_word(l2_keep(p), L2_LAST, L2_FIRST) : 0;
         return launch(kern, dim3((unsigned)grid), dim3(32 * W), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Y,
-                      p.M == MP ? 1 : 0, cnt, p.B, l2, p.status, cs);
+                      p.M == MP ? 1 : 0, cnt, p.B + 1, l2, p.status, cs);
     }
 
     // Two-level scan in one cooperative launch: as many blocks as the items
     // need, at most as many as fit on the device at once.
+    static int *fix_list(const Problem &p, void *ws) {
+        return reinterpret_cast<int *>(static_cast<char *>(ws) + ws_offset(p, sizeof(S), 9));
+    }
+
     template <int MODE>
     static cudaError_t scan(const Problem &p, const Batch &bt, const S *Y, const S *Z, S *GY, S *GZ, S *GX,
-                            const S *zi, S *X, S *ckpt, unsigned *cnt, cudaStream_t st) {
-        static bool done[kMaxDevices] = {};
-        static int resident[kMaxDevices] = {};
+                            const S *zi, S *X, S *ckpt, unsigned *cnt, cudaStream_t st, int *list = nullptr) {
+        static std::atomic<bool> done[kMaxDevices] = {};
+        static std::atomic<int> resident[kMaxDevices] = {};
         using SG = ScanGeo<S, MP>;
         auto kern = k2_scan<S, MP, MODE>;
         const size_t smem = (size_t)kScanWarps * SG::WARP_BYTES;
@@ -136,28 +144,30 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         int dev = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-        if (resident[dev] == 0) {
+        int res = resident[dev].load(std::memory_order_relaxed);
+        if (res == 0) {
             int per_sm = 0, sms = 0;
             if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScanWarps * 32, smem)) !=
                 cudaSuccess)
                 return err;
             if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
             if (per_sm < 1) return cudaErrorInvalidConfiguration;
-            resident[dev] = per_sm * sms;
+            res = per_sm * sms;
+            resident[dev].store(res, std::memory_order_relaxed);
         }
         const int64_t items = p.items;
         int64_t blocks = (items + kScanWarps - 1) / kScanWarps;
-        if (blocks > resident[dev]) blocks = resident[dev];
+        if (blocks > res) blocks = res;
         return launch(kern, dim3((unsigned)blocks), dim3(kScanWarps * 32), smem, st, true, bt, p.M, items, Y, Z, GY,
-                      GZ, GX, zi, X, ckpt, cnt, p.status);
+                      GZ, GX, zi, X, ckpt, cnt, p.status, list);
     }
 
     template <int MODE, bool EXACT, int SRC = SRC_STREAM>
     static cudaError_t rec_exact(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin,
                                  const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
                                  cudaStream_t st, const CoefSrc &cs = CoefSrc(), const S *sfw = nullptr,
-                                 S *ga = nullptr) {
-        static bool done[kMaxDevices] = {};
+                                 S *ga = nullptr, const Fix<S> &fx = Fix<S>()) {
+        static std::atomic<bool> done[kMaxDevices] = {};
         constexpr int RC = RecChunks<SRC>::N;
         using RG = RecGeo<S, MP, RC>;
         auto kern = k_rec<S, MP, EXACT, MODE, SRC>;
@@ -166,7 +176,7 @@ template <typename S, int MP> struct Launch {
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + RC - 1) / RC;
         return launch(kern, dim3((unsigned)grid), dim3(32), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
-                      out, Zout, gzi, reverse, cnt, p.B, l2, xs, p.status, cs, sfw, ga);
+                      out, Zout, gzi, reverse, cnt, p.B + 1, l2, xs, p.status, cs, sfw, ga, fx);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that
@@ -174,16 +184,20 @@ template <typename S, int MP> struct Launch {
     template <int MODE>
     static cudaError_t rec(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin, const S *zi,
                            S *out, S *Zout, S *gzi, int reverse, cudaStream_t st, unsigned *cnt = nullptr, int l2 = 0,
-                           int xs = MP) {
-        if (p.M == MP) return rec_exact<MODE, true>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
-        return rec_exact<MODE, false>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st);
+                           int xs = MP, const Fix<S> &fx = Fix<S>()) {
+        if (p.M == MP)
+            return rec_exact<MODE, true>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st, CoefSrc(),
+                                         nullptr, nullptr, fx);
+        return rec_exact<MODE, false>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st, CoefSrc(),
+                                      nullptr, nullptr, fx);
     }
 
     // the adjoint re-run that also writes Eq. 12's ga (M == MP only)
     static cudaError_t rec_grad(const Problem &p, const Batch &bt, const S *a, const S *gs, const S *Win, const S *zi,
-                                const S *s, S *ge, S *ga, S *gzi, cudaStream_t st, int l2) {
+                                const S *s, S *ge, S *ga, S *gzi, cudaStream_t st, int l2,
+                                const Fix<S> &fx = Fix<S>()) {
         return rec_exact<BWD_GRAD, true>(p, bt, a, gs, Win, zi, ge, nullptr, gzi, 1, nullptr, l2, MP, st, CoefSrc(), s,
-                                         ga);
+                                         ga, fx);
     }
 
     // the same with generated coefficient rows (rows are written whole, so
@@ -191,8 +205,9 @@ template <typename S, int MP> struct Launch {
     template <int MODE, int SRC>
     static cudaError_t rec_gen(const Problem &p, const Batch &bt, const S *u, const S *Xin, const S *zi, S *out,
                                S *Zout, S *gzi, int reverse, cudaStream_t st, const CoefSrc &cs,
-                               unsigned *cnt = nullptr) {
-        return rec_exact<MODE, true, SRC>(p, bt, nullptr, u, Xin, zi, out, Zout, gzi, reverse, cnt, 0, MP, st, cs);
+                               unsigned *cnt = nullptr, const Fix<S> &fx = Fix<S>()) {
+        return rec_exact<MODE, true, SRC>(p, bt, nullptr, u, Xin, zi, out, Zout, gzi, reverse, cnt, 0, MP, st, cs,
+                                          nullptr, nullptr, fx);
     }
 
     static cudaError_t grad_a(const Problem &p, const Batch &bt, const S *ge, const S *s, const S *zi, S *ga,
@@ -239,6 +254,33 @@ inline cudaError_t build_tables(const Problem &p, const Batch &bt, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Defect correction of the chunked scan (see Fix in the kernels): FP32
+// calls whose signals have chunk boundaries.  Pass 1 writes the defects
+// into the adjoint zero-state region Z (free in a forward, consumed by the
+// adjoint's main scan before its pass 1) and each signal's output scale
+// into its counter line; the correction scan writes the corrections into a
+// state region the call no longer needs (forward: the adjoint's W;
+// adjoint: the forward's X).
+template <typename S> inline bool refines(const Problem &p) {
+    return sizeof(S) == 4 && p.NQ > 0 && (p.off != nullptr || p.nC > 1);
+}
+template <typename S> inline Fix<S> fix_pass1(S *D, unsigned *cnt) {
+    Fix<S> f;
+    f.D = D;
+    f.scale = cnt;
+    return f;
+}
+template <typename S> inline Fix<S> fix_pass2(const Problem &p, const S *E, unsigned *cnt, const int *list,
+                                              S *ckpt = nullptr) {
+    Fix<S> f;
+    f.E = E;
+    f.scale = cnt;
+    f.ckpt = ckpt;
+    f.list = list;
+    f.list_n = cnt + (size_t)p.B * kCntStride;
+    return f;
+}
+
 template <typename S, int MP>
 int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, S *s, S *ckpt, int algo,
                          void *ws, cudaStream_t st) {
@@ -262,8 +304,18 @@ int Impl<S, MP>::forward(const Problem &p, const S *a, const S *e, const S *zi, 
     // keeps its last stages for an adjoint pass, which walks the chunks the
     // other way
     const int keep = LN::l2_keep(p), nblk = p.L / SRS;
+    const bool fix = refines<S>(p);
+    S *D = LN::region(p, ws, 2), *E = LN::region(p, ws, 3);
     TVLP_LAUNCH(2, (LN::template rec<FWD_RERUN>(p, bt, a, e, X, zi, s, nullptr, nullptr, 1, st, nullptr,
-                                                l2_word(keep, L2_FIRST, L2_FIRST, nblk - keep, L2_LAST))));
+                                                l2_word(keep, L2_FIRST, L2_FIRST, nblk - keep, L2_LAST), MP,
+                                                fix ? fix_pass1<S>(D, cnt) : Fix<S>())));
+    if (fix) {
+        int *list = LN::fix_list(p, ws);
+        TVLP_LAUNCH(3, (LN::template scan<CH_FWD_FIX>(p, bt, Y, D, GY, LN::region(p, ws, 5), GX, nullptr, E, nullptr,
+                                                      cnt, st, list)));
+        TVLP_LAUNCH(4, (LN::template rec<FWD_RERUN>(p, bt, a, e, X, zi, s, nullptr, nullptr, 1, st, nullptr, 0, MP,
+                                                    fix_pass2<S>(p, E, cnt, list, ckpt))));
+    }
     return OK;
 }
 
@@ -313,12 +365,24 @@ int Impl<S, MP>::backward(const Problem &p, const S *gs, const S *a, const S *s,
             TVLP_LAUNCH(k++,
                         (LN::template scan<CH_BWD>(p, bt, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt, st)));
         }
-        if (fused_ga) {
-            // the re-run writes ga as it goes (Eq. 12 from its own ge)
-            TVLP_LAUNCH(k++, (LN::rec_grad(p, bt, a, gs, Wst, zi, s, ge, ga, gzi, st, l2_word(0, L2_FIRST, L2_FIRST))));
-        } else {
-            TVLP_LAUNCH(k++, (LN::template rec<BWD_RERUN>(p, bt, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st,
-                                                          nullptr, l2_word(0, L2_FIRST, L2_FIRST))));
+        const bool fix = refines<S>(p);
+        S *E = LN::region(p, ws, 1);
+        auto rerun = [&](const Fix<S> &fx, int l2) -> cudaError_t {
+            // with fused_ga the re-run writes ga as it goes (Eq. 12 from its own ge)
+            if (fused_ga) return LN::rec_grad(p, bt, a, gs, Wst, zi, s, ge, ga, gzi, st, l2, fx);
+            return LN::template rec<BWD_RERUN>(p, bt, a, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, nullptr, l2, MP,
+                                               fx);
+        };
+        TVLP_LAUNCH(k++, (rerun(fix ? fix_pass1<S>(Z, cnt) : Fix<S>(), l2_word(0, L2_FIRST, L2_FIRST))));
+        if (fix) {
+            int *list = LN::fix_list(p, ws);
+            if (flags & BWD_REUSE_FORWARD)
+                TVLP_LAUNCH(k++, (LN::template scan<CH_TRANS_FIX>(p, bt, Y, Z, GY, GZ, GX, nullptr, E, nullptr, cnt,
+                                                                  st, list)));
+            else
+                TVLP_LAUNCH(k++, (LN::template scan<CH_BWD_FIX>(p, bt, Y, Z, GY, GZ, GX, nullptr, E, nullptr, cnt,
+                                                                st, list)));
+            TVLP_LAUNCH(k++, (rerun(fix_pass2<S>(p, E, cnt, list), 0)));
         }
     }
     if (ga != nullptr && !fused_ga) TVLP_LAUNCH(k, (LN::grad_a(q, bt, ge, s, zi, ga, st)));
@@ -341,15 +405,25 @@ int forward_gen_src(const Problem &p, const CoefSrc &src, const S *e, const S *z
     unsigned *cnt = LN::counters(p, ws);
     TVLP_LAUNCH(0, (LN::template summary<false, SRC>(p, bt, nullptr, e, Y, cnt, st, src)));
     TVLP_LAUNCH(1, (LN::template scan<CH_FWD>(p, bt, Y, nullptr, GY, nullptr, GX, zi, X, ckpt, cnt, st)));
-    if (src.cache != nullptr) {
-        // the summary pass left every generated row in the cache: stream it
-        const int keep = LN::l2_keep(p), nblk = p.L / SRS;
-        TVLP_LAUNCH(2, (LN::template rec_exact<FWD_RERUN, true>(p, bt, src.cache, e, X, zi, s, nullptr, nullptr, 1,
-                                                                nullptr, l2_word(keep, L2_FIRST, L2_FIRST,
-                                                                                 nblk - keep, L2_LAST),
-                                                                MP, st)));
-    } else {
-        TVLP_LAUNCH(2, (LN::template rec_gen<FWD_RERUN, SRC>(p, bt, e, X, zi, s, nullptr, nullptr, 1, st, src)));
+    auto rerun = [&](const Fix<S> &fx, bool first) -> cudaError_t {
+        if (src.cache != nullptr) {
+            // the summary pass left every generated row in the cache: stream it
+            const int keep = LN::l2_keep(p), nblk = p.L / SRS;
+            return LN::template rec_exact<FWD_RERUN, true>(
+                p, bt, src.cache, e, X, zi, s, nullptr, nullptr, 1, nullptr,
+                first ? l2_word(keep, L2_FIRST, L2_FIRST, nblk - keep, L2_LAST) : 0, MP, st, CoefSrc(), nullptr,
+                nullptr, fx);
+        }
+        return LN::template rec_gen<FWD_RERUN, SRC>(p, bt, e, X, zi, s, nullptr, nullptr, 1, st, src, nullptr, fx);
+    };
+    const bool fix = refines<S>(p);
+    S *D = LN::region(p, ws, 2), *E = LN::region(p, ws, 3);
+    TVLP_LAUNCH(2, (rerun(fix ? fix_pass1<S>(D, cnt) : Fix<S>(), true)));
+    if (fix) {
+        int *list = LN::fix_list(p, ws);
+        TVLP_LAUNCH(3, (LN::template scan<CH_FWD_FIX>(p, bt, Y, D, GY, LN::region(p, ws, 5), GX, nullptr, E, nullptr,
+                                                      cnt, st, list)));
+        TVLP_LAUNCH(4, (rerun(fix_pass2<S>(p, E, cnt, list, ckpt), false)));
     }
     return OK;
 }
@@ -385,12 +459,25 @@ int backward_gen_src(const Problem &p, const CoefSrc &src, const S *gs, const S 
         TVLP_LAUNCH(k++, (LN::template scan<CH_BWD>(p, bt, Y, nullptr, GY, nullptr, GX, nullptr, Wst, nullptr, cnt,
                                                     st)));
     }
-    if (rows != nullptr) {
-        TVLP_LAUNCH(k++, (LN::template rec_exact<BWD_RERUN, true>(p, bt, rows, gs, Wst, nullptr, ge, nullptr, gzi, 1,
-                                                                  nullptr, l2_word(0, L2_FIRST, L2_FIRST), MP, st)));
-    } else {
-        TVLP_LAUNCH(k++,
-                    (LN::template rec_gen<BWD_RERUN, SRC>(p, bt, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, src)));
+    auto rerun = [&](const Fix<S> &fx, int l2) -> cudaError_t {
+        if (rows != nullptr)
+            return LN::template rec_exact<BWD_RERUN, true>(p, bt, rows, gs, Wst, nullptr, ge, nullptr, gzi, 1, nullptr,
+                                                           l2, MP, st, CoefSrc(), nullptr, nullptr, fx);
+        return LN::template rec_gen<BWD_RERUN, SRC>(p, bt, gs, Wst, nullptr, ge, nullptr, gzi, 1, st, src, nullptr,
+                                                     fx);
+    };
+    const bool fix = refines<S>(p);
+    S *E = LN::region(p, ws, 1);
+    TVLP_LAUNCH(k++, (rerun(fix ? fix_pass1<S>(Z, cnt) : Fix<S>(), l2_word(0, L2_FIRST, L2_FIRST))));
+    if (fix) {
+        int *list = LN::fix_list(p, ws);
+        if (flags & BWD_REUSE_FORWARD)
+            TVLP_LAUNCH(k++,
+                        (LN::template scan<CH_TRANS_FIX>(p, bt, Y, Z, GY, GZ, GX, nullptr, E, nullptr, cnt, st, list)));
+        else
+            TVLP_LAUNCH(k++,
+                        (LN::template scan<CH_BWD_FIX>(p, bt, Y, Z, GY, GZ, GX, nullptr, E, nullptr, cnt, st, list)));
+        TVLP_LAUNCH(k++, (rerun(fix_pass2<S>(p, E, cnt, list), 0)));
     }
     return OK;
 }
@@ -431,11 +518,12 @@ int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, con
         if (src.kind == SRC_CONST) {
             if (p.off != nullptr) return EUNSUPPORTED;
             const int64_t tiles = (p.T + kGradRows - 1) / kGradRows;
-            // profiling slots 3 and 4: after the adjoint's three kernels
-            TVLP_LAUNCH(3, (launch(k_grad_const<MP>, dim3((unsigned)tiles, (unsigned)p.B), dim3(kGradThreads), 0, st,
+            // profiling slots 5 and 6: after the adjoint's kernels (three,
+            // and the two of the defect correction)
+            TVLP_LAUNCH(5, (launch(k_grad_const<MP>, dim3((unsigned)tiles, (unsigned)p.B), dim3(kGradThreads), 0, st,
                                    false, p.T, p.M, tiles, ge, s, zi, sc)));
             const int64_t n = (int64_t)p.B * p.M;
-            TVLP_LAUNCH(4, (launch(k_grad_const_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, p.B,
+            TVLP_LAUNCH(6, (launch(k_grad_const_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, p.B,
                                    p.M, MP, tiles, sc, gk)));
             return OK;
         }
@@ -445,10 +533,10 @@ int Impl<S, MP>::grad_src(const Problem &p, const CoefSrc &src, const S *ge, con
             const int64_t items = p.off != nullptr ? src.F : (int64_t)p.B * src.F;
             const int64_t n = items * p.M;
             float *lo = sc, *hi = sc + n;
-            TVLP_LAUNCH(3, (launch(k_grad_frames<MP>, dim3((unsigned)((items + FG::WARPS - 1) / FG::WARPS)),
+            TVLP_LAUNCH(5, (launch(k_grad_frames<MP>, dim3((unsigned)((items + FG::WARPS - 1) / FG::WARPS)),
                                    dim3(32 * FG::WARPS), 0, st, false, p.B, p.T, p.M, src.F, src.hop, src.inv_hop,
                                    src.k, ge, s, zi, lo, hi, p.off, src.foff)));
-            TVLP_LAUNCH(4, (launch(k_grad_frames_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, n,
+            TVLP_LAUNCH(6, (launch(k_grad_frames_finish, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, false, n,
                                    lo, hi, gk)));
             return OK;
         }

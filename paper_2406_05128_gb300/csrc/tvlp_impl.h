@@ -101,10 +101,13 @@ enum { BWD_REUSE_FORWARD = 1, BWD_FUSED_GA = 2 };
 //   4 GY [B*nG][YS]   group maps of the two-level scan
 //   5 GZ [B*nG][ZS]   adjoint group zero-state summaries
 //   6 GX [B*nG][ZS]   incoming state of every group
-//   7 CNT [B][32]     scan progress per signal (unsigned, one 128-byte
+//   7 CNT [B+1][32]   scan progress per signal (unsigned, one 128-byte
 //                     line each), zeroed by the kernel before each scan
 //   8 TAB [2][B+1]    varlen: first chunk and first scan group of every
 //                     signal (int), built at the start of each call
+//   9 LIST [NQ]       defect correction: the chunks pass 2 re-runs (int);
+//                     their count is word 0 of a counter line after the
+//                     signals' (CNT holds B+1 lines)
 // Group regions hold p.items rows.
 inline size_t rs_elems(int MP, size_t sz) { return (((size_t)MP * sz + 15) / 16) * 16 / sz; }
 inline size_t ys_elems(int MP, size_t sz) { return (size_t)(MP + 1) * rs_elems(MP, sz); }
@@ -112,16 +115,16 @@ inline size_t zs_elems(int MP, size_t sz) { return rs_elems(MP, sz); }
 inline size_t ws_offset(const Problem &p, size_t sz, int region) {
     const size_t items = (size_t)p.items;
     const size_t tab = p.off != nullptr ? 2 * ((size_t)p.B + 1) * sizeof(int) : 0;
-    const size_t rows[9] = {(size_t)p.NQ * ys_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
-                            (size_t)p.NQ * zs_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
-                            items * ys_elems(p.MP, sz),            items * zs_elems(p.MP, sz),
-                            items * zs_elems(p.MP, sz),            ((size_t)p.B * 32 * sizeof(unsigned) + sz - 1) / sz,
-                            (tab + sz - 1) / sz};
+    const size_t rows[10] = {(size_t)p.NQ * ys_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
+                             (size_t)p.NQ * zs_elems(p.MP, sz),     (size_t)p.NQ * p.MP,
+                             items * ys_elems(p.MP, sz),            items * zs_elems(p.MP, sz),
+                             items * zs_elems(p.MP, sz),            (((size_t)p.B + 1) * 32 * sizeof(unsigned) + sz - 1) / sz,
+                             (tab + sz - 1) / sz,                   ((size_t)p.NQ * sizeof(int) + sz - 1) / sz};
     size_t off = 0;
     for (int r = 0; r < region; ++r) off += align256(rows[r] * sz);
     return off;
 }
-inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 9); }
+inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 10); }
 
 // Records the caller's profiling event for kernel k (begin or end) when a
 // hook is installed on this thread (lp_tv_set_profile_events).

@@ -836,9 +836,11 @@ __global__ void __launch_bounds__(256, 1)
         }
         cp_async_wait<1>();
         if (!mbar_wait_warp(bars + slot, (k >> 1) & 1, kWaitLimit)) {
-            // a bulk copy never completed: record it, give the copy this warp
-            // still has in flight a bounded chance to land, and leave
+            // a bulk copy never completed: record it, give the copies this
+            // warp still has in flight (the late one and the next stage's) a
+            // bounded chance to land, and leave
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+            mbar_wait_warp(bars + slot, (k >> 1) & 1, kWaitLimit);
             if (more) mbar_wait_warp(bars + (slot ^ 1), ((k + 1) >> 1) & 1, kWaitLimit);
             cp_async_wait<0>();
             if (SRC != SRC_STREAM && cs.cache != nullptr) bulk_wait_all();
@@ -985,6 +987,51 @@ __global__ void __launch_bounds__(256, 1)
 // ---------------------------------------------------------------------------
 enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2, BWD_GRAD = 3 };
 
+// Defect correction of the chunked scan (FP32).  The chunk transfers P_c
+// come from M recursions in FP32, whose rounding on resonant filters is
+// amplified along the chain of chunk states well beyond the rounding of
+// the sequential recursion.  One correction sweep removes that excess:
+//   pass 1  the re-run from the scanned state x_c reaches the chunk's end
+//           state by the sequential recursion itself; its defect against
+//           the scanned state of the next chunk is d_c (forward:
+//           d_c = x_end(c) - x_{c+1}; adjoint: d_c = w_start(c) - w_{c-1});
+//   scan    the error of the scanned states obeys the same linear
+//           recurrence with the defects as its input,
+//           e_{c+1} = P_c e_c + d_c  (adjoint: e_{c-1} = P_c^T e_c + d_c);
+//   pass 2  every chunk whose correction is not negligible,
+//           max|e_c| > kFixTheta * max_t |out(t)| of its signal, re-runs
+//           from x_c + e_c and writes its outputs again.
+// The error of e_c itself is second order (e_c is already a small
+// multiple of the rounding), so the result has the rounding of the
+// sequential recursion.  A signal whose outputs are not finite is never
+// corrected (the comparisons fail), and neither is a chunk whose
+// correction is below the threshold: skipping it changes the result by
+// less than the threshold times the chunk's gain.  The decisions depend on
+// the signal's own values only, so batching leaves them unchanged.
+constexpr float kFixTheta = 2.5e-7f;
+constexpr int kScaleWord = 16;  // per-signal max |output| (float bits) in the signal's counter line
+
+template <typename S> struct Fix {
+    S *D = nullptr;             // pass 1: defect of every chunk, stride ZS (zero where none)
+    const S *E = nullptr;       // pass 2: correction of every chunk's incoming state, stride MP
+    S *ckpt = nullptr;          // pass 2, forward: corrected incoming state of re-run chunks [q][M]
+    unsigned *scale = nullptr;  // counter lines; word kScaleWord of line b = max |out| of signal b
+    // pass 2: the chunks to re-run, in the order the correction scan listed
+    // them, and their count (the word after the signals' counter lines)
+    const int *list = nullptr;
+    const unsigned *list_n = nullptr;
+};
+
+__device__ __forceinline__ float scale_of(const unsigned *scale, int64_t b) {
+    return __uint_as_float(__ldcg(scale + b * kCntStride + kScaleWord));
+}
+// max of |y| that keeps a NaN (fmax would drop it): a signal with any
+// non-finite output gets an infinite scale and is never corrected
+template <typename S> __device__ __forceinline__ S abs_max_nan(S m, S y) {
+    const S a = fabs(y);
+    return (a > m || a != a) ? a : m;
+}
+
 constexpr int kRecChunks = 16;  // chunks per warp (lanes 0 .. kRecChunks-1 own one each)
 // chunks per warp when the rows are generated: half the shared ring per
 // warp, so twice the warps fit on an SM to hide the generator's latency
@@ -1082,7 +1129,7 @@ __global__ void __launch_bounds__(32)
     k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
           S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
-          int *__restrict__ status, CoefSrc cs, const S *__restrict__ sfw, S *__restrict__ ga) {
+          int *__restrict__ status, CoefSrc cs, const S *__restrict__ sfw, S *__restrict__ ga, Fix<S> fx) {
     static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
     constexpr int RC = RecChunks<SRC>::N;
     using RG = RecGeo<S, MP, RC>;
@@ -1097,10 +1144,19 @@ __global__ void __launch_bounds__(32)
     // lanes past RC own no chunk; they read (and never write) the ring of
     // lane lane % RC so every shared access stays in range
     const bool owner = lane < RC;
-    const int64_t q = blk * RC + lane;
-    if (bt.off != nullptr) pdl_wait();  // the chunk tables come from a kernel before
+    // the chunk tables (varlen) and the corrections (pass 2 of the defect
+    // correction) come from the kernel before
+    if (bt.off != nullptr || fx.E != nullptr) pdl_wait();
     NQ = batch_chunks(bt, NQ);
-    const bool active = owner && q < NQ;
+    int64_t q = blk * RC + lane;
+    bool active = owner && q < NQ;
+    if (fx.E != nullptr) {
+        // pass 2: the warp takes RC entries of the list of chunks to re-run
+        const int64_t n_list = (int64_t)__ldcg(fx.list_n);
+        if (blk * RC >= n_list) return;
+        active = owner && q < n_list;
+        q = active ? (int64_t)__ldcg(fx.list + q) : 0;
+    }
     S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % RC) * RG::LW * 4);  // [NS][SRS*MP]
     uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)RC * RG::LW * 4);
     // BWD_GRAD: lanes without a chunk read this never-written stage instead
@@ -1143,6 +1199,7 @@ __global__ void __launch_bounds__(32)
     S h[WIN];
 #pragma unroll
     for (int m = 0; m < WIN; ++m) h[m] = S(0);
+    S ym = S(0);  // max |output| of the chunk (defect correction's scale)
     if (active) {
         if constexpr (MODE == FWD_RERUN) {
             // h[MP - j] = s(t0 - j)
@@ -1151,6 +1208,10 @@ __global__ void __launch_bounds__(32)
                 S v = S(0);
                 if (Xin != nullptr) {
                     if (j - 1 < xs) v = Xin[q * xs + (j - 1)];
+                    if (fx.E != nullptr) {
+                        v += fx.E[q * MP + (j - 1)];
+                        if (fx.ckpt != nullptr && j <= M) fx.ckpt[q * M + (j - 1)] = v;
+                    }
                 } else if (zi != nullptr && j <= M) {
                     v = zi[b * M + (j - 1)];
                 }
@@ -1160,8 +1221,10 @@ __global__ void __launch_bounds__(32)
             // h[j - 1] = q_j entering from the chunk's end
             if (Xin != nullptr) {
 #pragma unroll
-                for (int j = 0; j < MP; ++j)
+                for (int j = 0; j < MP; ++j) {
                     if (j < xs) h[j] = Xin[q * xs + j];
+                    if (fx.E != nullptr) h[j] += fx.E[q * MP + j];
+                }
             }
         }
     }
@@ -1197,7 +1260,10 @@ __global__ void __launch_bounds__(32)
             }
         }
         if (!mbar_wait_warp(bars + slot, (s >> 1) & 1, kWaitLimit)) {
+            // as in k1_summary: the late copy and the next stage's get a
+            // bounded chance to land before the warp leaves
             if (lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
+            mbar_wait_warp(bars + slot, (s >> 1) & 1, kWaitLimit);
             if (more) mbar_wait_warp(bars + (slot ^ 1), ((s + 1) >> 1) & 1, kWaitLimit);
             cp_async_wait<0>();
             if constexpr (GA) bulk_wait_all();
@@ -1221,14 +1287,26 @@ __global__ void __launch_bounds__(32)
                 if constexpr (MODE == FWD_RERUN) {
                     const S y0 = fwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * p);
                     const S y1 = fwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * p + 1);
-                    if (roff + r0 < n) out[base + roff + r0] = y0;
-                    if (roff + r0 + 1 < n) out[base + roff + r0 + 1] = y1;
+                    if (roff + r0 < n) {
+                        out[base + roff + r0] = y0;
+                        ym = abs_max_nan(ym, y0);
+                    }
+                    if (roff + r0 + 1 < n) {
+                        out[base + roff + r0 + 1] = y1;
+                        ym = abs_max_nan(ym, y1);
+                    }
                 } else {
                     const S y1 = bwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * pr);
                     const S y0 = bwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * pr + 1);
                     if constexpr (RERUN_B) {
-                        if (roff + r0 + 1 < n) out[base + roff + r0 + 1] = y1;
-                        if (roff + r0 < n) out[base + roff + r0] = y0;
+                        if (roff + r0 + 1 < n) {
+                            out[base + roff + r0 + 1] = y1;
+                            ym = abs_max_nan(ym, y1);
+                        }
+                        if (roff + r0 < n) {
+                            out[base + roff + r0] = y0;
+                            ym = abs_max_nan(ym, y0);
+                        }
                     }
                     // both rows are in registers and no other lane reads
                     // this ring: its rows take ga
@@ -1272,6 +1350,24 @@ __global__ void __launch_bounds__(32)
                 if (j < M) gzi[b * M + j] = h[j];
         }
     }
+    if constexpr (MODE == FWD_RERUN || RERUN_B) {
+        if (fx.D != nullptr) {
+            // pass 1: defect of the state this chunk hands on against the
+            // scanned state of the neighbouring chunk (stride ZS, as z)
+            constexpr int ZS = ((MP * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
+            const int64_t nCb = bt.off == nullptr ? bt.nC : (int64_t)(__ldg(bt.cstart + b + 1) - __ldg(bt.cstart + b));
+            const bool has = BWD ? c >= 1 : c + 1 < nCb;
+            const int64_t qn = BWD ? q - 1 : q + 1;
+#pragma unroll
+            for (int j = 0; j < MP; ++j) {
+                // forward: x_end[j] = h[MP-1-j]; adjoint: w_start[j] = h[j]
+                const S hv = BWD ? h[j] : h[MP - 1 - j];
+                fx.D[q * ZS + j] = has ? hv - Xin[qn * xs + j] : S(0);
+            }
+            const float ymf = (float)ym;
+            atomicMax(fx.scale + b * kCntStride + kScaleWord, __float_as_uint(ymf <= 3.0e38f ? ymf : INFINITY));
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1300,7 +1396,21 @@ __global__ void __launch_bounds__(32)
 // fresh).
 // Chunk map layout (stride YS, rows of RS): Y[0][k] = y[k], Y[r][k] = P[k][r-1].
 // ---------------------------------------------------------------------------
-enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2 };
+enum { CH_FWD = 0, CH_BWD = 1, CH_TRANS = 2, CH_FWD_FIX = 3, CH_TRANS_FIX = 4, CH_BWD_FIX = 5 };
+// The _FIX modes are the correction scans of the defect correction (see
+// Fix): vector scans like CH_TRANS, driven by the chunk defects (passed as
+// Z) instead of zero-state summaries, through the chunk maps and group
+// maps the main scan left in Y and GY (CH_FWD_FIX: the forward's maps,
+// straight; CH_TRANS_FIX: the forward's maps, transposed; CH_BWD_FIX: the
+// adjoint's own maps, straight, backwards).  They run right after a main
+// scan of the same call, whose counters stand at nG + 1 per signal, so
+// their counts start there.
+template <int MODE> struct ScanMode {
+    static constexpr bool REV = MODE == CH_BWD || MODE == CH_TRANS || MODE == CH_TRANS_FIX || MODE == CH_BWD_FIX;
+    static constexpr bool TRANS = MODE == CH_TRANS || MODE == CH_TRANS_FIX;
+    static constexpr bool VEC = MODE >= CH_TRANS;  // vector scan driven by Z, reusing GY
+    static constexpr bool FIX = MODE >= CH_FWD_FIX;
+};
 
 constexpr int kScanWarps = 4;       // warps per block
 constexpr int kScanDepth = 10;      // map slots per warp ring
@@ -1358,9 +1468,9 @@ __device__ __forceinline__ S hop(const S (&p)[MP + 1], S x, int lane) {
 }
 
 // coefficients of the lane's output component for one map held in shared
-// memory: straight (x -> P x + y, map at m) or transposed (w -> P^T w + z,
-// P from the map at m, z at zv)
-template <typename S, int MP, bool TRANS>
+// memory: straight (x -> P x + y, map at m; with DRIVE, x -> P x + z) or
+// transposed (w -> P^T w + z, P from the map at m, z at zv)
+template <typename S, int MP, bool TRANS, bool DRIVE = TRANS>
 __device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv, int j0) {
     constexpr int RS = YGeo<S, MP>::RS;
     if constexpr (TRANS) {
@@ -1385,6 +1495,7 @@ __device__ __forceinline__ void map_cols(S (&p)[MP + 1], const S *m, const S *zv
     } else {
 #pragma unroll
         for (int r = 0; r <= MP; ++r) p[r] = m[r * RS + j0];
+        if constexpr (DRIVE) p[0] = zv[j0];
     }
 }
 
@@ -1622,6 +1733,8 @@ template <typename S, int MP> struct ScanWarp {
         if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT_TMA);
         return ok;
     }
+    // after a wait on `bar` gave up: one more bounded wait for that late copy
+    __device__ void drain(int bar) { mbar_wait_warp(bars + bar, ((phase >> bar) & 1u) ^ 1u, kWaitLimit); }
 };
 
 // Runs step(i, map, z) for i = 0 .. n-1 along a contiguous run of n maps
@@ -1634,7 +1747,10 @@ __device__ __forceinline__ bool run_maps(ScanWarp<S, MP> &W, const S *map_lo, co
     if (n <= 0) return true;
     if (n <= D) {
         W.issue(0, n, map_lo, z_lo, 0);
-        if (!W.wait(0)) return false;
+        if (!W.wait(0)) {
+            W.drain(0);
+            return false;
+        }
         for (int i = 0; i < n; ++i) {
             const int mi = REVR ? n - 1 - i : i;
             step(i, W.map(mi), W.zv(mi));
@@ -1656,6 +1772,7 @@ __device__ __forceinline__ bool run_maps(ScanWarp<S, MP> &W, const S *map_lo, co
     issue(1);
     for (int j = 0; j < nb; ++j) {
         if (!W.wait(j & 1)) {
+            W.drain(j & 1);
             if (j + 1 < nb) W.wait((j + 1) & 1);  // the other half's copy, if any, is in flight
             return false;
         }
@@ -1704,11 +1821,13 @@ template <typename S, int MP, int MODE>
 __global__ void __launch_bounds__(kScanWarps * 32)
     k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
             S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
-            S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status) {
+            S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status,
+            int *__restrict__ fix_list) {
     using SG = ScanGeo<S, MP>;
     constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
-    constexpr bool REV = MODE != CH_FWD;
-    constexpr bool TRANS = MODE == CH_TRANS;
+    constexpr bool REV = ScanMode<MODE>::REV;
+    constexpr bool TRANS = ScanMode<MODE>::TRANS;
+    constexpr bool VEC = ScanMode<MODE>::VEC;
     extern __shared__ __align__(128) unsigned char k2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t)blockIdx.x * kScanWarps + warp;
@@ -1745,16 +1864,18 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         return Y + (sg.cbase + (int64_t)g * sg.G2) * YS;
     };
     auto group_zs = [&](const SigScan &sg, int g) -> const S * {
-        return TRANS ? Z + (sg.cbase + (int64_t)g * sg.G2) * ZS : nullptr;
+        return VEC ? Z + (sg.cbase + (int64_t)g * sg.G2) * ZS : nullptr;
     };
     auto hop_step = [&](const S *m, const S *z, S x) -> S {
         S p[MP + 1];
-        map_cols<S, MP, TRANS>(p, m, z, j0);
+        map_cols<S, MP, TRANS, VEC>(p, m, z, j0);
         return hop_smem<S, MP>(p, xb + ((nhop++) & 1) * RS, x, lane);
     };
-    // bounded wait until signal b's counter reaches `target`
-    auto wait_count = [&](int64_t b, unsigned target) -> bool {
-        return wait_counter(cnt + b * kCntStride, target, lane, status);
+    // bounded wait until signal b's counter reaches `target` (counted from
+    // where the main scan left it, for a correction scan)
+    auto wait_count = [&](int64_t b, const SigScan &sg, unsigned target) -> bool {
+        const unsigned base = ScanMode<MODE>::FIX ? (unsigned)sg.nG + 1u : 0u;
+        return wait_counter(cnt + b * kCntStride, base + target, lane, status);
     };
     // make this warp's global stores visible (also to bulk copies) before
     // bumping signal b's counter
@@ -1774,7 +1895,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         locate(item, b, g, sg);
         const int len = group_len(sg, g);
         bool ok;
-        if constexpr (TRANS) {
+        if constexpr (VEC) {
             S zeta = S(0);
             ok = run_maps<S, MP, REV>(W, group_maps(sg, g), group_zs(sg, g), len,
                                       [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
@@ -1851,7 +1972,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         if (g != 0) continue;
         held = false;
         const int nG = sg.nG;
-        if (!wait_count(b, (unsigned)nG)) return;
+        if (!wait_count(b, sg, (unsigned)nG)) return;
         fence_proxy_async_global();  // the group maps are read by bulk copies
         auto gidx = [&](int n) -> int64_t { return sg.gbase + (REV ? nG - 1 - n : n); };
         S x = S(0);
@@ -1859,7 +1980,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         // groups 0 .. nG-2 along the chain: the signal's group maps
         // [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG) backward
         const int64_t lo = sg.gbase + (REV ? 1 : 0);
-        const bool ok = run_maps<S, MP, REV>(W, GY + lo * YS, TRANS ? GZ + lo * ZS : nullptr, nG - 1,
+        const bool ok = run_maps<S, MP, REV>(W, GY + lo * YS, VEC ? GZ + lo * ZS : nullptr, nG - 1,
                                              [&](int n, const S *m, const S *z) {
                                                  if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
                                                  x = hop_step(m, z, x);
@@ -1877,11 +1998,23 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         SigScan sg;
         locate(item, b, g, sg);
         const int len = group_len(sg, g);
-        if (!wait_count(b, (unsigned)sg.nG + 1u)) return;
+        if (!wait_count(b, sg, (unsigned)sg.nG + 1u)) return;
+        const float fix_bar = ScanMode<MODE>::FIX ? kFixTheta * scale_of(cnt, b) : 0.f;
         auto put = [&](int ci, S x) {
             const int64_t q = sg.cbase + chunk_at(sg, g, len, ci);
             if (lane < MP) X[q * MP + lane] = x;
             if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[q * M + lane] = x;
+            if constexpr (ScanMode<MODE>::FIX) {
+                // list the chunk for pass 2 when its correction is finite and
+                // above the threshold of its (finite) signal
+                float em = lane < MP ? (float)fabs(x) : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) em = abs_max_nan(em, __shfl_xor_sync(0xffffffffu, em, o));
+                if (lane == 0 && em > fix_bar && em <= 3.0e38f) {
+                    const unsigned slot = atomicAdd(cnt + (int64_t)bt.n * kCntStride, 1u);
+                    fix_list[slot] = (int)q;
+                }
+            }
         };
         S x = lane < MP ? __ldcg(GX + item * ZS + lane) : S(0);
         auto step = [&](int i, const S *m, const S *z) {
@@ -1897,7 +2030,7 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         } else {
             // every map of the group but the last along the chain
             const int64_t off = REV ? 1 : 0;
-            const S *zlo = TRANS ? group_zs(sg, g) + off * ZS : nullptr;
+            const S *zlo = VEC ? group_zs(sg, g) + off * ZS : nullptr;
             if (!run_maps<S, MP, REV>(W, group_maps(sg, g) + off * YS, zlo, len - 1, step)) return;
         }
         put(len - 1, x);

@@ -75,6 +75,32 @@ def test_recompute_rebuilds_s_bitwise():
     assert torch.equal(s, s2)
 
 
+def test_recompute_bitwise_with_defect_correction():
+    """Resonant signals (literal generator, |k| <= 0.8) make the forward
+    re-run part of its chunks from corrected states; the checkpoints keep
+    those corrected states, so the recomputed s is still the forward's, bit
+    for bit, and the adjoint from it meets the oracle."""
+    w = inputs.make("ckl", 4, 48000, 22, seed=5, kmax=0.8, gen="literal", excitation="pulse")
+    a, e, gs, _ = _tensors(w)
+    s, ck = ops.lp_tv_forward(a, e, None, ckpt=True)
+    ge, ga, _ = ops.lp_tv_backward_recompute(gs, a, e, ck, None, need_gzi=False)
+    B, T, M = a.shape
+    chunk = _lib.lp_tv_pick_chunk(B, T, M)
+    s2 = torch.full_like(s, float("nan"))
+    ge2 = torch.empty_like(s)
+    ws = ops.workspace(B, T, M, chunk, a.dtype, a.device)
+    _lib.lp_tv_backward_recompute(_lib.LP_DTYPE_F32, B, T, M, gs.data_ptr(), a.data_ptr(), e.data_ptr(),
+                                  ck.data_ptr(), None, s2.data_ptr(), ge2.data_ptr(), None, None, chunk, 0,
+                                  ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert _lib.lp_tv_device_status() == 0
+    assert torch.equal(s, s2)
+    rs, rge, rga, _ = O.forward_backward(w.a, w.e, w.gs, None)
+    assert_close("s", s.cpu().numpy(), rs, TOL_F32)
+    assert_close("ge", ge.cpu().numpy(), rge, TOL_F32)
+    assert_close("ga", ga.cpu().numpy(), rga, TOL_F32)
+
+
 def test_gradcheck_f64_checkpointed():
     """torch.autograd.gradcheck in FP64 at B=2, T=256, M=4 with chunk-state
     checkpointing on (several chunks)."""

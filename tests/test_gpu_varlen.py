@@ -30,9 +30,10 @@ def _built():
     _lib.load()
 
 
-def _signals(lengths, M, seed, zi=True):
-    """One stable-generator workload per signal (float32 arrays)."""
-    ws = [inputs.make("vl", 1, max(n, 1), M, seed=seed + 31 * k, gen="stable", with_zi=zi)
+def _signals(lengths, M, seed, zi=True, gen="stable", kmax=0.95):
+    """One workload per signal (float32 arrays), stable generator by default."""
+    ws = [inputs.make("vl", 1, max(n, 1), M, seed=seed + 31 * k, gen=gen, kmax=kmax, with_zi=zi,
+                      excitation="pulse" if gen == "literal" else "noise")
           for k, n in enumerate(lengths)]
     return [(w.a[0, :n], w.e[0, :n], w.gs[0, :n], None if w.zi is None else w.zi[0]) for w, n in zip(ws, lengths)]
 
@@ -87,6 +88,22 @@ def test_varlen_alone_equals_in_the_mix():
     lengths = [4000, 123, 9000, 2048, 777]
     sig = _signals(lengths, M, seed=77)
     mix = _run(sig, M, chunk=chunk)
+    for k in range(len(sig)):
+        alone = _run([sig[k]], M, chunk=chunk)[0]
+        for x, y in zip(alone, mix[k]):
+            assert np.array_equal(x, y)
+
+
+def test_varlen_alone_equals_in_the_mix_resonant():
+    """Resonant signals (literal generator, |k| <= 0.8), whose chunks the
+    defect correction re-runs: its decisions depend on each signal's own
+    values, so results are still the same bits alone and in the mix, and
+    within the parity bound of the oracle."""
+    M, chunk = 22, 160
+    lengths = [48000, 7000, 30001, 160]
+    sig = _signals(lengths, M, seed=5, gen="literal", kmax=0.8)
+    mix = _run(sig, M, chunk=chunk)
+    _check_oracle(sig, mix)
     for k in range(len(sig)):
         alone = _run([sig[k]], M, chunk=chunk)[0]
         for x, y in zip(alone, mix[k]):
