@@ -1,5 +1,6 @@
 // C ABI of the time-varying LP library: argument checks, chunk selection
 // and dispatch to the per-order instantiations (see include/tvlp.h).
+#include <atomic>
 #include <limits.h>
 #include <stdint.h>
 #include <string.h>
@@ -190,40 +191,45 @@ template <> struct Dispatch<double> {
 };
 #undef TVLP_CASE
 
+// Per-device lookups cached on first use.  Host threads may make their first
+// calls at the same time: the cache entries are atomics, and a lookup done
+// twice stores the same value.
 int num_sms() {
-    static int cached[kMaxDevicesApi] = {};
+    static std::atomic<int> cached[kMaxDevicesApi] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesApi) {
         cudaGetLastError();
         return 152;
     }
-    if (cached[dev] == 0) {
-        int n = 0;
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             n = 152;
         }
-        cached[dev] = n;
+        cached[dev].store(n, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return n;
 }
 
 int *status_word() {
-    static int *cached[kMaxDevicesApi] = {};
+    static std::atomic<int *> cached[kMaxDevicesApi] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesApi) {
         cudaGetLastError();
         return nullptr;
     }
-    if (cached[dev] == nullptr) {
+    int *w = cached[dev].load(std::memory_order_relaxed);
+    if (w == nullptr) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_tvlp_status) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        cached[dev] = static_cast<int *>(ptr);
+        w = static_cast<int *>(ptr);
+        cached[dev].store(w, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return w;
 }
 
 Shape shape_for(int MP, int dtype) {

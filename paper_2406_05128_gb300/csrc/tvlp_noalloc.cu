@@ -10,6 +10,8 @@
 // of a caller-supplied workspace.
 #include <stdint.h>
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "tvlp.h"
@@ -24,23 +26,25 @@ namespace {
 constexpr int kMaxDev = 64;
 
 // Device address of the scratch array on the current device; looked up once
-// per device (the host-side symbol is not a device address).
+// per device (the host-side symbol is not a device address).  Two host
+// threads making their first call on a device at the same time both look it
+// up and store the same address: the cache entries are atomics.
 void *scratch_address() {
-    static void *cached[kMaxDev] = {};
+    static std::atomic<void *> cached[kMaxDev] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
         cudaGetLastError();
         return nullptr;
     }
-    if (cached[dev] == nullptr) {
-        void *ptr = nullptr;
+    void *ptr = cached[dev].load(std::memory_order_relaxed);
+    if (ptr == nullptr) {
         if (cudaGetSymbolAddress(&ptr, g_tvlp_noalloc_scratch) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        cached[dev] = ptr;
+        cached[dev].store(ptr, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return ptr;
 }
 
 }  // namespace

@@ -58,3 +58,73 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     with pytest.raises(_lib.LPError) as ei:
         _lib.lp_tv_forward_noalloc_f32(B, T, M, 16, 16, None, 16, None)  # rejected before any use of the pointers
     assert ei.value.code == _lib.LP_ETOOBIG
+
+
+def test_noalloc_without_initial_state_and_order_zero():
+    w = inputs.make("noalloc0", 2, 5000, 12, seed=23, gen="stable")
+    a, e = (torch.tensor(x, device=DEV) for x in (w.a, w.e))
+    want = ops.lp_tv_forward(a, e)
+    got = _noalloc(a, e, None)
+    torch.cuda.synchronize()
+    assert norm_err(got.cpu().numpy(), want.cpu().numpy()).max() <= TOL_F32
+    # M = 0: the filter is the identity, s = e
+    a0 = torch.zeros((2, 5000, 0), device=DEV)
+    got0 = _noalloc(a0, e, None)
+    torch.cuda.synchronize()
+    assert torch.equal(got0, e)
+
+
+def _largest_fitting_T(B, M):
+    """Largest T whose scratch fits the fixed array (need(T) is searched
+    by bisection; returns None if it is not monotone around the limit)."""
+    lim = _lib.LP_NOALLOC_SCRATCH_BYTES
+    lo, hi = 1, 1
+    while _lib.lp_tv_workspace_bytes(B, hi, M) <= lim:
+        hi *= 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if _lib.lp_tv_workspace_bytes(B, mid, M) <= lim:
+            lo = mid
+        else:
+            hi = mid
+    if _lib.lp_tv_workspace_bytes(B, lo, M) > lim or _lib.lp_tv_workspace_bytes(B, lo + 1, M) <= lim:
+        return None
+    return lo
+
+
+def test_noalloc_size_boundary():
+    """The largest problem whose scratch fits runs and matches the regular
+    forward; one more sample is rejected with LP_ETOOBIG."""
+    B, M = 1, 22
+    T = _largest_fitting_T(B, M)
+    if T is None:
+        pytest.skip("scratch size not monotone in T around the limit")
+    w = inputs.make("noallocmax", B, T, M, seed=24, gen="stable")
+    a, e = (torch.tensor(x, device=DEV) for x in (w.a, w.e))
+    want = ops.lp_tv_forward(a, e)
+    got = _noalloc(a, e, None)
+    torch.cuda.synchronize()
+    assert norm_err(got.cpu().numpy(), want.cpu().numpy()).max() <= TOL_F32
+    with pytest.raises(_lib.LPError) as ei:
+        _lib.lp_tv_forward_noalloc_f32(B, T + 1, M, 16, 16, None, 16, None)
+    assert ei.value.code == _lib.LP_ETOOBIG
+
+
+def test_noalloc_allocates_no_device_memory():
+    """Around a warmed-up call neither torch's allocator nor the device's
+    free memory changes."""
+    w = inputs.make("noallocmem", 3, 30000, 22, seed=25, gen="stable", with_zi=True)
+    a, e, zi = (torch.tensor(x, device=DEV) for x in (w.a, w.e, w.zi))
+    s = torch.empty((3, 30000), device=DEV)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        _lib.lp_tv_forward_noalloc_f32(3, 30000, 22, a.data_ptr(), e.data_ptr(), zi.data_ptr(), s.data_ptr(), stream)
+
+    call()
+    torch.cuda.synchronize()
+    alloc0, (free0, _) = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()
+    call()
+    torch.cuda.synchronize()
+    alloc1, (free1, _) = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()
+    assert alloc1 == alloc0 and free1 == free0, (alloc0, alloc1, free0, free1)
