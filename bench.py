@@ -39,11 +39,12 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd Msamples/s at M=22 vs plain sequential kernel (<=1e-4 rel); serving p99"
 UNIT = "Msamples/s"
 WORKLOAD = "batched forward+backward time-varying LP, B=32, T=48000, M=22, FP32"
-KERNELS_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun")
-KERNELS_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun", "grad_a")
+# the chunked FP32 calls end with the defect correction's scan and re-run
+KERNELS_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun", "fwd_fix_scan", "fwd_fix_rerun")
+KERNELS_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun", "bwd_fix_scan", "bwd_fix_rerun", "grad_a")
 # the chunked adjoint with LP_BWD_FUSED_GA at a compiled order: Eq. 12
 # inside the re-run
-KERNELS_BWD_FUSED = ("bwd_zero_state", "bwd_scan", "bwd_rerun_grad")
+KERNELS_BWD_FUSED = ("bwd_zero_state", "bwd_scan", "bwd_rerun_grad", "bwd_fix_scan", "bwd_fix_rerun_grad")
 KERNELS_PLAIN_FWD = ("plain_fwd",)
 KERNELS_PLAIN_BWD = ("plain_bwd", "grad_a")
 L2_FLUSH_BYTES = 256 << 20
@@ -61,6 +62,8 @@ def parse():
     ap.add_argument("--T", type=int, default=48000)
     ap.add_argument("--M", type=int, default=22)
     ap.add_argument("--gen", choices=("literal", "stable"), default="literal")
+    ap.add_argument("--kmax", type=float, default=None,
+                    help="bound of the reflection coefficients (default 0.95, the headline generator)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0, help="keep warming up at least this long")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -77,7 +80,7 @@ def parse():
                     help="the adjoint re-run writes dL/da itself instead of a pass of its own (LP_BWD_FUSED_GA)")
     ap.add_argument("--l2-set-aside-mb", type=int, default=0,
                     help="persisting L2 for the passes' evict-last stages (this process's context; 0: none)")
-    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train", "golf"),
+    ap.add_argument("--workload", choices=("headline", "uneven", "serving", "frames", "train", "golf", "framewise"),
                     default="headline",
                     help="headline: the batched B x T step; uneven: 256 signals of uneven lengths and orders; "
                          "serving: the request loop under Poisson arrivals; frames: the headline step with the "
@@ -119,15 +122,21 @@ def dist_env():
 
 def workload(args, rank):
     from paper_2406_05128_gb300 import inputs
-    return inputs.batched_headline(seed=2 + rank, gen=args.gen, B=args.B, T=args.T, M=args.M)
+    if args.kmax is None:
+        return inputs.batched_headline(seed=2 + rank, gen=args.gen, B=args.B, T=args.T, M=args.M)
+    return inputs.make(f"batched B={args.B} T={args.T} M={args.M}", args.B, args.T, args.M, seed=2 + rank,
+                       kmax=args.kmax, gen=args.gen, excitation="pulse")
 
 
-def config(args, l2):
-    return {"workload": WORKLOAD if (args.B, args.T, args.M) == (32, 48000, 22)
+def config(args):
+    """The workload (the same dict for both arms; how each arm runs it is
+    reported beside it)."""
+    kmax = 0.95 if args.kmax is None else args.kmax
+    return {"workload": WORKLOAD if (args.B, args.T, args.M, kmax) == (32, 48000, 22, 0.95)
             else f"batched forward+backward time-varying LP, B={args.B}, T={args.T}, M={args.M}, FP32",
-            "B": args.B, "T": args.T, "M": args.M, "coefficients": f"{args.gen} reflection generator, hop 120",
-            "excitation": "pulse train F0~U(100,600) Hz + 0.1 N(0,1)", "algo": args.algo,
-            "l2": l2}
+            "B": args.B, "T": args.T, "M": args.M,
+            "coefficients": f"{args.gen} reflection generator, |k| <= {kmax}, hop 120",
+            "excitation": "pulse train F0~U(100,600) Hz + 0.1 N(0,1)"}
 
 
 # ---------------------------------------------------------------------------
@@ -184,7 +193,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
         "n_gpus": args.gpus, "steps": steps, "warmup": warmup, "ms_per_step": round(dt * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config(args, "n/a (host CPU)"),
+        "config": config(args),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"full batch {w.a.shape[0]}x{w.a.shape[1]} (M={w.a.shape[2]}) per step, "
                                    "sequential FP64 C oracle, one thread per signal",
@@ -294,6 +303,14 @@ def load_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+def fp32_pipe_peak(dev, sm_max_hz):
+    """FP32 FMA pipe of the device: its SM count (read from the device) x 128
+    FP32 lanes per SM x 2 flop per FMA x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * sm_max_hz / 1e12, f"FP32 FMA pipe: {sms} SMs (device) x 128 lanes x 2 flop x max SM clock"
 
 
 # ---------------------------------------------------------------------------
@@ -613,7 +630,7 @@ def run_ours(args):
     peaks = load_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max / 1e12
+    fp32_peak_tflops, fp32_src = fp32_pipe_peak(dev, sm_max)
     nsamp = B * T
     MP = M  # exact instantiation for the benchmark orders
     bytes_per_sample = {
@@ -638,7 +655,7 @@ def run_ours(args):
         if ach_t / fp32_peak_tflops >= ach_b / hbm_peak:
             roof = {"bound": "alu", "achieved": round(ach_t, 3), "peak": round(fp32_peak_tflops, 2),
                     "unit": "TFLOP/s", "frac": round(ach_t / fp32_peak_tflops, 4),
-                    "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+                    "peak_source": fp32_src}
         else:
             roof = {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(ach_b / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
@@ -675,10 +692,12 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config(args, "flushed between timed steps (256 MiB write)") | {
-            "chunk": chunk, "launch": "host launches" if args.no_graph else "CUDA graph replay per step",
+        "config": config(args),
+        "launch_config": {
+            "algo": args.algo, "chunk": chunk,
+            "launch": "host launches" if args.no_graph else "CUDA graph replay per step",
             "ga": "separate pass" if names_b != KERNELS_BWD_FUSED else "written by the adjoint re-run",
-            "l2_persisting_bytes": l2_aside},
+            "l2": "flushed between timed steps (256 MiB write)", "l2_persisting_bytes": l2_aside},
         "roofline": roof, "step_roofline": step_roof, "kernels": kern_detail,
         "kernels_from": ("replays of the step graph with an event around each kernel, outside the timed region "
                          f"(mean step there {statistics.mean(prof_step_ms):.4f} ms)") if prof_step_ms
@@ -1069,8 +1088,8 @@ def run_serving(args):
 # reflection coefficients per 120-sample frame (interpolation + step-up), and
 # the gradient with respect to those frames
 # ---------------------------------------------------------------------------
-KERNELS_FRAMES_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun")
-KERNELS_FRAMES_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun")
+KERNELS_FRAMES_FWD = ("fwd_summary", "fwd_scan", "fwd_rerun", "fwd_fix_scan", "fwd_fix_rerun")
+KERNELS_FRAMES_BWD = ("bwd_zero_state", "bwd_scan", "bwd_rerun", "bwd_fix_scan", "bwd_fix_rerun")
 KERNELS_FRAMES_GRAD = ("grad_frames", "grad_frames_finish")
 
 
@@ -1097,7 +1116,7 @@ def run_frames(args):
     ws = ops.workspace_frames(B, T, M, hop, chunk, dev, cache_rows=not args.no_row_cache)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2 * 8)]
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2 * 12)]
     for x in ev:
         x.record(stream)
     torch.cuda.synchronize()
@@ -1105,7 +1124,7 @@ def run_frames(args):
 
     def fwd(profile):
         sp = torch.cuda.current_stream(dev).cuda_stream
-        keep = _lib.lp_tv_set_profile_events(handles[0:6]) if profile else None
+        keep = _lib.lp_tv_set_profile_events(handles[0:10]) if profile else None
         _lib.lp_tv_forward_frames(B, T, M, hop, k.data_ptr(), e.data_ptr(), None, s.data_ptr(), None, chunk,
                                   ws.data_ptr(), ws.numel(), sp)
         if profile:
@@ -1114,7 +1133,7 @@ def run_frames(args):
 
     def bwd(profile):
         sp = torch.cuda.current_stream(dev).cuda_stream
-        keep = _lib.lp_tv_set_profile_events(handles[6:16]) if profile else None
+        keep = _lib.lp_tv_set_profile_events(handles[10:24]) if profile else None
         _lib.lp_tv_backward_frames(B, T, M, hop, gs.data_ptr(), k.data_ptr(), s.data_ptr(), None, ge.data_ptr(),
                                    gk.data_ptr(), None, chunk, _lib.LP_BWD_REUSE_FORWARD, ws.data_ptr(), ws.numel(),
                                    sp)
@@ -1232,7 +1251,7 @@ def run_frames(args):
     streamed_bytes = {"fwd_rerun": 4 * M + 8, "bwd_zero_state": 4 * M + 4, "bwd_rerun": 4 * M + 8} if cached else {}
     peaks = load_peaks()
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
-    fp32_peak = 152 * 128 * 2 * sm_max / 1e12
+    fp32_peak, fp32_src = fp32_pipe_peak(dev, sm_max)
     kd = {}
     for n in names:
         m = statistics.mean(kern[n])
@@ -1261,7 +1280,7 @@ def run_frames(args):
                    "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(fp32_peak, 2),
                      "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
-                     "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock",
+                     "peak_source": fp32_src,
                      "traffic": None},
         "kernels": kd, "e2e": e2e, "clocks": sampler.summary(t_load, t1), "source_hash": source_hash(),
         "gpu_launches": (len(names)) * args.steps,
@@ -1509,6 +1528,99 @@ def run_golf(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Frame-wise overlap-add approximation (the GOLF-ff comparison of Sec. 4.3):
+# forward + adjoint of per-frame time-invariant filters at 75 % overlap,
+# timed beside the sample-wise step on the same shape.
+# ---------------------------------------------------------------------------
+def run_framewise(args):
+    import torch
+
+    from paper_2406_05128_gb300 import _lib, inputs, ops
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, T, M, hop = args.B, args.T, args.M, inputs.HOP
+    rng = np.random.default_rng(2)
+    F = ops.framewise_frames(T, hop)
+    af = torch.tensor(inputs.step_up(inputs.reflection_frames(rng, B, F, M, 0.95)).astype(np.float32), device=dev)
+    e = torch.tensor((inputs.pulse_train(rng, B, T) + 0.1 * rng.standard_normal((B, T))).astype(np.float32),
+                     device=dev)
+    gs = torch.tensor(rng.standard_normal((B, T)).astype(np.float32), device=dev)
+    s, ge = torch.empty((B, T), device=dev), torch.empty((B, T), device=dev)
+    y = torch.empty((B, 4 * hop, F), device=dev)
+    gaf = torch.empty((B, F, M), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sp = torch.cuda.current_stream(dev).cuda_stream
+        _lib.lp_framewise_forward(B, T, M, hop, af.data_ptr(), e.data_ptr(), s.data_ptr(), y.data_ptr(), sp)
+        _lib.lp_framewise_backward(B, T, M, hop, af.data_ptr(), y.data_ptr(), gs.data_ptr(), ge.data_ptr(),
+                                   gaf.data_ptr(), sp)
+
+    # the sample-wise step (Eq. 5 and Eqs. 11-12) on the same shape: a(t)
+    # streamed, the adjoint reusing the forward's transfers
+    w = inputs.batched_headline(seed=2, gen=args.gen, B=B, T=T, M=M)
+    a_s = torch.from_numpy(w.a).to(dev)
+    s2, ge2, ga2 = torch.empty((B, T), device=dev), torch.empty((B, T), device=dev), torch.empty_like(a_s)
+    chunk = args.chunk or _lib.lp_tv_pick_chunk(B, T, M)
+    ws = ops.workspace(B, T, M, chunk, torch.float32, dev)
+
+    def step_sw():
+        sp = torch.cuda.current_stream(dev).cuda_stream
+        _lib.lp_tv_forward(_lib.LP_DTYPE_F32, B, T, M, a_s.data_ptr(), e.data_ptr(), None, s2.data_ptr(), None,
+                           chunk, _lib.LP_ALGO_CHUNKED, ws.data_ptr(), ws.numel(), sp)
+        _lib.lp_tv_backward(_lib.LP_DTYPE_F32, B, T, M, gs.data_ptr(), a_s.data_ptr(), s2.data_ptr(), None,
+                            ge2.data_ptr(), ga2.data_ptr(), None, chunk, _lib.LP_ALGO_CHUNKED,
+                            _lib.LP_BWD_REUSE_FORWARD, ws.data_ptr(), ws.numel(), sp)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True, external=True), torch.cuda.Event(enable_timing=True,
+                                                                                          external=True)
+        with torch.cuda.graph(g):
+            ev0.record()
+            fn()
+            ev1.record()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(args.steps):
+            flush.zero_()
+            g.replay()
+            stream.synchronize()
+            out.append(ev0.elapsed_time(ev1))
+        return statistics.mean(out)
+
+    sampler = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    t0 = time.perf_counter()
+    ms_fw = timed(step)
+    ms_sw = timed(step_sw)
+    t1 = time.perf_counter()
+    sampler.stop()
+    nsamp = B * T
+    line = {
+        "metric": "frame-wise overlap-add LP fwd+bwd Msamples/s (GOLF-ff comparison)",
+        "value": round(nsamp / (ms_fw * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_fw, 5), "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"frame-wise overlap-add LP forward+backward, B={B}, T={T}, M={M}, frames of "
+                               f"{4 * hop} samples every {hop} (75% overlap), Hann window, FP32",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "gpu_launches": 2 * args.steps,
+        "sample_wise": {"ms_per_step": round(ms_sw, 5), "value": round(nsamp / (ms_sw * 1e-3) / 1e6, 3),
+                        "what": "the sample-wise filter (Eq. 5, Eqs. 11-12) on the same shape, a(t) streamed, "
+                                f"generator {args.gen}, chunk {chunk}"},
+        "sample_wise_over_framewise_time": round(ms_sw / ms_fw, 3),
+        "clocks": sampler.summary(t0, t1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1521,6 +1633,8 @@ def main():
         return run_frames(args)
     if args.workload == "train":
         return run_train(args)
+    if args.workload == "framewise":
+        return run_framewise(args)
     if args.workload == "golf":
         return run_golf(args)
     return run_ours(args)

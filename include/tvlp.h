@@ -307,7 +307,11 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
  * lp_tv_workspace_bytes_frames_varlen_cached adds the row cache described
  * above (4*M bytes per packed row, compiled orders): the varlen forward
  * keeps its generated rows in such a workspace, and a backward with
- * LP_BWD_REUSE_FORWARD on it streams them.
+ * LP_BWD_REUSE_FORWARD on it streams them.  Where the cached rows start
+ * depends on the chunk length and on workspace_bytes, and the backward
+ * cannot tell whether the forward wrote them: a backward with
+ * LP_BWD_REUSE_FORWARD must get the same workspace, workspace_bytes, chunk,
+ * offsets, frame_offsets and k as the forward, or it reads stale rows.
  */
 size_t lp_tv_workspace_bytes_frames(int B, int64_t T, int M, int hop,
                                     int chunk);
@@ -390,6 +394,43 @@ int lp_tv_l2_set_aside(size_t bytes, size_t *applied);
  * usable.  LP_EINVAL for another `which`, LP_ECUDA if the launch fails.
  */
 int lp_tv_selftest_wait(int which, void *stream);
+
+/*
+ * Frame-wise overlap-add approximation (Sec. 3.2: the frame-wise LP of the
+ * earlier GOLF work that the sample-wise filter replaces; Sec. 5.2: 75 %
+ * overlap; Sec. 4.3: the training-speed comparison of GOLF-ss with GOLF-ff).
+ * Not Eq. 5: every frame is filtered by a time-invariant filter (Eq. 2).
+ *   Frames of N = 4*hop samples start every hop samples: frame f covers
+ *   samples t_f .. t_f + N - 1, t_f = (f - 3)*hop, and there are
+ *   F = lp_framewise_num_frames(T, hop) = ceil(T/hop) + 3 of them, so every
+ *   sample lies in exactly four.  With w(n) = (1 - cos(2 pi n/N)) / 4 (the
+ *   four windows over a sample sum to one):
+ *     y_f(n) = w(n) e(t_f + n) - sum_{i=1..M} af_i y_f(n - i),  y_f(n<0) = 0
+ *     s(t)   = sum_f y_f(t - t_f)   (e = 0 outside 0..T-1)
+ *   The adjoint runs Eq. 11 with each frame's coefficients over the frame,
+ *     gu_f(n) = gs(t_f + n) - sum_i af_i gu_f(n + i),  gu_f(n >= N) = 0,
+ *     ge(t)   = sum_f w(t - t_f) gu_f(t - t_f),
+ *     gaf_i   = -sum_n gu_f(n) y_f(n - i)    (Eq. 12 summed over the frame).
+ * Arguments (DEVICE pointers, FP32, caller-owned):
+ *   af   [B][F][M] direct-form coefficients of every frame           (in)
+ *   e, s [B][T]    excitation (in) and output (out)
+ *   y    [B][N][F] frame outputs y_f(n) at y[(b*N + n)*F + f], written by
+ *                  the forward when not NULL, read by the backward;
+ *                  lp_framewise_outputs_bytes(B, T, hop) bytes
+ *   gs, ge [B][T]  dL/ds (in), dL/de (out); gaf [B][F][M] dL/daf (out)
+ * hop: a multiple of 8, 8 <= hop <= 512; 0 <= M <= 32.  One kernel per
+ * call, enqueued on `stream`; nothing is allocated.  Returns LP_OK,
+ * LP_EINVAL (shape, hop or a required NULL pointer), LP_EUNSUPPORTED
+ * (M > 32 or T >= 2^31) or LP_ECUDA.
+ */
+int64_t lp_framewise_num_frames(int64_t T, int hop);
+size_t lp_framewise_outputs_bytes(int B, int64_t T, int hop);
+int lp_framewise_forward_f32(int B, int64_t T, int M, int hop, const float *af,
+                             const float *e, float *s, float *y, void *stream);
+int lp_framewise_backward_f32(int B, int64_t T, int M, int hop,
+                              const float *af, const float *y,
+                              const float *gs, float *ge, float *gaf,
+                              void *stream);
 
 /*
  * Allocation-free forward filter (no counterpart in the paper; a service for

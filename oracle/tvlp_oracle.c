@@ -230,7 +230,8 @@ void tvlp_oracle_coeffs_adjoint_batch(int64_t B, int64_t T, int M, int hop,
 
 /*
  * Frame-wise approximation of Eq. 5 (Sec. 3.2, the method of the earlier
- * GOLF work that the sample-wise filter replaces; Sec. 4 uses 75 % overlap).
+ * GOLF work that the sample-wise filter replaces; Sec. 5.2 states the 75 %
+ * overlap, Sec. 4.3 lists the frame-wise decoder GOLF-ff).
  * The signal is cut into frames of N = 4*hop samples, one every hop
  * samples; frame f covers samples t_f .. t_f + N - 1 with t_f = (f - 3)*hop,
  * so with F = ceil(T/hop) + 3 frames every sample lies in exactly four.

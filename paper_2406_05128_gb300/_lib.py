@@ -45,6 +45,8 @@ EXPORTS = (
     "lp_tv_backward_frames_varlen_f32", "lp_tv_l2_set_aside", "lp_tv_workspace_bytes_ti", "lp_tv_forward_ti_f32", "lp_tv_backward_ti_f32",
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
     "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
+    "lp_framewise_num_frames", "lp_framewise_outputs_bytes", "lp_framewise_forward_f32",
+    "lp_framewise_backward_f32",
 )
 
 LP_SERVE_SYNTH = 0
@@ -148,6 +150,14 @@ def _declare(lib):
     lib.lp_tv_selftest_wait.restype = i32
     lib.lp_tv_workspace_bytes_ti.argtypes = [i32, i64, i32, i32]
     lib.lp_tv_workspace_bytes_ti.restype = sz
+    lib.lp_framewise_num_frames.argtypes = [i64, i32]
+    lib.lp_framewise_num_frames.restype = i64
+    lib.lp_framewise_outputs_bytes.argtypes = [i32, i64, i32]
+    lib.lp_framewise_outputs_bytes.restype = sz
+    lib.lp_framewise_forward_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.lp_framewise_forward_f32.restype = i32
+    lib.lp_framewise_backward_f32.argtypes = [i32, i64, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.lp_framewise_backward_f32.restype = i32
     lib.lp_tv_forward_ti_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.lp_tv_forward_ti_f32.restype = i32
     lib.lp_tv_backward_ti_f32.argtypes = [i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
@@ -352,3 +362,19 @@ def lp_tv_l2_set_aside(nbytes: int) -> int:
     got = ctypes.c_size_t()
     _check(load().lp_tv_l2_set_aside(int(nbytes), ctypes.byref(got)), "lp_tv_l2_set_aside")
     return got.value
+
+
+def lp_framewise_num_frames(T: int, hop: int) -> int:
+    return load().lp_framewise_num_frames(T, hop)
+
+
+def lp_framewise_outputs_bytes(B: int, T: int, hop: int) -> int:
+    return load().lp_framewise_outputs_bytes(B, T, hop)
+
+
+def lp_framewise_forward(B, T, M, hop, af, e, s, y, stream):
+    _check(load().lp_framewise_forward_f32(B, T, M, hop, af, e, s, y, stream), "lp_framewise_forward_f32")
+
+
+def lp_framewise_backward(B, T, M, hop, af, y, gs, ge, gaf, stream):
+    _check(load().lp_framewise_backward_f32(B, T, M, hop, af, y, gs, ge, gaf, stream), "lp_framewise_backward_f32")

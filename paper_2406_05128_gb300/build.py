@@ -52,6 +52,7 @@ def _units():
     units.append((os.path.join(CSRC, "tvlp_serve.cu"), os.path.join(BUILD, "tvlp_serve.o"), []))
     units.append((os.path.join(CSRC, "tvlp_selftest.cu"), os.path.join(BUILD, "tvlp_selftest.o"), []))
     units.append((os.path.join(CSRC, "tvlp_check.cu"), os.path.join(BUILD, "tvlp_check.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_framewise.cu"), os.path.join(BUILD, "tvlp_framewise.o"), []))
     return units
 
 

@@ -558,3 +558,70 @@ def lp_tv_backward_frames_varlen(packed: Packed, frames: PackedFrames, gs, k, s,
                                           _ptr(zi), _ptr(ge), _ptr(gk), _ptr(gzi), chunk, flags, _ptr(ws),
                                           ws.numel(), _stream(dev))
     return ge, gk, gzi
+
+
+# ---------------------------------------------------------------------------
+# Frame-wise overlap-add approximation (the GOLF-ff comparison of Sec. 4.3):
+# per-frame time-invariant filters on Hann-windowed frames of 4*hop samples,
+# one every hop samples, overlap-added (lp_framewise_* in include/tvlp.h).
+# ---------------------------------------------------------------------------
+def framewise_frames(T: int, hop: int) -> int:
+    """Frames of the frame-wise approximation: ceil(T / hop) + 3."""
+    return -(-T // hop) + 3
+
+
+def lp_framewise_forward(af, e, hop: int, *, keep_outputs: bool = True):
+    """s [B, T] from per-frame direct-form coefficients af [B, F, M] and e
+    [B, T]; with keep_outputs also the frame outputs y [B, 4*hop, F] the
+    backward needs.  Returns (s, y or None)."""
+    B, F, M = af.shape
+    T = e.shape[1]
+    dev = af.device
+    _check(af, "af", (B, framewise_frames(T, hop), M), torch.float32, dev)
+    _check(e, "e", (B, T), torch.float32, dev)
+    with torch.cuda.device(dev):
+        s = torch.empty((B, T), device=dev)
+        y = torch.empty((B, 4 * hop, F), device=dev) if keep_outputs else None
+        _lib.lp_framewise_forward(B, T, M, hop, _ptr(af), _ptr(e), _ptr(s), _ptr(y), _stream(dev))
+    return s, y
+
+
+def lp_framewise_backward(gs, af, y, hop: int):
+    """(ge [B, T], gaf [B, F, M]) for dL/ds = gs, from the forward's frame
+    outputs y."""
+    B, F, M = af.shape
+    T = gs.shape[1]
+    dev = af.device
+    _check(gs, "gs", (B, T), torch.float32, dev)
+    _check(af, "af", (B, framewise_frames(T, hop), M), torch.float32, dev)
+    _check(y, "y", (B, 4 * hop, F), torch.float32, dev)
+    with torch.cuda.device(dev):
+        ge = torch.empty((B, T), device=dev)
+        gaf = torch.empty((B, F, M), device=dev)
+        _lib.lp_framewise_backward(B, T, M, hop, _ptr(af), _ptr(y), _ptr(gs), _ptr(ge), _ptr(gaf), _stream(dev))
+    return ge, gaf
+
+
+class LPFramewiseFunction(torch.autograd.Function):
+    """Differentiable frame-wise approximation: gradients for af and e."""
+
+    @staticmethod
+    def forward(ctx, af, e, hop):
+        af, e = af.contiguous(), e.contiguous()
+        s, y = lp_framewise_forward(af, e, hop)
+        ctx.hop = hop
+        ctx.save_for_backward(af, y)
+        return s
+
+    @staticmethod
+    def backward(ctx, gs):
+        af, y = ctx.saved_tensors
+        ge, gaf = lp_framewise_backward(gs.contiguous(), af, y, ctx.hop)
+        need_af, need_e = ctx.needs_input_grad[:2]
+        return (gaf if need_af else None, ge if need_e else None, None)
+
+
+def lp_filter_framewise(af, e, hop: int):
+    """Differentiable frame-wise overlap-add filter (not Eq. 5: each frame is
+    filtered with its own time-invariant coefficients af [B, F, M])."""
+    return LPFramewiseFunction.apply(af, e, hop)

@@ -1,6 +1,6 @@
 """Pins of the frame-wise overlap-add oracle (the approximation of Eq. 5
 that the paper's sample-wise filter replaces, Sec. 3.2; 75 % overlap as in
-Sec. 4), checked against things other than itself:
+Sec. 5.2), checked against things other than itself:
 
 * zero coefficients: the four scaled Hann windows over every sample sum to
   one, so s = e and dL/de = dL/ds exactly (up to rounding);
