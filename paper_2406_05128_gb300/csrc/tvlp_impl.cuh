@@ -79,6 +79,9 @@ inline Batch batch_of(const Problem &p, void *ws, size_t sz) {
     bt.off = p.off;
     bt.n = p.B;
     bt.cstart = bt.gstart = nullptr;
+    bt.sig = bt.ord = nullptr;
+    bt.aoff = nullptr;
+    bt.ldz = 0;
     if (p.off != nullptr) {
         int *tab = reinterpret_cast<int *>(static_cast<char *>(ws) + ws_offset(p, sz, 8));
         bt.cstart = tab;

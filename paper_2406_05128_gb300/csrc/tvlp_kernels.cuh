@@ -272,6 +272,15 @@ __device__ __forceinline__ void bulk_load_l2(void *dst, const void *src, unsigne
         : "memory");
 }
 
+// Prefetch [p, p + bytes) into L2 (one bulk prefetch of the 16-byte
+// aligned span inside it; nothing outside the range is touched).
+__device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes) {
+    const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+    const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 constexpr int kWaitLimit = 1 << 18;  // mbarrier polls before a wait gives up (well under a second)
 
 // Load the MP coefficients of one shared-memory row (8-byte aligned for
@@ -405,7 +414,22 @@ struct Batch {
     const int *cstart;   // varlen: [n+1] first chunk of every signal
     const int *gstart;   // varlen: [n+1] first scan group of every signal
     int n;               // signals
+    // Mixed orders (one class of signals that share a padded order inside a
+    // batch of signals of different orders; nullptr otherwise): signal b of
+    // the class is signal sig[b] of the batch, with rows
+    // [off[sig[b]], off[sig[b]+1]), order ord[sig[b]], coefficient rows of
+    // that order starting at element aoff[sig[b]] of a, and initial state
+    // at zi[sig[b] * ldz]
+    const int *sig;
+    const int *ord;
+    const int64_t *aoff;
+    int ldz;
 };
+
+// The batch-wide index of class signal b.
+__device__ __forceinline__ int64_t global_signal(const Batch &bt, int64_t b) {
+    return bt.sig != nullptr ? (int64_t)__ldg(bt.sig + b) : b;
+}
 
 // chunks per scan group for a signal of nC chunks: about sqrt(nC / 4)
 __host__ __device__ inline int group_size(int64_t nC) {
@@ -433,11 +457,15 @@ __device__ __forceinline__ int64_t batch_chunks(const Batch &bt, int64_t bound) 
 }
 
 struct ChunkPos {
-    int64_t b, c;  // signal, chunk within the signal
-    int64_t base;  // row of the chunk's first sample
-    int valid;     // rows of the chunk inside the signal (<= L)
+    int64_t b, c;   // signal (in the class, for mixed orders), chunk within the signal
+    int64_t base;   // row of the chunk's first sample
+    int valid;      // rows of the chunk inside the signal (<= L)
+    int64_t g;      // the signal's index in the batch
+    int m;          // its order
+    int64_t abase;  // element of `a` where the chunk's coefficient rows start (rows of m)
 };
-__device__ __forceinline__ ChunkPos chunk_pos(const Batch &bt, int64_t q, int L) {
+// M: the call's order (every signal's, unless the batch has mixed orders)
+__device__ __forceinline__ ChunkPos chunk_pos(const Batch &bt, int64_t q, int L, int M) {
     ChunkPos p;
     int64_t len;
     if (bt.off == nullptr) {
@@ -445,12 +473,21 @@ __device__ __forceinline__ ChunkPos chunk_pos(const Batch &bt, int64_t q, int L)
         p.c = q - p.b * bt.nC;
         p.base = p.b * bt.T + p.c * (int64_t)L;
         len = bt.T;
+        p.g = p.b;
     } else {
         p.b = find_signal(bt.cstart, bt.n, q);
         p.c = q - __ldg(bt.cstart + p.b);
-        const int64_t o = __ldg(bt.off + p.b);
+        p.g = global_signal(bt, p.b);
+        const int64_t o = __ldg(bt.off + p.g);
         p.base = o + p.c * (int64_t)L;
-        len = __ldg(bt.off + p.b + 1) - o;
+        len = __ldg(bt.off + p.g + 1) - o;
+    }
+    if (bt.ord != nullptr) {
+        p.m = __ldg(bt.ord + p.g);
+        p.abase = __ldg(bt.aoff + p.g) + p.c * (int64_t)L * p.m;
+    } else {
+        p.m = M;
+        p.abase = p.base * (int64_t)M;
     }
     const int64_t rem = len - p.c * (int64_t)L;
     p.valid = rem < 0 ? 0 : (rem < L ? (int)rem : L);
@@ -601,15 +638,16 @@ static __global__ void __launch_bounds__(kTableThreads)
 //   backward: q_{k+1} after the chunk, i.e. the pending dL/ds(c*L - 1 - k)
 // ---------------------------------------------------------------------------
 template <typename S, int MP, typename GE, bool BWD>
-__device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int k,
-                                               int lane, int64_t my_base, int my_valid, bool exact, int l2) {
+__device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int L, int k,
+                                               int lane, int64_t my_abase, int my_m, int my_valid, bool exact,
+                                               int l2) {
     constexpr int CPW = GE::CPW;
     constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
     const int roff = BWD ? L - (k + 1) * SRS : k * SRS;  // chunk-local first row of the stage
     int nvalid = my_valid - roff;
     nvalid = nvalid < 0 ? 0 : (nvalid > SRS ? SRS : nvalid);
     const bool mine = lane < CPW;
-    const S *src_a = a + (my_base + roff) * (int64_t)MP;
+    const S *src_a = a + my_abase + (int64_t)roff * MP;
     const bool tma_a = mine && exact && nvalid == SRS && aligned16(src_a);
     const unsigned ntma = __popc(__ballot_sync(0xffffffffu, tma_a));
     if (lane == 0) mbar_arrive_expect_tx(bar, ntma * A_BYTES);
@@ -623,22 +661,23 @@ __device__ __forceinline__ void k1_issue_stage(S *a_st, uint64_t *bar, const S *
     while (slow) {
         const int ch = __ffs(slow) - 1;
         slow &= slow - 1;
-        const int64_t base = __shfl_sync(0xffffffffu, my_base, ch);
+        const int64_t abase = __shfl_sync(0xffffffffu, my_abase, ch);
+        const int m = __shfl_sync(0xffffffffu, my_m, ch);
         const int nv = __shfl_sync(0xffffffffu, nvalid, ch);
         S *dst = a_st + ch * GE::CS;
         if (exact) {
-            const S *s0 = a + (base + roff) * (int64_t)MP;
+            const S *s0 = a + abase + (int64_t)roff * MP;
             for (int idx = lane; idx < SRS * MP; idx += 32) {
                 const bool v = idx < nv * MP;
                 cp_async<sizeof(S)>(dst + idx, v ? s0 + idx : a, v ? (int)sizeof(S) : 0);
             }
         } else {
-            // padded order: the M real coefficients of every row; the padded
+            // padded order: the m real coefficients of every row; the padded
             // columns were zeroed once and are never written
             for (int r = 0; r < SRS; ++r) {
-                if (lane < M) {
+                if (lane < m) {
                     const bool v = r < nv;
-                    const S *s0 = v ? a + (base + roff + r) * (int64_t)M + lane : a;
+                    const S *s0 = v ? a + abase + (int64_t)(roff + r) * m + lane : a;
                     cp_async<sizeof(S)>(dst + r * MP + lane, s0, v ? (int)sizeof(S) : 0);
                 }
             }
@@ -728,11 +767,13 @@ __device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__rest
     }
 }
 
+// The body of k1_summary for block `bid` of its launch (a mixed-order launch
+// runs the bodies of several orders, each block one of them).
 template <typename S, int MP, int G, int R, bool BWD, int SRC = SRC_STREAM>
-__global__ void __launch_bounds__(256, 1)
-    k1_summary(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
-               S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
-               int *__restrict__ status, CoefSrc cs) {
+__device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a,
+                                        const S *__restrict__ u, S *__restrict__ Y, int exact_flag,
+                                        unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int *__restrict__ status,
+                                        const CoefSrc &cs) {
     static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
     using GE = SumGeo<S, MP, G, R>;
     constexpr int CPW = GE::CPW, NS = GE::NS, WIN = MP + SR;
@@ -742,7 +783,7 @@ __global__ void __launch_bounds__(256, 1)
     const int wpb = blockDim.x >> 5;
     if (bt.off != nullptr) pdl_wait();  // the chunk tables come from the kernel before
     NQ = batch_chunks(bt, NQ);
-    const int64_t q0 = ((int64_t)blockIdx.x * wpb + warp) * CPW;
+    const int64_t q0 = (bid * wpb + warp) * CPW;
     if (q0 >= NQ) return;
     const bool exact = exact_flag != 0;
     unsigned char *wbase = k1_smem + (size_t)warp * GE::WARP_BYTES;
@@ -758,19 +799,21 @@ __global__ void __launch_bounds__(256, 1)
     }
     __syncwarp();
     // lane ch < CPW describes chunk q0 + ch: its first row and valid rows
-    int64_t my_base = 0, my_b = 0, my_t0 = 0;
-    int my_valid = 0;
+    int64_t my_base = 0, my_b = 0, my_t0 = 0, my_abase = 0;
+    int my_valid = 0, my_m = M;
     if (lane < CPW && q0 + lane < NQ) {
-        const ChunkPos cp = chunk_pos(bt, q0 + lane, L);
+        const ChunkPos cp = chunk_pos(bt, q0 + lane, L, M);
         my_base = cp.base;
         my_valid = cp.valid;
-        my_b = cp.b;
+        my_b = cp.g;
         my_t0 = cp.c * (int64_t)L;
+        my_abase = cp.abase;
+        my_m = cp.m;
     }
     // stage k of the coefficient rows into ring slot `slot`
     auto stage = [&](int slot, int k) {
         if constexpr (SRC == SRC_STREAM)
-            k1_issue_stage<S, MP, GE, BWD>(a_buf + slot * GE::A_STAGE, bars + slot, a, M, L, k, lane, my_base,
+            k1_issue_stage<S, MP, GE, BWD>(a_buf + slot * GE::A_STAGE, bars + slot, a, L, k, lane, my_abase, my_m,
                                            my_valid, exact, l2);
         else {
             float *st_rows = reinterpret_cast<float *>(a_buf + slot * GE::A_STAGE);
@@ -816,7 +859,7 @@ __global__ void __launch_bounds__(256, 1)
     pdl_release();
     // the scan that follows counts finished groups per signal from zero
     // (warp 0 of block 0 always owns chunks, so it is still here)
-    if (scan_cnt != nullptr && blockIdx.x == 0 && warp == 0)
+    if (scan_cnt != nullptr && bid == 0 && warp == 0)
         for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     // generated rows may read frames an earlier kernel wrote: after the wait
     if constexpr (SRC != SRC_STREAM) stage(0, 0);
@@ -966,6 +1009,14 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
+template <typename S, int MP, int G, int R, bool BWD, int SRC = SRC_STREAM>
+__global__ void __launch_bounds__(256, 1)
+    k1_summary(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
+               S *__restrict__ Y, int exact_flag, unsigned *__restrict__ scan_cnt, int n_cnt, int l2,
+               int *__restrict__ status, CoefSrc cs) {
+    k1_body<S, MP, G, R, BWD, SRC>(blockIdx.x, bt, M, L, NQ, a, u, Y, exact_flag, scan_cnt, n_cnt, l2, status, cs);
+}
+
 // ---------------------------------------------------------------------------
 // One recursion per lane over its chunk ("lane per chunk"): a warp owns 32
 // consecutive chunks.  Each lane has a private ring of two stages of SRS
@@ -998,9 +1049,10 @@ enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2, BWD_GRAD = 3 };
 //   scan    the error of the scanned states obeys the same linear
 //           recurrence with the defects as its input,
 //           e_{c+1} = P_c e_c + d_c  (adjoint: e_{c-1} = P_c^T e_c + d_c);
-//   pass 2  every chunk whose correction is not negligible,
-//           max|e_c| > kFixTheta * max_t |out(t)| of its signal, re-runs
-//           from x_c + e_c and writes its outputs again.
+//   pass 2  every chunk whose correction is not negligible, at its start
+//           or carried through the chunk (max(|e_c|, |P_c e_c|) >
+//           kFixTheta * max_t |out(t)| of its signal), re-runs from
+//           x_c + e_c and writes its outputs again.
 // The error of e_c itself is second order (e_c is already a small
 // multiple of the rounding), so the result has the rounding of the
 // sequential recursion.  A signal whose outputs are not finite is never
@@ -1008,7 +1060,7 @@ enum { FWD_RERUN = 0, BWD_ZERO = 1, BWD_RERUN = 2, BWD_GRAD = 3 };
 // correction is below the threshold: skipping it changes the result by
 // less than the threshold times the chunk's gain.  The decisions depend on
 // the signal's own values only, so batching leaves them unchanged.
-constexpr float kFixTheta = 2.5e-7f;
+constexpr float kFixTheta = 2.0e-6f;
 constexpr int kScaleWord = 16;  // per-signal max |output| (float bits) in the signal's counter line
 
 template <typename S> struct Fix {
@@ -1058,13 +1110,13 @@ template <typename S, int MP, int RC = kRecChunks> struct RecGeo {
 
 template <typename S, int MP, bool EXACT, bool BWD>
 __device__ __forceinline__ void rec_issue_stage(S *a_st, uint64_t *bar, const S *__restrict__ a, int M, int L, int s,
-                                                bool active, int64_t base, int n, int l2, bool owner) {
+                                                bool active, int64_t abase, int n, int l2, bool owner) {
     constexpr unsigned A_BYTES = SRS * MP * sizeof(S);
     const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
     int nv = n - roff;
     nv = nv < 0 ? 0 : (nv > SRS ? SRS : nv);
     if (!active) nv = 0;
-    const S *src_a = a + (base + roff) * (int64_t)M;
+    const S *src_a = a + abase + (int64_t)roff * M;
     const bool tma_a = EXACT && nv == SRS && aligned16(src_a);
     const unsigned ntma = __popc(__ballot_sync(0xffffffffu, tma_a));
     if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, ntma * A_BYTES);
@@ -1124,12 +1176,15 @@ __device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restric
     for (int r = 0; r < SRS; ++r) uv[r] = (active && roff + r < n) ? __ldg(u + base + roff + r) : S(0);
 }
 
+// The body of k_rec for block `bid` of `nblocks` (a mixed-order launch runs
+// the bodies of several orders, each block one of them).
 template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM>
-__global__ void __launch_bounds__(32)
-    k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
-          const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
-          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
-          int *__restrict__ status, CoefSrc cs, const S *__restrict__ sfw, S *__restrict__ ga, Fix<S> fx) {
+__device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt, int M, int L, int64_t NQ,
+                                         const S *__restrict__ a, const S *__restrict__ u, const S *__restrict__ Xin,
+                                         const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
+                                         S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt,
+                                         int l2, int xs, int *__restrict__ status, const CoefSrc &cs,
+                                         const S *__restrict__ sfw, S *__restrict__ ga, const Fix<S> &fx) {
     static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
     constexpr int RC = RecChunks<SRC>::N;
     using RG = RecGeo<S, MP, RC>;
@@ -1140,7 +1195,9 @@ __global__ void __launch_bounds__(32)
     static_assert(!GA || (EXACT && SRC == SRC_STREAM), "fused gradient rows need exact streamed rows");
     extern __shared__ __align__(128) unsigned char rec_smem[];
     const int lane = threadIdx.x & 31;
-    const int64_t blk = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    // pass 2 of the defect correction walks its list from the first block,
+    // so the few warps with work are the first to be scheduled
+    const int64_t blk = (reverse && fx.E == nullptr) ? nblocks - 1 - bid : bid;
     // lanes past RC own no chunk; they read (and never write) the ring of
     // lane lane % RC so every shared access stays in range
     const bool owner = lane < RC;
@@ -1169,22 +1226,34 @@ __global__ void __launch_bounds__(32)
         mbar_init_fence();
     }
     __syncwarp();
-    int64_t b = 0, c = 0, base = 0;
-    int n = 0;
+    // b: the chunk's signal (in its class, for mixed orders), g: the
+    // signal's index in the batch, m: its order
+    int64_t b = 0, c = 0, base = 0, g = 0, abase = 0;
+    int n = 0, m = M;
     if (active) {
-        const ChunkPos cp = chunk_pos(bt, q, L);
+        const ChunkPos cp = chunk_pos(bt, q, L, M);
         b = cp.b;
         c = cp.c;
         base = cp.base;
         n = cp.valid;
+        g = cp.g;
+        m = cp.m;
+        abase = cp.abase;
+    }
+    const int ldz = bt.ldz > 0 ? bt.ldz : M;  // initial-state stride per signal
+    if (SRC == SRC_STREAM && fx.E != nullptr && active) {
+        // pass 2 re-runs few chunks and is bound by the latency of its
+        // stages: bring the chunk's rows and inputs into L2 at once
+        l2_prefetch(a + abase, (size_t)n * m * sizeof(S));
+        l2_prefetch(u + base, (size_t)n * sizeof(S));
     }
     const int nblk = L / SRS;
     auto stage = [&](int slot, int s) {
         if constexpr (SRC == SRC_STREAM)
-            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + slot * RG::A_ST, bars + slot, a, M, L, s, active, base, n, l2,
-                                               owner);
+            rec_issue_stage<S, MP, EXACT, BWD>(a_ring + slot * RG::A_ST, bars + slot, a, m, L, s, active, abase, n,
+                                               l2, owner);
         else
-            rec_gen_stage<MP, BWD, SRC, RC>(rec_smem, slot, bars + slot, cs, M, L, s, lane, b, c * (int64_t)L, n,
+            rec_gen_stage<MP, BWD, SRC, RC>(rec_smem, slot, bars + slot, cs, M, L, s, lane, g, c * (int64_t)L, n,
                                             active);
     };
     S ucur[SRS], unxt[SRS];
@@ -1193,7 +1262,7 @@ __global__ void __launch_bounds__(32)
     pdl_wait();
     pdl_release();
     // a scan that follows counts finished groups per signal from zero
-    if (scan_cnt != nullptr && blockIdx.x == 0)
+    if (scan_cnt != nullptr && bid == 0)
         for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     if constexpr (SRC != SRC_STREAM) stage(0, 0);
     S h[WIN];
@@ -1212,8 +1281,8 @@ __global__ void __launch_bounds__(32)
                         v += fx.E[q * MP + (j - 1)];
                         if (fx.ckpt != nullptr && j <= M) fx.ckpt[q * M + (j - 1)] = v;
                     }
-                } else if (zi != nullptr && j <= M) {
-                    v = zi[b * M + (j - 1)];
+                } else if (zi != nullptr && j <= m) {
+                    v = zi[g * ldz + (j - 1)];
                 }
                 h[MP - j] = v;
             }
@@ -1254,7 +1323,7 @@ __global__ void __launch_bounds__(32)
                 S v = S(0);
                 if (active && l < n) {
                     if (t >= 0) v = __ldg(sfw + base + l);
-                    else if (zi != nullptr) v = __ldg(zi + b * M + (-t - 1));
+                    else if (zi != nullptr) v = __ldg(zi + g * ldz + (-t - 1));
                 }
                 sv[k] = v;
             }
@@ -1320,7 +1389,7 @@ __global__ void __launch_bounds__(32)
             if (active) {
                 int nv = n - roff;
                 nv = nv < 0 ? 0 : (nv > SRS ? SRS : nv);
-                S *dst = ga + (base + roff) * (int64_t)MP;
+                S *dst = ga + abase + (int64_t)roff * MP;
                 if (nv == SRS && aligned16(dst)) {
                     fence_proxy_async();
                     bulk_store(dst, ar, (unsigned)(SRS * MP * sizeof(S)));
@@ -1347,7 +1416,7 @@ __global__ void __launch_bounds__(32)
         if (gzi != nullptr && c == 0) {
 #pragma unroll
             for (int j = 0; j < MP; ++j)
-                if (j < M) gzi[b * M + j] = h[j];
+                if (j < m) gzi[g * ldz + j] = h[j];
         }
     }
     if constexpr (MODE == FWD_RERUN || RERUN_B) {
@@ -1368,6 +1437,16 @@ __global__ void __launch_bounds__(32)
             atomicMax(fx.scale + b * kCntStride + kScaleWord, __float_as_uint(ymf <= 3.0e38f ? ymf : INFINITY));
         }
     }
+}
+
+template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM>
+__global__ void __launch_bounds__(32)
+    k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
+          const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
+          S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
+          int *__restrict__ status, CoefSrc cs, const S *__restrict__ sfw, S *__restrict__ ga, Fix<S> fx) {
+    rec_body<S, MP, EXACT, MODE, SRC>(blockIdx.x, gridDim.x, bt, M, L, NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
+                                      scan_cnt, n_cnt, l2, xs, status, cs, sfw, ga, fx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1817,12 +1896,15 @@ __device__ __forceinline__ bool wait_counter(const unsigned *c, unsigned target,
     return ok;
 }
 
+// The body of k2_scan for block `bid` of `nblocks` (a mixed-order launch runs
+// the bodies of several orders, each block one of them; every block of the
+// launch is resident, so the waits between blocks of one order end).
 template <typename S, int MP, int MODE>
-__global__ void __launch_bounds__(kScanWarps * 32)
-    k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
-            S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
-            S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status,
-            int *__restrict__ fix_list) {
+__device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt, int M, int64_t items_bound,
+                                          const S *__restrict__ Y, const S *__restrict__ Z, S *__restrict__ GY,
+                                          S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
+                                          S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt,
+                                          int *__restrict__ status, int *__restrict__ fix_list) {
     using SG = ScanGeo<S, MP>;
     constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
     constexpr bool REV = ScanMode<MODE>::REV;
@@ -1830,8 +1912,8 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     constexpr bool VEC = ScanMode<MODE>::VEC;
     extern __shared__ __align__(128) unsigned char k2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w0 = (int64_t)blockIdx.x * kScanWarps + warp;
-    const int64_t wstep = (int64_t)gridDim.x * kScanWarps;
+    const int64_t w0 = bid * kScanWarps + warp;
+    const int64_t wstep = nblocks * kScanWarps;
     int64_t n_items = items_bound;
     if (bt.off != nullptr) {
         const int64_t n = __ldg(bt.gstart + bt.n);
@@ -1870,6 +1952,15 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         S p[MP + 1];
         map_cols<S, MP, TRANS, VEC>(p, m, z, j0);
         return hop_smem<S, MP>(p, xb + ((nhop++) & 1) * RS, x, lane);
+    };
+    // the same hop, also giving the lane's component of P x (the map's
+    // constant term taken off again)
+    auto hop_step_pe = [&](const S *m, const S *z, S x, S &pe) -> S {
+        S p[MP + 1];
+        map_cols<S, MP, TRANS, VEC>(p, m, z, j0);
+        const S xn = hop_smem<S, MP>(p, xb + ((nhop++) & 1) * RS, x, lane);
+        pe = xn - p[0];
+        return xn;
     };
     // bounded wait until signal b's counter reaches `target` (counted from
     // where the main scan left it, for a correction scan)
@@ -1976,7 +2067,11 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         fence_proxy_async_global();  // the group maps are read by bulk copies
         auto gidx = [&](int n) -> int64_t { return sg.gbase + (REV ? nG - 1 - n : n); };
         S x = S(0);
-        if (MODE == CH_FWD && zi != nullptr && lane < M) x = zi[b * M + lane];
+        if (MODE == CH_FWD && zi != nullptr) {
+            const int64_t gs_ = global_signal(bt, b);
+            const int m = bt.ord != nullptr ? __ldg(bt.ord + gs_) : M;
+            if (lane < m) x = zi[gs_ * (bt.ldz > 0 ? bt.ldz : M) + lane];
+        }
         // groups 0 .. nG-2 along the chain: the signal's group maps
         // [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG) backward
         const int64_t lo = sg.gbase + (REV ? 1 : 0);
@@ -1999,15 +2094,19 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         locate(item, b, g, sg);
         const int len = group_len(sg, g);
         if (!wait_count(b, sg, (unsigned)sg.nG + 1u)) return;
-        const float fix_bar = ScanMode<MODE>::FIX ? kFixTheta * scale_of(cnt, b) : 0.f;
-        auto put = [&](int ci, S x) {
+        constexpr bool FIX = ScanMode<MODE>::FIX;
+        const float fix_bar = FIX ? kFixTheta * scale_of(cnt, b) : 0.f;
+        // pe (FIX): the lane's component of P_c x, the chunk's correction
+        // carried to the chunk's end
+        auto put = [&](int ci, S x, S pe) {
             const int64_t q = sg.cbase + chunk_at(sg, g, len, ci);
             if (lane < MP) X[q * MP + lane] = x;
             if (MODE == CH_FWD && ckpt != nullptr && lane < M) ckpt[q * M + lane] = x;
-            if constexpr (ScanMode<MODE>::FIX) {
-                // list the chunk for pass 2 when its correction is finite and
-                // above the threshold of its (finite) signal
-                float em = lane < MP ? (float)fabs(x) : 0.f;
+            if constexpr (FIX) {
+                // list the chunk for pass 2 when its correction, at its start
+                // or carried to its end, is finite and above the threshold
+                // of its (finite) signal
+                float em = lane < MP ? (float)abs_max_nan(fabs(x), pe) : 0.f;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) em = abs_max_nan(em, __shfl_xor_sync(0xffffffffu, em, o));
                 if (lane == 0 && em > fix_bar && em <= 3.0e38f) {
@@ -2018,23 +2117,43 @@ __global__ void __launch_bounds__(kScanWarps * 32)
         };
         S x = lane < MP ? __ldcg(GX + item * ZS + lane) : S(0);
         auto step = [&](int i, const S *m, const S *z) {
-            put(i, x);
-            x = hop_step(m, z, x);
+            if constexpr (FIX) {
+                S pe;
+                const S xn = hop_step_pe(m, z, x, pe);
+                put(i, x, pe);
+                x = xn;
+            } else {
+                put(i, x, S(0));
+                x = hop_step(m, z, x);
+            }
         };
+        // the main scans need every map of the group but the last along the
+        // chain; the correction scans also carry the last chunk's correction
+        // through its own map
+        const int nh = FIX ? len : len - 1;
         if (held) {
             // the group's maps are still in slots 0 .. len-1
-            for (int i = 0; i + 1 < len; ++i) {
+            for (int i = 0; i < nh; ++i) {
                 const int mi = REV ? len - 1 - i : i;
                 step(i, W.map(mi), W.zv(mi));
             }
         } else {
-            // every map of the group but the last along the chain
-            const int64_t off = REV ? 1 : 0;
+            const int64_t off = (REV && !FIX) ? 1 : 0;
             const S *zlo = VEC ? group_zs(sg, g) + off * ZS : nullptr;
-            if (!run_maps<S, MP, REV>(W, group_maps(sg, g) + off * YS, zlo, len - 1, step)) return;
+            if (!run_maps<S, MP, REV>(W, group_maps(sg, g) + off * YS, zlo, nh, step)) return;
         }
-        put(len - 1, x);
+        if (!FIX) put(len - 1, x, S(0));
     }
+}
+
+template <typename S, int MP, int MODE>
+__global__ void __launch_bounds__(kScanWarps * 32)
+    k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
+            S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
+            S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status,
+            int *__restrict__ fix_list) {
+    scan_body<S, MP, MODE>(blockIdx.x, gridDim.x, bt, M, items_bound, Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, status,
+                           fix_list);
 }
 
 // ---------------------------------------------------------------------------
