@@ -263,6 +263,56 @@ int lp_tv_backward_varlen_f64(int n, const int64_t *offsets, int64_t total,
                               void *stream);
 
 /*
+ * Mixed orders (uneven batching of signals of different lengths AND orders
+ * in one call; no counterpart in the paper, whose Eq. 5 fixes one order per
+ * filter): signal b has len_b = offsets[b+1] - offsets[b] samples and its
+ * own order M_b = orders[b], 1 <= M_b <= 32.  Each call runs one launch per
+ * kernel role over the whole batch: signals are grouped by the padded order
+ * the kernels are compiled for (2, 4, 8, 12, 16, 22, 30, 32), and each block
+ * of a launch runs the code of its group's order; a signal keeps its own
+ * order inside its group.
+ *   offsets [n+1]  DEVICE, int64: rows of signal b in e, s, gs, ge are
+ *                  [offsets[b], offsets[b+1]); offsets[0] = 0, non-decreasing
+ *   orders  [n]    DEVICE, int32
+ *   offsets_host, orders_host: the same arrays in HOST memory (the library
+ *                  plans the groups, grids and workspace from them)
+ *   a, ga          coefficients of signal b: len_b rows of M_b values,
+ *                  row-major, starting at element aoff[b] with aoff[0] = 0
+ *                  and aoff[b+1] = aoff[b] + len_b*M_b rounded up to a
+ *                  multiple of 4 (so every block starts 16-byte aligned);
+ *                  lp_tv_mixed_coeff_offsets writes aoff [n+1] (HOST) and
+ *                  returns the total element count
+ *   zi, gzi [n][32] initial state: zi[b*32 + j-1] = s_b(-j), j <= M_b
+ *                  (NULL: zero state)
+ * `chunk` 0 picks each group's chunk length from its signal count and
+ * lengths; with a fixed chunk a signal's results do not depend on the rest
+ * of the batch (bit for bit), and equal those of a single-order varlen call
+ * with that chunk.  The chunked algorithm with the defect correction, as for
+ * the other FP32 calls; no checkpoints and no LP_BWD_FUSED_GA.  Workspace:
+ * lp_tv_workspace_bytes_mixed (0 for invalid arguments).  Errors as for
+ * the varlen calls; an order outside 1..32 gives LP_EINVAL or
+ * LP_EUNSUPPORTED.  A backward with LP_BWD_REUSE_FORWARD must get the
+ * forward's workspace, chunk, offsets and orders.
+ */
+int64_t lp_tv_mixed_coeff_offsets(int n, const int64_t *offsets_host,
+                                  const int *orders_host, int64_t *aoff_host);
+size_t lp_tv_workspace_bytes_mixed(int n, const int64_t *offsets_host,
+                                   const int *orders_host, int chunk);
+int lp_tv_forward_mixed_f32(int n, const int64_t *offsets, const int *orders,
+                            const int64_t *offsets_host,
+                            const int *orders_host, const float *a,
+                            const float *e, const float *zi, float *s,
+                            int chunk, void *workspace, size_t workspace_bytes,
+                            void *stream);
+int lp_tv_backward_mixed_f32(int n, const int64_t *offsets, const int *orders,
+                             const int64_t *offsets_host,
+                             const int *orders_host, const float *gs,
+                             const float *a, const float *s, const float *zi,
+                             float *ge, float *ga, float *gzi, int chunk,
+                             int flags, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
+/*
  * Coefficients generated in the kernels instead of streamed (FP32, chunked
  * algorithm; the per-sample coefficient preparation of Sec. 4.3 and the
  * time-invariant filter of Sec. 2.2 / Eq. 2).  Every pass that would read

@@ -46,7 +46,8 @@ EXPORTS = (
     "lp_serve_default_config", "lp_serve_create", "lp_serve_destroy", "lp_serve_submit",
     "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
     "lp_framewise_num_frames", "lp_framewise_outputs_bytes", "lp_framewise_forward_f32",
-    "lp_framewise_backward_f32",
+    "lp_framewise_backward_f32", "lp_tv_mixed_coeff_offsets", "lp_tv_workspace_bytes_mixed",
+    "lp_tv_forward_mixed_f32", "lp_tv_backward_mixed_f32",
 )
 
 LP_SERVE_SYNTH = 0
@@ -150,6 +151,14 @@ def _declare(lib):
     lib.lp_tv_selftest_wait.restype = i32
     lib.lp_tv_workspace_bytes_ti.argtypes = [i32, i64, i32, i32]
     lib.lp_tv_workspace_bytes_ti.restype = sz
+    lib.lp_tv_mixed_coeff_offsets.argtypes = [i32, vp, vp, vp]
+    lib.lp_tv_mixed_coeff_offsets.restype = i64
+    lib.lp_tv_workspace_bytes_mixed.argtypes = [i32, vp, vp, i32]
+    lib.lp_tv_workspace_bytes_mixed.restype = sz
+    lib.lp_tv_forward_mixed_f32.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+    lib.lp_tv_forward_mixed_f32.restype = i32
+    lib.lp_tv_backward_mixed_f32.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+    lib.lp_tv_backward_mixed_f32.restype = i32
     lib.lp_framewise_num_frames.argtypes = [i64, i32]
     lib.lp_framewise_num_frames.restype = i64
     lib.lp_framewise_outputs_bytes.argtypes = [i32, i64, i32]
@@ -378,3 +387,23 @@ def lp_framewise_forward(B, T, M, hop, af, e, s, y, stream):
 
 def lp_framewise_backward(B, T, M, hop, af, y, gs, ge, gaf, stream):
     _check(load().lp_framewise_backward_f32(B, T, M, hop, af, y, gs, ge, gaf, stream), "lp_framewise_backward_f32")
+
+
+def lp_tv_mixed_coeff_offsets(n, offsets_host, orders_host, aoff_host):
+    """offsets_host / orders_host / aoff_host: addresses of HOST arrays."""
+    return load().lp_tv_mixed_coeff_offsets(n, offsets_host, orders_host, aoff_host)
+
+
+def lp_tv_workspace_bytes_mixed(n, offsets_host, orders_host, chunk=0):
+    return load().lp_tv_workspace_bytes_mixed(n, offsets_host, orders_host, chunk)
+
+
+def lp_tv_forward_mixed(n, offsets, orders, offsets_host, orders_host, a, e, zi, s, chunk, ws, ws_bytes, stream):
+    _check(load().lp_tv_forward_mixed_f32(n, offsets, orders, offsets_host, orders_host, a, e, zi, s, chunk, ws,
+                                          ws_bytes, stream), "lp_tv_forward_mixed_f32")
+
+
+def lp_tv_backward_mixed(n, offsets, orders, offsets_host, orders_host, gs, a, s, zi, ge, ga, gzi, chunk, flags, ws,
+                         ws_bytes, stream):
+    _check(load().lp_tv_backward_mixed_f32(n, offsets, orders, offsets_host, orders_host, gs, a, s, zi, ge, ga, gzi,
+                                           chunk, flags, ws, ws_bytes, stream), "lp_tv_backward_mixed_f32")

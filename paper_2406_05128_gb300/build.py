@@ -53,6 +53,13 @@ def _units():
     units.append((os.path.join(CSRC, "tvlp_selftest.cu"), os.path.join(BUILD, "tvlp_selftest.o"), []))
     units.append((os.path.join(CSRC, "tvlp_check.cu"), os.path.join(BUILD, "tvlp_check.o"), []))
     units.append((os.path.join(CSRC, "tvlp_framewise.cu"), os.path.join(BUILD, "tvlp_framewise.o"), []))
+    # mixed orders: the host side, and the fused kernels in parallel parts
+    units.append((os.path.join(CSRC, "tvlp_mixed.cu"), os.path.join(BUILD, "tvlp_mixed.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_mixed_k1.cu"), os.path.join(BUILD, "tvlp_mixed_k1.o"), []))
+    for name in ("tvlp_mixed_rec", "tvlp_mixed_scan"):
+        for part in (0, 1):
+            units.append((os.path.join(CSRC, name + ".cu"), os.path.join(BUILD, f"{name}_{part}.o"),
+                          [f"-DTVLP_MIX_PART={part}"]))
     return units
 
 

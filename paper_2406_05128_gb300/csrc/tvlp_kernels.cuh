@@ -1178,7 +1178,7 @@ __device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restric
 
 // The body of k_rec for block `bid` of `nblocks` (a mixed-order launch runs
 // the bodies of several orders, each block one of them).
-template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM>
+template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM, int RC = RecChunks<SRC>::N>
 __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt, int M, int L, int64_t NQ,
                                          const S *__restrict__ a, const S *__restrict__ u, const S *__restrict__ Xin,
                                          const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
@@ -1186,7 +1186,7 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
                                          int l2, int xs, int *__restrict__ status, const CoefSrc &cs,
                                          const S *__restrict__ sfw, S *__restrict__ ga, const Fix<S> &fx) {
     static_assert(SRC == SRC_STREAM || sizeof(S) == 4, "generated coefficient rows are FP32");
-    constexpr int RC = RecChunks<SRC>::N;
+    static_assert(RC >= 1 && RC <= 32, "chunks per warp");
     using RG = RecGeo<S, MP, RC>;
     constexpr int NS = RG::NS, WIN = MP + SR;
     constexpr bool BWD = MODE != FWD_RERUN;
@@ -1510,15 +1510,15 @@ template <typename S, int MP> struct UseMma {
     static constexpr bool ON = sizeof(S) == 4 && MP >= 8;
 };
 
-template <typename S, int MP> struct ScanGeo {
+template <typename S, int MP, int D = kScanDepth> struct ScanGeo {
     static constexpr int RS = YGeo<S, MP>::RS;
     static constexpr int YS = YGeo<S, MP>::YS;
     static constexpr int ZS = RS;         // a z vector: MP values padded to 16 bytes
     // per warp: kScanDepth map slots, kScanDepth z slots, two mbarriers,
     // two state-exchange buffers of RS values, and (FP32) the tile of the
     // running product of the tensor-core composition
-    static constexpr size_t MAPS_BYTES = size_t(kScanDepth) * YS * sizeof(S);
-    static constexpr size_t ZS_BYTES = size_t(kScanDepth) * ZS * sizeof(S);
+    static constexpr size_t MAPS_BYTES = size_t(D) * YS * sizeof(S);
+    static constexpr size_t ZS_BYTES = size_t(D) * ZS * sizeof(S);
     static constexpr size_t BAR_OFF = MAPS_BYTES + ZS_BYTES;
     static constexpr size_t XB_OFF = BAR_OFF + 16;
     static constexpr size_t R_OFF = ((XB_OFF + 2 * RS * sizeof(S) + 15) / 16) * 16;
@@ -1528,7 +1528,7 @@ template <typename S, int MP> struct ScanGeo {
     static_assert((YS * sizeof(S)) % 16 == 0 && (ZS * sizeof(S)) % 16 == 0, "16-byte maps");
     static_assert(BAR_OFF % 16 == 0 && WARP_BYTES % 128 == 0, "aligned warp slices");
     static_assert(RS <= 32, "a padded row fits the lanes of a warp");
-    static_assert(kScanDepth % 2 == 0, "two halves for double buffering");
+    static_assert(D % 2 == 0, "two halves for double buffering");
 };
 
 // x_new[lane] = p[0] + sum_{r=1..MP} p[r] * x[r-1], x held one component per lane
@@ -1769,8 +1769,8 @@ __device__ __forceinline__ S hop_smem(const S (&p)[MP + 1], S *xb, S x, int lane
 // bulk (TMA) copies of contiguous runs of maps, completing on one of two
 // mbarriers.  A run of up to kScanDepth maps arrives in one copy; a longer
 // run streams in batches of kScanDepth/2 through the two halves.
-template <typename S, int MP> struct ScanWarp {
-    using SG = ScanGeo<S, MP>;
+template <typename S, int MP, int D = kScanDepth> struct ScanWarp {
+    using SG = ScanGeo<S, MP, D>;
     S *maps, *zs, *xb;
     float *rs;  // tensor-core composition tile (FP32 only)
     uint64_t *bars;
@@ -1819,10 +1819,10 @@ template <typename S, int MP> struct ScanWarp {
 // Runs step(i, map, z) for i = 0 .. n-1 along a contiguous run of n maps
 // (memory order from map_lo / z_lo; the chain visits it backwards when
 // REVR).  False when a copy never landed (status set; nothing in flight).
-template <typename S, int MP, bool REVR, typename Step>
-__device__ __forceinline__ bool run_maps(ScanWarp<S, MP> &W, const S *map_lo, const S *z_lo, int n, Step step) {
-    using SG = ScanGeo<S, MP>;
-    constexpr int D = kScanDepth, H = kScanDepth / 2;
+template <typename S, int MP, bool REVR, int DEPTH, typename Step>
+__device__ __forceinline__ bool run_maps(ScanWarp<S, MP, DEPTH> &W, const S *map_lo, const S *z_lo, int n, Step step) {
+    using SG = ScanGeo<S, MP, DEPTH>;
+    constexpr int D = DEPTH, H = DEPTH / 2;
     if (n <= 0) return true;
     if (n <= D) {
         W.issue(0, n, map_lo, z_lo, 0);
@@ -1899,13 +1899,13 @@ __device__ __forceinline__ bool wait_counter(const unsigned *c, unsigned target,
 // The body of k2_scan for block `bid` of `nblocks` (a mixed-order launch runs
 // the bodies of several orders, each block one of them; every block of the
 // launch is resident, so the waits between blocks of one order end).
-template <typename S, int MP, int MODE>
+template <typename S, int MP, int MODE, int DEPTH = kScanDepth>
 __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt, int M, int64_t items_bound,
                                           const S *__restrict__ Y, const S *__restrict__ Z, S *__restrict__ GY,
                                           S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
                                           S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt,
                                           int *__restrict__ status, int *__restrict__ fix_list) {
-    using SG = ScanGeo<S, MP>;
+    using SG = ScanGeo<S, MP, DEPTH>;
     constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
     constexpr bool REV = ScanMode<MODE>::REV;
     constexpr bool TRANS = ScanMode<MODE>::TRANS;
@@ -1919,7 +1919,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         const int64_t n = __ldg(bt.gstart + bt.n);
         n_items = n < items_bound ? n : items_bound;
     }
-    ScanWarp<S, MP> W;
+    ScanWarp<S, MP, DEPTH> W;
     W.init(k2_smem + (size_t)warp * SG::WARP_BYTES, lane, status);
     pdl_wait();
     pdl_release();
@@ -1988,7 +1988,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         bool ok;
         if constexpr (VEC) {
             S zeta = S(0);
-            ok = run_maps<S, MP, REV>(W, group_maps(sg, g), group_zs(sg, g), len,
+            ok = run_maps<S, MP, REV, DEPTH>(W, group_maps(sg, g), group_zs(sg, g), len,
                                       [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
             if (lane < ZS) GZ[item * ZS + lane] = lane < MP ? zeta : S(0);
         } else if constexpr (UseMma<S, MP>::ON) {
@@ -2001,7 +2001,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
                 rs[idx] = (r == j && j < MP) ? 1.f : 0.f;
             }
             __syncwarp();
-            ok = run_maps<S, MP, REV>(W, group_maps(sg, g), nullptr, len,
+            ok = run_maps<S, MP, REV, DEPTH>(W, group_maps(sg, g), nullptr, len,
                                       [&](int, const S *m, const S *) { compose_mma<MP>(rs, m, lane); });
             // row 0 of the group map: y_g (column MP); row j+1: column j of Phi_g
             S *gy = GY + item * YS;
@@ -2017,7 +2017,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
 #pragma unroll
             for (int k = 0; k < MP; ++k) col[k] = (k == lane) ? S(1) : S(0);
             S yv = S(0);
-            ok = run_maps<S, MP, REV>(W, group_maps(sg, g), nullptr, len, [&](int, const S *m, const S *) {
+            ok = run_maps<S, MP, REV, DEPTH>(W, group_maps(sg, g), nullptr, len, [&](int, const S *m, const S *) {
                 if constexpr (!YLane<MP>::ON) yv = hop_step(m, nullptr, yv);
                 compose_step<S, MP>(col, m, lane);
             });
@@ -2049,7 +2049,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         int g;
         SigScan sg;
         locate(w0, b, g, sg);
-        held = group_len(sg, g) <= kScanDepth;
+        held = group_len(sg, g) <= DEPTH;
     }
 
     // ---- phase B1: the warp owning group 0 of a signal chains that
@@ -2075,7 +2075,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         // groups 0 .. nG-2 along the chain: the signal's group maps
         // [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG) backward
         const int64_t lo = sg.gbase + (REV ? 1 : 0);
-        const bool ok = run_maps<S, MP, REV>(W, GY + lo * YS, VEC ? GZ + lo * ZS : nullptr, nG - 1,
+        const bool ok = run_maps<S, MP, REV, DEPTH>(W, GY + lo * YS, VEC ? GZ + lo * ZS : nullptr, nG - 1,
                                              [&](int n, const S *m, const S *z) {
                                                  if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
                                                  x = hop_step(m, z, x);
@@ -2140,7 +2140,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         } else {
             const int64_t off = (REV && !FIX) ? 1 : 0;
             const S *zlo = VEC ? group_zs(sg, g) + off * ZS : nullptr;
-            if (!run_maps<S, MP, REV>(W, group_maps(sg, g) + off * YS, zlo, nh, step)) return;
+            if (!run_maps<S, MP, REV, DEPTH>(W, group_maps(sg, g) + off * YS, zlo, nh, step)) return;
         }
         if (!FIX) put(len - 1, x, S(0));
     }

@@ -625,3 +625,97 @@ def lp_filter_framewise(af, e, hop: int):
     """Differentiable frame-wise overlap-add filter (not Eq. 5: each frame is
     filtered with its own time-invariant coefficients af [B, F, M])."""
     return LPFramewiseFunction.apply(af, e, hop)
+
+
+# ---------------------------------------------------------------------------
+# Mixed orders: signals of different lengths and orders in one call
+# (lp_tv_*_mixed_f32 in include/tvlp.h).
+# ---------------------------------------------------------------------------
+class PackedMixed:
+    """Layout of a mixed-order batch: rows of e, s, gs, ge back to back
+    (signal b at rows offsets[b] .. offsets[b+1]), and each signal's
+    coefficient rows of its own order M_b as one block of a flat array,
+    starting at element aoff[b] (a multiple of 4).  Keeps host and device
+    copies of the offsets and orders."""
+
+    def __init__(self, lengths, orders, device):
+        import numpy as np
+        self.lengths = [int(x) for x in lengths]
+        self.orders = [int(x) for x in orders]
+        assert len(self.lengths) == len(self.orders)
+        self.n = len(self.lengths)
+        self.offsets_host = np.zeros(self.n + 1, dtype=np.int64)
+        self.offsets_host[1:] = np.cumsum(self.lengths)
+        self.orders_host = np.asarray(self.orders, dtype=np.int32)
+        self.aoff = np.zeros(self.n + 1, dtype=np.int64)
+        n_a = _lib.lp_tv_mixed_coeff_offsets(self.n, self.offsets_host.ctypes.data, self.orders_host.ctypes.data,
+                                             self.aoff.ctypes.data)
+        if n_a < 0:
+            raise ValueError("invalid lengths or orders")
+        self.total = int(self.offsets_host[-1])
+        self.total_a = int(n_a)
+        self.device = torch.device(device)
+        self.offsets = torch.tensor(self.offsets_host, device=device)
+        self.orders_dev = torch.tensor(self.orders_host, device=device)
+
+    def pack_rows(self, xs):
+        out = torch.zeros((self.total,), dtype=torch.float32, device=self.device)
+        for x, st, n in zip(xs, self.offsets_host[:-1], self.lengths):
+            out[int(st):int(st) + n] = x
+        return out
+
+    def unpack_rows(self, rows):
+        return [rows[int(st):int(st) + n] for st, n in zip(self.offsets_host[:-1], self.lengths)]
+
+    def pack_coeffs(self, xs):
+        """Per-signal [len_b, M_b] tensors into the flat coefficient array."""
+        out = torch.zeros((max(self.total_a, 1),), dtype=torch.float32, device=self.device)
+        for x, ao, n, m in zip(xs, self.aoff[:-1], self.lengths, self.orders):
+            out[int(ao):int(ao) + n * m] = x.reshape(-1)
+        return out
+
+    def unpack_coeffs(self, flat):
+        return [flat[int(ao):int(ao) + n * m].reshape(n, m)
+                for ao, n, m in zip(self.aoff[:-1], self.lengths, self.orders)]
+
+    def workspace(self, chunk: int = 0):
+        nb = _lib.lp_tv_workspace_bytes_mixed(self.n, self.offsets_host.ctypes.data, self.orders_host.ctypes.data,
+                                              chunk)
+        if nb == 0 and self.n > 0:
+            raise ValueError("invalid mixed batch")
+        return torch.empty(max(nb, 256), dtype=torch.uint8, device=self.device)
+
+
+def lp_tv_forward_mixed(pm: PackedMixed, a, e, zi=None, *, chunk: int = 0, ws=None):
+    """Eq. 5 for every signal of a mixed batch with its own order; a: the
+    flat coefficient array, e: packed rows, zi: [n, 32] or None."""
+    dev = pm.device
+    _check(e, "e", (pm.total,), torch.float32, dev)
+    _check(zi, "zi", (pm.n, 32), torch.float32, dev)
+    with torch.cuda.device(dev):
+        s = torch.empty((pm.total,), device=dev)
+        if ws is None:
+            ws = pm.workspace(chunk)
+        _lib.lp_tv_forward_mixed(pm.n, _ptr(pm.offsets), _ptr(pm.orders_dev), pm.offsets_host.ctypes.data,
+                                 pm.orders_host.ctypes.data, _ptr(a), _ptr(e), _ptr(zi), _ptr(s), chunk, _ptr(ws),
+                                 ws.numel(), _stream(dev))
+    return s
+
+
+def lp_tv_backward_mixed(pm: PackedMixed, gs, a, s, zi=None, *, need_ga: bool = True, need_gzi: bool = True,
+                         chunk: int = 0, ws=None, reuse_forward: bool = False):
+    """(ge [total], ga (flat, like a) or None, gzi [n, 32] or None)."""
+    dev = pm.device
+    _check(gs, "gs", (pm.total,), torch.float32, dev)
+    with torch.cuda.device(dev):
+        ge = torch.empty((pm.total,), device=dev)
+        ga = torch.zeros_like(a) if need_ga else None
+        gzi = torch.zeros((pm.n, 32), device=dev) if need_gzi else None
+        if ws is None:
+            ws = pm.workspace(chunk)
+            reuse_forward = False
+        flags = _lib.LP_BWD_REUSE_FORWARD if reuse_forward else 0
+        _lib.lp_tv_backward_mixed(pm.n, _ptr(pm.offsets), _ptr(pm.orders_dev), pm.offsets_host.ctypes.data,
+                                  pm.orders_host.ctypes.data, _ptr(gs), _ptr(a), _ptr(s), _ptr(zi), _ptr(ge),
+                                  _ptr(ga), _ptr(gzi), chunk, flags, _ptr(ws), ws.numel(), _stream(dev))
+    return ge, ga, gzi

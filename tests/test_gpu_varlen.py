@@ -178,3 +178,99 @@ def test_uneven_full_length_sampled():
         for name, x, r in (("s", pk.unpack(s)[k], rs), ("ge", pk.unpack(ge)[k], rge), ("ga", pk.unpack(ga)[k], rga)):
             err = norm_err(x.cpu().numpy()[None], r)
             assert err.max() <= TOL_F32, (name, k, err)
+
+
+# ---------------------------------------------------------------------------
+# Mixed orders in one call (lp_tv_*_mixed_f32)
+# ---------------------------------------------------------------------------
+def _mixed_signals(lengths, orders, seed, gen="stable", kmax=0.95, zi=True):
+    out = []
+    for k, (n, m) in enumerate(zip(lengths, orders)):
+        w = inputs.make("mx", 1, max(n, 1), m, seed=seed + 31 * k, gen=gen, kmax=kmax, with_zi=zi,
+                        excitation="pulse" if gen == "literal" else "noise")
+        out.append((w.a[0, :n], w.e[0, :n], w.gs[0, :n], None if w.zi is None else w.zi[0]))
+    return out
+
+
+def _run_mixed(sig, orders, chunk=0, zi=True, reuse=True):
+    lengths = [x[0].shape[0] for x in sig]
+    pm = ops.PackedMixed(lengths, orders, DEV)
+    a = pm.pack_coeffs([torch.tensor(x[0], device=DEV) for x in sig])
+    e = pm.pack_rows([torch.tensor(x[1], device=DEV) for x in sig])
+    gs = pm.pack_rows([torch.tensor(x[2], device=DEV) for x in sig])
+    z = None
+    if zi:
+        z = torch.zeros((pm.n, 32), device=DEV)
+        for b, x in enumerate(sig):
+            z[b, :orders[b]] = torch.tensor(x[3], device=DEV)
+    ws = pm.workspace(chunk)
+    s = ops.lp_tv_forward_mixed(pm, a, e, z, chunk=chunk, ws=ws)
+    ge, ga, gzi = ops.lp_tv_backward_mixed(pm, gs, a, s, z, need_gzi=zi, chunk=chunk, ws=ws, reuse_forward=reuse)
+    torch.cuda.synchronize()
+    assert _lib.lp_tv_device_status() == 0
+    out = []
+    for b in range(pm.n):
+        out.append((pm.unpack_rows(s)[b].cpu().numpy(), pm.unpack_rows(ge)[b].cpu().numpy(),
+                    pm.unpack_coeffs(ga)[b].cpu().numpy(),
+                    None if gzi is None else gzi[b, :orders[b]].cpu().numpy()))
+    return out
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+@pytest.mark.parametrize("zi", [True, False])
+def test_mixed_orders_match_oracle(reuse, zi):
+    """Signals of orders 16, 22, 30 and of orders that pad (5, 17, 26) with
+    ragged and empty lengths, in one call per direction."""
+    lengths = [5000, 0, 3001, 160, 161, 2400, 1, 4800, 999, 777, 1500]
+    orders = [16, 22, 30, 22, 16, 30, 5, 17, 26, 30, 22]
+    sig = _mixed_signals(lengths, orders, seed=300)
+    got = _run_mixed(sig, orders, zi=zi, reuse=reuse)
+    _check_oracle(sig, got, zi=zi)
+
+
+def test_mixed_orders_alone_equals_in_the_mix_and_single_order_calls():
+    """With a fixed chunk: every signal's results are the same bits alone,
+    in the mixed batch, and in a single-order varlen call of its order."""
+    chunk = 160
+    lengths = [4000, 123, 9000, 2048, 777, 3500]
+    orders = [16, 30, 22, 16, 22, 30]
+    sig = _mixed_signals(lengths, orders, seed=700)
+    mix = _run_mixed(sig, orders, chunk=chunk)
+    for k in range(len(sig)):
+        alone = _run_mixed([sig[k]], [orders[k]], chunk=chunk)[0]
+        single = _run([sig[k]], orders[k], chunk=chunk)[0]
+        for x, y, z in zip(alone, mix[k], single):
+            assert np.array_equal(x, y)
+            assert np.array_equal(x, z)
+
+
+def test_mixed_resonant_signals():
+    """Resonant signals (literal generator, |k| <= 0.8) of three orders in
+    one call: the defect correction runs per order group.  (At order 30
+    this generator diverges, max |s| about 1e25: beyond FP32 for any
+    algorithm, so the orders here stop at 22.)"""
+    lengths = [48000, 30000, 20000, 48000]
+    orders = [22, 16, 12, 22]
+    sig = _mixed_signals(lengths, orders, seed=5, gen="literal", kmax=0.8, zi=False)
+    got = _run_mixed(sig, orders, zi=False)
+    _check_oracle(sig, got, zi=False)
+
+
+def test_uneven_batching_one_call():
+    """The uneven workload (reduced size): lengths uniform in [1200, 24000],
+    orders drawn from {16, 22, 30}, all in one mixed call per direction,
+    each signal against the oracle."""
+    rng = np.random.default_rng(4)
+    n = 24
+    lengths = rng.integers(1200, 24001, size=n).tolist()
+    orders = rng.choice([16, 22, 30], size=n).tolist()
+    sig = _mixed_signals(lengths, orders, seed=900)
+    got = _run_mixed(sig, orders)
+    _check_oracle(sig, got)
+
+
+def test_mixed_invalid_orders():
+    pm_ok = ops.PackedMixed([10, 20], [4, 8], DEV)
+    with pytest.raises(ValueError):
+        ops.PackedMixed([10, 20], [4, 40], DEV).workspace()
+    assert pm_ok.total_a == 40 + 160
