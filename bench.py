@@ -775,14 +775,16 @@ def run_uneven(args):
         e = pk.pack([x[1] for x in sig])
         gs = pk.pack([x[2] for x in sig])
         del sig
-        chunk, tried = autotune.tune_varlen(lens, M, device=dev, iters=5)
+        chunk, shape, tried, tried_shapes = autotune.tune_varlen(lens, M, device=dev, iters=5, shapes=True)
         nb = _lib.lp_tv_workspace_bytes_varlen(pk.n, pk.total, M, chunk)
         ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
         s = torch.empty_like(e)
         ge = torch.empty_like(e)
         ga = torch.empty_like(a)
         buckets.append(dict(M=M, idx=idx, lens=lens, pk=pk, a=a, e=e, gs=gs, s=s, ge=ge, ga=ga, ws=ws, chunk=chunk,
-                            tried={str(k): round(v, 4) for k, v in tried.items()}))
+                            shape=shape, tried={str(k): round(v, 4) for k, v in tried.items()},
+                            tried_shapes={f"{k[0]}x lanes, {k[1]} chunks/warp": round(v, 4)
+                                          for k, v in tried_shapes.items()}))
     stream = torch.cuda.current_stream(dev)
     # the same signals as one mixed-order batch: one call per direction
     pm = ops.PackedMixed(lengths, orders, dev)
@@ -806,6 +808,7 @@ def run_uneven(args):
     def step_per_order():
         sp = torch.cuda.current_stream(dev).cuda_stream
         for bk in buckets:
+            _lib.lp_tv_set_threads_per_chunk(*bk["shape"])  # the tuned launch shape of this order
             pk = bk["pk"]
             _lib.lp_tv_forward_varlen(_lib.LP_DTYPE_F32, pk.n, pk.offsets.data_ptr(), pk.total, bk["M"],
                                       bk["a"].data_ptr(), bk["e"].data_ptr(), None, bk["s"].data_ptr(), None,
@@ -814,6 +817,7 @@ def run_uneven(args):
                                        bk["gs"].data_ptr(), bk["a"].data_ptr(), bk["s"].data_ptr(), None,
                                        bk["ge"].data_ptr(), bk["ga"].data_ptr(), None, bk["chunk"],
                                        _lib.LP_BWD_REUSE_FORWARD, bk["ws"].data_ptr(), bk["ws"].numel(), sp)
+        _lib.lp_tv_set_threads_per_chunk(1, 16)
 
     def timed(step):
         for _ in range(max(3, args.warmup)):
@@ -916,7 +920,10 @@ def run_uneven(args):
                                f"M from {list(UNEVEN_ORDERS)}, FP32, stable reflection generator, hop 120",
                    "samples": nsamp,
                    "buckets": [{"M": bk["M"], "signals": len(bk["lens"]), "samples": sum(bk["lens"]),
-                                "chunk": bk["chunk"], "autotune_ms": bk["tried"]} for bk in buckets],
+                                "chunk": bk["chunk"], "autotune_ms": bk["tried"],
+                                "launch_shape": {"summary_lane_factor": bk["shape"][0],
+                                                 "rerun_chunks_per_warp": bk["shape"][1]},
+                                "autotune_shape_ms": bk["tried_shapes"]} for bk in buckets],
                    "l2": "inputs far beyond L2, no flush"},
         "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "GB/s": round(gbs, 1),
                           "frac_of_hbm": round(gbs / hbm, 4)},

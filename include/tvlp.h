@@ -124,6 +124,22 @@ int lp_tv_check_finite_f64(const double *x, size_t n, void *stream);
  */
 int lp_tv_set_profile_events(void **events, int n);
 
+/*
+ * Threads per signal of the chunked FP32 calls with streamed coefficients
+ * (uniform and varlen batches; the choice an autotuner makes beside the
+ * chunk length, no counterpart in the paper).  Applies to the later calls
+ * made from the calling thread:
+ *   k1_lane_factor       1: the summary pass runs a chunk's M+1 recursions
+ *                        on G lanes (the default packing for the order),
+ *                        2: on 2G lanes with half the recursions each;
+ *   rerun_chunks_per_warp  16 (default) or 8 chunks per warp in the
+ *                        one-recursion passes.
+ * 0 selects the default.  Results are the same up to floating-point
+ * rounding (the packing changes the order of the summary's operations).
+ * LP_EINVAL for other values.  Mixed-order calls keep their own shapes.
+ */
+int lp_tv_set_threads_per_chunk(int k1_lane_factor, int rerun_chunks_per_warp);
+
 /* Human-readable name of an error code. Never NULL. */
 const char *lp_strerror(int code);
 

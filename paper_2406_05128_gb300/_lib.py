@@ -47,7 +47,7 @@ EXPORTS = (
     "lp_serve_poll", "lp_serve_drain", "lp_serve_stats_get", "lp_serve_now_ns",
     "lp_framewise_num_frames", "lp_framewise_outputs_bytes", "lp_framewise_forward_f32",
     "lp_framewise_backward_f32", "lp_tv_mixed_coeff_offsets", "lp_tv_workspace_bytes_mixed",
-    "lp_tv_forward_mixed_f32", "lp_tv_backward_mixed_f32",
+    "lp_tv_forward_mixed_f32", "lp_tv_backward_mixed_f32", "lp_tv_set_threads_per_chunk",
 )
 
 LP_SERVE_SYNTH = 0
@@ -151,6 +151,8 @@ def _declare(lib):
     lib.lp_tv_selftest_wait.restype = i32
     lib.lp_tv_workspace_bytes_ti.argtypes = [i32, i64, i32, i32]
     lib.lp_tv_workspace_bytes_ti.restype = sz
+    lib.lp_tv_set_threads_per_chunk.argtypes = [i32, i32]
+    lib.lp_tv_set_threads_per_chunk.restype = i32
     lib.lp_tv_mixed_coeff_offsets.argtypes = [i32, vp, vp, vp]
     lib.lp_tv_mixed_coeff_offsets.restype = i64
     lib.lp_tv_workspace_bytes_mixed.argtypes = [i32, vp, vp, i32]
@@ -407,3 +409,7 @@ def lp_tv_backward_mixed(n, offsets, orders, offsets_host, orders_host, gs, a, s
                          ws_bytes, stream):
     _check(load().lp_tv_backward_mixed_f32(n, offsets, orders, offsets_host, orders_host, gs, a, s, zi, ge, ga, gzi,
                                            chunk, flags, ws, ws_bytes, stream), "lp_tv_backward_mixed_f32")
+
+
+def lp_tv_set_threads_per_chunk(k1_lane_factor: int = 1, rerun_chunks_per_warp: int = 16):
+    _check(load().lp_tv_set_threads_per_chunk(k1_lane_factor, rerun_chunks_per_warp), "lp_tv_set_threads_per_chunk")

@@ -31,7 +31,10 @@ namespace tvlp {
 namespace {
 thread_local void **g_prof_events = nullptr;
 thread_local int g_prof_n = 0;
+thread_local LaunchShape g_shape = {1, 16};
 }  // namespace
+
+LaunchShape launch_shape() { return g_shape; }
 
 void profile_mark(int k, bool end, cudaStream_t st) {
     if (g_prof_events == nullptr || k < 0 || k >= g_prof_n) return;
@@ -708,6 +711,16 @@ const char *lp_strerror(int code) {
 }
 
 const char *lp_version(void) { return "tvlp 0.1 sm_103a"; }
+
+int lp_tv_set_threads_per_chunk(int k1_lane_factor, int rerun_chunks_per_warp) {
+    if (k1_lane_factor == 0) k1_lane_factor = 1;
+    if (rerun_chunks_per_warp == 0) rerun_chunks_per_warp = 16;
+    if ((k1_lane_factor != 1 && k1_lane_factor != 2) || (rerun_chunks_per_warp != 16 && rerun_chunks_per_warp != 8))
+        return LP_EINVAL;
+    g_shape.k1_lane_factor = k1_lane_factor;
+    g_shape.rec_chunks = rerun_chunks_per_warp;
+    return LP_OK;
+}
 
 int lp_tv_set_profile_events(void **events, int n) {
     if (events != nullptr && n < 0) return LP_EINVAL;

@@ -13,10 +13,13 @@ constexpr int kMaxDevices = 64;
 
 template <typename S, int MP> using DefaultSumGeo = SumGeo<S, MP, Pack<MP>::G, Pack<MP>::R>;
 
-template <typename S, int MP> inline int k1_warps_per_block() {
-    int w = (int)(kSmemBudget / DefaultSumGeo<S, MP>::WARP_BYTES);
+template <typename S, int MP> using WideSumGeo = SumGeo<S, MP, PackWide<MP>::G, PackWide<MP>::R>;
+
+template <typename GE> inline int k1_warps_for() {
+    int w = (int)(kSmemBudget / GE::WARP_BYTES);
     return w > 8 ? 8 : (w < 1 ? 1 : w);
 }
+template <typename S, int MP> inline int k1_warps_per_block() { return k1_warps_for<DefaultSumGeo<S, MP>>(); }
 
 // Launch with programmatic stream serialization (the kernel may start while
 // the previous kernel on the stream finishes; see pdl_wait in the kernels),
@@ -112,21 +115,32 @@ template <typename S, int MP> struct Launch {
         return k < 0 ? 0 : k;
     }
 
-    template <bool BWD, int SRC = SRC_STREAM>
-    static cudaError_t summary(const Problem &p, const Batch &bt, const S *a, const S *u, S *Y, unsigned *cnt,
-                               cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
+    template <typename G1, bool BWD, int SRC>
+    static cudaError_t summary_as(const Problem &p, const Batch &bt, const S *a, const S *u, S *Y, unsigned *cnt,
+                                  cudaStream_t st, const CoefSrc &cs) {
         static std::atomic<bool> done[kMaxDevices] = {};
-        const int W = k1_warps_per_block<S, MP>();
-        const size_t smem = (size_t)W * GE::WARP_BYTES;
-        auto kern = k1_summary<S, MP, GE::G, GE::R, BWD, SRC>;
+        const int W = k1_warps_for<G1>();
+        const size_t smem = (size_t)W * G1::WARP_BYTES;
+        auto kern = k1_summary<S, MP, G1::G, G1::R, BWD, SRC>;
         cudaError_t err = allow_smem(kern, smem, done);
         if (err != cudaSuccess) return err;
-        const int64_t per_block = (int64_t)W * GE::CPW;
+        const int64_t per_block = (int64_t)W * G1::CPW;
         const int64_t grid = (p.NQ + per_block - 1) / per_block;
         // the next pass (re-run or adjoint re-run) starts on this pass's first stages
         const int l2 = SRC == SRC_STREAM ? l2_word(l2_keep(p), L2_LAST, L2_FIRST) : 0;
         return launch(kern, dim3((unsigned)grid), dim3(32 * W), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Y,
                       p.M == MP ? 1 : 0, cnt, p.B + 1, l2, p.status, cs);
+    }
+
+    template <bool BWD, int SRC = SRC_STREAM>
+    static cudaError_t summary(const Problem &p, const Batch &bt, const S *a, const S *u, S *Y, unsigned *cnt,
+                               cudaStream_t st, const CoefSrc &cs = CoefSrc()) {
+        if constexpr (SRC == SRC_STREAM && sizeof(S) == 4) {
+            // the autotuner's alternative: twice the lanes per chunk
+            if (launch_shape().k1_lane_factor == 2)
+                return summary_as<WideSumGeo<S, MP>, BWD, SRC>(p, bt, a, u, Y, cnt, st, cs);
+        }
+        return summary_as<GE, BWD, SRC>(p, bt, a, u, Y, cnt, st, cs);
     }
 
     // Two-level scan in one cooperative launch: as many blocks as the items
@@ -165,21 +179,34 @@ template <typename S, int MP> struct Launch {
                       GZ, GX, zi, X, ckpt, cnt, p.status, list);
     }
 
-    template <int MODE, bool EXACT, int SRC = SRC_STREAM>
-    static cudaError_t rec_exact(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin,
-                                 const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
-                                 cudaStream_t st, const CoefSrc &cs = CoefSrc(), const S *sfw = nullptr,
-                                 S *ga = nullptr, const Fix<S> &fx = Fix<S>()) {
+    template <int MODE, bool EXACT, int SRC, int RC>
+    static cudaError_t rec_as(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin, const S *zi,
+                              S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs, cudaStream_t st,
+                              const CoefSrc &cs, const S *sfw, S *ga, const Fix<S> &fx) {
         static std::atomic<bool> done[kMaxDevices] = {};
-        constexpr int RC = RecChunks<SRC>::N;
         using RG = RecGeo<S, MP, RC>;
-        auto kern = k_rec<S, MP, EXACT, MODE, SRC>;
+        auto kern = k_rec<S, MP, EXACT, MODE, SRC, RC>;
         constexpr size_t smem = MODE == BWD_GRAD ? RG::SMEM_GA : RG::SMEM;
         cudaError_t err = allow_smem(kern, smem, done);
         if (err != cudaSuccess) return err;
         const int64_t grid = (p.NQ + RC - 1) / RC;
         return launch(kern, dim3((unsigned)grid), dim3(32), smem, st, false, bt, p.M, p.L, p.NQ, a, u, Xin, zi,
                       out, Zout, gzi, reverse, cnt, p.B + 1, l2, xs, p.status, cs, sfw, ga, fx);
+    }
+
+    template <int MODE, bool EXACT, int SRC = SRC_STREAM>
+    static cudaError_t rec_exact(const Problem &p, const Batch &bt, const S *a, const S *u, const S *Xin,
+                                 const S *zi, S *out, S *Zout, S *gzi, int reverse, unsigned *cnt, int l2, int xs,
+                                 cudaStream_t st, const CoefSrc &cs = CoefSrc(), const S *sfw = nullptr,
+                                 S *ga = nullptr, const Fix<S> &fx = Fix<S>()) {
+        if constexpr (SRC == SRC_STREAM && sizeof(S) == 4 && MODE != BWD_GRAD) {
+            // the autotuner's alternative: 8 chunks per warp
+            if (launch_shape().rec_chunks == 8)
+                return rec_as<MODE, EXACT, SRC, 8>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs, st, cs,
+                                                   sfw, ga, fx);
+        }
+        return rec_as<MODE, EXACT, SRC, RecChunks<SRC>::N>(p, bt, a, u, Xin, zi, out, Zout, gzi, reverse, cnt, l2, xs,
+                                                            st, cs, sfw, ga, fx);
     }
 
     // one recursion per chunk; `cnt`, when given, is zeroed for a scan that

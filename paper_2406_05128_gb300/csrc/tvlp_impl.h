@@ -126,6 +126,16 @@ inline size_t ws_offset(const Problem &p, size_t sz, int region) {
 }
 inline size_t ws_bytes(const Problem &p, size_t sz) { return ws_offset(p, sz, 10); }
 
+// Threads per signal of the streamed FP32 calls made from this thread
+// (lp_tv_set_threads_per_chunk): the summary pass's lanes per chunk
+// (1: the default packing, 2: twice the lanes) and the re-run passes'
+// chunks per warp (16 or 8).
+struct LaunchShape {
+    int k1_lane_factor;
+    int rec_chunks;
+};
+LaunchShape launch_shape();
+
 // Records the caller's profiling event for kernel k (begin or end) when a
 // hook is installed on this thread (lp_tv_set_profile_events).
 void profile_mark(int k, bool end, cudaStream_t st);

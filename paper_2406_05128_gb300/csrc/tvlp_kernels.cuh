@@ -69,6 +69,18 @@ template <> struct Pack<16> { static constexpr int G = 4,  R = 5; };
 template <> struct Pack<22> { static constexpr int G = 4,  R = 6; };
 template <> struct Pack<30> { static constexpr int G = 8,  R = 4; };
 template <> struct Pack<32> { static constexpr int G = 16, R = 3; };
+// The alternative packing the autotuner can choose: twice the lanes per
+// chunk, half the recursions per lane (more threads per signal, fewer
+// independent chains per lane; odd R runs without packed pairs).
+template <int MP> struct PackWide;
+template <> struct PackWide<2>  { static constexpr int G = 2,  R = 2; };
+template <> struct PackWide<4>  { static constexpr int G = 2,  R = 3; };
+template <> struct PackWide<8>  { static constexpr int G = 4,  R = 3; };
+template <> struct PackWide<12> { static constexpr int G = 4,  R = 4; };
+template <> struct PackWide<16> { static constexpr int G = 8,  R = 3; };
+template <> struct PackWide<22> { static constexpr int G = 8,  R = 3; };
+template <> struct PackWide<30> { static constexpr int G = 16, R = 2; };
+template <> struct PackWide<32> { static constexpr int G = 32, R = 2; };
 
 // Bank-conflict helper: `groups` readers at multiples of `stride_words`
 // reading 8-byte words; worst number of readers sharing a bank pair.
@@ -1439,14 +1451,14 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
     }
 }
 
-template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM>
+template <typename S, int MP, bool EXACT, int MODE, int SRC = SRC_STREAM, int RC = RecChunks<SRC>::N>
 __global__ void __launch_bounds__(32)
     k_rec(Batch bt, int M, int L, int64_t NQ, const S *__restrict__ a, const S *__restrict__ u,
           const S *__restrict__ Xin, const S *__restrict__ zi, S *__restrict__ out, S *__restrict__ Zout,
           S *__restrict__ gzi, int reverse, unsigned *__restrict__ scan_cnt, int n_cnt, int l2, int xs,
           int *__restrict__ status, CoefSrc cs, const S *__restrict__ sfw, S *__restrict__ ga, Fix<S> fx) {
-    rec_body<S, MP, EXACT, MODE, SRC>(blockIdx.x, gridDim.x, bt, M, L, NQ, a, u, Xin, zi, out, Zout, gzi, reverse,
-                                      scan_cnt, n_cnt, l2, xs, status, cs, sfw, ga, fx);
+    rec_body<S, MP, EXACT, MODE, SRC, RC>(blockIdx.x, gridDim.x, bt, M, L, NQ, a, u, Xin, zi, out, Zout, gzi,
+                                          reverse, scan_cnt, n_cnt, l2, xs, status, cs, sfw, ga, fx);
 }
 
 // ---------------------------------------------------------------------------

@@ -166,9 +166,20 @@ __global__ void __launch_bounds__(kMixGradRows)
     __syncthreads();
     // element idx of the tile is row idx / m, coefficient idx % m + 1: a
     // thread per element keeps the shared stores conflict-free
-    for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
-        const int rr = idx / m, i = idx - rr * m + 1;
-        tile[idx] = -g_t[rr] * s_t[32 + rr - i];
+    {
+        // (row, coefficient) of the thread's element, advanced without a
+        // division per element
+        const int step_r = kMixGradRows / m, step_i = kMixGradRows - step_r * m;
+        int rr = threadIdx.x / m, i = threadIdx.x - rr * m;
+        for (int idx = threadIdx.x; idx < rows * m; idx += kMixGradRows) {
+            tile[idx] = -g_t[rr] * s_t[32 + rr - i - 1];
+            rr += step_r;
+            i += step_i;
+            if (i >= m) {
+                i -= m;
+                ++rr;
+            }
+        }
     }
     fence_proxy_async();
     __syncthreads();

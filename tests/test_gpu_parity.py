@@ -250,3 +250,24 @@ def test_autograd_matches_oracle_f32():
     assert_close("s", s.detach().cpu().numpy(), rs, TOL_F32)
     assert_close("ge", e.grad.cpu().numpy(), rge, TOL_F32)
     assert_close("ga", a.grad.cpu().numpy(), rga, TOL_F32)
+
+
+@pytest.mark.parametrize("shape", [(2, 16), (1, 8), (2, 8)])
+def test_parity_launch_shapes(shape):
+    """The autotuner's alternative launch shapes (summary lanes per chunk,
+    re-run chunks per warp) against the oracle, uniform and varlen."""
+    from paper_2406_05128_gb300 import autotune
+    w = inputs.make("shape", 3, 7001, 22, seed=41, gen="stable", with_zi=True)
+    with autotune.use_shape(shape):
+        got = _run(w, chunk=96)
+    _compare(w, got, TOL_F32)
+    w16 = inputs.make("shape16", 2, 3001, 16, seed=42, gen="stable", with_zi=True)
+    with autotune.use_shape(shape):
+        got16 = _run(w16, chunk=0, reuse=False)
+    _compare(w16, got16, TOL_F32)
+
+
+def test_autotuner_picks_a_shape():
+    from paper_2406_05128_gb300 import autotune
+    L, shape, res, res_sh = autotune.tune_uniform(4, 12000, 22, iters=2, shapes=True)
+    assert L in res and shape in autotune.SHAPES and set(res_sh) == set(autotune.SHAPES)

@@ -133,3 +133,14 @@ def test_selftest_rejects_unknown_wait_without_launching(lib):
     from paper_2406_05128_gb300 import _lib
     assert lib.lp_tv_selftest_wait(0, None) == _lib.LP_EINVAL
     assert lib.lp_tv_selftest_wait(3, None) == _lib.LP_EINVAL
+
+
+def test_threads_per_chunk_arguments(lib):
+    """The launch-shape setting (host only): defaults and the two
+    alternatives are accepted, anything else is LP_EINVAL."""
+    from paper_2406_05128_gb300 import _lib
+    assert lib.lp_tv_set_threads_per_chunk(0, 0) == _lib.LP_OK
+    assert lib.lp_tv_set_threads_per_chunk(2, 8) == _lib.LP_OK
+    assert lib.lp_tv_set_threads_per_chunk(1, 16) == _lib.LP_OK
+    assert lib.lp_tv_set_threads_per_chunk(3, 16) == _lib.LP_EINVAL
+    assert lib.lp_tv_set_threads_per_chunk(1, 12) == _lib.LP_EINVAL
