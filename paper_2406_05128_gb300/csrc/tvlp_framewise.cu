@@ -106,13 +106,17 @@ __global__ void __launch_bounds__(32, 1) k_fw_forward(int64_t T, int M, int hop,
         float *orow = acc + (lane + p) * row;
 #pragma unroll 1
         for (int j0 = 0; j0 < hop; j0 += SR) {
+            // the block's inputs first, its outputs after: no shared-memory
+            // access waits inside the recursion
+            float uu[SR], vv[SR];
+#pragma unroll
+            for (int j = 0; j < SR; ++j) uu[j] = valid ? win[p * hop + j0 + j] * ir[j0 + j] : 0.f;
+#pragma unroll
+            for (int j = 0; j < SR; ++j) vv[j] = fwd_step_win<float, MP, WIN>(h, c, uu[j], j);
 #pragma unroll
             for (int j = 0; j < SR; ++j) {
-                const int n = p * hop + j0 + j;
-                const float u = valid ? win[n] * ir[j0 + j] : 0.f;
-                const float v = fwd_step_win<float, MP, WIN>(h, c, u, j);
-                orow[j0 + j] += v;
-                if (yb != nullptr && valid) yb[(int64_t)n * F + f] = v;
+                orow[j0 + j] += vv[j];
+                if (yb != nullptr && valid) yb[(int64_t)(p * hop + j0 + j) * F + f] = vv[j];
             }
             slide<float, MP, WIN>(h);
         }
@@ -155,15 +159,18 @@ __global__ void __launch_bounds__(32, 1) k_fw_backward(int64_t T, int M, int hop
 #pragma unroll 1
         for (int j0 = hop - SR; j0 >= 0; j0 -= SR) {
             const int nh = p * hop + j0 + SR - 1;  // first (latest) step of the block
+            float uu[SR], vv[SR];
+#pragma unroll
+            for (int j = 0; j < SR; ++j) uu[j] = valid ? ir[j0 + SR - 1 - j] : 0.f;
 #pragma unroll
             for (int j = 0; j < SR; ++j) {
-                const int jj = SR - 1 - j;  // offset in the hop row
-                const float u = valid ? ir[j0 + jj] : 0.f;
-                const float v = bwd_step_win<float, MP, WIN>(q, c, u, j);
-                orow[j0 + jj] += win[nh - j] * v;
+                const float v = bwd_step_win<float, MP, WIN>(q, c, uu[j], j);
+                vv[j] = v;
 #pragma unroll
                 for (int i = 1; i <= MP; ++i) g[i - 1] = fmaf(-v, yw[j + i - 1], g[i - 1]);
             }
+#pragma unroll
+            for (int j = 0; j < SR; ++j) orow[j0 + SR - 1 - j] += win[nh - j] * vv[j];
             slide<float, MP, WIN>(q);
 #pragma unroll
             for (int k = 0; k < WIN - SR; ++k) yw[k] = yw[k + SR];
