@@ -1184,8 +1184,51 @@ template <typename S, bool BWD>
 __device__ __forceinline__ void rec_load_inputs(S (&uv)[SRS], const S *__restrict__ u, int L, int s, bool active,
                                                 int64_t base, int n) {
     const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
+    const S *src = u + base + roff;
+    if (active && roff + SRS <= n && aligned16(src)) {
+        // a full, aligned stage: 16-byte loads
+        if constexpr (sizeof(S) == 4) {
 #pragma unroll
-    for (int r = 0; r < SRS; ++r) uv[r] = (active && roff + r < n) ? __ldg(u + base + roff + r) : S(0);
+            for (int k = 0; k < SRS / 4; ++k) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + k);
+                uv[4 * k] = v.x;
+                uv[4 * k + 1] = v.y;
+                uv[4 * k + 2] = v.z;
+                uv[4 * k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < SRS / 2; ++k) {
+                const double2 v = __ldg(reinterpret_cast<const double2 *>(src) + k);
+                uv[2 * k] = v.x;
+                uv[2 * k + 1] = v.y;
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < SRS; ++r) uv[r] = (active && roff + r < n) ? __ldg(src + r) : S(0);
+}
+
+// A lane's outputs of one stage (rows roff .. roff + SRS - 1 of its chunk,
+// the first nv of them valid) from registers to memory: 16-byte stores when
+// the stage is full and aligned.
+template <typename S>
+__device__ __forceinline__ void rec_store_outputs(S *dst, const S (&yv)[SRS], int nv) {
+    if (nv == SRS && aligned16(dst)) {
+        if constexpr (sizeof(S) == 4) {
+#pragma unroll
+            for (int k = 0; k < SRS / 4; ++k)
+                reinterpret_cast<float4 *>(dst)[k] = make_float4(yv[4 * k], yv[4 * k + 1], yv[4 * k + 2], yv[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < SRS / 2; ++k) reinterpret_cast<double2 *>(dst)[k] = make_double2(yv[2 * k], yv[2 * k + 1]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < SRS; ++r)
+        if (r < nv) dst[r] = yv[r];
 }
 
 // The body of k_rec for block `bid` of `nblocks` (a mixed-order launch runs
@@ -1354,6 +1397,7 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
         S *ar = a_ring + slot * RG::A_ST;
         const S *ar_read = (GA && !owner) ? idle_rows : ar;
         const int roff = BWD ? L - (s + 1) * SRS : s * SRS;
+        S yv[SRS];  // the stage's outputs, stored after the stage
 #pragma unroll
         for (int cb = 0; cb < SRS / SR; ++cb) {
             const int rb = BWD ? (SRS / SR - 1 - cb) * SR : cb * SR;  // first stage row of the block
@@ -1368,26 +1412,18 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
                 if constexpr (MODE == FWD_RERUN) {
                     const S y0 = fwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * p);
                     const S y1 = fwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * p + 1);
-                    if (roff + r0 < n) {
-                        out[base + roff + r0] = y0;
-                        ym = abs_max_nan(ym, y0);
-                    }
-                    if (roff + r0 + 1 < n) {
-                        out[base + roff + r0 + 1] = y1;
-                        ym = abs_max_nan(ym, y1);
-                    }
+                    yv[r0] = y0;
+                    yv[r0 + 1] = y1;
+                    if (roff + r0 < n) ym = abs_max_nan(ym, y0);
+                    if (roff + r0 + 1 < n) ym = abs_max_nan(ym, y1);
                 } else {
                     const S y1 = bwd_step_win<S, MP, WIN>(h, c1, ucur[r0 + 1], 2 * pr);
                     const S y0 = bwd_step_win<S, MP, WIN>(h, c0, ucur[r0], 2 * pr + 1);
                     if constexpr (RERUN_B) {
-                        if (roff + r0 + 1 < n) {
-                            out[base + roff + r0 + 1] = y1;
-                            ym = abs_max_nan(ym, y1);
-                        }
-                        if (roff + r0 < n) {
-                            out[base + roff + r0] = y0;
-                            ym = abs_max_nan(ym, y0);
-                        }
+                        yv[r0 + 1] = y1;
+                        yv[r0] = y0;
+                        if (roff + r0 + 1 < n) ym = abs_max_nan(ym, y1);
+                        if (roff + r0 < n) ym = abs_max_nan(ym, y0);
                     }
                     // both rows are in registers and no other lane reads
                     // this ring: its rows take ga
@@ -1396,6 +1432,12 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
                 }
             }
             slide<S, MP, WIN>(h);
+        }
+        if constexpr (MODE == FWD_RERUN || RERUN_B) {
+            if (active) {
+                const int nv = n - roff < 0 ? 0 : (n - roff > SRS ? SRS : n - roff);
+                rec_store_outputs<S>(out + base + roff, yv, nv);
+            }
         }
         if constexpr (GA) {
             if (active) {
