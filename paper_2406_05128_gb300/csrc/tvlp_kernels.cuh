@@ -120,7 +120,6 @@ template <typename S, int MP, int G_, int R_> struct SumGeo {
     static constexpr int CS = SRS * MP + conflict_free_pad(SRS * MP * WPS, GPH, 4) / WPS;
     static constexpr int A_STAGE = CPW * CS;
     static constexpr int U_STAGE = CPW * SRS;               // input samples of a stage
-    static constexpr int UPL = (U_STAGE + 31) / 32;         // input samples each lane stages
     // per-warp slice: the stage ring then NS mbarriers, rounded to 128 bytes
     // so every warp's bulk-copy destinations stay 16-byte aligned
     static constexpr size_t RING_BYTES = size_t(NS) * (A_STAGE + U_STAGE) * sizeof(S);
@@ -643,8 +642,8 @@ static __global__ void __launch_bounds__(kTableThreads)
 // staged in shared memory, SRS rows per stage, two stages in a ring: a full,
 // 16-byte-aligned chunk-stage arrives as one bulk (TMA) copy completing on
 // the stage's mbarrier; others (a ragged tail, a misaligned start, a padded
-// order) use cp.async with zero fill.  Input samples are loaded by the warp
-// one stage ahead and parked in shared memory next to the coefficients.
+// order) use cp.async with zero fill.  The stage's input samples travel in
+// the same cp.async group, into a slot next to the coefficients.
 // Output Y[q][r][k] (per-chunk stride YS):
 //   forward:  s(c*L + L - 1 - k) of recursion r
 //   backward: q_{k+1} after the chunk, i.e. the pending dL/ds(c*L - 1 - k)
@@ -762,20 +761,36 @@ __device__ __forceinline__ void k1_cache_stage(float *__restrict__ cache, const 
     bulk_commit();
 }
 
-// Input samples of stage k for the warp's chunks: element e = lane + 32*i
-// (i < UPL) is row e % SRS of chunk e / SRS; zero past the signal's end.
-template <typename S, int MP, typename GE, bool BWD>
-__device__ __forceinline__ void k1_load_inputs(S (&uv)[GE::UPL], const S *__restrict__ u, int L, int k, int lane,
-                                               int64_t my_base, int my_valid) {
+// Input samples of stage k for the warp's chunks into the stage's input slot
+// (16-byte cp.async pieces, element copies with zero fill at a ragged or
+// misaligned piece); the coefficient issue that follows commits the group.
+template <typename S, typename GE, bool BWD>
+__device__ __forceinline__ void k1_stage_inputs(S *u_st, const S *__restrict__ u, int L, int k, int lane,
+                                                int64_t my_base, int my_valid) {
+    constexpr int E = 16 / (int)sizeof(S);  // samples per piece
+    constexpr int PPC = SRS / E;             // pieces per chunk-stage
+    constexpr int NP = GE::CPW * PPC;
     const int roff = BWD ? L - (k + 1) * SRS : k * SRS;
 #pragma unroll
-    for (int i = 0; i < GE::UPL; ++i) {
-        const int e = lane + 32 * i;
-        const int ch = (e / SRS) < GE::CPW ? e / SRS : 0;
+    for (int p0 = 0; p0 < NP; p0 += 32) {
+        const int pc = p0 + lane;
+        const int ch = pc < NP ? pc / PPC : 0;
         const int64_t base = __shfl_sync(0xffffffffu, my_base, ch);
         const int valid = __shfl_sync(0xffffffffu, my_valid, ch);
-        const int r = e % SRS;
-        uv[i] = (e < GE::U_STAGE && roff + r < valid) ? __ldg(u + base + roff + r) : S(0);
+        if (pc < NP) {
+            const int r = (pc % PPC) * E;  // first row of the piece
+            S *dst = u_st + ch * SRS + r;
+            const S *src = u + base + roff + r;
+            if (roff + r + E <= valid && aligned16(src)) {
+                cp_async<16>(dst, src, 16);
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const bool v = roff + r + i < valid;
+                    cp_async<sizeof(S)>(dst + i, v ? src + i : u, v ? (int)sizeof(S) : 0);
+                }
+            }
+        }
     }
 }
 
@@ -824,6 +839,7 @@ __device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int
     }
     // stage k of the coefficient rows into ring slot `slot`
     auto stage = [&](int slot, int k) {
+        k1_stage_inputs<S, GE, BWD>(u_buf + slot * GE::U_STAGE, u, L, k, lane, my_base, my_valid);
         if constexpr (SRC == SRC_STREAM)
             k1_issue_stage<S, MP, GE, BWD>(a_buf + slot * GE::A_STAGE, bars + slot, a, L, k, lane, my_abase, my_m,
                                            my_valid, exact, l2);
@@ -864,9 +880,7 @@ __device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int
     }
     const S flag0 = (g == 0) ? S(1) : S(0);
 
-    S uv[GE::UPL];
     if constexpr (SRC == SRC_STREAM) stage(0, 0);
-    k1_load_inputs<S, MP, GE, BWD>(uv, u, L, 0, lane, my_base, my_valid);
     pdl_wait();
     pdl_release();
     // the scan that follows counts finished groups per signal from zero
@@ -875,9 +889,6 @@ __device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int
         for (int i = lane; i < n_cnt * kCntStride; i += 32) scan_cnt[i] = 0u;
     // generated rows may read frames an earlier kernel wrote: after the wait
     if constexpr (SRC != SRC_STREAM) stage(0, 0);
-#pragma unroll
-    for (int i = 0; i < GE::UPL; ++i)
-        if (lane + 32 * i < GE::U_STAGE) u_buf[lane + 32 * i] = uv[i];
 #pragma unroll 1
     for (int k = 0; k < nblk; ++k) {
         const int slot = k & 1;
@@ -885,7 +896,6 @@ __device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int
         if (more) {
             // the other slot was consumed in the previous iteration
             stage(slot ^ 1, k + 1);
-            k1_load_inputs<S, MP, GE, BWD>(uv, u, L, k + 1, lane, my_base, my_valid);
         } else {
             cp_async_commit();
         }
@@ -977,13 +987,6 @@ __device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int
 #pragma unroll
                 for (int kk = 0; kk < R; ++kk) slide<S, MP, WIN>(h[kk]);
             }
-        }
-        // park the next stage's input samples in the slot this iteration read
-        // last time round (consumed before the previous iteration ended)
-        if (more) {
-#pragma unroll
-            for (int i = 0; i < GE::UPL; ++i)
-                if (lane + 32 * i < GE::U_STAGE) u_buf[(slot ^ 1) * GE::U_STAGE + lane + 32 * i] = uv[i];
         }
         __syncwarp();
     }
