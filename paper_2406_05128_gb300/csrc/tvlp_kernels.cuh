@@ -1863,6 +1863,16 @@ template <typename S, int MP, int D = kScanDepth> struct ScanWarp {
             if (z_src) bulk_load(zs + slot0 * SG::ZS, z_src, zb, bars + bar);
         }
     }
+    // n z vectors alone into z slots [slot0, slot0+n)
+    __device__ void issue_z(int slot0, int n, const S *z_src, int bar) {
+        __syncwarp();
+        if (lane == 0) {
+            const unsigned zb = (unsigned)(n * SG::ZS * sizeof(S));
+            fence_proxy_async();
+            mbar_arrive_expect_tx(bars + bar, zb);
+            bulk_load(zs + slot0 * SG::ZS, z_src, zb, bars + bar);
+        }
+    }
     __device__ bool wait(int bar) {
         const bool ok = mbar_wait_warp(bars + bar, (phase >> bar) & 1u, kWaitLimit);
         phase ^= 1u << bar;
@@ -1953,6 +1963,101 @@ __device__ __forceinline__ bool wait_counter(const unsigned *c, unsigned target,
     return ok;
 }
 
+// Map slots of a chain block: its whole shared memory (the slices of
+// kScanWarps item warps) as one ring, an even number of slots.
+template <typename S, int MP> struct ChainCap {
+    using G = ScanGeo<S, MP>;
+    static constexpr size_t TOTAL = size_t(kScanWarps) * G::WARP_BYTES;
+    // ScanGeo<S, MP, d>::WARP_BYTES, spelled out for a run-time d
+    static constexpr size_t bytes(int d) {
+        return ((((size_t(d) * (G::YS + G::ZS) * sizeof(S) + 16 + 2 * G::RS * sizeof(S)) + 15) / 16 * 16 +
+                 G::R_BYTES + 127) /
+                128) *
+               128;
+    }
+    static constexpr int fit(int d) { return bytes(d) <= TOTAL ? d : fit(d - 2); }
+    static constexpr int N = fit(int(TOTAL / ((G::YS + G::ZS) * sizeof(S))) & ~1);
+    static_assert(N >= kScanDepth, "a chain block holds at least a warp's ring");
+    static_assert(ScanGeo<S, MP, N>::WARP_BYTES <= TOTAL, "the ring fits the block");
+};
+
+// Phase B1 in a chain block: warp 0 runs the chain of signals cb, cb +
+// n_chain, ... with every group map the chain needs copied into the block's
+// shared memory at once (one bulk copy; a chain longer than the ring
+// streams through its halves).  A vector scan's group maps come from an
+// earlier launch, so their copy starts before the wait for phase A and only
+// the group vectors follow it.  Returns false when a wait gave up.
+template <typename S, int MP, int MODE>
+__device__ __forceinline__ bool chain_block(int64_t cb, int64_t n_chain, const Batch &bt, int M, const S *GY,
+                                            const S *GZ, S *GX, const S *zi, unsigned *cnt, int *status) {
+    constexpr int CAP = ChainCap<S, MP>::N;
+    using SG = ScanGeo<S, MP, CAP>;
+    constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
+    constexpr bool REV = ScanMode<MODE>::REV, TRANS = ScanMode<MODE>::TRANS, VEC = ScanMode<MODE>::VEC;
+    extern __shared__ __align__(128) unsigned char k2_smem[];
+    const int lane = threadIdx.x & 31;
+    ScanWarp<S, MP, CAP> W;
+    W.init(k2_smem, lane, status);
+    const int j0 = lane < MP ? lane : 0;
+    int nhop = 0;
+    auto hop_step = [&](const S *m, const S *z, S x) -> S {
+        S p[MP + 1];
+        map_cols<S, MP, TRANS, VEC>(p, m, z, j0);
+        return hop_smem<S, MP>(p, W.xb + ((nhop++) & 1) * RS, x, lane);
+    };
+    for (int64_t b = cb; b < bt.n; b += n_chain) {
+        const SigScan sg = sig_scan(bt, b);
+        const int nG = sg.nG, nh = nG - 1;
+        // step n takes group gidx(n)'s incoming state through that group's
+        // map: groups [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG)
+        // backward, visited from the top
+        auto gidx = [&](int n) -> int64_t { return sg.gbase + (REV ? nG - 1 - n : n); };
+        const int64_t lo = sg.gbase + (REV ? 1 : 0);
+        const bool early = VEC && nh > 0 && nh <= CAP;
+        if (early) W.issue(0, nh, GY + lo * YS, nullptr, 0);
+        const unsigned base = ScanMode<MODE>::FIX ? (unsigned)nG + 1u : 0u;
+        if (!wait_counter(cnt + b * kCntStride, base + (unsigned)nG, lane, status)) {
+            if (early) W.wait(0);
+            return false;
+        }
+        fence_proxy_async_global();  // the group maps and vectors are read by bulk copies
+        S x = S(0);
+        if (MODE == CH_FWD && zi != nullptr) {
+            const int64_t gs_ = global_signal(bt, b);
+            const int m = bt.ord != nullptr ? __ldg(bt.ord + gs_) : M;
+            if (lane < m) x = zi[gs_ * (bt.ldz > 0 ? bt.ldz : M) + lane];
+        }
+        if (early) {
+            W.issue_z(0, nh, GZ + lo * ZS, 1);
+            const bool ok0 = W.wait(0);
+            const bool ok1 = W.wait(1);
+            if (!ok0 || !ok1) {
+                if (!ok0) W.drain(0);
+                if (!ok1) W.drain(1);
+                return false;
+            }
+            for (int n = 0; n < nh; ++n) {
+                const int mi = REV ? nh - 1 - n : n;
+                if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
+                x = hop_step(W.map(mi), W.zv(mi), x);
+            }
+        } else {
+            const bool ok = run_maps<S, MP, REV, CAP>(W, GY + lo * YS, VEC ? GZ + lo * ZS : nullptr, nh,
+                                                      [&](int n, const S *m, const S *z) {
+                                                          if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
+                                                          x = hop_step(m, z, x);
+                                                      });
+            if (!ok) return false;
+        }
+        if (lane < ZS) GX[gidx(nG - 1) * ZS + lane] = lane < MP ? x : S(0);
+        fence_proxy_async_global();
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(cnt + b * kCntStride, 1u);
+    }
+    return true;
+}
+
 // The body of k2_scan for block `bid` of `nblocks` (a mixed-order launch runs
 // the bodies of several orders, each block one of them; every block of the
 // launch is resident, so the waits between blocks of one order end).
@@ -1961,7 +2066,8 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
                                           const S *__restrict__ Y, const S *__restrict__ Z, S *__restrict__ GY,
                                           S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
                                           S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt,
-                                          int *__restrict__ status, int *__restrict__ fix_list) {
+                                          int *__restrict__ status, int *__restrict__ fix_list,
+                                          int64_t n_chain = 0) {
     using SG = ScanGeo<S, MP, DEPTH>;
     constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
     constexpr bool REV = ScanMode<MODE>::REV;
@@ -1969,6 +2075,18 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     constexpr bool VEC = ScanMode<MODE>::VEC;
     extern __shared__ __align__(128) unsigned char k2_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the last n_chain blocks of the launch run the chains (phase B1), one
+    // signal at a time in warp 0; the others work on scan items
+    if constexpr (DEPTH == kScanDepth) {
+        if (bid >= nblocks - n_chain) {
+            pdl_wait();
+            pdl_release();
+            if (warp == 0) chain_block<S, MP, MODE>(bid - (nblocks - n_chain), n_chain, bt, M, GY, GZ, GX, zi, cnt,
+                                                    status);
+            return;
+        }
+    }
+    nblocks -= n_chain;
     const int64_t w0 = bid * kScanWarps + warp;
     const int64_t wstep = nblocks * kScanWarps;
     int64_t n_items = items_bound;
@@ -2112,7 +2230,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     // ---- phase B1: the warp owning group 0 of a signal chains that
     // signal's group maps once, storing every group's incoming state in GX;
     // its count then reaches the group count + 1 ----
-    for (int64_t item = w0; item < n_items; item += wstep) {
+    for (int64_t item = w0; n_chain == 0 && item < n_items; item += wstep) {
         int64_t b;
         int g;
         SigScan sg;
@@ -2208,9 +2326,9 @@ __global__ void __launch_bounds__(kScanWarps * 32)
     k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
             S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
             S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status,
-            int *__restrict__ fix_list) {
+            int *__restrict__ fix_list, int n_chain) {
     scan_body<S, MP, MODE>(blockIdx.x, gridDim.x, bt, M, items_bound, Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, status,
-                           fix_list);
+                           fix_list, n_chain);
 }
 
 // ---------------------------------------------------------------------------
