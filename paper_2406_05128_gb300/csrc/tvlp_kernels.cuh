@@ -2281,9 +2281,11 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
                 // list the chunk for pass 2 when its correction, at its start
                 // or carried to its end, is finite and above the threshold
                 // of its (finite) signal
-                float em = lane < MP ? (float)abs_max_nan(fabs(x), pe) : 0.f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) em = abs_max_nan(em, __shfl_xor_sync(0xffffffffu, em, o));
+                // one warp max over the bit patterns: for non-negative
+                // floats they order as the values, and a NaN (sign cleared)
+                // stays above every finite value and infinity
+                const float el = lane < MP ? fabsf((float)abs_max_nan(fabs(x), pe)) : 0.f;
+                const float em = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(el)));
                 if (lane == 0 && em > fix_bar && em <= 3.0e38f) {
                     const unsigned slot = atomicAdd(cnt + (int64_t)bt.n * kCntStride, 1u);
                     fix_list[slot] = (int)q;
