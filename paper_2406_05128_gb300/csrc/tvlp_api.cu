@@ -1,6 +1,7 @@
 // C ABI of the time-varying LP library: argument checks, chunk selection
 // and dispatch to the per-order instantiations (see include/tvlp.h).
 #include <atomic>
+#include <cmath>
 #include <limits.h>
 #include <stdint.h>
 #include <string.h>
@@ -245,6 +246,15 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // summaries run in waves of resident blocks, each chunk costing L steps; the
 // two-level scan costs its group compositions and hops; the re-run is L
 // sequential steps.
+// smallest r with r * r >= x (x >= 0)
+int64_t isqrt_ceil(int64_t x) {
+    if (x <= 0) return 0;
+    int64_t r = (int64_t)std::sqrt((double)x);
+    while (r * r < x) ++r;
+    while (r > 0 && (r - 1) * (r - 1) >= x) --r;
+    return r;
+}
+
 int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
     constexpr int SRV = 16;  // chunk lengths are multiples of the stage height
     if (T <= 0 || B <= 0) return SRV;
@@ -340,7 +350,11 @@ int make_problem_varlen(int n, int64_t total, int M, int chunk, int dtype, const
     if (L <= 0) return LP_EINVAL;
     p->L = L;
     p->NQ = ceil_div(total, L) + n;
-    p->items = p->NQ;
+    // scan groups: a signal of c chunks has ceil(c / g) groups of g >=
+    // sqrt(c / 4) chunks, at most 2 sqrt(c) + 1; over the batch (sum of c
+    // at most NQ) at most 2 sqrt(n NQ) + n by Cauchy-Schwarz
+    const int64_t bound = 2 * isqrt_ceil((int64_t)n * p->NQ) + n + 1;
+    p->items = bound < p->NQ ? bound : p->NQ;
     return LP_OK;
 }
 

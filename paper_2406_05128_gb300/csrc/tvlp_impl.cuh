@@ -177,7 +177,7 @@ template <typename S, int MP> struct Launch {
         // a chain block per signal (phase B1 with the signal's group maps all
         // in its shared memory) when they fit beside one warp per item;
         // otherwise the warp of each signal's first group runs its chain
-        const int64_t n_chain = (p.off == nullptr && blocks + p.B <= res) ? p.B : 0;
+        const int64_t n_chain = blocks + p.B <= res ? p.B : 0;
         if (blocks > res) blocks = res;
         return launch(kern, dim3((unsigned)(blocks + n_chain)), dim3(kScanWarps * 32), smem, st, true, bt, p.M, items,
                       Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, p.status, list, (int)n_chain);

@@ -2008,6 +2008,7 @@ __device__ __forceinline__ bool chain_block(int64_t cb, int64_t n_chain, const B
     for (int64_t b = cb; b < bt.n; b += n_chain) {
         const SigScan sg = sig_scan(bt, b);
         const int nG = sg.nG, nh = nG - 1;
+        if (nG <= 0) continue;  // an empty signal of a varlen batch has no groups
         // step n takes group gidx(n)'s incoming state through that group's
         // map: groups [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG)
         // backward, visited from the top

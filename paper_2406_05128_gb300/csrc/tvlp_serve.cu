@@ -59,8 +59,11 @@ __global__ void k_carry_state(const float *__restrict__ s, const int64_t *__rest
 
 constexpr int kCarryThreads = 256;
 constexpr int kMaxInflight = 16;
-constexpr int kFwdKernels = 4;  // varlen tables, summary, scan, re-run
-constexpr int kBwdKernels = 5;  // varlen tables, zero-state, scan, re-run, coefficient gradient
+// varlen tables, summary, scan, re-run, correction scan, correction re-run
+constexpr int kFwdKernels = 6;
+// varlen tables, zero-state, scan, re-run, correction scan, correction
+// re-run, coefficient gradient
+constexpr int kBwdKernels = 7;
 
 struct Rec {
     Request req;
