@@ -271,3 +271,21 @@ def test_autotuner_picks_a_shape():
     from paper_2406_05128_gb300 import autotune
     L, shape, res, res_sh = autotune.tune_uniform(4, 12000, 22, iters=2, shapes=True)
     assert L in res and shape in autotune.SHAPES and set(res_sh) == set(autotune.SHAPES)
+
+
+def test_scan_without_room_for_chain_blocks():
+    """B=40 x 48000 at chunk 160 has 1360 scan items: their 340 blocks fill
+    the cooperative grid, so the warp of each signal's first group runs the
+    signal's chain (no chain blocks)."""
+    w = inputs.make("nochain", 40, 48000, 22, seed=71, gen="stable", with_zi=True)
+    _compare(w, _run(w, chunk=160), TOL_F32)
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_scan_chain_longer_than_chain_ring(reuse):
+    """Two signals of 240000 samples at chunk 32: 7500 chunks in groups of
+    44, so each chain has 170 group maps, more than a chain block holds at
+    once; the chain streams through the halves of its ring (and the item
+    warps through theirs, their groups being longer than a warp's ring)."""
+    w = inputs.make("longchain", 2, 240000, 22, seed=72, gen="stable", with_zi=True)
+    _compare(w, _run(w, chunk=32, reuse=reuse), TOL_F32)
