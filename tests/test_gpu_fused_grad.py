@@ -155,3 +155,20 @@ def test_headline_size_fused_equals_separate():
     _, ((ge, ga, _), (ge2, ga2, _)) = _uniform(w, torch.float32, 160, True, False)
     _same_bits(ge, ge2)
     _same_bits(ga, ga2)
+
+
+@pytest.mark.parametrize("reuse,zi", [(True, True), (False, False)])
+def test_resonant_fused_equals_separate(reuse, zi):
+    """Resonant signals (literal generator, |k| <= 0.8): the defect
+    correction re-runs listed chunks of the adjoint, and in the fused path
+    that second pass writes their ga rows again.  Both paths take the same
+    steps, so ge, ga and gzi agree bit for bit, and meet the oracle."""
+    w = inputs.make("resfg", 4, 48000, 22, seed=5, kmax=0.8, gen="literal", excitation="pulse", with_zi=zi)
+    s, ((ge, ga, gzi), (ge2, ga2, gzi2)) = _uniform(w, torch.float32, 0, reuse, zi)
+    _same_bits(ge, ge2)
+    _same_bits(ga, ga2)
+    _same_bits(gzi, gzi2)
+    rs, rge, rga, _ = O.forward_backward(w.a, w.e, w.gs, w.zi if zi else None)
+    assert_close("s", s, rs, TOL_F32)
+    assert_close("ge", ge, rge, TOL_F32)
+    assert_close("ga", ga, rga, TOL_F32)
