@@ -305,3 +305,39 @@ def test_frames_varlen_row_cache_same_bits(M):
                 assert err <= TOL_F32, (b, err)
     for x, y in zip(*got):
         assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_frames_resonant_with_and_without_row_cache(reuse):
+    """Resonant frames (literal generator, |k| <= 0.8, no per-order decay):
+    the defect correction re-runs listed chunks, from generated rows without
+    the row cache and from the cached rows with it.  Both give the same bits.
+    The filter is checked against the oracle run on the rows the kernels
+    generated (kept by the row cache), since on resonant filters the FP32
+    rounding of a(t) alone is amplified; dL/dk against the oracle's adjoint
+    of the step-up on two signals (it is O(M^3) per sample)."""
+    B, T, M, hop = 4, 48000, 22, 120
+    rng = np.random.default_rng(61)
+    k = inputs.reflection_frames(rng, B, O.n_frames(T, hop), M, 0.8, 1.0).astype(np.float32)
+    e = inputs.pulse_train(rng, B, T).astype(np.float32) + 0.1 * rng.standard_normal((B, T)).astype(np.float32)
+    gs = rng.standard_normal((B, T)).astype(np.float32)
+    kt, et, gst = _t(k), _t(e), _t(gs)
+    got = []
+    for cache in (False, True):
+        ws = ops.workspace_frames(B, T, M, hop, 0, DEV, cache_rows=cache)
+        s = ops.lp_tv_forward_frames(kt, et, hop, chunk=0, ws=ws)
+        ge, gk, _ = ops.lp_tv_backward_frames(gst, kt, s, hop, need_gzi=False, ws=ws, reuse_forward=reuse)
+        torch.cuda.synchronize()
+        assert _lib.lp_tv_device_status() == 0
+        got.append([x.cpu().numpy() for x in (s, ge, gk)])
+        if cache:
+            n0 = _lib.lp_tv_workspace_bytes_frames(B, T, M, hop, 0)
+            rows = ws[n0:n0 + B * T * M * 4].view(torch.float32).reshape(B, T, M).cpu().numpy()
+    for x, y in zip(*got):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    s, ge, gk = got[1]
+    rs, rge, rga, _ = O.forward_backward(rows, e, gs)
+    _close("s", s, rs)
+    _close("ge", ge, rge)
+    sel = [0, B - 1]
+    _close("gk", gk[sel], O.coeffs_adjoint(k[sel], rga[sel], hop))
