@@ -430,9 +430,13 @@ int lp_tv_backward_ti_f32(int B, int64_t T, int M, const float *gs,
  * Device status word of the current device: 0 while every bounded wait
  * inside the kernels completed, 1 once a shared-memory bulk-copy wait gave
  * up, 2 once a scan wait for other warps' results gave up (the kernel then
- * stopped early and its outputs are not valid).  Reads
- * it synchronously (waits for the device's outstanding work) and clears it
- * when `reset` is non-zero.  Returns the status or LP_ECUDA.
+ * stopped early and its outputs are not valid).  In a library compiled with
+ * TVLP_CHECK_BOUNDS (the checked build the tests use), 16 + n records that
+ * index check n failed: a chunk, scan item or correction-list entry built on
+ * the device lay outside the range it must lie in, and the work it guards
+ * was skipped.  Reads it synchronously (waits for the device's outstanding
+ * work) and clears it when `reset` is non-zero.  Returns the status or
+ * LP_ECUDA.
  */
 int lp_tv_device_status(int reset);
 

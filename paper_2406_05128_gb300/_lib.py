@@ -203,11 +203,14 @@ def library_path() -> str:
 
 
 def load(path: str | None = None):
-    """Load (once) and return the ctypes handle of libtvlp.so."""
+    """Load (once) and return the ctypes handle of libtvlp.so: `path`, else
+    the build named by the TVLP_LIBRARY environment variable (the checked
+    build with index checks, build.build(checks=True), for tests), else the
+    package's own build."""
     global _lib
     with _lock:
         if _lib is None:
-            p = path or _build.LIB
+            p = path or os.environ.get("TVLP_LIBRARY") or _build.LIB
             if not os.path.exists(p):
                 raise LPLibraryMissing(
                     f"{p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "

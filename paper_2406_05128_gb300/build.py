@@ -21,6 +21,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtvlp.so")
 PLAN_LIB = os.path.join(BUILD, "libtvlp_plan.so")
+# the checked build (index checks in the kernels, TVLP_CHECK_BOUNDS): a
+# library of its own for tests, never the one the package loads
+BUILD_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(BUILD_CHECK, "libtvlp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
@@ -40,25 +44,21 @@ def _sources():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
 
 
-def _units():
+def _units(out=BUILD):
     units = []
     for scalar, orders in (("float", F32_ORDERS), ("double", F64_ORDERS)):
         for mp in orders:
-            obj = os.path.join(BUILD, f"inst_{scalar}_{mp}.o")
+            obj = os.path.join(out, f"inst_{scalar}_{mp}.o")
             units.append((os.path.join(CSRC, "tvlp_inst.cu"), obj,
                           [f"-DTVLP_SCALAR={scalar}", f"-DTVLP_MP={mp}"]))
-    units.append((os.path.join(CSRC, "tvlp_api.cu"), os.path.join(BUILD, "tvlp_api.o"), []))
-    units.append((os.path.join(CSRC, "tvlp_noalloc.cu"), os.path.join(BUILD, "tvlp_noalloc.o"), []))
-    units.append((os.path.join(CSRC, "tvlp_serve.cu"), os.path.join(BUILD, "tvlp_serve.o"), []))
-    units.append((os.path.join(CSRC, "tvlp_selftest.cu"), os.path.join(BUILD, "tvlp_selftest.o"), []))
-    units.append((os.path.join(CSRC, "tvlp_check.cu"), os.path.join(BUILD, "tvlp_check.o"), []))
-    units.append((os.path.join(CSRC, "tvlp_framewise.cu"), os.path.join(BUILD, "tvlp_framewise.o"), []))
+    for name in ("tvlp_api", "tvlp_noalloc", "tvlp_serve", "tvlp_selftest", "tvlp_check", "tvlp_framewise"):
+        units.append((os.path.join(CSRC, name + ".cu"), os.path.join(out, name + ".o"), []))
     # mixed orders: the host side, and the fused kernels in parallel parts
-    units.append((os.path.join(CSRC, "tvlp_mixed.cu"), os.path.join(BUILD, "tvlp_mixed.o"), []))
-    units.append((os.path.join(CSRC, "tvlp_mixed_k1.cu"), os.path.join(BUILD, "tvlp_mixed_k1.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_mixed.cu"), os.path.join(out, "tvlp_mixed.o"), []))
+    units.append((os.path.join(CSRC, "tvlp_mixed_k1.cu"), os.path.join(out, "tvlp_mixed_k1.o"), []))
     for name in ("tvlp_mixed_rec", "tvlp_mixed_scan"):
         for part in (0, 1):
-            units.append((os.path.join(CSRC, name + ".cu"), os.path.join(BUILD, f"{name}_{part}.o"),
+            units.append((os.path.join(CSRC, name + ".cu"), os.path.join(out, f"{name}_{part}.o"),
                           [f"-DTVLP_MIX_PART={part}"]))
     return units
 
@@ -70,9 +70,9 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(unit, verbose: bool, ptxas_v: bool):
+def _compile(unit, verbose: bool, ptxas_v: bool, checks: bool = False):
     src, obj, defs = unit
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *defs, *(["-DTVLP_CHECK_BOUNDS"] if checks else []), "-c", src, "-o", obj]
     if ptxas_v:
         cmd += ["-Xptxas", "-v"]
     if verbose:
@@ -101,28 +101,34 @@ def build_plan(force: bool = False) -> str:
     return PLAN_LIB
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, jobs: int | None = None) -> str:
-    """Compile every instantiation (in parallel) and link libtvlp.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, jobs: int | None = None,
+          checks: bool = False) -> str:
+    """Compile every instantiation (in parallel) and link libtvlp.so; with
+    checks=True the checked build (index checks in the kernels) into its
+    own folder."""
+    out, lib = (BUILD_CHECK, LIB_CHECK) if checks else (BUILD, LIB)
+    os.makedirs(out, exist_ok=True)
     deps = _sources()
-    todo = [u for u in _units() if force or ptxas_v or _stale(u[1], deps)]
+    units = _units(out)
+    todo = [u for u in units if force or ptxas_v or _stale(u[1], deps)]
     if todo:
         jobs = jobs or max(1, min(len(todo), os.cpu_count() or 4))
         with ThreadPoolExecutor(jobs) as ex:
-            logs = list(ex.map(lambda u: _compile(u, verbose, ptxas_v), todo))
+            logs = list(ex.map(lambda u: _compile(u, verbose, ptxas_v, checks), todo))
         if ptxas_v:
             for u, log in zip(todo, logs):
                 print(f"== {os.path.basename(u[1])}\n{log}")
-    objs = [u[1] for u in _units()]
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [u[1] for u in units]
+    if force or todo or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")
-        os.replace(tmp, LIB)
-    build_plan(force)
-    return LIB
+        os.replace(tmp, lib)
+    if not checks:
+        build_plan(force)
+    return lib
 
 
 if __name__ == "__main__":

@@ -56,6 +56,29 @@ constexpr int SRS = 16;  // rows per staged copy; chunk lengths are multiples of
 // Status codes written by kernels to the device status word.
 enum { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_SCAN = 2 };
 
+// Index checks of a checked build (TVLP_CHECK_BOUNDS): the indices that come
+// from tables and lists built on the device are checked against the ranges
+// they must lie in.  A failed check records DEV_BOUNDS + its location in
+// the status word (the first failure wins) and the caller skips the work
+// the index guards; nothing traps.  Other builds compile the checks out.
+constexpr int DEV_BOUNDS = 16;
+enum {
+    CHK_FIX_LIST_ENTRY = 1,  // pass 2: a listed chunk outside [0, NQ)
+    CHK_CHUNK_SIGNAL = 2,    // a varlen chunk outside its signal's chunks
+    CHK_SCAN_ITEM = 3,       // a scan item outside its signal's groups
+    CHK_SCAN_CHUNK = 4,      // a group's chunks outside the batch's chunks
+    CHK_FIX_LIST_SLOT = 5,   // the correction list past the batch's chunks
+    CHK_CHAIN_GROUPS = 6,    // a chain's groups past the scan items
+};
+#ifdef TVLP_CHECK_BOUNDS
+__device__ __forceinline__ bool index_ok(bool ok, int where, int *status) {
+    if (!ok) atomicCAS(status, 0, DEV_BOUNDS + where);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool index_ok(bool, int, int *) { return true; }
+#endif
+
 constexpr int kCntStride = 32;  // scan counters sit 128 bytes apart, one L2 line each
 
 // Packing of the MP+1 summary recursions of one chunk onto G lanes with R
@@ -836,6 +859,9 @@ __device__ __forceinline__ void k1_body(int64_t bid, Batch bt, int M, int L, int
         my_t0 = cp.c * (int64_t)L;
         my_abase = cp.abase;
         my_m = cp.m;
+        if (bt.off != nullptr && !index_ok(cp.b >= 0 && cp.b < bt.n && q0 + lane < __ldg(bt.cstart + cp.b + 1),
+                                           CHK_CHUNK_SIGNAL, status))
+            my_valid = 0;  // stage nothing
     }
     // stage k of the coefficient rows into ring slot `slot`
     auto stage = [&](int slot, int k) {
@@ -1271,6 +1297,7 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
         if (blk * RC >= n_list) return;
         active = owner && q < n_list;
         q = active ? (int64_t)__ldcg(fx.list + q) : 0;
+        if (active && !index_ok(q >= 0 && q < NQ, CHK_FIX_LIST_ENTRY, status)) active = false;
     }
     S *a_ring = reinterpret_cast<S *>(rec_smem + (size_t)(lane % RC) * RG::LW * 4);  // [NS][SRS*MP]
     uint64_t *bars = reinterpret_cast<uint64_t *>(rec_smem + (size_t)RC * RG::LW * 4);
@@ -1297,6 +1324,9 @@ __device__ __forceinline__ void rec_body(int64_t bid, int64_t nblocks, Batch bt,
         g = cp.g;
         m = cp.m;
         abase = cp.abase;
+        if (bt.off != nullptr &&
+            !index_ok(cp.b >= 0 && cp.b < bt.n && q < __ldg(bt.cstart + cp.b + 1), CHK_CHUNK_SIGNAL, status))
+            active = false;
     }
     const int ldz = bt.ldz > 0 ? bt.ldz : M;  // initial-state stride per signal
     if (SRC == SRC_STREAM && fx.E != nullptr && active) {
@@ -1988,8 +2018,9 @@ template <typename S, int MP> struct ChainCap {
 // earlier launch, so their copy starts before the wait for phase A and only
 // the group vectors follow it.  Returns false when a wait gave up.
 template <typename S, int MP, int MODE>
-__device__ __forceinline__ bool chain_block(int64_t cb, int64_t n_chain, const Batch &bt, int M, const S *GY,
-                                            const S *GZ, S *GX, const S *zi, unsigned *cnt, int *status) {
+__device__ __forceinline__ bool chain_block(int64_t cb, int64_t n_chain, const Batch &bt, int M, int64_t items_bound,
+                                            const S *GY, const S *GZ, S *GX, const S *zi, unsigned *cnt,
+                                            int *status) {
     constexpr int CAP = ChainCap<S, MP>::N;
     using SG = ScanGeo<S, MP, CAP>;
     constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
@@ -2009,6 +2040,7 @@ __device__ __forceinline__ bool chain_block(int64_t cb, int64_t n_chain, const B
         const SigScan sg = sig_scan(bt, b);
         const int nG = sg.nG, nh = nG - 1;
         if (nG <= 0) continue;  // an empty signal of a varlen batch has no groups
+        if (!index_ok(sg.gbase >= 0 && sg.gbase + nG <= items_bound, CHK_CHAIN_GROUPS, status)) continue;
         // step n takes group gidx(n)'s incoming state through that group's
         // map: groups [gbase, gbase + nG-1) forward, [gbase + 1, gbase + nG)
         // backward, visited from the top
@@ -2082,8 +2114,9 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         if (bid >= nblocks - n_chain) {
             pdl_wait();
             pdl_release();
-            if (warp == 0) chain_block<S, MP, MODE>(bid - (nblocks - n_chain), n_chain, bt, M, GY, GZ, GX, zi, cnt,
-                                                    status);
+            if (warp == 0)
+                chain_block<S, MP, MODE>(bid - (nblocks - n_chain), n_chain, bt, M, items_bound, GY, GZ, GX, zi, cnt,
+                                         status);
             return;
         }
     }
@@ -2104,10 +2137,19 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     int nhop = 0;  // hops so far (selects the exchange buffer)
 
     // scan item -> (signal, group) and the signal's scan geometry
+    // the batch's chunks (the chunk-map and list regions hold at least these)
+    const int64_t total_chunks = bt.off == nullptr ? (int64_t)bt.n * bt.nC : (int64_t)__ldg(bt.cstart + bt.n);
     auto locate = [&](int64_t item, int64_t &b, int &g, SigScan &sg) {
         b = bt.off == nullptr ? item / bt.nG : (int64_t)find_signal(bt.gstart, bt.n, item);
         sg = sig_scan(bt, b);
         g = (int)(item - sg.gbase);
+    };
+    // a located item lies in its signal's groups, and the signal's chunks
+    // and groups in the batch's (checked builds; skip the item otherwise)
+    auto located_ok = [&](int64_t b, int g, const SigScan &sg) -> bool {
+        return index_ok(b >= 0 && b < bt.n && g >= 0 && g < sg.nG && sg.gbase + sg.nG <= items_bound, CHK_SCAN_ITEM,
+                        status) &&
+               index_ok(sg.cbase >= 0 && sg.cbase + sg.nC <= total_chunks, CHK_SCAN_CHUNK, status);
     };
     auto group_len = [&](const SigScan &sg, int g) -> int {
         const int64_t lo = (int64_t)g * sg.G2;
@@ -2160,6 +2202,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         int g;
         SigScan sg;
         locate(item, b, g, sg);
+        if (!located_ok(b, g, sg)) continue;
         const int len = group_len(sg, g);
         bool ok;
         if constexpr (VEC) {
@@ -2225,7 +2268,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         int g;
         SigScan sg;
         locate(w0, b, g, sg);
-        held = group_len(sg, g) <= DEPTH;
+        held = located_ok(b, g, sg) && group_len(sg, g) <= DEPTH;
     }
 
     // ---- phase B1: the warp owning group 0 of a signal chains that
@@ -2236,6 +2279,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         int g;
         SigScan sg;
         locate(item, b, g, sg);
+        if (!located_ok(b, g, sg)) continue;
         if (g != 0) continue;
         held = false;
         const int nG = sg.nG;
@@ -2268,6 +2312,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         int g;
         SigScan sg;
         locate(item, b, g, sg);
+        if (!located_ok(b, g, sg)) continue;
         const int len = group_len(sg, g);
         if (!wait_count(b, sg, (unsigned)sg.nG + 1u)) return;
         constexpr bool FIX = ScanMode<MODE>::FIX;
@@ -2289,7 +2334,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
                 const float em = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(el)));
                 if (lane == 0 && em > fix_bar && em <= 3.0e38f) {
                     const unsigned slot = atomicAdd(cnt + (int64_t)bt.n * kCntStride, 1u);
-                    fix_list[slot] = (int)q;
+                    if (index_ok((int64_t)slot < total_chunks, CHK_FIX_LIST_SLOT, status)) fix_list[slot] = (int)q;
                 }
             }
         };
