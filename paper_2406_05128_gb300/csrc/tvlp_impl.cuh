@@ -178,9 +178,10 @@ template <typename S, int MP> struct Launch {
         // in its shared memory) when they fit beside one warp per item;
         // otherwise the warp of each signal's first group runs its chain
         const int64_t n_chain = blocks + p.B <= res ? p.B : 0;
+        const int chain_regs = ChainRegs<S, MP>::ON ? 1 : 0;
         if (blocks > res) blocks = res;
         return launch(kern, dim3((unsigned)(blocks + n_chain)), dim3(kScanWarps * 32), smem, st, true, bt, p.M, items,
-                      Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, p.status, list, (int)n_chain);
+                      Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, p.status, list, (int)n_chain, chain_regs);
     }
 
     template <int MODE, bool EXACT, int SRC, int RC>

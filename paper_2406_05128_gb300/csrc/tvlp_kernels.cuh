@@ -1852,6 +1852,29 @@ __device__ __forceinline__ S hop_smem(const S (&p)[MP + 1], S *xb, S x, int lane
     return lane < MP ? (a0 + a1) + (a2 + a3) : S(0);
 }
 
+// The lane's coefficients of one map read from global memory through L2
+// (another block may have written it): straight, p[r] = row r at column j0
+// (row 0, the map's own constant term, unless the scan is driven by z);
+// transposed, p[k+1] = row j0+1 at column k.  Driven scans set p[0] from z.
+template <typename S, int MP, bool TRANS, bool VEC>
+__device__ __forceinline__ void chain_map_cols(S (&p)[MP + 1], const S *__restrict__ m, int j0) {
+    constexpr int RS = YGeo<S, MP>::RS;
+    if constexpr (TRANS) {
+        const S *row = m + (j0 + 1) * RS;
+#pragma unroll
+        for (int k = 0; k < RS; k += 4) {
+            const float4 v = __ldcg(reinterpret_cast<const float4 *>(row + k));
+            if (k + 0 < MP) p[k + 1] = v.x;
+            if (k + 1 < MP) p[k + 2] = v.y;
+            if (k + 2 < MP) p[k + 3] = v.z;
+            if (k + 3 < MP) p[k + 4] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int r = VEC ? 1 : 0; r <= MP; ++r) p[r] = __ldcg(m + r * RS + j0);
+    }
+}
+
 // A warp's map buffers: kScanDepth map slots and their z slots, filled by
 // bulk (TMA) copies of contiguous runs of maps, completing on one of two
 // mbarriers.  A run of up to kScanDepth maps arrives in one copy; a longer
@@ -1979,14 +2002,15 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 }
 
 // Warp-collective bounded wait until *c >= target: lane 0 polls with relaxed
-// loads (sleeping between polls), then every lane takes one acquire load
-// before reading what the count guards.  After kScanSpin polls it records
-// DEV_TIMEOUT_SCAN and returns false.
+// loads (sleeping about SLEEP_NS between polls), then every lane takes one
+// acquire load before reading what the count guards.  After kScanSpin polls
+// it records DEV_TIMEOUT_SCAN and returns false.
+template <unsigned SLEEP_NS = 256>
 __device__ __forceinline__ bool wait_counter(const unsigned *c, unsigned target, int lane, int *status) {
     bool ok = false;
     for (int it = 0; it < kScanSpin && !ok; ++it) {
         ok = __shfl_sync(0xffffffffu, lane == 0 ? (ld_relaxed(c) >= target) : false, 0);
-        if (!ok) __nanosleep(256);
+        if (!ok) __nanosleep(SLEEP_NS);
     }
     (void)ld_acquire(c);
     if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT_SCAN);
@@ -2091,6 +2115,117 @@ __device__ __forceinline__ bool chain_block(int64_t cb, int64_t n_chain, const B
     return true;
 }
 
+// Phase B1 in a chain block with the group maps in registers: the chain
+// of signal cb (one signal per chain block) is cut into kScanWarps pieces of
+// up to KM steps, one per warp.  Each warp holds its pieces' map columns in
+// registers (lane j: column j, MP + 1 values a map), so a hop only publishes
+// and reads the state through shared memory; the state passes from warp to
+// warp through an mbarrier (arrive with release, bounded wait with
+// acquire).  FP32 orders up to 22 and chains of up to kScanWarps * KM steps;
+// other chains take the shared-memory chain.  Returns false when a wait gave
+// up.
+template <typename S, int MP> struct ChainRegs {
+    static constexpr int KM = 9;  // maps per warp
+    // the maps take most of a thread's registers, which costs the item
+    // blocks no occupancy only where shared memory already holds the scan to
+    // two blocks per SM
+    static constexpr bool ON = sizeof(S) == 4 && MP <= 22 && ChainCap<S, MP>::TOTAL * 3 > size_t(227) * 1024;
+};
+
+template <typename S, int MP, int MODE>
+__device__ __forceinline__ bool chain_block_regs(int64_t cb, const Batch &bt, int M, int64_t items_bound,
+                                                 const S *GY, const S *GZ, S *GX, const S *zi, unsigned *cnt,
+                                                 int *status) {
+    constexpr int KM = ChainRegs<S, MP>::KM, NW = kScanWarps;
+    constexpr int YS = YGeo<S, MP>::YS, RS = YGeo<S, MP>::RS, ZS = RS;
+    constexpr bool REV = ScanMode<MODE>::REV, TRANS = ScanMode<MODE>::TRANS, VEC = ScanMode<MODE>::VEC;
+    extern __shared__ __align__(128) unsigned char k2_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // [NW][2][RS] the warps' publish buffers, [NW-1][RS] the hand-offs, then
+    // NW-1 mbarriers (16-byte aligned)
+    S *xb = reinterpret_cast<S *>(k2_smem) + (size_t)warp * 2 * RS;
+    S *xh = reinterpret_cast<S *>(k2_smem) + (size_t)NW * 2 * RS;
+    constexpr size_t HB_OFF = ((size_t(NW * 2 + NW - 1) * RS * sizeof(S) + 15) / 16) * 16;
+    uint64_t *hb = reinterpret_cast<uint64_t *>(k2_smem + HB_OFF);
+    if (threadIdx.x == 0) {
+        for (int w = 0; w + 1 < NW; ++w) mbar_init(hb + w, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (cb >= bt.n) return true;
+    const int64_t b = cb;
+    const SigScan sg = sig_scan(bt, b);
+    const int nG = sg.nG, nh = nG - 1;
+    if (nG <= 0) return true;  // an empty signal of a varlen batch has no groups
+    if (!index_ok(sg.gbase >= 0 && sg.gbase + nG <= items_bound, CHK_CHAIN_GROUPS, status)) return true;
+    auto gidx = [&](int n) -> int64_t { return sg.gbase + (REV ? nG - 1 - n : n); };
+    const int j0 = lane < MP ? lane : 0;
+    // this warp's steps [n0, n1); the warp with the last step (or warp 0 for
+    // a chain of one group) stores the final state and publishes
+    const int n0 = warp * KM, n1 = n0 + KM < nh ? n0 + KM : nh;
+    const bool mine = n0 < n1;
+    const bool last = nh == 0 ? warp == 0 : (mine && n1 == nh);
+    if (!mine && !last) return true;
+    S pm[KM][MP + 1];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (n0 + k < n1) {
+            // a vector scan's maps come from an earlier launch: before the wait
+            if constexpr (VEC) chain_map_cols<S, MP, TRANS, true>(pm[k], GY + gidx(n0 + k) * YS, j0);
+        }
+    }
+    const unsigned base = ScanMode<MODE>::FIX ? (unsigned)nG + 1u : 0u;
+    // the chain is the scan's critical path: poll for its start closely
+    if (!wait_counter<32>(cnt + b * kCntStride, base + (unsigned)nG, lane, status)) return false;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (n0 + k < n1) {
+            if constexpr (VEC) pm[k][0] = __ldcg(GZ + gidx(n0 + k) * ZS + j0);
+            else chain_map_cols<S, MP, TRANS, false>(pm[k], GY + gidx(n0 + k) * YS, j0);
+        }
+    }
+    S x = S(0);
+    if (warp == 0) {
+        if (MODE == CH_FWD && zi != nullptr) {
+            const int64_t gs_ = global_signal(bt, b);
+            const int m = bt.ord != nullptr ? __ldg(bt.ord + gs_) : M;
+            if (lane < m) x = zi[gs_ * (bt.ldz > 0 ? bt.ldz : M) + lane];
+        }
+    } else {
+        // the state after the previous warp's steps
+        if (!mbar_wait_warp(hb + (warp - 1), 0u, kWaitLimit)) {
+            if (lane == 0) atomicExch(status, DEV_TIMEOUT_SCAN);
+            return false;
+        }
+        x = lane < MP ? xh[(warp - 1) * RS + lane] : S(0);
+    }
+    int nhop = 0;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        const int n = n0 + k;
+        if (n < n1) {
+            if (lane < ZS) GX[gidx(n) * ZS + lane] = lane < MP ? x : S(0);
+            x = hop_smem<S, MP>(pm[k], xb + ((nhop++) & 1) * RS, x, lane);
+        }
+    }
+    if (!last) {
+        // hand the state to the next warp (this warp's GX entries are read by
+        // bulk copies once the last warp publishes)
+        if (lane < RS) xh[warp * RS + lane] = lane < MP ? x : S(0);
+        fence_proxy_async_global();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(hb + warp))
+                                    : "memory");
+        return true;
+    }
+    if (lane < ZS) GX[gidx(nh) * ZS + lane] = lane < MP ? x : S(0);
+    fence_proxy_async_global();
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(cnt + b * kCntStride, 1u);
+    return true;
+}
+
 // The body of k2_scan for block `bid` of `nblocks` (a mixed-order launch runs
 // the bodies of several orders, each block one of them; every block of the
 // launch is resident, so the waits between blocks of one order end).
@@ -2100,7 +2235,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
                                           S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
                                           S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt,
                                           int *__restrict__ status, int *__restrict__ fix_list,
-                                          int64_t n_chain = 0) {
+                                          int64_t n_chain = 0, int chain_regs = 0) {
     using SG = ScanGeo<S, MP, DEPTH>;
     constexpr int YS = SG::YS, ZS = SG::ZS, RS = SG::RS;
     constexpr bool REV = ScanMode<MODE>::REV;
@@ -2114,9 +2249,17 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         if (bid >= nblocks - n_chain) {
             pdl_wait();
             pdl_release();
-            if (warp == 0)
-                chain_block<S, MP, MODE>(bid - (nblocks - n_chain), n_chain, bt, M, items_bound, GY, GZ, GX, zi, cnt,
-                                         status);
+            const int64_t cb = bid - (nblocks - n_chain);
+            if constexpr (ChainRegs<S, MP>::ON) {
+                // one signal per chain block, its chain short enough for the
+                // warps' registers
+                if (chain_regs && n_chain >= bt.n && cb < bt.n &&
+                    sig_scan(bt, cb).nG - 1 <= kScanWarps * ChainRegs<S, MP>::KM) {
+                    chain_block_regs<S, MP, MODE>(cb, bt, M, items_bound, GY, GZ, GX, zi, cnt, status);
+                    return;
+                }
+            }
+            if (warp == 0) chain_block<S, MP, MODE>(cb, n_chain, bt, M, items_bound, GY, GZ, GX, zi, cnt, status);
             return;
         }
     }
@@ -2184,7 +2327,7 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     // where the main scan left it, for a correction scan)
     auto wait_count = [&](int64_t b, const SigScan &sg, unsigned target) -> bool {
         const unsigned base = ScanMode<MODE>::FIX ? (unsigned)sg.nG + 1u : 0u;
-        return wait_counter(cnt + b * kCntStride, base + target, lane, status);
+        return wait_counter<64>(cnt + b * kCntStride, base + target, lane, status);
     };
     // make this warp's global stores visible (also to bulk copies) before
     // bumping signal b's counter
@@ -2369,14 +2512,17 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     }
 }
 
+// With the register chain compiled in, one block per SM as the launch bound
+// lets ptxas give every variant its registers without spilling (shared
+// memory holds the scan to two blocks per SM in any case).
 template <typename S, int MP, int MODE>
-__global__ void __launch_bounds__(kScanWarps * 32)
+__global__ void __launch_bounds__(kScanWarps * 32, ChainRegs<S, MP>::ON ? 1 : 0)
     k2_scan(Batch bt, int M, int64_t items_bound, const S *__restrict__ Y, const S *__restrict__ Z,
             S *__restrict__ GY, S *__restrict__ GZ, S *__restrict__ GX, const S *__restrict__ zi,
             S *__restrict__ X, S *__restrict__ ckpt, unsigned *__restrict__ cnt, int *__restrict__ status,
-            int *__restrict__ fix_list, int n_chain) {
+            int *__restrict__ fix_list, int n_chain, int chain_regs) {
     scan_body<S, MP, MODE>(blockIdx.x, gridDim.x, bt, M, items_bound, Y, Z, GY, GZ, GX, zi, X, ckpt, cnt, status,
-                           fix_list, n_chain);
+                           fix_list, n_chain, chain_regs);
 }
 
 // ---------------------------------------------------------------------------

@@ -281,6 +281,18 @@ def test_scan_without_room_for_chain_blocks():
     _compare(w, _run(w, chunk=160), TOL_F32)
 
 
+@pytest.mark.parametrize("T", [865, 961, 11521, 11841])
+@pytest.mark.parametrize("reuse", [True, False])
+def test_scan_chain_split_across_warps(T, reuse):
+    """Chains of 9, 10, 36 and 37 group steps at M=22, chunk 32: a chain
+    block's four warps take up to nine steps each with their maps in
+    registers and hand the state on, so these lengths end a chain at a
+    warp's last step, one past it, at the last warp's last step, and one
+    step too long for the registers (the shared-memory chain)."""
+    w = inputs.make("split", 3, T, 22, seed=73, gen="stable", with_zi=True)
+    _compare(w, _run(w, chunk=32, reuse=reuse), TOL_F32)
+
+
 @pytest.mark.parametrize("reuse", [True, False])
 def test_scan_chain_longer_than_chain_ring(reuse):
     """Two signals of 240000 samples at chunk 32: 7500 chunks in groups of

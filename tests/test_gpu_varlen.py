@@ -110,6 +110,17 @@ def test_varlen_alone_equals_in_the_mix_resonant():
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("reuse", [True, False])
+def test_varlen_chain_lengths_across_warp_splits(reuse):
+    """M=22 at chunk 32, signals whose chains have 0, 1, 8, 9, 10, 17, 18,
+    27, 35, 36, 37 and 40 group steps in one call: each chain block picks
+    the register chain (four warps of up to nine steps) or, past 36 steps,
+    the shared-memory chain for its own signal."""
+    lengths = [1, 33, 769, 865, 961, 2721, 2881, 6049, 10081, 11521, 11841, 14081]
+    sig = _signals(lengths, 22, seed=77)
+    _check_oracle(sig, _run(sig, 22, chunk=32, reuse=reuse))
+
+
 def test_varlen_equals_uniform_call():
     """Equal lengths: the varlen call reproduces the uniform call bit for bit."""
     M, chunk, B, T = 22, 160, 4, 3200
