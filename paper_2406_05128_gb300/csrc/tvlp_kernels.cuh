@@ -2170,10 +2170,15 @@ __device__ __forceinline__ bool chain_block_regs(int64_t cb, const Batch &bt, in
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
         if (n0 + k < n1) {
-            // a vector scan's maps come from an earlier launch: before the wait
+            // a vector scan's maps come from a scan two or more launches
+            // back: loaded before the waits
             if constexpr (VEC) chain_map_cols<S, MP, TRANS, true>(pm[k], GY + gidx(n0 + k) * YS, j0);
         }
     }
+    // the group maps are two launches old; what follows may need the
+    // previous kernel's results
+    pdl_wait();
+    pdl_release();
     const unsigned base = ScanMode<MODE>::FIX ? (unsigned)nG + 1u : 0u;
     // the chain is the scan's critical path: poll for its start closely
     if (!wait_counter<32>(cnt + b * kCntStride, base + (unsigned)nG, lane, status)) return false;
@@ -2247,18 +2252,18 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     // signal at a time in warp 0; the others work on scan items
     if constexpr (DEPTH == kScanDepth) {
         if (bid >= nblocks - n_chain) {
-            pdl_wait();
-            pdl_release();
             const int64_t cb = bid - (nblocks - n_chain);
             if constexpr (ChainRegs<S, MP>::ON) {
                 // one signal per chain block, its chain short enough for the
-                // warps' registers
+                // warps' registers (it waits for the previous kernel itself)
                 if (chain_regs && n_chain >= bt.n && cb < bt.n &&
                     sig_scan(bt, cb).nG - 1 <= kScanWarps * ChainRegs<S, MP>::KM) {
                     chain_block_regs<S, MP, MODE>(cb, bt, M, items_bound, GY, GZ, GX, zi, cnt, status);
                     return;
                 }
             }
+            pdl_wait();
+            pdl_release();
             if (warp == 0) chain_block<S, MP, MODE>(cb, n_chain, bt, M, items_bound, GY, GZ, GX, zi, cnt, status);
             return;
         }
@@ -2273,8 +2278,6 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
     }
     ScanWarp<S, MP, DEPTH> W;
     W.init(k2_smem + (size_t)warp * SG::WARP_BYTES, lane, status);
-    pdl_wait();
-    pdl_release();
     S *xb = W.xb;
     const int j0 = lane < MP ? lane : 0;
     int nhop = 0;  // hops so far (selects the exchange buffer)
@@ -2338,6 +2341,25 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         if (lane == 0) atomicAdd(cnt + b * kCntStride, 1u);
     };
 
+    // A vector scan's chunk maps come from a kernel two or more launches
+    // back (the z vectors from the previous one): the copy of the first
+    // group's maps into slots 0 .. len-1 starts before the wait.
+    bool pre = false;
+    if constexpr (VEC) {
+        if (w0 < n_items) {
+            int64_t b;
+            int g;
+            SigScan sg;
+            locate(w0, b, g, sg);
+            if (located_ok(b, g, sg) && group_len(sg, g) <= DEPTH) {
+                W.issue(0, group_len(sg, g), group_maps(sg, g), nullptr, 0);
+                pre = true;
+            }
+        }
+    }
+    pdl_wait();
+    pdl_release();
+
     // ---- phase A: fold every group's chunk maps; the counter of signal b
     // reaches its group count when all its groups are done ----
     for (int64_t item = w0; item < n_items; item += wstep) {
@@ -2350,8 +2372,24 @@ __device__ __forceinline__ void scan_body(int64_t bid, int64_t nblocks, Batch bt
         bool ok;
         if constexpr (VEC) {
             S zeta = S(0);
-            ok = run_maps<S, MP, REV, DEPTH>(W, group_maps(sg, g), group_zs(sg, g), len,
-                                      [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
+            if (pre && item == w0) {
+                // the maps are on their way: add the z vectors
+                W.issue_z(0, len, group_zs(sg, g), 1);
+                const bool ok0 = W.wait(0), ok1 = W.wait(1);
+                if (!ok0 || !ok1) {
+                    if (!ok0) W.drain(0);
+                    if (!ok1) W.drain(1);
+                    return;
+                }
+                for (int i = 0; i < len; ++i) {
+                    const int mi = REV ? len - 1 - i : i;
+                    zeta = hop_step(W.map(mi), W.zv(mi), zeta);
+                }
+                ok = true;
+            } else {
+                ok = run_maps<S, MP, REV, DEPTH>(W, group_maps(sg, g), group_zs(sg, g), len,
+                                                 [&](int, const S *m, const S *z) { zeta = hop_step(m, z, zeta); });
+            }
             if (lane < ZS) GZ[item * ZS + lane] = lane < MP ? zeta : S(0);
         } else if constexpr (UseMma<S, MP>::ON) {
             // the running product in the warp's tile, starting from the
