@@ -242,10 +242,6 @@ Shape shape_for(int MP, int dtype) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Rough cost model (cycles) of the chunked scan for chunk length L:
-// summaries run in waves of resident blocks, each chunk costing L steps; the
-// two-level scan costs its group compositions and hops; the re-run is L
-// sequential steps.
 // smallest r with r * r >= x (x >= 0)
 int64_t isqrt_ceil(int64_t x) {
     if (x <= 0) return 0;
@@ -255,6 +251,10 @@ int64_t isqrt_ceil(int64_t x) {
     return r;
 }
 
+// Rough cost model (cycles) of the chunked scan for chunk length L:
+// summaries run in waves of resident blocks, each chunk costing L steps; the
+// two-level scan costs its group compositions and hops; the re-run is L
+// sequential steps.
 int pick_chunk_impl(int B, int64_t T, int MP, int dtype) {
     constexpr int SRV = 16;  // chunk lengths are multiples of the stage height
     if (T <= 0 || B <= 0) return SRV;
