@@ -293,6 +293,14 @@ def test_scan_chain_split_across_warps(T, reuse):
     _compare(w, _run(w, chunk=32, reuse=reuse), TOL_F32)
 
 
+@pytest.mark.parametrize("M", [17, 21])
+def test_scan_chain_split_padded_order(M):
+    """Orders padded to 22 take the register chain too: the initial state
+    has M < 22 components (chains of 35 steps at chunk 32)."""
+    w = inputs.make("splitpad", 3, 10081, M, seed=74 + M, gen="stable", with_zi=True)
+    _compare(w, _run(w, chunk=32), TOL_F32)
+
+
 @pytest.mark.parametrize("reuse", [True, False])
 def test_scan_chain_longer_than_chain_ring(reuse):
     """Two signals of 240000 samples at chunk 32: 7500 chunks in groups of
